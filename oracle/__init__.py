@@ -1,0 +1,22 @@
+"""FP64 CPU oracle of adaptive BDDC in 3D (Mandel, Sousedik, Sistek).
+
+TEST INFRASTRUCTURE ONLY.  Imported by tests/, by __graft_entry__.smoke() and
+by the CPU-baseline leg of bench.py; the CUDA library and its binding never
+import, call or link anything here, and nothing here imports them.
+
+Modules: fe (Q1 elements, assembly), globs (faces/edges/corners, weights),
+bddc (Schur complements, Lemma 2.1 preconditioner, PCG, Lanczos estimate),
+adaptive (pair eigenproblems and face constraints, Algorithm 3.1),
+native (the cyclic Jacobi helper in jacobi.c).
+"""
+from .bddc import Model, pcg, lanczos_condition, lanczos_tridiagonal
+from .adaptive import adapt, pair_problem, orthonormal_rows
+
+
+def run(prob, averages=(), tau=None, tol=1e-8, maxit=1000):
+    """Setup (+ adapt when tau is given) + solve.  Returns (model, adapt_result, pcg_result)."""
+    m = Model(prob, averages=averages)
+    m.schur()
+    ad = adapt(m, tau) if tau is not None else None
+    res = m.solve(tol=tol, maxit=maxit)
+    return m, ad, res

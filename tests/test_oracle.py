@@ -1,0 +1,327 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics
+(closed forms, theorems, brute force), not against the oracle itself."""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+from paper_0910_5863_gb300 import problems as P
+import oracle
+from oracle import fe, globs as G, native
+from oracle.adaptive import pair_problem, pair_data, orthonormal_rows
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = int(v)
+    return out
+
+
+# --- generator --------------------------------------------------------------
+
+def test_splitmix64_reference_value():
+    # Vigna's splitmix64 from state 0: first output 0xE220A8397B1DCDAF
+    assert int(P.splitmix64_raw(0, 1)[0]) == 0xE220A8397B1DCDAF
+    # plain-integer restatement for a second state
+    s = 12345
+    z = (s + P.GOLDEN) & P.MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & P.MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & P.MASK64
+    z ^= z >> 31
+    assert int(P.splitmix64_raw(12345, 1)[0]) == z
+
+
+def test_random_high_count():
+    prob = P.config_adaptive_poisson()
+    assert (prob.coef == 1e4).sum() == round(0.2 * 24 ** 3)
+    assert prob.nsub == 27 and prob.dirichlet.sum() == 25 * 25
+
+
+# --- elements -------------------------------------------------------------------
+
+def test_poisson_element_closed_form():
+    h = 0.25
+    xe = P.box_mesh(1, 1, 1, h)[0][P.box_mesh(1, 1, 1, h)[1][0]]
+    K = fe.poisson_element(xe, 3.0) * 12 / (3.0 * h)
+    for a in range(8):
+        for b in range(8):
+            hd = bin(a ^ b).count("1")
+            expect = {0: 4.0, 1: 0.0, 2: -1.0, 3: -1.0}[hd]
+            assert abs(K[a, b] - expect) < 1e-12
+
+
+def test_elasticity_element_null_space():
+    xyz, el = P.box_mesh(1, 1, 1, 0.5)
+    xe = xyz[el[0]]
+    K = fe.elasticity_element(xe, 2.0, 0.3)
+    assert np.allclose(K, K.T, atol=1e-12)
+    w = np.linalg.eigvalsh(K)
+    assert (np.abs(w) < 1e-10 * w.max()).sum() == 6
+    assert np.linalg.matrix_rank(K, tol=1e-10 * w.max()) == 18
+    # rigid body modes: translations and rotations x -> omega cross x
+    for t in np.eye(3):
+        u = np.tile(t, 8)
+        assert np.linalg.norm(K @ u) < 1e-12
+    for om in np.eye(3):
+        u = np.cross(om[None, :], xe).ravel()
+        assert np.linalg.norm(K @ u) < 1e-12
+
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_patch_test_linear_field(ncomp):
+    prob = (P.poisson_cube(4, 2) if ncomp == 1 else P.elasticity_cube(4, 2))
+    prob.dirichlet[:] = False
+    K, F, dofs = fe.assemble_global(prob)
+    rng = np.random.default_rng(0)
+    Aff = rng.standard_normal((ncomp, 3))
+    u = (prob.xyz @ Aff.T).ravel()
+    r = K @ u
+    # interior nodes carry no load for a linear field
+    x = prob.xyz
+    interior = np.all((x > 1e-9) & (x < x.max(axis=0) - 1e-9), axis=1)
+    r = r.reshape(-1, ncomp)
+    assert np.abs(r[interior]).max() < 1e-11
+
+
+# --- globs ----------------------------------------------------------------------
+
+def test_fig3_glob_counts():
+    g = _golden("fig3_globs.txt")
+    prob = P.elasticity_cube(8, 2)
+    prob.dirichlet[:] = False
+    m = oracle.Model(prob, averages=("edge",))
+    nc, ne, nf = m.globs.counts()
+    assert (nc, ne, nf) == (g["corners"], g["edges"], g["faces"])
+    assert m.dofs.n == g["dofs"]
+    # W^c: all local dofs, corner dofs assembled
+    wc = sum(s.gdof.size for s in m.subs) - sum((len(m.globs.sets[n]) - 1) * 3 for n in m.globs.corners)
+    assert wc == g["wc_size"]
+    rows = sum(gc.rows.shape[0] * (len(gc.subs) - 1) for gc in m.constraints)
+    assert rows == g["edge_average_rows"]
+
+
+def test_config_glob_counts():
+    m = oracle.Model(P.config_small())
+    assert m.globs.counts() == (6, 6, 12) and m.nG == 444
+    m = oracle.Model(P.config_adaptive_poisson())
+    assert m.globs.counts() == (28, 36, 54) and m.dofs.n == 15000
+
+
+# --- Schur complements ----------------------------------------------------------
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_schur_properties(ncomp):
+    prob = P.poisson_cube(6, 2, coef="lognormal") if ncomp == 1 else P.elasticity_cube(4, 2)
+    m = oracle.Model(prob)
+    m.schur()
+    floating = 0
+    for s in m.subs:
+        S = s.S
+        assert np.allclose(S, S.T, atol=1e-12 * np.abs(S).max())
+        w = np.linalg.eigvalsh(S)
+        assert w.min() > -1e-10 * w.max()
+        A = s.A.toarray()
+        has_dirichlet = s.gdof.size < s.nodes.size * ncomp
+        if not has_dirichlet:
+            floating += 1
+            if ncomp == 1:
+                assert np.linalg.norm(S @ np.ones(s.G.size)) < 1e-10 * np.abs(S).max()
+            else:
+                xn = prob.xyz[s.free_nodes][s.G[::3] // 3]
+                for om in np.eye(3):
+                    u = np.cross(om[None, :], xn).ravel()
+                    assert np.linalg.norm(S @ u) < 1e-9 * np.abs(S).max() * np.linalg.norm(u)
+        else:
+            # a different route: S = ((A^{-1})_GG)^{-1}
+            Ainv = np.linalg.inv(A)
+            S2 = np.linalg.inv(Ainv[np.ix_(s.G, s.G)])
+            assert np.linalg.norm(S2 - S) < 1e-8 * np.linalg.norm(S)
+        # energy minimality: any other extension has larger energy
+        rng = np.random.default_rng(1)
+        xG = rng.standard_normal(s.G.size)
+        xI = -np.linalg.solve(A[np.ix_(s.I, s.I)], A[np.ix_(s.I, s.G)] @ xG)
+        for _ in range(3):
+            v = np.zeros(A.shape[0])
+            v[s.G] = xG
+            v[s.I] = xI + 0.1 * rng.standard_normal(s.I.size)
+            assert v @ A @ v >= xG @ S @ xG - 1e-9
+    assert floating > 0
+
+
+# --- whole solve vs sparse direct -----------------------------------------------
+
+@pytest.mark.parametrize("which", ["small_ef", "small_corner", "elast"])
+def test_solve_matches_sparse_direct(which):
+    if which == "small_ef":
+        prob, av = P.config_small(), ("edge", "face")
+    elif which == "small_corner":
+        prob, av = P.poisson_cube(8, 2, coef="lognormal"), ()
+    else:
+        prob, av = P.elasticity_cube(4, 2), ("edge", "face")
+    m, _, res = oracle.run(prob, averages=av, tol=1e-13)
+    u = spla.spsolve(m.K.tocsc(), m.F)
+    assert res.converged
+    assert np.linalg.norm(res.u - u) <= 1e-10 * np.linalg.norm(u)
+
+
+# --- the preconditioner ---------------------------------------------------------
+
+def _dense_op(f, n):
+    return np.column_stack([f(e) for e in np.eye(n)])
+
+
+def test_preconditioner_theorem_bounds():
+    m = oracle.Model(P.config_small(), averages=("edge", "face"))
+    m.schur()
+    M = _dense_op(m.apply_M, m.nG)
+    S = _dense_op(m.apply_S, m.nG)
+    assert np.linalg.norm(M - M.T) < 1e-10 * np.linalg.norm(M)
+    lam = np.sort(np.linalg.eigvals(M @ S).real)
+    assert lam[0] > 1 - 1e-9          # Theorem 2.1: lambda >= 1
+    # Lanczos estimate from PCG vs the dense spectrum
+    res = m.solve(tol=1e-8)
+    tmin, tmax = res.condition()
+    assert abs(tmax - lam[-1]) < 0.01 * lam[-1]
+    assert tmin > 1 - 1e-6
+
+
+def test_all_interface_primal_is_exact():
+    m = oracle.Model(P.poisson_cube(6, 2, coef="lognormal"))
+    m.schur()
+    m.globs.corners = list(m.globs.interface_nodes)
+    m.globs.corner_set = set(m.globs.corners)
+    M = _dense_op(m.apply_M, m.nG)
+    S = _dense_op(m.apply_S, m.nG)
+    assert np.linalg.norm(M @ S - np.eye(m.nG)) < 1e-9
+    res = m.solve(tol=1e-10)
+    assert res.iters == 1
+
+
+# --- adaptive constraints ---------------------------------------------------------
+
+def _two_substructures():
+    prob = P.poisson_cube(6, 2, coef="lognormal", s_xyz=(2, 1, 1), seed=3)
+    m = oracle.Model(prob)
+    assert len(m.globs.faces) == 1 and not m.globs.corners
+    # one corner so that Assumptions 1 and 2 hold (the floating substructure)
+    face = m.globs.faces[(0, 1)]
+    m.globs.corners = [face[len(face) // 2]]
+    m.globs.corner_set = set(m.globs.corners)
+    m.globs.faces[(0, 1)] = [n for n in face if n != m.globs.corners[0]]
+    m.schur()
+    return m
+
+
+def test_two_substructure_pair_problem_is_the_global_one():
+    """Corollary 3.1 with one pair: lambda_max(M S) = omega_12, and after adding
+    the k top eigen-constraints lambda_max(M S) = lambda_{12,k+1}."""
+    m = _two_substructures()
+    res = pair_problem(m, 0, 1, tau=1.0)
+    lam = res.lam
+    M = _dense_op(m.apply_M, m.nG)
+    S = _dense_op(m.apply_S, m.nG)
+    lmax = np.linalg.eigvals(M @ S).real.max()
+    assert abs(lmax - lam[0]) < 1e-8 * lam[0]
+    for k in (1, 2, 3):
+        m2 = _two_substructures()
+        r2 = pair_problem(m2, 0, 1, tau=lam[k] * (1 + 1e-9))
+        assert r2.selected == k
+        rows = orthonormal_rows(r2.face_rows)
+        m2.add_constraint("adaptive", m2.globs.faces[(0, 1)], (0, 1), rows)
+        M2 = _dense_op(m2.apply_M, m2.nG)
+        lmax2 = np.linalg.eigvals(M2 @ S).real.max()
+        assert abs(lmax2 - lam[k]) < 1e-7 * lam[k]
+
+
+def test_condensed_pencil_matches_full_pencil():
+    m = _two_substructures()
+    res = pair_problem(m, 0, 1, tau=1.0)
+    pd = pair_data(m, 0, 1)
+    Sc = pd["Sc"]
+    N = Sc.shape[0]
+    ns = pd["pos_i"].size
+    IE = np.zeros((N, N))
+    for k in range(ns):
+        a, b = pd["pos_i"][k], pd["pos_j"][k]
+        IE[a, a], IE[a, b] = pd["dj"][k], -pd["dj"][k]
+        IE[b, a], IE[b, b] = -pd["di"][k], pd["di"][k]
+    Lf = IE.T @ Sc @ IE
+    w = sla.eigh(Lf, Sc, eigvals_only=True)       # S^c is SPD: substructure 0 is clamped
+    w = np.sort(w)[::-1]
+    nz = res.lam[res.lam > 1e-8 * res.lam[0]]
+    assert np.allclose(w[: nz.size], nz, rtol=1e-9)
+    assert np.all(np.abs(w[nz.size:]) < 1e-8 * w[0])
+
+
+def test_constraint_rows_prop41_lemma32():
+    m = oracle.Model(P.poisson_cube(8, 2, coef="lognormal"))
+    m.schur()
+    for (i, j) in list(m.globs.faces)[:4]:
+        res = pair_problem(m, i, j, tau=2.0)
+        ns = res.s_gdofs.size
+        d = res.d_full
+        if d.shape[0] == 0:
+            continue
+        scale = np.abs(d).max()
+        assert np.abs(d[:, :ns] + d[:, ns:]).max() < 1e-10 * scale      # Prop. 4.1
+        v = np.random.default_rng(0).standard_normal(ns)
+        assert np.abs(d @ np.concatenate([v, v])).max() < 1e-10 * scale * np.abs(v).sum()  # Lemma 3.2
+
+
+def test_jacobi_against_brute_force():
+    rng = np.random.default_rng(5)
+    for n in (1, 2, 7, 20, 41):
+        A = rng.standard_normal((n, n))
+        A = A + A.T
+        w, V = native.jacobi_eigh(A)
+        assert np.allclose(w, np.linalg.eigvalsh(A), atol=1e-12 * max(1, np.abs(w).max()))
+        assert np.linalg.norm(A @ V - V * w) < 1e-11 * np.linalg.norm(A)
+        assert np.linalg.norm(V.T @ V - np.eye(n)) < 1e-12
+
+
+def test_face_eigs_tiny_faces_brute_force():
+    """Pair eigenvalues on small faces against a generic generalized eigensolver
+    on the deflated pencil."""
+    m = oracle.Model(P.poisson_cube(6, 2, coef="lognormal", seed=7))
+    m.schur()
+    for (i, j) in list(m.globs.faces)[:3]:
+        res = pair_problem(m, i, j, tau=1.0, keep_matrices=True)
+        Sh, L = res.Shat, res.L
+        mu, V = np.linalg.eigh(Sh)
+        keep = mu > 1e-12 * mu.max()
+        Q = V[:, keep]
+        w = sla.eigh(Q.T @ L @ Q, Q.T @ Sh @ Q, eigvals_only=True)[::-1]
+        assert np.allclose(res.lam, w, rtol=1e-9, atol=1e-10 * w[0])
+
+
+def test_orthonormal_rows_rank_drop():
+    rng = np.random.default_rng(2)
+    a = rng.standard_normal((2, 10))
+    rows = np.vstack([a, a[0] + 2 * a[1], 3 * a[1]])
+    q = orthonormal_rows(rows)
+    assert q.shape[0] == 2
+    assert np.allclose(q @ q.T, np.eye(2), atol=1e-12)
+    # same span
+    assert np.linalg.norm(rows - rows @ q.T @ q) < 1e-10 * np.linalg.norm(rows)
+
+
+def test_adaptive_indicator_bounds_condition():
+    """Adaptive BDDC on a jump problem: omega~ predicts the corner-only condition
+    number, and with the constraints kappa falls below tau."""
+    prob = P.poisson_cube(12, 2, coef="random_high", seed=2)
+    m0, _, r0 = oracle.run(prob)
+    m1, ad, r1 = oracle.run(prob, tau=10.0)
+    k0 = r0.condition()[1]
+    k1 = r1.condition()[1]
+    assert ad.n_added > 0
+    assert k1 < 10.0 * 1.01
+    assert 0.3 * ad.omega < k0 < 3 * ad.omega
+    assert r1.iters < r0.iters
