@@ -1,0 +1,280 @@
+"""Benchmark: adaptive BDDC setup + solve time at relative residual 1e-8.
+
+Workload (the timed step): Q1 Poisson on 24^3 elements of the unit cube,
+3x3x3 cubic substructures of 8^3 elements, k = 1 with exactly 20% of the
+elements (seeded) at k = 1e4, u = 0 on x = 0, nodal loads U[-1, 1]; corners
+only as initial constraints, adaptive face constraints for lambda > tau = 10,
+PCG to ||r|| <= 1e-8 ||r_0||.  One step = classification + assembly +
+interior elimination + coarse setup + pair eigenproblems + adaptive coarse
+setup + condensed rhs + PCG + recovery, with the mesh arrays resident in HBM.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+(the reference arm of this paper-only build) on the host cores instead.
+Under torchrun every rank solves its own replica on its own GPU (the path
+needs no collective); value = max over ranks of the per-step time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BDDC setup+solve s at rel.res 1e-8, mixed vs FP64 GPU; % tensor-core peak"
+WORKLOAD = "poisson24_3x3x3_jump1e4_adaptive_tau10"
+TAU = 10.0
+# FP64 dense peak: the measured bf16 burst peak times the nominal FP64/BF16 ratio (1.25 / 2250 TFLOP/s)
+NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("bf16_tflops", 1900.0), d.get("hbm_gbs", 6800.0), "measured"
+    return 1900.0, 6800.0, "fallback"
+
+
+def _config(prob, seed):
+    return {"workload": WORKLOAD, "mesh": "24x24x24 Q1 hex", "substructures": prob.nsub,
+            "free_dofs": int((~prob.dirichlet).sum()), "tau": TAU, "tol": 1e-8, "seed": seed,
+            "precision": "fp64", "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_0910_5863_gb300 import problems as P
+    from paper_0910_5863_gb300 import bddc as B
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = P.config_adaptive_poisson(seed=args.seed)
+    # inputs resident in HBM
+    d_xyz = torch.from_numpy(np.ascontiguousarray(prob.xyz)).to(dev)
+    d_el = torch.from_numpy(np.ascontiguousarray(prob.elems, dtype=np.int64)).to(dev)
+    d_coef = torch.from_numpy(np.ascontiguousarray(prob.coef)).to(dev)
+    d_sub = torch.from_numpy(np.ascontiguousarray(prob.elem_sub, dtype=np.int32)).to(dev)
+    d_dir = torch.from_numpy(np.ascontiguousarray(prob.dirichlet, dtype=np.uint8)).to(dev)
+    f_host = B.free_load_vector(prob)
+    d_f = torch.from_numpy(f_host).to(dev)
+    d_u = torch.zeros_like(d_f)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    solver = B.Solver(tol=1e-8, stream=stream.cuda_stream)
+
+    def step():
+        solver.set_mesh(prob.ncomp, d_xyz, d_el, d_coef, prob.nu, d_sub, prob.nsub, d_dir)
+        solver.setup()
+        ad = solver.adapt(TAU)
+        _, info = solver.solve(d_f, d_u)
+        return ad, info
+
+    for _ in range(args.warmup):
+        ad, info = step()
+    torch.cuda.synchronize()
+    launches0 = solver.launch_count()
+    clocks = Clocks(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    phases = {k: [] for k in B.PHASES}
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ad, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        for k, (ms, fl) in solver.phase_times().items():
+            phases[k].append((ms, fl))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = solver.launch_count() - launches0
+    t_step = sum(times) / len(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_step], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    # end-to-end through the C ABI with host buffers (mesh and f from host, u back to host)
+    mesh_host = [np.ascontiguousarray(prob.xyz), np.ascontiguousarray(prob.elems, dtype=np.int64),
+                 np.ascontiguousarray(prob.coef), np.ascontiguousarray(prob.elem_sub, dtype=np.int32),
+                 np.ascontiguousarray(prob.dirichlet, dtype=np.uint8)]
+    u_host = np.zeros_like(f_host)
+    e2e_times = []
+    for it in range(max(2, args.steps // 2) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solver.set_mesh(prob.ncomp, mesh_host[0], mesh_host[1], mesh_host[2], prob.nu, mesh_host[3], prob.nsub,
+                        mesh_host[4])
+        solver.setup()
+        solver.adapt(TAU)
+        solver.solve(f_host, u_host)
+        t1 = time.perf_counter()
+        if it > 0:
+            e2e_times.append(t1 - t0)
+    h2d = sum(a.nbytes for a in mesh_host) + f_host.nbytes
+    d2h = u_host.nbytes
+
+    # roofline: the batched partial Cholesky of the interior elimination (FP64)
+    bf16, hbm, src = _peaks()
+    fp64_peak = bf16 * NOMINAL_FP64_OVER_BF16
+    ie = phases["interior_elimination"]
+    ie_ms = sum(m for m, _ in ie) / len(ie)
+    ie_flop = ie[-1][1]
+    achieved = ie_flop / (ie_ms / 1e3) / 1e12
+    phase_ms = {k: round(sum(m for m, _ in v) / len(v), 4) for k, v in phases.items()}
+    dominant = max(phase_ms, key=phase_ms.get)
+    line = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(prob, args.seed),
+        "roofline": {"bound": "tensor", "kernel": "pchol_panel+pchol_update (interior elimination, FP64)",
+                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                     "traffic": None,
+                     "peak_source": f"{src} bf16 {bf16} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250",
+                     "flop_per_launch": ie_flop, "ms_per_launch": ie_ms},
+        "e2e": {"value": statistics.median(e2e_times), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "phase_ms": phase_ms, "dominant_phase": dominant,
+        "iters": info["iters"], "kappa": info["kappa"], "n_added": ad["n_added"], "omega": ad["omega"],
+    }
+    return line
+
+
+def run_oracle(args, sample_note):
+    """The FP64 CPU oracle on the same workload (host cores)."""
+    from paper_0910_5863_gb300 import problems as P
+    import oracle
+
+    prob = P.config_adaptive_poisson(seed=args.seed)
+    t0 = time.perf_counter()
+    m = oracle.Model(prob)
+    m.schur()
+    ad = oracle.adapt(m, TAU)
+    res = m.solve(tol=1e-8)
+    t1 = time.perf_counter()
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count())))
+    return t1 - t0, cores, res.iters, ad.n_added
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        for _ in range(min(args.warmup, 1)):
+            run_oracle(args, "")
+        times = []
+        for _ in range(args.steps):
+            t, cores, iters, added = run_oracle(args, "")
+            times.append(t)
+        v = statistics.median(times)
+        cfg = _config(__import__("paper_0910_5863_gb300.problems", fromlist=["x"]).config_adaptive_poisson(args.seed),
+                      args.seed)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+                "steps": len(times), "warmup": 0, "ms_per_step": v * 1e3, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                                 "sample": "the whole workload per step (setup + adapt + solve), median of steps"},
+                "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "iters": iters, "n_added": added}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    line = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            t, cores, iters, added = run_oracle(args, "")
+            line["cpu_baseline"] = {"value": t, "unit": "s", "cores": cores, "kind": "oracle",
+                                    "sample": "one full run of the workload (setup + adapt + solve)",
+                                    "iters": iters, "n_added": added}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * bddc.h -- C ABI of the GB300 (sm_103a) adaptive BDDC library.
+ *
+ * The library computes the data-parallel hot path of adaptive BDDC in three
+ * dimensions (Mandel, Sousedik, Sistek, "Adaptive BDDC in three
+ * dimensions"): substructure Schur complements by batched dense Cholesky
+ * (Section 2, eq. (reduced-problem)), the pairwise face generalized
+ * eigenproblems and the adaptive face constraints (Section 3, eq.
+ * (eig-matrix), (d-def), Algorithm 3.1), and PCG with the BDDC preconditioner
+ * of Lemma 2.1 (eqs. (BDDC-prec)-(BDDC-Dc)) on one GPU.
+ *
+ * Conventions shared by every call
+ *  - Every call returns a bddc_status; nothing aborts, traps or throws across
+ *    the ABI.  bddc_last_error() gives a one-line reason for the last failure.
+ *  - Pointers are plain host or device addresses; ``mem`` says which
+ *    (BDDC_MEM_HOST / BDDC_MEM_DEVICE).  Inputs are copied during the call;
+ *    the caller keeps ownership of every buffer it passes.
+ *  - One handle serves one thread and one CUDA stream (bddc_options.stream,
+ *    NULL = the legacy default stream).  Calls on one handle are not
+ *    re-entrant.
+ *  - Free degrees of freedom ("global dofs") are numbered node-major over the
+ *    non-Dirichlet nodes in increasing node id, ncomp consecutive dofs per
+ *    node.  Interface dofs (dofs of nodes in more than one substructure)
+ *    are numbered by increasing global dof.
+ *  - Device memory is allocated with cudaMalloc by the handle and released by
+ *    bddc_destroy.
+ */
+#ifndef BDDC_H
+#define BDDC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BDDC_API __attribute__((visibility("default")))
+#else
+#define BDDC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BDDC_OK = 0,
+    BDDC_EINVAL = 1,       /* bad argument or size */
+    BDDC_ENOMEM = 2,       /* device or host allocation failed */
+    BDDC_ENOTSPD = 3,      /* non-positive pivot in a Cholesky factorization */
+    BDDC_EASSUMPTION = 4,  /* Assumption 1 or 2 of the paper violated (too few corners) */
+    BDDC_ENOCONV = 5,      /* PCG reached maxit; the best iterate is returned */
+    BDDC_ETIMEOUT = 6,     /* a bounded device wait gave up; the context stays usable */
+    BDDC_ECUDA = 7,        /* a CUDA runtime error */
+    BDDC_ESTATE = 8        /* call out of order (e.g. solve before setup) */
+} bddc_status;
+
+typedef enum { BDDC_MEM_HOST = 0, BDDC_MEM_DEVICE = 1 } bddc_mem;
+
+typedef enum {
+    BDDC_FP64 = 0,         /* every dense factorization in FP64 */
+    BDDC_MIXED = 1         /* FP32 factorizations + FP64 refinement; FP64 coarse, eigen, PCG */
+} bddc_precision;
+
+enum { BDDC_AVG_EDGE = 1, BDDC_AVG_FACE = 2 };
+
+typedef struct {
+    int precision;         /* bddc_precision, default BDDC_FP64 */
+    double tol;            /* PCG relative residual tolerance, default 1e-8 */
+    int maxit;             /* PCG iteration limit, default 1000 */
+    double drop_rel;       /* per-face rank drop of adaptive rows, default 1e-10 */
+    double timeout_s;      /* limit of every bounded device wait, default 10 s */
+    void *stream;          /* cudaStream_t; NULL = default stream */
+} bddc_options;
+
+typedef struct bddc_handle bddc_handle;
+
+typedef struct {
+    int n_faces;           /* face pairs examined */
+    int n_added;           /* adaptive constraints added (after rank drop) */
+    int n_ties;            /* eigenvalues within 1e-6 relative of tau */
+    double omega;          /* condition number indicator max_ij lambda_ij,1 (eq. (cond-ind)) */
+} bddc_adapt_info;
+
+typedef struct {
+    int iters;             /* PCG iterations */
+    int converged;         /* 1 if ||r_k|| <= tol ||r_0|| */
+    double relres;         /* ||r_k|| / ||r_0|| of the recurrence */
+    double kappa;          /* Lanczos estimate lambda_max / lambda_min */
+    double setup_ms;       /* last bddc_setup + bddc_adapt, device time */
+    double solve_ms;       /* this solve, device time */
+} bddc_solve_info;
+
+/* Fills *opt with the defaults above. */
+BDDC_API void bddc_default_options(bddc_options *opt);
+
+/* Creates a handle.  opt may be NULL (defaults).  *out receives the handle.
+ * Errors: BDDC_ENOMEM, BDDC_ECUDA (no device). */
+BDDC_API bddc_status bddc_create(const bddc_options *opt, bddc_handle **out);
+
+/* Releases every host and device buffer of the handle.  NULL is allowed. */
+BDDC_API void bddc_destroy(bddc_handle *h);
+
+/* Defines the problem from a trilinear hexahedral (Q1) mesh (Section 2: each
+ * substructure is a union of elements and A_i is the subassembly of its
+ * element matrices).
+ *   ncomp      1 = scalar diffusion -div(k grad u), 3 = linear elasticity
+ *   nn, xyz    nodes, xyz row-major (nn x 3) float64
+ *   ne, elems  elements, row-major (ne x 8) int64 node ids, local node
+ *              a = ax + 2 ay + 4 az for the reference corner (ax, ay, az)
+ *   coef       (ne) float64: k_e (ncomp 1) or Young modulus E_e (ncomp 3)
+ *   nu         Poisson ratio (ncomp 3; ignored for ncomp 1)
+ *   elem_sub   (ne) int32 substructure of each element, 0 <= s < nsub
+ *   dirichlet  (nn) uint8, non-zero = every component of the node fixed to 0
+ *   mem        where the arrays live
+ * Classifies the interface into faces, edges and corners (Section 2; corner
+ * = a one-node edge set, or an edge-set node with at most one element-edge
+ * neighbour in its own set and no neighbour whose set is a strict superset),
+ * on the full mesh, then drops Dirichlet nodes.  Resets constraints to
+ * corners only.  Errors: BDDC_EINVAL (sizes, ids out of range), BDDC_ENOMEM. */
+BDDC_API bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double *xyz, int64_t ne,
+                             const int64_t *elems, const double *coef, double nu, const int32_t *elem_sub,
+                             int32_t nsub, const uint8_t *dirichlet, int mem);
+
+/* Adds arithmetic averages as initial constraints (Section 2, eq. (Wtilde);
+ * one coarse dof per glob and component): flags = BDDC_AVG_EDGE | BDDC_AVG_FACE.
+ * Must follow bddc_set_mesh_q1 and precede bddc_setup. */
+BDDC_API bddc_status bddc_set_averages(bddc_handle *h, int flags);
+
+/* Numeric setup: assembles A_i on the device, factors A_II and forms
+ * S_i = A_GG - A_GI A_II^{-1} A_IG (Section 2), the averaging weights
+ * delta_i = diag(A_i) / sum_k diag(A_k) (Section 7), and the local saddle
+ * and coarse operators of the preconditioner for the current constraints.
+ * Errors: BDDC_ESTATE (no mesh), BDDC_ENOTSPD, BDDC_EASSUMPTION, BDDC_ECUDA. */
+BDDC_API bddc_status bddc_setup(bddc_handle *h);
+
+/* Algorithm 3.1: for every pair of substructures sharing a face solves the
+ * pair eigenproblem (eq. (eig-matrix)) and adds, for every eigenvalue
+ * lambda > tau, the face part of d = w^T (I-E)^T S^c (I-E) (eq. (d-def))
+ * as a weighted-average face constraint (edge parts dropped, Remark of
+ * Section 3), then rebuilds the preconditioner.  info may be NULL.
+ * Errors: BDDC_ESTATE (no setup), BDDC_ENOTSPD, BDDC_EASSUMPTION. */
+BDDC_API bddc_status bddc_adapt(bddc_handle *h, double tau, bddc_adapt_info *info);
+
+/* Solves sum_i R_i^T A_i R_i u = f: condensed right-hand side, PCG with the
+ * BDDC preconditioner to ||r|| <= tol ||r_0|| from x_0 = 0, interior
+ * recovery.  f and u are global free-dof vectors (length n_free) in memory
+ * ``mem``.  info may be NULL.  Errors: BDDC_ESTATE, BDDC_ENOCONV (u holds the
+ * last iterate), BDDC_ETIMEOUT, BDDC_ECUDA. */
+BDDC_API bddc_status bddc_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_info *info);
+
+/* Extreme eigenvalues of the Lanczos matrix built from the last solve's PCG
+ * coefficients alpha_k, beta_k (caption of Table 1 of the paper). */
+BDDC_API bddc_status bddc_condition_estimate(const bddc_handle *h, double *lmin, double *lmax);
+
+/* Sizes after bddc_set_mesh_q1 (any pointer may be NULL). */
+BDDC_API bddc_status bddc_get_sizes(const bddc_handle *h, int64_t *n_free, int64_t *n_interface, int *n_corners,
+                           int *n_edges, int *n_faces, int *n_coarse);
+
+/* Corner node ids (ascending) into nodes[cap]; *n = count. */
+BDDC_API bddc_status bddc_get_corners(const bddc_handle *h, int64_t *nodes, int cap, int *n);
+
+/* Face f (0 <= f < n_faces, faces ordered by (i, j), i < j): the pair, the
+ * eigenvalues computed by the last bddc_adapt in descending order (the
+ * selected ones plus the largest rejected one; at most cap) and the number
+ * selected (lambda > tau) and kept after the rank drop. */
+BDDC_API bddc_status bddc_get_face_eigs(const bddc_handle *h, int f, int32_t *i, int32_t *j, double *lam, int cap,
+                               int *n_lam, int *n_selected, int *n_kept);
+
+/* Interface dofs (global dof ids, ascending) of substructure s into gdofs[cap]. */
+BDDC_API bddc_status bddc_get_interface_dofs(const bddc_handle *h, int s, int64_t *gdofs, int cap, int *n);
+
+/* S_s after bddc_setup, n x n column-major into S (ld >= n), ordered as
+ * bddc_get_interface_dofs; mem = where S lives. */
+BDDC_API bddc_status bddc_get_schur(const bddc_handle *h, int s, double *S, int ld, int mem);
+
+/* One application of the preconditioner (z = M r) or of the assembled Schur
+ * operator (y = S x) to an interface vector (length n_interface). */
+BDDC_API bddc_status bddc_apply_preconditioner(bddc_handle *h, const double *r, double *z, int mem);
+BDDC_API bddc_status bddc_apply_schur(bddc_handle *h, const double *x, double *y, int mem);
+
+/* Device time (CUDA events on the handle's stream) and algorithmic FLOPs of
+ * the phases of the last setup / adapt / solve, in this order:
+ *   0 Q1 assembly + weights          1 interior elimination (partial Cholesky of A_i)
+ *   2 coarse operators (setup)       3 pair condensations (adapt)
+ *   4 face eigenproblems (adapt)     5 coarse operators (adapt)
+ *   6 condensed right-hand side      7 PCG                       8 interior recovery
+ * FLOPs of phase 1 are the dense count sum_i n_I^3/3 + n_I^2 n_G + n_I n_G^2;
+ * other phases report 0 FLOPs.  ms[cap], flop[cap] may be NULL; *n = 9. */
+BDDC_API bddc_status bddc_get_phase_times(const bddc_handle *h, double *ms, double *flop, int cap, int *n);
+
+/* Number of kernel launches made by the handle so far (all phases). */
+BDDC_API int64_t bddc_launch_count(const bddc_handle *h);
+
+BDDC_API const char *bddc_status_str(bddc_status s);
+BDDC_API const char *bddc_last_error(const bddc_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDDC_H */

@@ -1,0 +1,259 @@
+"""Python binding of the C ABI in include/bddc.h (argument marshalling only).
+
+Every numeric step runs in the CUDA library libbddc.so; this module converts
+numpy arrays / torch tensors to pointers and status codes to exceptions.  It
+fails loudly when the library has not been built (``python -m
+paper_0910_5863_gb300.build``): there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbddc.so")
+
+MEM_HOST, MEM_DEVICE = 0, 1
+FP64, MIXED = 0, 1
+AVG_EDGE, AVG_FACE = 1, 2
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTSPD", 4: "EASSUMPTION", 5: "ENOCONV", 6: "ETIMEOUT",
+          7: "ECUDA", 8: "ESTATE"}
+
+EXPORTS = ["bddc_default_options", "bddc_create", "bddc_destroy", "bddc_set_mesh_q1", "bddc_set_averages",
+           "bddc_setup", "bddc_adapt", "bddc_solve", "bddc_condition_estimate", "bddc_get_sizes",
+           "bddc_get_corners", "bddc_get_face_eigs", "bddc_get_interface_dofs", "bddc_get_schur",
+           "bddc_apply_preconditioner", "bddc_apply_schur", "bddc_launch_count", "bddc_status_str",
+           "bddc_last_error", "bddc_get_phase_times"]
+PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
+          "coarse_adapt", "condensed_rhs", "pcg", "recovery"]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int), ("drop_rel", C.c_double),
+                ("timeout_s", C.c_double), ("stream", C.c_void_p)]
+
+
+class AdaptInfo(C.Structure):
+    _fields_ = [("n_faces", C.c_int), ("n_added", C.c_int), ("n_ties", C.c_int), ("omega", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("relres", C.c_double), ("kappa", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+
+
+class BddcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libbddc.so; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} missing (run paper_0910_5863_gb300.build.build())")
+    lib = C.CDLL(path)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "bddc_default_options": (None, [vp]),
+        "bddc_create": (i32, [vp, vp]),
+        "bddc_destroy": (None, [vp]),
+        "bddc_set_mesh_q1": (i32, [vp, i32, i64, vp, i64, vp, vp, dbl, vp, C.c_int32, vp, i32]),
+        "bddc_set_averages": (i32, [vp, i32]),
+        "bddc_setup": (i32, [vp]),
+        "bddc_adapt": (i32, [vp, dbl, vp]),
+        "bddc_solve": (i32, [vp, vp, vp, i32, vp]),
+        "bddc_condition_estimate": (i32, [vp, vp, vp]),
+        "bddc_get_sizes": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "bddc_get_corners": (i32, [vp, vp, i32, vp]),
+        "bddc_get_face_eigs": (i32, [vp, i32, vp, vp, vp, i32, vp, vp, vp]),
+        "bddc_get_interface_dofs": (i32, [vp, i32, vp, i32, vp]),
+        "bddc_get_schur": (i32, [vp, i32, vp, i32, i32]),
+        "bddc_apply_preconditioner": (i32, [vp, vp, vp, i32]),
+        "bddc_apply_schur": (i32, [vp, vp, vp, i32]),
+        "bddc_launch_count": (i64, [vp]),
+        "bddc_status_str": (C.c_char_p, [i32]),
+        "bddc_last_error": (C.c_char_p, [vp]),
+        "bddc_get_phase_times": (i32, [vp, vp, vp, i32, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """(pointer, mem) of a C-contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data, MEM_HOST
+    import torch
+    assert isinstance(a, torch.Tensor) and a.is_contiguous()
+    return a.data_ptr(), (MEM_DEVICE if a.is_cuda else MEM_HOST)
+
+
+class Solver:
+    """One handle of the library (one GPU, one stream)."""
+
+    def __init__(self, precision=FP64, tol=1e-8, maxit=1000, drop_rel=1e-10, timeout_s=10.0, stream=None):
+        self.lib = load()
+        opt = Options()
+        self.lib.bddc_default_options(C.byref(opt))
+        opt.precision = precision
+        opt.tol = tol
+        opt.maxit = maxit
+        opt.drop_rel = drop_rel
+        opt.timeout_s = timeout_s
+        opt.stream = stream
+        h = C.c_void_p()
+        st = self.lib.bddc_create(C.byref(opt), C.byref(h))
+        if st != 0:
+            raise BddcError(st, "bddc_create failed")
+        self.h = h
+        self.nfree = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bddc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise BddcError(st, self.lib.bddc_last_error(self.h).decode())
+
+    # -- problem ------------------------------------------------------------
+    def set_mesh(self, ncomp, xyz, elems, coef, nu, elem_sub, nsub, dirichlet):
+        """Arrays: numpy (host) or torch CUDA tensors (device), all in the same memory."""
+        arrs = [xyz, elems, coef, elem_sub, dirichlet]
+        ptrs = [_ptr(a) for a in arrs]
+        mem = ptrs[0][1]
+        assert all(p[1] == mem for p in ptrs), "all mesh arrays must live in the same memory"
+        nn = xyz.shape[0]
+        ne = elems.shape[0]
+        self._check(self.lib.bddc_set_mesh_q1(self.h, ncomp, nn, ptrs[0][0], ne, ptrs[1][0], ptrs[2][0], float(nu),
+                                              ptrs[3][0], int(nsub), ptrs[4][0], mem))
+        self.nfree = self.sizes()["n_free"]
+
+    def set_problem(self, prob):
+        """Host arrays of a paper_0910_5863_gb300.problems.Problem."""
+        self.set_mesh(prob.ncomp, np.ascontiguousarray(prob.xyz, dtype=np.float64),
+                      np.ascontiguousarray(prob.elems, dtype=np.int64),
+                      np.ascontiguousarray(prob.coef, dtype=np.float64), prob.nu,
+                      np.ascontiguousarray(prob.elem_sub, dtype=np.int32), prob.nsub,
+                      np.ascontiguousarray(prob.dirichlet, dtype=np.uint8))
+
+    def set_averages(self, edge=False, face=False):
+        self._check(self.lib.bddc_set_averages(self.h, (AVG_EDGE if edge else 0) | (AVG_FACE if face else 0)))
+
+    def setup(self):
+        self._check(self.lib.bddc_setup(self.h))
+
+    def adapt(self, tau):
+        info = AdaptInfo()
+        self._check(self.lib.bddc_adapt(self.h, float(tau), C.byref(info)))
+        return {"n_faces": info.n_faces, "n_added": info.n_added, "n_ties": info.n_ties, "omega": info.omega}
+
+    def solve(self, f, u=None, check=True):
+        """f: global free-dof load vector (numpy or torch CUDA).  Returns (u, info)."""
+        if u is None:
+            if isinstance(f, np.ndarray):
+                u = np.zeros_like(f)
+            else:
+                import torch
+                u = torch.zeros_like(f)
+        pf, mem = _ptr(f)
+        pu, mem2 = _ptr(u)
+        assert mem == mem2
+        info = SolveInfo()
+        st = self.lib.bddc_solve(self.h, pf, pu, mem, C.byref(info))
+        out = {"iters": info.iters, "converged": bool(info.converged), "relres": info.relres, "kappa": info.kappa}
+        if check or st not in (0, 5):
+            self._check(st)
+        out["status"] = STATUS.get(st, st)
+        return u, out
+
+    def condition_estimate(self):
+        lo, hi = C.c_double(), C.c_double()
+        self._check(self.lib.bddc_condition_estimate(self.h, C.byref(lo), C.byref(hi)))
+        return lo.value, hi.value
+
+    # -- inspection --------------------------------------------------------
+    def sizes(self):
+        nf, ni = C.c_int64(), C.c_int64()
+        nc, ne, nfa, nco = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.bddc_get_sizes(self.h, C.byref(nf), C.byref(ni), C.byref(nc), C.byref(ne), C.byref(nfa),
+                                            C.byref(nco)))
+        return {"n_free": nf.value, "n_interface": ni.value, "n_corners": nc.value, "n_edges": ne.value,
+                "n_faces": nfa.value, "n_coarse": nco.value}
+
+    def corners(self):
+        n = C.c_int()
+        self._check(self.lib.bddc_get_corners(self.h, None, 0, C.byref(n)))
+        out = np.zeros(n.value, dtype=np.int64)
+        self._check(self.lib.bddc_get_corners(self.h, out.ctypes.data, n.value, C.byref(n)))
+        return out
+
+    def face_eigs(self, f):
+        i, j = C.c_int32(), C.c_int32()
+        nl, ns, nk = C.c_int(), C.c_int(), C.c_int()
+        buf = np.zeros(64)
+        self._check(self.lib.bddc_get_face_eigs(self.h, f, C.byref(i), C.byref(j), buf.ctypes.data, 64, C.byref(nl),
+                                                C.byref(ns), C.byref(nk)))
+        return {"pair": (i.value, j.value), "lam": buf[: nl.value].copy(), "selected": ns.value, "kept": nk.value}
+
+    def interface_dofs(self, s):
+        n = C.c_int()
+        self._check(self.lib.bddc_get_interface_dofs(self.h, s, None, 0, C.byref(n)))
+        out = np.zeros(n.value, dtype=np.int64)
+        self._check(self.lib.bddc_get_interface_dofs(self.h, s, out.ctypes.data, n.value, C.byref(n)))
+        return out
+
+    def schur(self, s):
+        n = self.interface_dofs(s).size
+        S = np.zeros((n, n))
+        self._check(self.lib.bddc_get_schur(self.h, s, S.ctypes.data, n, MEM_HOST))
+        return S.T.copy()   # column-major -> row-major (symmetric anyway)
+
+    def apply_preconditioner(self, r):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        z = np.zeros_like(r)
+        self._check(self.lib.bddc_apply_preconditioner(self.h, r.ctypes.data, z.ctypes.data, MEM_HOST))
+        return z
+
+    def apply_schur(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        self._check(self.lib.bddc_apply_schur(self.h, x.ctypes.data, y.ctypes.data, MEM_HOST))
+        return y
+
+    def phase_times(self):
+        """{phase: (ms, algorithmic flop)} of the last setup / adapt / solve."""
+        ms = np.zeros(16)
+        fl = np.zeros(16)
+        n = C.c_int()
+        self._check(self.lib.bddc_get_phase_times(self.h, ms.ctypes.data, fl.ctypes.data, 16, C.byref(n)))
+        return {PHASES[k]: (ms[k], fl[k]) for k in range(n.value)}
+
+    def launch_count(self):
+        return int(self.lib.bddc_launch_count(self.h))
+
+
+def free_load_vector(prob):
+    """Global free-dof load vector of a Problem (node-major over non-Dirichlet nodes)."""
+    return np.ascontiguousarray(prob.load[~prob.dirichlet].reshape(-1), dtype=np.float64)

@@ -1,0 +1,1838 @@
+// Host orchestration and C ABI of the adaptive BDDC library.
+//
+// Phases (the hot path of the method, all numeric work in CUDA kernels):
+//   bddc_set_mesh_q1  classification of the interface into faces, edges and
+//                     corners (Section 2), index maps, device buffers;
+//   bddc_setup        Q1 assembly of A_i, batched partial Cholesky giving
+//                     S_i = A_GG - A_GI A_II^{-1} A_IG (Section 2), weights,
+//                     local saddle + coarse operators of the preconditioner;
+//   bddc_adapt        pair condensations, the face eigenproblems and the new
+//                     face constraints (Section 3, Algorithm 3.1);
+//   bddc_solve        condensed right-hand side, PCG (Lemma 2.1
+//                     preconditioner), interior recovery.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/bddc.h"
+#include "assembly.h"
+#include "common.cuh"
+#include "dense.h"
+#include "eig.h"
+#include "host_util.h"
+#include "pcg.h"
+
+using namespace bddc;
+
+namespace {
+
+struct SubData {
+    std::vector<int64_t> nodes;   // local nodes (sorted), Dirichlet included
+    std::vector<int64_t> gI, gG;  // global dofs of interior / interface (sorted)
+    int nI = 0, nG = 0, n = 0, ld = 0, ldS = 0;
+    std::vector<int> RG;          // interface index of each interface position
+    std::vector<int> cpos, rpos;  // corner / remaining interface positions
+    std::vector<int> corner_coarse;  // global coarse index of each corner dof (cpos order)
+    bool floating = false;
+    // constraint rows (averages and adaptive) over interface positions
+    int na = 0;
+    std::vector<int> row_coarse;  // global coarse index of each row
+    // device
+    double *A = nullptr, *S = nullptr, *P = nullptr, *Phi = nullptr, *Cb = nullptr;
+    int capA = 0;                 // row capacity of Cb
+    size_t offI = 0;              // offset in packed interior vectors
+};
+
+struct FacePair {
+    int i, j;
+    std::vector<int64_t> s_g;        // shared non-corner dofs (sorted)
+    std::vector<int> pos_i, pos_j;   // their interface positions in i and j
+    std::vector<int> face_idx;       // indices into s of the face dofs
+    std::vector<int> ci_pos, cj_pos; // shared corner dofs (interface positions)
+    bool floating = false;
+    int nnull = 0;
+    std::vector<double> N0;          // ns x nnull
+    // results of the last adapt
+    std::vector<double> lam;
+    int nsel = 0, nkept = 0, ties = 0;
+};
+
+struct GlobRows {               // one glob with constraint rows (c . w equal for all sharing subs)
+    std::vector<int> subs;
+    std::vector<int64_t> gdofs;
+    int nrows = 0;
+    std::vector<double> rows;   // host rows (row-major nrows x gdofs) for averages
+    int face = -1;              // >= 0: adaptive rows of that face (device buffer)
+    int coarse0 = 0;            // first global coarse index
+};
+
+struct PhaseTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+}  // namespace
+
+struct bddc_handle {
+    bddc_options opt;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t launches = 0;
+    Arena ar;
+    DevStatus *dst = nullptr;
+    // mesh
+    int ncomp = 1;
+    int64_t nn = 0, ne = 0;
+    int nsub = 0;
+    double nu = 0.0;
+    std::vector<double> xyz, coef;
+    std::vector<int64_t> elems;
+    std::vector<int32_t> esub;
+    std::vector<uint8_t> dirich;
+    bool have_mesh = false, have_setup = false;
+    // numbering / classification
+    std::vector<int64_t> node_first;
+    int64_t nfree = 0;
+    std::vector<int> node_set;              // set id per node
+    std::vector<std::vector<int>> sets;     // set id -> sorted substructures
+    std::vector<int64_t> corners;
+    std::vector<char> is_corner;
+    int n_edges = 0;
+    std::vector<std::pair<std::vector<int>, std::vector<int64_t>>> edge_globs;  // (subs, nodes)
+    std::vector<FacePair> faces;
+    std::vector<SubData> subs;
+    int nG = 0;
+    std::vector<int64_t> iface_gdof;
+    std::vector<int> gptr, gsub;
+    std::vector<int64_t> gent;
+    std::vector<int64_t> offG;               // packed offset per sub
+    int64_t sumG = 0, sumI = 0;
+    std::vector<std::vector<int32_t>> colors;
+    int avg_flags = 0;
+    std::vector<GlobRows> globs;
+    int nC = 0, n_corner_dofs = 0;
+    // preconditioner / PCG
+    IfaceOps ops{};
+    PcgBuffers pb{};
+    std::vector<double> alpha, beta;
+    int last_iters = 0;
+    double setup_ms = 0.0, adapt_ms = 0.0;
+    // adapt results
+    double omega = 0.0;
+    std::vector<double *> face_rows_dev;
+    int face_row_ld = 0;
+    // phase timing: events [2k, 2k+1] bracket phase k
+    static constexpr int kPhases = 9;
+    cudaEvent_t ev[2 * kPhases] = {};
+    bool ev_used[kPhases] = {};
+    double phase_ms[kPhases] = {};
+    double phase_flop[kPhases] = {};
+};
+
+namespace {
+
+void fail_check(bddc_handle *h, const char *where) {
+    DevStatus hs;
+    BDDC_CUDA(cudaMemcpyAsync(&hs, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+    BDDC_CUDA(cudaStreamSynchronize(h->stream));
+    if (hs.code == BDDC_DEV_ERR_NOTSPD)
+        throw Error{BDDC_ENOTSPD, std::string(where) + ": non-positive pivot in matrix " + std::to_string(hs.item) +
+                                      " near column " + std::to_string(hs.pos)};
+    if (hs.code == BDDC_DEV_ERR_TIMEOUT) throw Error{BDDC_ETIMEOUT, std::string(where) + ": device wait timed out"};
+    if (hs.code != 0) throw Error{BDDC_ECUDA, std::string(where) + ": device error " + std::to_string(hs.code)};
+}
+
+void phase_begin(bddc_handle *h, int k) {
+    BDDC_CUDA(cudaEventRecord(h->ev[2 * k], h->stream));
+    h->ev_used[k] = true;
+}
+void phase_end(bddc_handle *h, int k) { BDDC_CUDA(cudaEventRecord(h->ev[2 * k + 1], h->stream)); }
+void phase_collect(bddc_handle *h, int k0, int k1) {
+    for (int k = k0; k <= k1; ++k) {
+        if (!h->ev_used[k]) continue;
+        float ms = 0.f;
+        BDDC_CUDA(cudaEventSynchronize(h->ev[2 * k + 1]));
+        BDDC_CUDA(cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]));
+        h->phase_ms[k] = ms;
+    }
+}
+
+void reset_status(bddc_handle *h) { BDDC_CUDA(cudaMemsetAsync(h->dst, 0, sizeof(DevStatus), h->stream)); }
+
+void check_launch(bddc_handle *h) {
+    h->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error{BDDC_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
+// ---- batched partial Cholesky ------------------------------------------------
+template <typename T>
+void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs, const std::string &tag) {
+    if (descs.empty()) return;
+    int nsteps = 0;
+    for (auto &d : descs) nsteps = std::max(nsteps, (d.nstop + kPanelNB - 1) / kPanelNB);
+    std::vector<int2> pitems;
+    std::vector<int4> uitems;
+    std::vector<int> poff(nsteps + 1, 0), uoff(nsteps + 1, 0);
+    for (int s = 0; s < nsteps; ++s) {
+        int kb = s * kPanelNB;
+        poff[s] = (int)pitems.size();
+        uoff[s] = (int)uitems.size();
+        for (int m = 0; m < (int)descs.size(); ++m) {
+            const auto &d = descs[m];
+            if (kb >= d.nstop) continue;
+            int nb = std::min(kPanelNB, d.nstop - kb);
+            int below = d.n - kb - nb;
+            int np = std::max(1, (below + kPanelRows - 1) / kPanelRows);
+            for (int r = 0; r < np; ++r) pitems.push_back(make_int2(m, r));
+            int tn = d.n - kb - nb;
+            int nt = (tn + kTile - 1) / kTile;
+            for (int ti = 0; ti < nt; ++ti)
+                for (int tj = 0; tj <= ti; ++tj) uitems.push_back(make_int4(m, ti, tj, 0));
+        }
+    }
+    poff[nsteps] = (int)pitems.size();
+    uoff[nsteps] = (int)uitems.size();
+    auto *dd = h->ar.upload("pc_desc_" + tag, descs, h->stream);
+    auto *dp = h->ar.upload("pc_pit_" + tag, pitems, h->stream);
+    auto *du = h->ar.upload("pc_uit_" + tag, uitems, h->stream);
+    for (int s = 0; s < nsteps; ++s) {
+        int kb = s * kPanelNB;
+        launch_pchol_panel<T>(dd, dp + poff[s], poff[s + 1] - poff[s], kb, h->dst, h->stream);
+        check_launch(h);
+        if (uoff[s + 1] > uoff[s]) {
+            launch_pchol_update<T>(dd, du + uoff[s], uoff[s + 1] - uoff[s], kb, h->stream);
+            check_launch(h);
+        }
+    }
+}
+
+void run_gathers(bddc_handle *h, const std::vector<GatherOp> &ops, const std::string &tag) {
+    if (ops.empty()) return;
+    std::vector<int2> items;
+    for (int k = 0; k < (int)ops.size(); ++k)
+        for (int q = 0; q < (ops[k].nc + 7) / 8; ++q) items.push_back(make_int2(k, q));
+    auto *d_ops = h->ar.upload("g_ops_" + tag, ops, h->stream);
+    auto *d_items = h->ar.upload("g_it_" + tag, items, h->stream);
+    launch_gather(d_ops, d_items, (int)items.size(), h->stream);
+    check_launch(h);
+}
+
+void run_diag(bddc_handle *h, const std::vector<DiagOp> &ops, const std::string &tag) {
+    if (ops.empty()) return;
+    auto *d = h->ar.upload("d_ops_" + tag, ops, h->stream);
+    launch_diag_set(d, (int)ops.size(), h->stream);
+    check_launch(h);
+}
+
+void run_gemm(bddc_handle *h, const std::vector<GemmDesc> &descs, const std::string &tag) {
+    if (descs.empty()) return;
+    std::vector<int4> items;
+    for (int k = 0; k < (int)descs.size(); ++k)
+        for (int a = 0; a < (descs[k].m + kTile - 1) / kTile; ++a)
+            for (int b = 0; b < (descs[k].n + kTile - 1) / kTile; ++b) items.push_back(make_int4(k, a, b, 0));
+    auto *dd = h->ar.upload("gm_desc_" + tag, descs, h->stream);
+    auto *di = h->ar.upload("gm_it_" + tag, items, h->stream);
+    launch_gemm(dd, di, (int)items.size(), h->stream);
+    check_launch(h);
+}
+
+void zero(bddc_handle *h, double *p, size_t n) {
+    launch_zero(p, n, h->stream);
+    check_launch(h);
+}
+
+GatherOp gop(const double *src, int ld_src, double *dst, int ld_dst, int nr, int nc) {
+    GatherOp o;
+    memset(&o, 0, sizeof(o));
+    o.src = src;
+    o.ld_src = ld_src;
+    o.dst = dst;
+    o.ld_dst = ld_dst;
+    o.nr = nr;
+    o.nc = nc;
+    o.scale = 1.0;
+    return o;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---- classification ------------------------------------------------------
+const int HEX_EDGES[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
+                              {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+
+void classify(bddc_handle *h) {
+    const int64_t nn = h->nn, ne = h->ne;
+    const int c = h->ncomp;
+    // free dofs
+    h->node_first.assign(nn, -1);
+    int64_t nf = 0;
+    for (int64_t v = 0; v < nn; ++v)
+        if (!h->dirich[v]) {
+            h->node_first[v] = nf;
+            nf += c;
+        }
+    h->nfree = nf;
+    // node -> set of substructures
+    std::vector<std::vector<int>> nsets(nn);
+    for (int64_t e = 0; e < ne; ++e)
+        for (int a = 0; a < 8; ++a) {
+            auto &v = nsets[h->elems[e * 8 + a]];
+            int s = h->esub[e];
+            if (std::find(v.begin(), v.end(), s) == v.end()) v.push_back(s);
+        }
+    std::map<std::vector<int>, int> set_id;
+    h->sets.clear();
+    h->node_set.assign(nn, -1);
+    for (int64_t v = 0; v < nn; ++v) {
+        auto &s = nsets[v];
+        std::sort(s.begin(), s.end());
+        auto it = set_id.find(s);
+        int id;
+        if (it == set_id.end()) {
+            id = (int)h->sets.size();
+            set_id[s] = id;
+            h->sets.push_back(s);
+        } else {
+            id = it->second;
+        }
+        h->node_set[v] = id;
+    }
+    // element-edge neighbours of nodes in edge sets (set size >= 3)
+    std::vector<std::vector<int64_t>> nb(nn);
+    for (int64_t e = 0; e < ne; ++e)
+        for (auto &ed : HEX_EDGES) {
+            int64_t a = h->elems[e * 8 + ed[0]], b = h->elems[e * 8 + ed[1]];
+            if (h->sets[h->node_set[a]].size() >= 3) nb[a].push_back(b);
+            if (h->sets[h->node_set[b]].size() >= 3) nb[b].push_back(a);
+        }
+    auto is_superset = [&](int big, int small) {
+        const auto &B = h->sets[big], &S = h->sets[small];
+        if (B.size() <= S.size()) return false;
+        return std::includes(B.begin(), B.end(), S.begin(), S.end());
+    };
+    std::vector<int> set_count(h->sets.size(), 0);
+    for (int64_t v = 0; v < nn; ++v) set_count[h->node_set[v]]++;
+    h->is_corner.assign(nn, 0);
+    for (int64_t v = 0; v < nn; ++v) {
+        int sid = h->node_set[v];
+        if (h->sets[sid].size() < 3) continue;
+        if (set_count[sid] == 1) {
+            h->is_corner[v] = 1;
+            continue;
+        }
+        auto &L = nb[v];
+        std::sort(L.begin(), L.end());
+        L.erase(std::unique(L.begin(), L.end()), L.end());
+        int same = 0;
+        bool sup = false;
+        for (int64_t m : L) {
+            int ms = h->node_set[m];
+            if (ms == sid) same++;
+            if (is_superset(ms, sid)) sup = true;
+        }
+        if (same <= 1 && !sup) h->is_corner[v] = 1;
+    }
+    h->corners.clear();
+    for (int64_t v = 0; v < nn; ++v) {
+        if (h->is_corner[v] && h->dirich[v]) h->is_corner[v] = 0;
+        if (h->is_corner[v]) h->corners.push_back(v);
+    }
+    // globs
+    std::map<std::vector<int>, std::vector<int64_t>> glob_nodes;
+    for (int64_t v = 0; v < nn; ++v) {
+        const auto &s = h->sets[h->node_set[v]];
+        if (s.size() < 2 || h->dirich[v] || h->is_corner[v]) continue;
+        glob_nodes[s].push_back(v);
+    }
+    h->edge_globs.clear();
+    std::vector<std::pair<std::pair<int, int>, std::vector<int64_t>>> face_list;
+    for (auto &kv : glob_nodes) {
+        if (kv.first.size() == 2)
+            face_list.push_back({{kv.first[0], kv.first[1]}, kv.second});
+        else
+            h->edge_globs.push_back({kv.first, kv.second});
+    }
+    std::sort(face_list.begin(), face_list.end());
+    h->n_edges = (int)h->edge_globs.size();
+
+    // substructures
+    const int ns = h->nsub;
+    h->subs.assign(ns, SubData());
+    std::vector<std::vector<int64_t>> snodes(ns);
+    for (int64_t e = 0; e < ne; ++e)
+        for (int a = 0; a < 8; ++a) snodes[h->esub[e]].push_back(h->elems[e * 8 + a]);
+    std::vector<char> is_iface_node(nn, 0);
+    for (int64_t v = 0; v < nn; ++v) is_iface_node[v] = h->sets[h->node_set[v]].size() >= 2 && !h->dirich[v];
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        auto &L = snodes[s];
+        std::sort(L.begin(), L.end());
+        L.erase(std::unique(L.begin(), L.end()), L.end());
+        sd.nodes = L;
+        bool touches_dirichlet = false;
+        for (int64_t v : L) {
+            if (h->dirich[v]) {
+                touches_dirichlet = true;
+                continue;
+            }
+            for (int k = 0; k < c; ++k) (is_iface_node[v] ? sd.gG : sd.gI).push_back(h->node_first[v] + k);
+        }
+        sd.floating = !touches_dirichlet;
+        sd.nI = (int)sd.gI.size();
+        sd.nG = (int)sd.gG.size();
+        sd.n = sd.nI + sd.nG;
+        sd.ld = round_up(std::max(sd.n, 1), 8);
+        sd.ldS = round_up(std::max(sd.nG, 1), 8);
+    }
+    // interface numbering and gather maps
+    std::vector<int64_t> all;
+    for (auto &sd : h->subs) all.insert(all.end(), sd.gG.begin(), sd.gG.end());
+    std::sort(all.begin(), all.end());
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    h->iface_gdof = all;
+    h->nG = (int)all.size();
+    std::vector<int> gidx(h->nfree, -1);
+    for (int x = 0; x < h->nG; ++x) gidx[all[x]] = x;
+    h->offG.assign(ns, 0);
+    int64_t off = 0, offI = 0;
+    std::vector<std::vector<std::pair<int, int64_t>>> ent(h->nG);
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        h->offG[s] = off;
+        sd.offI = offI;
+        sd.RG.resize(sd.nG);
+        for (int k = 0; k < sd.nG; ++k) {
+            sd.RG[k] = gidx[sd.gG[k]];
+            ent[sd.RG[k]].push_back({s, off + k});
+        }
+        off += sd.nG;
+        offI += sd.nI;
+        sd.cpos.clear();
+        sd.rpos.clear();
+    }
+    h->sumG = off;
+    h->sumI = offI;
+    // node of each free dof
+    std::vector<int64_t> dof_node(h->nfree);
+    for (int64_t v = 0; v < nn; ++v)
+        if (h->node_first[v] >= 0)
+            for (int k = 0; k < c; ++k) dof_node[h->node_first[v] + k] = v;
+    for (auto &sd : h->subs) {
+        for (int k = 0; k < sd.nG; ++k) (h->is_corner[dof_node[sd.gG[k]]] ? sd.cpos : sd.rpos).push_back(k);
+    }
+    h->gptr.assign(h->nG + 1, 0);
+    h->gent.clear();
+    h->gsub.clear();
+    for (int x = 0; x < h->nG; ++x) {
+        for (auto &pe : ent[x]) {
+            h->gent.push_back(pe.second);
+            h->gsub.push_back(pe.first);
+        }
+        h->gptr[x + 1] = (int)h->gent.size();
+    }
+    // corner dofs: global coarse indices 0..n_corner_dofs-1 in global dof order
+    std::vector<int64_t> cdofs;
+    for (int64_t v : h->corners)
+        for (int k = 0; k < c; ++k) cdofs.push_back(h->node_first[v] + k);
+    h->n_corner_dofs = (int)cdofs.size();
+    std::map<int64_t, int> cidx;
+    for (int k = 0; k < (int)cdofs.size(); ++k) cidx[cdofs[k]] = k;
+    for (auto &sd : h->subs) {
+        sd.corner_coarse.clear();
+        for (int p : sd.cpos) sd.corner_coarse.push_back(cidx[sd.gG[p]]);
+    }
+    // Assumption 1: every floating substructure needs corners that fix its rigid modes
+    auto rank_corners = [&](const std::vector<int64_t> &cn) {
+        // number of independent rigid modes fixed: 1 (scalar) or affine rank test (elasticity)
+        if (cn.empty()) return 0;
+        if (c == 1) return 1;
+        // elasticity: need 3 non-collinear points
+        const double *x0 = &h->xyz[cn[0] * 3];
+        int best = 1;
+        for (size_t a = 1; a < cn.size(); ++a) {
+            const double *xa = &h->xyz[cn[a] * 3];
+            double d1[3] = {xa[0] - x0[0], xa[1] - x0[1], xa[2] - x0[2]};
+            if (d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2] > 0) best = std::max(best, 2);
+            for (size_t b = a + 1; b < cn.size(); ++b) {
+                const double *xb = &h->xyz[cn[b] * 3];
+                double d2[3] = {xb[0] - x0[0], xb[1] - x0[1], xb[2] - x0[2]};
+                double cr[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2], d1[0] * d2[1] - d1[1] * d2[0]};
+                double n1 = std::sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+                double n2 = std::sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+                if (std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) > 1e-8 * n1 * n2) return 3;
+            }
+        }
+        return best;
+    };
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        if (!sd.floating) continue;
+        std::vector<int64_t> cn;
+        for (size_t k = 0; k < sd.cpos.size(); k += c) cn.push_back(dof_node[sd.gG[sd.cpos[k]]]);
+        int need = (c == 1) ? 1 : 3;
+        if (rank_corners(cn) < need)
+            throw Error{BDDC_EASSUMPTION, "Assumption 1: floating substructure " + std::to_string(s) +
+                                              " has too few corners to fix its rigid body modes"};
+    }
+    // face pairs
+    h->faces.clear();
+    for (auto &fl : face_list) {
+        FacePair fp;
+        fp.i = fl.first.first;
+        fp.j = fl.first.second;
+        auto &si = h->subs[fp.i], &sj = h->subs[fp.j];
+        std::map<int64_t, int> pi, pj;
+        for (int k = 0; k < si.nG; ++k) pi[si.gG[k]] = k;
+        for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = k;
+        std::vector<int64_t> cn;
+        for (int k = 0; k < si.nG; ++k) {
+            int64_t g = si.gG[k];
+            int64_t v = dof_node[g];
+            const auto &S = h->sets[h->node_set[v]];
+            bool both = std::binary_search(S.begin(), S.end(), fp.i) && std::binary_search(S.begin(), S.end(), fp.j);
+            if (!both) continue;
+            if (h->is_corner[v]) {
+                fp.ci_pos.push_back(k);
+                fp.cj_pos.push_back(pj.at(g));
+                if (g % c == 0 || c == 1) cn.push_back(v);
+                continue;
+            }
+            fp.s_g.push_back(g);
+        }
+        // s sorted by global dof (si.gG is sorted so s_g is too)
+        for (size_t k = 0; k < fp.s_g.size(); ++k) {
+            int64_t g = fp.s_g[k];
+            fp.pos_i.push_back(pi.at(g));
+            fp.pos_j.push_back(pj.at(g));
+            const auto &S = h->sets[h->node_set[dof_node[g]]];
+            if (S.size() == 2) fp.face_idx.push_back((int)k);
+        }
+        fp.floating = si.floating && sj.floating;
+        const int nsd = (int)fp.s_g.size();
+        if (fp.floating) {
+            int need = (c == 1) ? 1 : 3;
+            std::vector<int64_t> cnu;
+            for (size_t k = 0; k < fp.ci_pos.size(); k += c) cnu.push_back(dof_node[si.gG[fp.ci_pos[k]]]);
+            if (rank_corners(cnu) < need)
+                throw Error{BDDC_EASSUMPTION, "Assumption 2: corners shared by substructures " + std::to_string(fp.i) +
+                                                  " and " + std::to_string(fp.j) + " do not fix relative rigid motions"};
+            // null space of S^ on s: rigid modes, identical on both sides; N0 orthonormal with N = [N0; N0]
+            int nr = (c == 1) ? 1 : 6;
+            std::vector<double> R((size_t)nsd * nr, 0.0);
+            for (int k = 0; k < nsd; ++k) {
+                int64_t g = fp.s_g[k];
+                int comp = (int)(g % c);
+                const double *x = &h->xyz[dof_node[g] * 3];
+                if (c == 1) {
+                    R[k] = 1.0;
+                } else {
+                    R[(size_t)comp * nsd + k] = 1.0;  // translations
+                    // rotations omega x x: e_a x x, component comp
+                    double rot[3][3] = {{0, -x[2], x[1]}, {x[2], 0, -x[0]}, {-x[1], x[0], 0}};
+                    // omega = e_a: (e_a x x)_comp = rot[comp][a]... (e_a x x) = -x x e_a
+                    for (int a = 0; a < 3; ++a) R[(size_t)(3 + a) * nsd + k] = -rot[comp][a];
+                }
+            }
+            // modified Gram-Schmidt, then scale by 1/sqrt(2)
+            int kept = 0;
+            std::vector<double> Q;
+            for (int a = 0; a < nr; ++a) {
+                std::vector<double> v(R.begin() + (size_t)a * nsd, R.begin() + (size_t)(a + 1) * nsd);
+                for (int b = 0; b < kept; ++b) {
+                    double d = 0;
+                    for (int k = 0; k < nsd; ++k) d += v[k] * Q[(size_t)b * nsd + k];
+                    for (int k = 0; k < nsd; ++k) v[k] -= d * Q[(size_t)b * nsd + k];
+                }
+                double nrm = 0;
+                for (double t : v) nrm += t * t;
+                nrm = std::sqrt(nrm);
+                if (nrm < 1e-10) continue;
+                for (double &t : v) t /= nrm;
+                Q.insert(Q.end(), v.begin(), v.end());
+                kept++;
+            }
+            for (double &t : Q) t /= std::sqrt(2.0);
+            fp.N0 = Q;
+            fp.nnull = kept;
+        }
+        h->faces.push_back(fp);
+    }
+    // element colouring (greedy, nodes shared => different colours)
+    h->colors.clear();
+    std::vector<int> ecol(ne, -1);
+    std::vector<std::vector<int64_t>> node_elems(nn);
+    for (int64_t e = 0; e < ne; ++e)
+        for (int a = 0; a < 8; ++a) node_elems[h->elems[e * 8 + a]].push_back(e);
+    for (int64_t e = 0; e < ne; ++e) {
+        uint64_t used = 0;
+        for (int a = 0; a < 8; ++a)
+            for (int64_t f : node_elems[h->elems[e * 8 + a]])
+                if (ecol[f] >= 0 && ecol[f] < 64) used |= (1ull << ecol[f]);
+        int col = 0;
+        while (col < 64 && (used >> col) & 1ull) ++col;
+        BDDC_REQUIRE(col < 64, BDDC_EINVAL, "element colouring needs more than 64 colours");
+        ecol[e] = col;
+        if ((int)h->colors.size() <= col) h->colors.resize(col + 1);
+        h->colors[col].push_back((int32_t)e);
+    }
+}
+
+// positions of each node's first dof in the dense local ordering [interior; interface]
+std::vector<int32_t> element_positions(bddc_handle *h) {
+    std::vector<int32_t> pos(h->ne * 8, -1);
+    std::vector<std::map<int64_t, int>> lp(h->nsub);
+    for (int s = 0; s < h->nsub; ++s) {
+        auto &sd = h->subs[s];
+        for (int k = 0; k < sd.nI; k += h->ncomp) lp[s][sd.gI[k]] = k;
+        for (int k = 0; k < sd.nG; k += h->ncomp) lp[s][sd.gG[k]] = sd.nI + k;
+    }
+    for (int64_t e = 0; e < h->ne; ++e) {
+        int s = h->esub[e];
+        for (int a = 0; a < 8; ++a) {
+            int64_t v = h->elems[e * 8 + a];
+            if (h->node_first[v] < 0) continue;
+            pos[e * 8 + a] = lp[s].at(h->node_first[v]);
+        }
+    }
+    return pos;
+}
+
+void build_average_globs(bddc_handle *h) {
+    h->globs.clear();
+    const int c = h->ncomp;
+    auto add = [&](const std::vector<int> &subs, const std::vector<int64_t> &nodes) {
+        GlobRows g;
+        g.subs = subs;
+        for (int64_t v : nodes)
+            for (int k = 0; k < c; ++k) g.gdofs.push_back(h->node_first[v] + k);
+        g.nrows = c;
+        g.rows.assign((size_t)c * g.gdofs.size(), 0.0);
+        for (int comp = 0; comp < c; ++comp)
+            for (size_t k = comp; k < g.gdofs.size(); k += c) g.rows[(size_t)comp * g.gdofs.size() + k] = 1.0;
+        h->globs.push_back(g);
+    };
+    if (h->avg_flags & BDDC_AVG_EDGE)
+        for (auto &eg : h->edge_globs) add(eg.first, eg.second);
+    if (h->avg_flags & BDDC_AVG_FACE)
+        for (auto &fp : h->faces) {
+            std::set<int64_t> ns;
+            for (int k : fp.face_idx) ns.insert(fp.s_g[k] - fp.s_g[k] % c);
+            GlobRows g;
+            g.subs = {fp.i, fp.j};
+            for (int64_t g0 : ns)
+                for (int k = 0; k < c; ++k) g.gdofs.push_back(g0 + k);
+            g.nrows = c;
+            g.rows.assign((size_t)c * g.gdofs.size(), 0.0);
+            for (int comp = 0; comp < c; ++comp)
+                for (size_t k = comp; k < g.gdofs.size(); k += c) g.rows[(size_t)comp * g.gdofs.size() + k] = 1.0;
+            h->globs.push_back(g);
+        }
+}
+
+// Lays out the constraint rows of every substructure, numbers the coarse
+// dofs and fills the constraint buffers (averages from the host, adaptive
+// rows copied on the device from the face row buffers).
+void layout_constraints(bddc_handle *h) {
+    const int ns = h->nsub;
+    int nC = h->n_corner_dofs;
+    std::vector<std::vector<std::pair<int, int>>> sub_rows(ns);  // (glob, row)
+    for (int gi = 0; gi < (int)h->globs.size(); ++gi) {
+        auto &g = h->globs[gi];
+        g.coarse0 = nC;
+        nC += g.nrows;
+        for (int s : g.subs)
+            for (int r = 0; r < g.nrows; ++r) sub_rows[s].push_back({gi, r});
+    }
+    h->nC = nC;
+    std::vector<GatherOp> ops;
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        sd.na = (int)sub_rows[s].size();
+        sd.capA = std::max(1, sd.na);
+        sd.Cb = h->ar.get_t<double>("Cb_" + std::to_string(s), (size_t)sd.capA * sd.nG);
+        std::vector<double> host((size_t)sd.capA * sd.nG, 0.0);
+        std::map<int64_t, int> pos;
+        for (int k = 0; k < sd.nG; ++k) pos[sd.gG[k]] = k;
+        sd.row_coarse.clear();
+        for (int m = 0; m < sd.na; ++m) {
+            auto &g = h->globs[sub_rows[s][m].first];
+            int r = sub_rows[s][m].second;
+            sd.row_coarse.push_back(g.coarse0 + r);
+            if (g.face >= 0) continue;
+            for (size_t k = 0; k < g.gdofs.size(); ++k)
+                host[(size_t)pos.at(g.gdofs[k]) * sd.capA + m] = g.rows[(size_t)r * g.gdofs.size() + k];
+        }
+        BDDC_CUDA(cudaMemcpyAsync(sd.Cb, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        // adaptive rows: one gather per (sub, face glob): Cb[m0 + l, facepos] = rows[l, f]
+        for (int m = 0; m < sd.na;) {
+            auto &g = h->globs[sub_rows[s][m].first];
+            if (g.face < 0) {
+                ++m;
+                continue;
+            }
+            auto &fp = h->faces[g.face];
+            int nf = (int)fp.face_idx.size();
+            // column map over interface positions: face index or -1
+            std::vector<int> cmap(sd.nG, -1);
+            for (int f = 0; f < nf; ++f) {
+                int k = fp.face_idx[f];
+                cmap[(s == fp.i) ? fp.pos_i[k] : fp.pos_j[k]] = f;
+            }
+            int *dcm = h->ar.upload("cmap_" + std::to_string(s) + "_" + std::to_string(g.face), cmap, h->stream);
+            // face rows stored column-major (l, f) with ld = nrows: Cb[m + l, k] = rows(l, cmap[k])
+            GatherOp o = gop(h->face_rows_dev[g.face], g.nrows, sd.Cb, sd.capA, g.nrows, sd.nG);
+            o.dst_row_off = m;
+            o.cmap = dcm;
+            ops.push_back(o);
+            m += g.nrows;
+        }
+    }
+    run_gathers(h, ops, "cons");
+}
+
+// Builds the local saddle operators (P~_i, Phi~_i, S_C,i), the coarse matrix
+// and its inverse for the current constraints (Remark 5.1: all constraints
+// primal).  Two partial Cholesky passes on augmented matrices per substructure:
+//   M1 = [S_rr . . .; I 0 . .; C_r 0 0 .; S_cr 0 0 0], stop n_r:
+//        trailing = -[[S_rr^-1, Z_a, Z_c]; [Z_a^T, G, H]; [Z_c^T, H^T, J]]
+//   M2 = [G . . .; Z_a K . .; H^T Z_c^T J .; I 0 0 0], stop n_a:
+//        trailing = [[P_rr, -Phi_rc, -Phi_ra]; [., J - H^T G^-1 H, -H^T G^-1]; [., ., -G^-1]]
+// with K = S_rr^-1, Z = K [S_rc, C_r^T], G = C_r K C_r^T, H = C_r K S_rc, J = S_cr K S_rc.
+void coarse_setup(bddc_handle *h) {
+    const int ns = h->nsub;
+    layout_constraints(h);
+    std::vector<PcholDesc<double>> d1, d2;
+    std::vector<GatherOp> g1, g2, g3;
+    std::vector<DiagOp> id1, id2;
+    std::vector<double *> M1(ns), M2(ns), SCi(ns);
+    std::vector<int> N1(ns), N2(ns), ld1(ns), ld2(ns);
+    // map arrays uploaded per sub
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        const int nr = (int)sd.rpos.size(), nc = (int)sd.cpos.size(), na = sd.na;
+        N1[s] = 2 * nr + na + nc;
+        ld1[s] = round_up(std::max(N1[s], 1), 8);
+        N2[s] = na + nr + nc + na;
+        ld2[s] = round_up(std::max(N2[s], 1), 8);
+        M1[s] = h->ar.get_t<double>("M1_" + std::to_string(s), (size_t)ld1[s] * N1[s]);
+        M2[s] = h->ar.get_t<double>("M2_" + std::to_string(s), (size_t)ld2[s] * std::max(N2[s], 1));
+        zero(h, M1[s], (size_t)ld1[s] * N1[s]);
+        zero(h, M2[s], (size_t)ld2[s] * std::max(N2[s], 1));
+        int *drpos = h->ar.upload("rpos_" + std::to_string(s), sd.rpos, h->stream);
+        int *dcpos = h->ar.upload("cpos_" + std::to_string(s), sd.cpos, h->stream);
+        // M1 blocks
+        GatherOp o = gop(sd.S, sd.ldS, M1[s], ld1[s], nr, nr);
+        o.rmap = drpos;
+        o.cmap = drpos;
+        o.dst_lower = 1;
+        g1.push_back(o);
+        if (na > 0) {
+            o = gop(sd.Cb, sd.capA, M1[s], ld1[s], na, nr);
+            o.cmap = drpos;
+            o.dst_row_off = 2 * nr;
+            g1.push_back(o);
+        }
+        if (nc > 0) {
+            o = gop(sd.S, sd.ldS, M1[s], ld1[s], nc, nr);
+            o.rmap = dcpos;
+            o.cmap = drpos;
+            o.dst_row_off = 2 * nr + na;
+            g1.push_back(o);
+        }
+        id1.push_back(DiagOp{M1[s], ld1[s], nr, 0, nr, 1.0});
+        d1.push_back(PcholDesc<double>{M1[s], N1[s], ld1[s], nr, 0});
+    }
+    run_gathers(h, g1, "M1");
+    run_diag(h, id1, "M1");
+    run_pchol<double>(h, d1, "M1");
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        const int nr = (int)sd.rpos.size(), nc = (int)sd.cpos.size(), na = sd.na;
+        // M2[0:K, 0:K] = -M1(perm, perm), perm = (a, id, c) in M1 coordinates
+        std::vector<int> perm;
+        for (int k = 0; k < na; ++k) perm.push_back(2 * nr + k);
+        for (int k = 0; k < nr; ++k) perm.push_back(nr + k);
+        for (int k = 0; k < nc; ++k) perm.push_back(2 * nr + na + k);
+        int K = (int)perm.size();
+        int *dperm = h->ar.upload("perm2_" + std::to_string(s), perm, h->stream);
+        if (K > 0) {
+            GatherOp o = gop(M1[s], ld1[s], M2[s], ld2[s], K, K);
+            o.rmap = dperm;
+            o.cmap = dperm;
+            o.src_sym = 1;
+            o.dst_lower = 1;
+            o.scale = -1.0;
+            g2.push_back(o);
+        }
+        if (na > 0) id2.push_back(DiagOp{M2[s], ld2[s], K, 0, na, 1.0});
+        d2.push_back(PcholDesc<double>{M2[s], N2[s], ld2[s], na, 0});
+    }
+    run_gathers(h, g2, "M2");
+    run_diag(h, id2, "M2");
+    run_pchol<double>(h, d2, "M2");
+    // extraction of P~, Phi~, S_C,i
+    std::vector<CoarseAsmDesc> cad;
+    std::vector<int> Rc_all;
+    std::vector<int64_t> offc(ns);
+    int64_t oc = 0;
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        offc[s] = oc;
+        oc += (int)sd.cpos.size() + sd.na;
+    }
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        const int nr = (int)sd.rpos.size(), nc = (int)sd.cpos.size(), na = sd.na, nG = sd.nG;
+        const int nci = nc + na;
+        double *dl = h->ar.get_t<double>("delta", h->sumG) + h->offG[s];
+        // row map over interface positions into T2 (offset na): r_k -> na + k, corners -> -1
+        std::vector<int> rm(nG, -1);
+        for (int k = 0; k < nr; ++k) rm[sd.rpos[k]] = na + k;
+        int *drm = h->ar.upload("rmP_" + std::to_string(s), rm, h->stream);
+        GatherOp o = gop(M2[s], ld2[s], sd.P, sd.ldS, nG, nG);
+        o.rmap = drm;
+        o.cmap = drm;
+        o.src_sym = 1;
+        o.rscale = dl;
+        o.cscale = dl;
+        g3.push_back(o);
+        // Phi~: columns corners then averages
+        std::vector<int> cm(nci);
+        for (int m = 0; m < nc; ++m) cm[m] = na + nr + m;
+        for (int m = 0; m < na; ++m) cm[nc + m] = na + nr + nc + m;
+        int *dcm = h->ar.upload("cmPhi_" + std::to_string(s), cm, h->stream);
+        if (nci > 0) {
+            o = gop(M2[s], ld2[s], sd.Phi, sd.ldS, nG, nci);
+            o.rmap = drm;
+            o.cmap = dcm;
+            o.src_sym = 1;
+            o.scale = -1.0;
+            o.rscale = dl;
+            g3.push_back(o);
+        }
+        // identity on the corner rows (accumulate): Phi[cpos[m], m] += delta
+        std::vector<int> cr(nG, -1);
+        for (int m = 0; m < nc; ++m) cr[sd.cpos[m]] = m;
+        int *dcr = h->ar.upload("crPhi_" + std::to_string(s), cr, h->stream);
+        // S_C,i = -T2(cm, cm) + [S_cc 0; 0 0]
+        double *sci = h->ar.get_t<double>("SCi_" + std::to_string(s), (size_t)std::max(nci, 1) * std::max(nci, 1));
+        SCi[s] = sci;
+        if (nci > 0) {
+            o = gop(M2[s], ld2[s], sci, nci, nci, nci);
+            o.rmap = dcm;
+            o.cmap = dcm;
+            o.src_sym = 1;
+            o.scale = -1.0;
+            g3.push_back(o);
+        }
+        std::vector<int> Rc;
+        for (int m = 0; m < nc; ++m) Rc.push_back(sd.corner_coarse[m]);
+        for (int m = 0; m < na; ++m) Rc.push_back(sd.row_coarse[m]);
+        Rc_all.insert(Rc_all.end(), Rc.begin(), Rc.end());
+        (void)dcr;
+    }
+    run_gathers(h, g3, "ext");
+    std::vector<GatherOp> g4;
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        const int nc = (int)sd.cpos.size(), nci = nc + sd.na, nG = sd.nG;
+        double *dl = h->ar.get_t<double>("delta", h->sumG) + h->offG[s];
+        if (nc > 0) {
+            int *dcr = h->ar.get_t<int>("crPhi_" + std::to_string(s), nG);
+            GatherOp o = gop(nullptr, 0, sd.Phi, sd.ldS, nG, nc);
+            o.rmap = dcr;
+            o.rscale = dl;
+            o.accumulate = 1;
+            g4.push_back(o);
+            int *dcpos = h->ar.get_t<int>("cpos_" + std::to_string(s), nc);
+            o = gop(sd.S, sd.ldS, SCi[s], nci, nc, nc);
+            o.rmap = dcpos;
+            o.cmap = dcpos;
+            o.accumulate = 1;
+            g4.push_back(o);
+        }
+    }
+    run_gathers(h, g4, "ext2");
+    int *dRc = h->ar.upload("Rc", Rc_all, h->stream);
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        int nci = (int)sd.cpos.size() + sd.na;
+        cad.push_back(CoarseAsmDesc{SCi[s], dRc + offc[s], nci, std::max(nci, 1)});
+    }
+    const int nC = h->nC;
+    BDDC_REQUIRE(nC > 0, BDDC_EASSUMPTION, "no coarse degrees of freedom");
+    BDDC_REQUIRE(nC <= 12000, BDDC_EINVAL, "coarse problem larger than 12000 dofs");
+    double *SC = h->ar.get_t<double>("SC", (size_t)nC * nC);
+    zero(h, SC, (size_t)nC * nC);
+    auto *dcad = h->ar.upload("cad", cad, h->stream);
+    launch_coarse_assemble(dcad, ns, SC, nC, h->stream);
+    check_launch(h);
+    // inverse by partial Cholesky of [[S_C, .]; [I, 0]]
+    int ldm = round_up(2 * nC, 8);
+    double *MC = h->ar.get_t<double>("MC", (size_t)ldm * 2 * nC);
+    zero(h, MC, (size_t)ldm * 2 * nC);
+    std::vector<GatherOp> g5{gop(SC, nC, MC, ldm, nC, nC)};
+    g5[0].dst_lower = 1;
+    run_gathers(h, g5, "MC");
+    run_diag(h, {DiagOp{MC, ldm, nC, 0, nC, 1.0}}, "MC");
+    run_pchol<double>(h, {PcholDesc<double>{MC, 2 * nC, ldm, nC, 0}}, "MC");
+    double *SCinv = h->ar.get_t<double>("SCinv", (size_t)nC * nC);
+    GatherOp o = gop(MC, ldm, SCinv, nC, nC, nC);
+    o.src_row_off = nC;
+    o.src_col_off = nC;
+    o.src_sym = 1;
+    o.scale = -1.0;
+    run_gathers(h, {o}, "SCinv");
+    fail_check(h, "coarse setup");
+    // interface operator descriptors
+    std::vector<int> nci_v(ns);
+    std::vector<int2> cdot;
+    for (int s = 0; s < ns; ++s) {
+        nci_v[s] = (int)h->subs[s].cpos.size() + h->subs[s].na;
+        for (int m = 0; m < nci_v[s]; m += 8) cdot.push_back(make_int2(s, m));
+    }
+    h->ops.nci = h->ar.upload("nci", nci_v, h->stream);
+    h->ops.offc = h->ar.upload("offc", offc, h->stream);
+    h->ops.Rc = dRc;
+    h->ops.SCinv = SCinv;
+    h->ops.nC = nC;
+    // coarse gather map
+    std::vector<std::vector<int64_t>> cl(nC);
+    for (int s = 0; s < ns; ++s)
+        for (int m = 0; m < nci_v[s]; ++m) cl[Rc_all[offc[s] + m]].push_back(offc[s] + m);
+    std::vector<int> cptr(nC + 1, 0);
+    std::vector<int64_t> cent;
+    for (int k = 0; k < nC; ++k) {
+        cent.insert(cent.end(), cl[k].begin(), cl[k].end());
+        cptr[k + 1] = (int)cent.size();
+    }
+    h->ops.cptr = h->ar.upload("cptr", cptr, h->stream);
+    h->ops.cent = h->ar.upload("cent", cent, h->stream);
+    h->ops.cdot = h->ar.upload("cdot", cdot, h->stream);
+    h->ops.ncdot = (int)cdot.size();
+    h->pb.cl = h->ar.get_t<double>("cl", std::max<int64_t>(oc, 1));
+    h->pb.uc = h->ar.get_t<double>("uc", nC);
+}
+
+void alloc_solver_buffers(bddc_handle *h) {
+    const int ns = h->nsub;
+    std::vector<double *> S(ns), P(ns), Phi(ns);
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        sd.A = h->ar.get_t<double>("A_" + std::to_string(s), (size_t)sd.ld * std::max(sd.n, 1));
+        sd.S = h->ar.get_t<double>("S_" + std::to_string(s), (size_t)sd.ldS * std::max(sd.nG, 1));
+        sd.P = h->ar.get_t<double>("P_" + std::to_string(s), (size_t)sd.ldS * std::max(sd.nG, 1));
+        S[s] = sd.S;
+        P[s] = sd.P;
+    }
+    h->ops.nsub = ns;
+    h->ops.nG = h->nG;
+    std::vector<int> nGi(ns), ldS(ns), RG;
+    std::vector<int2> rb;
+    for (int s = 0; s < ns; ++s) {
+        nGi[s] = h->subs[s].nG;
+        ldS[s] = h->subs[s].ldS;
+        RG.insert(RG.end(), h->subs[s].RG.begin(), h->subs[s].RG.end());
+        for (int r = 0; r < nGi[s]; r += 64) rb.push_back(make_int2(s, r));
+    }
+    h->ops.nGi = h->ar.upload("nGi", nGi, h->stream);
+    h->ops.ldS = h->ar.upload("ldS", ldS, h->stream);
+    h->ops.off = h->ar.upload("offG", h->offG, h->stream);
+    h->ops.RG = h->ar.upload("RG", RG, h->stream);
+    h->ops.S = h->ar.upload("Sptr", S, h->stream);
+    h->ops.P = h->ar.upload("Pptr", P, h->stream);
+    h->ops.gptr = h->ar.upload("gptr", h->gptr, h->stream);
+    h->ops.gent = h->ar.upload("gent", h->gent, h->stream);
+    h->ops.gsub = h->ar.upload("gsub", h->gsub, h->stream);
+    h->ops.rowblk = h->ar.upload("rowblk", rb, h->stream);
+    h->ops.nrowblk = (int)rb.size();
+    const int nG = std::max(h->nG, 1);
+    h->pb.x = h->ar.get_t<double>("x", nG);
+    h->pb.r = h->ar.get_t<double>("r", nG);
+    h->pb.z = h->ar.get_t<double>("z", nG);
+    h->pb.p0 = h->ar.get_t<double>("p0", nG);
+    h->pb.p1 = h->ar.get_t<double>("p1", nG);
+    h->pb.q = h->ar.get_t<double>("q", nG);
+    h->pb.zl = h->ar.get_t<double>("zl", std::max<int64_t>(h->sumG, 1));
+    h->pb.yl = h->ar.get_t<double>("yl", std::max<int64_t>(h->sumG, 1));
+    h->pb.partial = h->ar.get_t<double>("partial", 4096);
+    int maxit = std::max(h->opt.maxit, 1);
+    h->pb.alpha = h->ar.get_t<double>("alpha", maxit);
+    h->pb.beta = h->ar.get_t<double>("beta", maxit);
+    h->pb.iters = h->ar.get_t<int>("iters", 4);
+    h->pb.converged = h->pb.iters + 1;
+    h->pb.relres = h->ar.get_t<double>("relres", 1);
+}
+
+void set_phi_pointers(bddc_handle *h) {
+    const int ns = h->nsub;
+    std::vector<double *> Phi(ns);
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        int nci = (int)sd.cpos.size() + sd.na;
+        sd.Phi = h->ar.get_t<double>("Phi_" + std::to_string(s), (size_t)sd.ldS * std::max(nci, 1));
+        Phi[s] = sd.Phi;
+    }
+    h->ops.Phi = h->ar.upload("Phiptr", Phi, h->stream);
+}
+
+// ---- phases --------------------------------------------------------------
+void do_setup(bddc_handle *h) {
+    const int ns = h->nsub;
+    reset_status(h);
+    phase_begin(h, 0);
+    // element geometry and assembly
+    double *grads = h->ar.get_t<double>("grads", (size_t)h->ne * 8 * 8 * 3);
+    double *wdet = h->ar.get_t<double>("wdet", (size_t)h->ne * 8);
+    const double *dxyz = h->ar.get_t<double>("xyz", h->nn * 3);
+    const int64_t *delems = h->ar.get_t<int64_t>("elems", h->ne * 8);
+    launch_element_geometry(dxyz, delems, h->ne, grads, wdet, h->stream);
+    check_launch(h);
+    std::vector<double *> Aptr(ns);
+    std::vector<int> lds(ns);
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        zero(h, sd.A, (size_t)sd.ld * sd.n);
+        Aptr[s] = sd.A;
+        lds[s] = sd.ld;
+    }
+    AssemblyArgs aa;
+    aa.grads = grads;
+    aa.wdet = wdet;
+    aa.coef = h->ar.get_t<double>("coef", h->ne);
+    aa.elem_sub = h->ar.get_t<int32_t>("esub", h->ne);
+    aa.elem_pos = h->ar.get_t<int32_t>("epos", h->ne * 8);
+    aa.A = h->ar.upload("Aptr", Aptr, h->stream);
+    aa.ld = h->ar.upload("Ald", lds, h->stream);
+    aa.nu = h->nu;
+    aa.ncomp = h->ncomp;
+    for (size_t col = 0; col < h->colors.size(); ++col) {
+        const int32_t *ce = h->ar.get_t<int32_t>("color_" + std::to_string(col), h->colors[col].size());
+        launch_element_scatter(aa, ce, (int)h->colors[col].size(), h->stream);
+        check_launch(h);
+    }
+    // weights: diag of the interface block (before elimination of interiors)
+    double *diag = h->ar.get_t<double>("diag", std::max<int64_t>(h->sumG, 1));
+    std::vector<GatherOp> gd;
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        if (sd.nG == 0) continue;
+        // a 1 x nG gather with column stride ld + 1 walks the diagonal of the interface block
+        gd.push_back(gop(sd.A + (size_t)sd.nI * sd.ld + sd.nI, sd.ld + 1, diag + h->offG[s], 1, 1, sd.nG));
+    }
+    run_gathers(h, gd, "diag");
+    double *total = h->ar.get_t<double>("wtotal", std::max(h->nG, 1));
+    double *delta = h->ar.get_t<double>("delta", std::max<int64_t>(h->sumG, 1));
+    launch_weights(h->ops, diag, total, delta, h->stream);
+    check_launch(h);
+    phase_end(h, 0);
+    phase_begin(h, 1);
+    // interior elimination: partial Cholesky of every A_i with nstop = n_I
+    double fl = 0.0;
+    for (auto &sd : h->subs)
+        fl += (double)sd.nI * sd.nI * sd.nI / 3.0 + (double)sd.nI * sd.nI * sd.nG + (double)sd.nI * sd.nG * sd.nG;
+    h->phase_flop[1] = fl;
+    std::vector<PcholDesc<double>> d;
+    for (int s = 0; s < ns; ++s) d.push_back(PcholDesc<double>{h->subs[s].A, h->subs[s].n, h->subs[s].ld, h->subs[s].nI, 0});
+    run_pchol<double>(h, d, "AII");
+    // S_i full from the trailing lower block
+    std::vector<GatherOp> gs;
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        GatherOp o = gop(sd.A, sd.ld, sd.S, sd.ldS, sd.nG, sd.nG);
+        o.src_row_off = sd.nI;
+        o.src_col_off = sd.nI;
+        o.src_sym = 1;
+        gs.push_back(o);
+    }
+    run_gathers(h, gs, "S");
+    phase_end(h, 1);
+    fail_check(h, "interior factorization");
+    build_average_globs(h);
+    // coarse numbering needs the glob list; Phi buffers depend on the row counts
+    for (int s = 0; s < ns; ++s) h->subs[s].na = 0;
+    {
+        // count rows per sub to size Phi before coarse_setup lays them out
+        std::vector<int> na(ns, 0);
+        for (auto &g : h->globs)
+            for (int s : g.subs) na[s] += g.nrows;
+        for (int s = 0; s < ns; ++s) h->subs[s].na = na[s];
+        set_phi_pointers(h);
+    }
+    phase_begin(h, 2);
+    coarse_setup(h);
+    phase_end(h, 2);
+    h->face_rows_dev.assign(h->faces.size(), nullptr);
+    phase_collect(h, 0, 2);
+}
+
+}  // namespace
+
+// ===========================================================================
+// adapt
+namespace {
+
+void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
+    const int nf = (int)h->faces.size();
+    reset_status(h);
+    // the pair problems use the initial constraints only; drop rows of an earlier adapt
+    h->globs.erase(std::remove_if(h->globs.begin(), h->globs.end(), [](const GlobRows &g) { return g.face >= 0; }),
+                   h->globs.end());
+    if (nf == 0) {
+        if (info) *info = bddc_adapt_info{0, 0, 0, 0.0};
+        return;
+    }
+    phase_begin(h, 3);
+    // E1: per (sub, face) Schur complement of S_i onto t = [s (s order); shared corners]
+    std::vector<PcholDesc<double>> dE1, dE2, dE3;
+    std::vector<GatherOp> gE1, gE2, gE3, gQ;
+    std::vector<DiagOp> idE3;
+    struct PairBufs {
+        double *T[2];
+        int nT[2], ldT[2], no[2];
+        double *Y;
+        int nY, ldY;
+        double *M3;
+        int ldM3;
+        double *Q, *W1, *C;
+        int ns, nc;
+    };
+    std::vector<PairBufs> pbufs(nf);
+    int nmax = 0;
+    for (int f = 0; f < nf; ++f) {
+        auto &fp = h->faces[f];
+        auto &B = pbufs[f];
+        const int ns = (int)fp.s_g.size(), nc = (int)fp.ci_pos.size();
+        B.ns = ns;
+        B.nc = nc;
+        nmax = std::max(nmax, ns);
+        for (int side = 0; side < 2; ++side) {
+            int s = side ? fp.j : fp.i;
+            auto &sd = h->subs[s];
+            const auto &spos = side ? fp.pos_j : fp.pos_i;
+            const auto &cpos = side ? fp.cj_pos : fp.ci_pos;
+            std::vector<char> in_t(sd.nG, 0);
+            for (int p : spos) in_t[p] = 1;
+            for (int p : cpos) in_t[p] = 1;
+            std::vector<int> perm;
+            for (int k = 0; k < sd.nG; ++k)
+                if (!in_t[k]) perm.push_back(k);
+            int no = (int)perm.size();
+            perm.insert(perm.end(), spos.begin(), spos.end());
+            perm.insert(perm.end(), cpos.begin(), cpos.end());
+            int n = (int)perm.size();
+            B.nT[side] = n;
+            B.no[side] = no;
+            B.ldT[side] = round_up(std::max(n, 1), 8);
+            B.T[side] = h->ar.get_t<double>("E1_" + std::to_string(f) + "_" + std::to_string(side), (size_t)B.ldT[side] * n);
+            int *dp = h->ar.upload("E1p_" + std::to_string(f) + "_" + std::to_string(side), perm, h->stream);
+            GatherOp o = gop(sd.S, sd.ldS, B.T[side], B.ldT[side], n, n);
+            o.rmap = dp;
+            o.cmap = dp;
+            o.dst_lower = 1;
+            gE1.push_back(o);
+            dE1.push_back(PcholDesc<double>{B.T[side], n, B.ldT[side], no, 0});
+        }
+    }
+    run_gathers(h, gE1, "E1");
+    run_pchol<double>(h, dE1, "E1");
+    // E2: pair matrix [C; s_i; s_j], eliminate C -> S^ (2 ns)
+    for (int f = 0; f < nf; ++f) {
+        auto &B = pbufs[f];
+        const int ns = B.ns, nc = B.nc;
+        B.nY = nc + 2 * ns;
+        B.ldY = round_up(std::max(B.nY, 1), 8);
+        B.Y = h->ar.get_t<double>("E2_" + std::to_string(f), (size_t)B.ldY * std::max(B.nY, 1));
+        zero(h, B.Y, (size_t)B.ldY * std::max(B.nY, 1));
+        for (int side = 0; side < 2; ++side) {
+            const int o0 = B.no[side];  // trailing offset: [s (ns); C (nc)]
+            // C block (accumulate both sides)
+            if (nc > 0) {
+                GatherOp o = gop(B.T[side], B.ldT[side], B.Y, B.ldY, nc, nc);
+                o.src_row_off = o0 + ns;
+                o.src_col_off = o0 + ns;
+                o.src_sym = 1;
+                o.dst_lower = 1;
+                o.accumulate = 1;
+                (side ? gE3 : gE2).push_back(o);  // two passes to avoid write conflicts
+                o = gop(B.T[side], B.ldT[side], B.Y, B.ldY, ns, nc);
+                o.src_row_off = o0;
+                o.src_col_off = o0 + ns;
+                o.src_sym = 1;
+                o.dst_row_off = nc + side * ns;
+                gE2.push_back(o);
+            }
+            GatherOp o = gop(B.T[side], B.ldT[side], B.Y, B.ldY, ns, ns);
+            o.src_row_off = o0;
+            o.src_col_off = o0;
+            o.src_sym = 1;
+            o.dst_row_off = nc + side * ns;
+            o.dst_col_off = nc + side * ns;
+            o.dst_lower = 1;
+            gE2.push_back(o);
+        }
+        dE2.push_back(PcholDesc<double>{B.Y, B.nY, B.ldY, nc, 0});
+    }
+    run_gathers(h, gE2, "E2a");
+    run_gathers(h, gE3, "E2b");
+    gE3.clear();
+    run_pchol<double>(h, dE2, "E2");
+    // E3: M3 = [[Mww, ., .], [Mbw, Mbb, .], [0, I, 0]] from S^ blocks, + deflation, eliminate 2 ns
+    std::vector<DeflateDesc> defl;
+    std::vector<PairWeightDesc> pw;
+    for (int f = 0; f < nf; ++f) {
+        auto &fp = h->faces[f];
+        auto &B = pbufs[f];
+        const int ns = B.ns, nc = B.nc;
+        int n3 = 3 * ns;
+        B.ldM3 = round_up(std::max(n3, 1), 8);
+        B.M3 = h->ar.get_t<double>("M3_" + std::to_string(f), (size_t)B.ldM3 * std::max(n3, 1));
+        zero(h, B.M3, (size_t)B.ldM3 * std::max(n3, 1));
+        if (ns == 0) continue;
+        // S^ blocks live in Y at offset nc: S11 at (nc, nc), S21 at (nc+ns, nc), S22 at (nc+ns, nc+ns)
+        auto blk = [&](int bi, int bj, int dro, int dco, double scale, int lower, std::vector<GatherOp> &dst) {
+            GatherOp o = gop(B.Y, B.ldY, B.M3, B.ldM3, ns, ns);
+            o.src_row_off = nc + bi * ns;
+            o.src_col_off = nc + bj * ns;
+            o.src_sym = 1;
+            o.dst_row_off = dro;
+            o.dst_col_off = dco;
+            o.scale = scale;
+            o.dst_lower = lower;
+            o.accumulate = 1;
+            dst.push_back(o);
+        };
+        // (w2,w2) = S11 + S12 + S21 + S22 ; (b,w2) = S11 + S12 ; (b,b) = S11
+        // each pass writes every target once so passes can run in parallel over pairs
+        blk(0, 0, 0, 0, 1.0, 1, gE3);
+        blk(0, 0, ns, 0, 1.0, 0, gE3);
+        blk(0, 0, ns, ns, 1.0, 1, gE3);
+        blk(0, 1, 0, 0, 1.0, 1, gQ);
+        blk(0, 1, ns, 0, 1.0, 0, gQ);
+        idE3.push_back(DiagOp{B.M3, B.ldM3, 2 * ns, ns, ns, 1.0});
+        if (fp.nnull > 0) {
+            double *N0 = h->ar.upload("N0_" + std::to_string(f), fp.N0, h->stream);
+            defl.push_back(DeflateDesc{B.Y + (size_t)nc * B.ldY + nc, B.ldY, B.M3, B.ldM3, N0, ns, fp.nnull});
+        }
+        dE3.push_back(PcholDesc<double>{B.M3, n3, B.ldM3, 2 * ns, 0});
+        // pair weights for Q
+        double *di = h->ar.get_t<double>("pwi_" + std::to_string(f), ns);
+        double *dj = h->ar.get_t<double>("pwj_" + std::to_string(f), ns);
+        int *pi = h->ar.upload("ppi_" + std::to_string(f), fp.pos_i, h->stream);
+        int *pj = h->ar.upload("ppj_" + std::to_string(f), fp.pos_j, h->stream);
+        double *diag = h->ar.get_t<double>("diag", h->sumG);
+        pw.push_back(PairWeightDesc{diag + h->offG[fp.i], diag + h->offG[fp.j], pi, pj, di, dj, ns});
+    }
+    run_gathers(h, gE3, "E3a");
+    run_gathers(h, gQ, "E3b");
+    // pass 3: S21 into (w2,w2) and S22 into (w2,w2)
+    {
+        std::vector<GatherOp> g;
+        for (int f = 0; f < nf; ++f) {
+            auto &B = pbufs[f];
+            const int ns = B.ns, nc = B.nc;
+            if (ns == 0) continue;
+            GatherOp o = gop(B.Y, B.ldY, B.M3, B.ldM3, ns, ns);
+            o.src_row_off = nc + ns;
+            o.src_col_off = nc;
+            o.src_sym = 1;
+            o.dst_lower = 1;
+            o.accumulate = 1;
+            g.push_back(o);
+        }
+        run_gathers(h, g, "E3c");
+        g.clear();
+        for (int f = 0; f < nf; ++f) {
+            auto &B = pbufs[f];
+            const int ns = B.ns, nc = B.nc;
+            if (ns == 0) continue;
+            GatherOp o = gop(B.Y, B.ldY, B.M3, B.ldM3, ns, ns);
+            o.src_row_off = nc + ns;
+            o.src_col_off = nc + ns;
+            o.src_sym = 1;
+            o.dst_lower = 1;
+            o.accumulate = 1;
+            g.push_back(o);
+        }
+        run_gathers(h, g, "E3d");
+    }
+    run_diag(h, idE3, "E3");
+    if (!defl.empty()) {
+        auto *dd = h->ar.upload("defl", defl, h->stream);
+        launch_deflate(dd, (int)defl.size(), h->stream);
+        check_launch(h);
+    }
+    run_pchol<double>(h, dE3, "E3");
+    {
+        auto *dpw = h->ar.upload("pw", pw, h->stream);
+        launch_pair_weights(dpw, (int)pw.size(), h->stream);
+        check_launch(h);
+    }
+    phase_end(h, 3);
+    phase_begin(h, 4);
+    // Q = Dj S_i,ss Dj + Di S_j,ss Di ; W1 = Q X ; C = X^T W1 with X = R^-T at M3[2ns:3ns, ns:2ns]
+    std::vector<GatherOp> gq1, gq2;
+    std::vector<GemmDesc> gm1, gm2;
+    std::vector<EigDesc> eds;
+    std::vector<int> eig_face;
+    for (int f = 0; f < nf; ++f) {
+        auto &fp = h->faces[f];
+        auto &B = pbufs[f];
+        const int ns = B.ns;
+        if (ns == 0) continue;
+        int ldq = round_up(ns, 8);
+        B.Q = h->ar.get_t<double>("Q_" + std::to_string(f), (size_t)ldq * ns);
+        B.W1 = h->ar.get_t<double>("W1_" + std::to_string(f), (size_t)ldq * ns);
+        B.C = h->ar.get_t<double>("C_" + std::to_string(f), (size_t)ldq * ns);
+        double *di = h->ar.get_t<double>("pwi_" + std::to_string(f), ns);
+        double *dj = h->ar.get_t<double>("pwj_" + std::to_string(f), ns);
+        int *pi = h->ar.get_t<int>("ppi_" + std::to_string(f), ns);
+        int *pj = h->ar.get_t<int>("ppj_" + std::to_string(f), ns);
+        GatherOp o = gop(h->subs[fp.i].S, h->subs[fp.i].ldS, B.Q, ldq, ns, ns);
+        o.rmap = pi;
+        o.cmap = pi;
+        o.rscale = dj;
+        o.cscale = dj;
+        gq1.push_back(o);
+        o = gop(h->subs[fp.j].S, h->subs[fp.j].ldS, B.Q, ldq, ns, ns);
+        o.rmap = pj;
+        o.cmap = pj;
+        o.rscale = di;
+        o.cscale = di;
+        o.accumulate = 1;
+        gq2.push_back(o);
+        const double *X = B.M3 + (size_t)ns * B.ldM3 + 2 * ns;
+        GemmDesc g1{B.Q, X, B.W1, ldq, B.ldM3, ldq, ns, ns, ns, 0, 0, 1.0, 0.0};
+        GemmDesc g2{X, B.W1, B.C, B.ldM3, ldq, ldq, ns, ns, ns, 1, 0, 1.0, 0.0};
+        gm1.push_back(g1);
+        gm2.push_back(g2);
+        int nface = (int)fp.face_idx.size();
+        int *fpos = h->ar.upload("fpos_" + std::to_string(f), fp.face_idx, h->stream);
+        EigDesc e;
+        e.C = B.C;
+        e.n = ns;
+        e.ld = ldq;
+        e.W1 = B.W1;
+        e.ldw = ldq;
+        e.face_pos = fpos;
+        e.nface = nface;
+        e.lam = h->ar.get_t<double>("lam_" + std::to_string(f), kEigCap + 1);
+        e.vec = h->ar.get_t<double>("vec_" + std::to_string(f), (size_t)kEigCap * ns);
+        e.work = h->ar.get_t<double>("ework_" + std::to_string(f), (size_t)10 * ns + 16);
+        e.rows = h->ar.get_t<double>("frows_" + std::to_string(f), (size_t)kEigCap * std::max(nface, 1));
+        e.counts = h->ar.get_t<int>("fcnt_" + std::to_string(f), 8);
+        eds.push_back(e);
+        eig_face.push_back(f);
+    }
+    run_gathers(h, gq1, "Q1");
+    run_gathers(h, gq2, "Q2");
+    run_gemm(h, gm1, "W1");
+    run_gemm(h, gm2, "C");
+    auto *ded = h->ar.upload("eigdesc", eds, h->stream);
+    launch_face_eig_n(ded, (int)eds.size(), nmax, tau, h->opt.drop_rel, h->dst, h->stream);
+    check_launch(h);
+    phase_end(h, 4);
+    fail_check(h, "adapt");
+    // results back to the host
+    int n_added = 0, n_ties = 0;
+    double omega = 0.0;
+    h->face_rows_dev.assign(nf, nullptr);
+    for (size_t k = 0; k < eds.size(); ++k) {
+        int f = eig_face[k];
+        auto &fp = h->faces[f];
+        int cnt[8];
+        BDDC_CUDA(cudaMemcpyAsync(cnt, eds[k].counts, 8 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        std::vector<double> lam(kEigCap + 1);
+        BDDC_CUDA(cudaMemcpyAsync(lam.data(), eds[k].lam, lam.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        fp.nsel = cnt[0];
+        fp.nkept = cnt[1];
+        fp.ties = cnt[3];
+        lam.resize(cnt[2]);
+        fp.lam = lam;
+        if (!lam.empty()) omega = std::max(omega, lam[0]);
+        n_added += fp.nkept;
+        n_ties += fp.ties;
+        BDDC_REQUIRE(cnt[4] == 0, BDDC_EINVAL, "more than 48 eigenvalues above tau on one face");
+        h->face_rows_dev[f] = eds[k].rows;
+        if (fp.nkept > 0) {
+            GlobRows g;
+            g.subs = {fp.i, fp.j};
+            for (int idx : fp.face_idx) g.gdofs.push_back(fp.s_g[idx]);
+            g.nrows = fp.nkept;
+            g.face = f;
+            h->globs.push_back(g);
+        }
+    }
+    h->omega = omega;
+    // rows are stored row-major (l * nf + f); the constraint gather reads src(l, cmap[k]) = src[cmap[k] * ld + l]
+    // which needs the transpose: rows[f * kEigCap + l].  Transpose on the device via a gather.
+    {
+        std::vector<GatherOp> gt;
+        for (size_t k = 0; k < eds.size(); ++k) {
+            int f = eig_face[k];
+            auto &fp = h->faces[f];
+            if (fp.nkept == 0) continue;
+            int nface = (int)fp.face_idx.size();
+            double *T = h->ar.get_t<double>("frowsT_" + std::to_string(f), (size_t)nface * fp.nkept);
+            // T(l, f) = rows[l * nface + f]: read with ld_src = 1 and row map l -> l * nface
+            GatherOp o = gop(eds[k].rows, 1, T, fp.nkept, fp.nkept, nface);
+            std::vector<int> rm(fp.nkept);
+            for (int l = 0; l < fp.nkept; ++l) rm[l] = l * nface;
+            int *drm = h->ar.upload("frT_rm_" + std::to_string(f), rm, h->stream);
+            o.rmap = drm;
+            gt.push_back(o);
+            h->face_rows_dev[f] = T;
+        }
+        run_gathers(h, gt, "frT");
+    }
+    // rebuild the preconditioner with the new constraints
+    {
+        const int ns = h->nsub;
+        std::vector<int> na(ns, 0);
+        for (auto &g : h->globs)
+            for (int s : g.subs) na[s] += g.nrows;
+        for (int s = 0; s < ns; ++s) h->subs[s].na = na[s];
+        set_phi_pointers(h);
+    }
+    phase_begin(h, 5);
+    coarse_setup(h);
+    phase_end(h, 5);
+    phase_collect(h, 3, 5);
+    if (info) {
+        info->n_faces = nf;
+        info->n_added = n_added;
+        info->n_ties = n_ties;
+        info->omega = omega;
+    }
+}
+
+// ===========================================================================
+void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_info *info) {
+    const int ns = h->nsub;
+    reset_status(h);
+    double *df = h->ar.get_t<double>("f", std::max<int64_t>(h->nfree, 1));
+    phase_begin(h, 6);
+    if (mem == BDDC_MEM_DEVICE)
+        BDDC_CUDA(cudaMemcpyAsync(df, f, h->nfree * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    else
+        BDDC_CUDA(cudaMemcpyAsync(df, f, h->nfree * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    double *yI = h->ar.get_t<double>("yI", std::max<int64_t>(h->sumI, 1));
+    double *gl = h->ar.get_t<double>("gl", std::max<int64_t>(h->sumG, 1));
+    const int64_t *gIall = h->ar.get_t<int64_t>("gIall", std::max<int64_t>(h->sumI, 1));
+    const int64_t *gGall = h->ar.get_t<int64_t>("gGall", std::max<int64_t>(h->sumG, 1));
+    launch_gatherv(yI, gIall, df, h->sumI, h->stream);
+    check_launch(h);
+    (void)gGall;
+    std::vector<TrsvDesc<double>> tv;
+    std::vector<GemmDesc> gm;
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        if (sd.nI == 0) continue;
+        tv.push_back(TrsvDesc<double>{sd.A, yI + sd.offI, sd.nI, sd.ld});
+        // g_i = -L21 y = -A_GI A_II^{-1} f_I  (f_G is added once after assembly)
+        gm.push_back(GemmDesc{sd.A + sd.nI, yI + sd.offI, gl + h->offG[s], sd.ld, std::max(sd.nI, 1), std::max(sd.nG, 1),
+                              sd.nG, 1, sd.nI, 0, 0, -1.0, 0.0});
+    }
+    auto *dtv = h->ar.upload("trsv", tv, h->stream);
+    launch_trsv<double>(dtv, (int)tv.size(), 0, h->stream);
+    check_launch(h);
+    zero(h, gl, h->sumG);
+    run_gemm(h, gm, "cond");
+    launch_iface_assemble(h->ops, gl, h->pb.r, h->stream);
+    check_launch(h);
+    // g = f_G - sum_i R_i^T A_GI A_II^{-1} f_I
+    launch_gatherv_add(h->pb.r, h->ar.get_t<int64_t>("ifgdof", std::max(h->nG, 1)), df, h->nG, h->stream);
+    check_launch(h);
+    phase_end(h, 6);
+    phase_begin(h, 7);
+    int nblocks = 0;
+    cudaError_t e = launch_pcg(h->ops, h->pb, PCG_SOLVE, h->opt.tol, h->opt.maxit, h->dst, h->opt.timeout_s,
+                               h->stream, &nblocks);
+    BDDC_REQUIRE(e == cudaSuccess, BDDC_ECUDA, std::string("PCG launch: ") + cudaGetErrorString(e));
+    h->launches++;
+    phase_end(h, 7);
+    phase_begin(h, 8);
+    // recovery: t = y - L21^T u_G ; u_I = L11^-T t
+    double *ug = h->ar.get_t<double>("ugl", std::max<int64_t>(h->sumG, 1));
+    const int64_t *RGall = h->ar.get_t<int64_t>("RG64", std::max<int64_t>(h->sumG, 1));
+    launch_gatherv(ug, RGall, h->pb.x, h->sumG, h->stream);
+    check_launch(h);
+    std::vector<GemmDesc> gr;
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        if (sd.nI == 0 || sd.nG == 0) continue;
+        gr.push_back(GemmDesc{sd.A + sd.nI, ug + h->offG[s], yI + sd.offI, sd.ld, std::max(sd.nG, 1), std::max(sd.nI, 1),
+                              sd.nI, 1, sd.nG, 1, 0, -1.0, 1.0});
+    }
+    run_gemm(h, gr, "rec");
+    launch_trsv<double>(dtv, (int)tv.size(), 1, h->stream);
+    check_launch(h);
+    double *du = h->ar.get_t<double>("u", std::max<int64_t>(h->nfree, 1));
+    launch_scatter(du, gIall, yI, h->sumI, h->stream);
+    check_launch(h);
+    const int64_t *ifg = h->ar.get_t<int64_t>("ifgdof", std::max(h->nG, 1));
+    launch_scatter(du, ifg, h->pb.x, h->nG, h->stream);
+    check_launch(h);
+    phase_end(h, 8);
+    if (mem == BDDC_MEM_DEVICE)
+        BDDC_CUDA(cudaMemcpyAsync(u, du, h->nfree * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    else
+        BDDC_CUDA(cudaMemcpyAsync(u, du, h->nfree * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int it[2];
+    double rr;
+    BDDC_CUDA(cudaMemcpyAsync(it, h->pb.iters, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    BDDC_CUDA(cudaMemcpyAsync(&rr, h->pb.relres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    BDDC_CUDA(cudaStreamSynchronize(h->stream));
+    fail_check(h, "solve");
+    phase_collect(h, 6, 8);
+    h->last_iters = it[0];
+    h->alpha.assign(it[0], 0.0);
+    h->beta.assign(std::max(it[0] - 1, 0), 0.0);
+    if (it[0] > 0) BDDC_CUDA(cudaMemcpy(h->alpha.data(), h->pb.alpha, it[0] * sizeof(double), cudaMemcpyDeviceToHost));
+    if (it[0] > 1) BDDC_CUDA(cudaMemcpy(h->beta.data(), h->pb.beta, (it[0] - 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    if (info) {
+        info->iters = it[0];
+        info->converged = it[1];
+        info->relres = rr;
+        double lmin = 1, lmax = 1;
+        bddc_condition_estimate(h, &lmin, &lmax);
+        info->kappa = lmax / lmin;
+        info->setup_ms = h->phase_ms[0] + h->phase_ms[1] + h->phase_ms[2] + h->phase_ms[3] + h->phase_ms[4] +
+                         h->phase_ms[5];
+        info->solve_ms = h->phase_ms[6] + h->phase_ms[7] + h->phase_ms[8];
+    }
+    if (!it[1]) throw Error{BDDC_ENOCONV, "PCG did not reach the tolerance within maxit"};
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+extern "C" {
+
+void bddc_default_options(bddc_options *opt) {
+    if (!opt) return;
+    opt->precision = BDDC_FP64;
+    opt->tol = 1e-8;
+    opt->maxit = 1000;
+    opt->drop_rel = 1e-10;
+    opt->timeout_s = 10.0;
+    opt->stream = nullptr;
+}
+
+const char *bddc_status_str(bddc_status s) {
+    switch (s) {
+        case BDDC_OK: return "ok";
+        case BDDC_EINVAL: return "invalid argument";
+        case BDDC_ENOMEM: return "out of memory";
+        case BDDC_ENOTSPD: return "matrix not positive definite";
+        case BDDC_EASSUMPTION: return "too few corners (Assumption 1 or 2)";
+        case BDDC_ENOCONV: return "PCG did not converge";
+        case BDDC_ETIMEOUT: return "device wait timed out";
+        case BDDC_ECUDA: return "CUDA error";
+        case BDDC_ESTATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char *bddc_last_error(const bddc_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+#define BDDC_TRY(h, ...)                                    \
+    try {                                                   \
+        __VA_ARGS__;                                        \
+        (h)->err.clear();                                   \
+        return BDDC_OK;                                     \
+    } catch (const Error &e_) {                             \
+        (h)->err = e_.msg;                                  \
+        return (bddc_status)e_.status;                      \
+    } catch (const std::exception &e_) {                    \
+        (h)->err = e_.what();                               \
+        return BDDC_EINVAL;                                 \
+    }
+
+bddc_status bddc_create(const bddc_options *opt, bddc_handle **out) {
+    if (!out) return BDDC_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return BDDC_ECUDA;
+    bddc_handle *h = new (std::nothrow) bddc_handle();
+    if (!h) return BDDC_ENOMEM;
+    if (opt)
+        h->opt = *opt;
+    else
+        bddc_default_options(&h->opt);
+    h->stream = (cudaStream_t)h->opt.stream;
+    if (cudaMalloc(&h->dst, sizeof(DevStatus)) != cudaSuccess) {
+        delete h;
+        return BDDC_ENOMEM;
+    }
+    cudaMemset(h->dst, 0, sizeof(DevStatus));
+    for (auto &e : h->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaFree(h->dst);
+            delete h;
+            return BDDC_ECUDA;
+        }
+    }
+    *out = h;
+    return BDDC_OK;
+}
+
+void bddc_destroy(bddc_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    h->ar.release();
+    cudaFree(h->dst);
+    for (auto &e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double *xyz, int64_t ne,
+                             const int64_t *elems, const double *coef, double nu, const int32_t *elem_sub,
+                             int32_t nsub, const uint8_t *dirichlet, int mem) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(ncomp == 1 || ncomp == 3, BDDC_EINVAL, "ncomp must be 1 or 3");
+        BDDC_REQUIRE(nn > 0 && ne > 0 && nsub > 0, BDDC_EINVAL, "empty mesh");
+        BDDC_REQUIRE(xyz && elems && coef && elem_sub && dirichlet, BDDC_EINVAL, "null array");
+        h->have_mesh = h->have_setup = false;
+        h->ncomp = ncomp;
+        h->nn = nn;
+        h->ne = ne;
+        h->nsub = nsub;
+        h->nu = nu;
+        h->xyz.resize(nn * 3);
+        h->elems.resize(ne * 8);
+        h->coef.resize(ne);
+        h->esub.resize(ne);
+        h->dirich.resize(nn);
+        auto cp = [&](void *dst, const void *src, size_t bytes) {
+            BDDC_CUDA(cudaMemcpy(dst, src, bytes, mem == BDDC_MEM_DEVICE ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+        };
+        cp(h->xyz.data(), xyz, nn * 3 * sizeof(double));
+        cp(h->elems.data(), elems, ne * 8 * sizeof(int64_t));
+        cp(h->coef.data(), coef, ne * sizeof(double));
+        cp(h->esub.data(), elem_sub, ne * sizeof(int32_t));
+        cp(h->dirich.data(), dirichlet, nn);
+        for (int64_t k = 0; k < ne * 8; ++k)
+            BDDC_REQUIRE(h->elems[k] >= 0 && h->elems[k] < nn, BDDC_EINVAL, "element node id out of range");
+        for (int64_t e = 0; e < ne; ++e)
+            BDDC_REQUIRE(h->esub[e] >= 0 && h->esub[e] < nsub, BDDC_EINVAL, "substructure id out of range");
+        classify(h);
+        for (auto &sd : h->subs) BDDC_REQUIRE(sd.n > 0, BDDC_EINVAL, "substructure without free dofs");
+        h->avg_flags = 0;
+        // device copies of the mesh and index maps
+        h->ar.upload("xyz", h->xyz, h->stream);
+        h->ar.upload("elems", h->elems, h->stream);
+        h->ar.upload("coef", h->coef, h->stream);
+        h->ar.upload("esub", h->esub, h->stream);
+        h->ar.upload("epos", element_positions(h), h->stream);
+        for (size_t col = 0; col < h->colors.size(); ++col)
+            h->ar.upload("color_" + std::to_string(col), h->colors[col], h->stream);
+        std::vector<int64_t> gIall, gGall, RG64;
+        for (auto &sd : h->subs) {
+            gIall.insert(gIall.end(), sd.gI.begin(), sd.gI.end());
+            gGall.insert(gGall.end(), sd.gG.begin(), sd.gG.end());
+            for (int x : sd.RG) RG64.push_back(x);
+        }
+        h->ar.upload("gIall", gIall, h->stream);
+        h->ar.upload("gGall", gGall, h->stream);
+        h->ar.upload("RG64", RG64, h->stream);
+        h->ar.upload("ifgdof", h->iface_gdof, h->stream);
+        alloc_solver_buffers(h);
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        h->have_mesh = true;
+    });
+}
+
+bddc_status bddc_set_averages(bddc_handle *h, int flags) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(h->have_mesh, BDDC_ESTATE, "no mesh");
+        h->avg_flags = flags & (BDDC_AVG_EDGE | BDDC_AVG_FACE);
+        h->have_setup = false;
+    });
+}
+
+bddc_status bddc_setup(bddc_handle *h) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(h->have_mesh, BDDC_ESTATE, "no mesh");
+        h->have_setup = false;
+        do_setup(h);
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        h->have_setup = true;
+    });
+}
+
+bddc_status bddc_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(h->have_setup, BDDC_ESTATE, "adapt before setup");
+        BDDC_REQUIRE(tau > 0, BDDC_EINVAL, "tau must be positive");
+        do_adapt(h, tau, info);
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+bddc_status bddc_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_info *info) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(h->have_setup, BDDC_ESTATE, "solve before setup");
+        BDDC_REQUIRE(f && u, BDDC_EINVAL, "null vector");
+        do_solve(h, f, u, mem, info);
+    });
+}
+
+bddc_status bddc_condition_estimate(const bddc_handle *h, double *lmin, double *lmax) {
+    if (!h || !lmin || !lmax) return BDDC_EINVAL;
+    const int k = (int)h->alpha.size();
+    if (k == 0) {
+        *lmin = *lmax = 1.0;
+        return BDDC_OK;
+    }
+    // Lanczos tridiagonal from the PCG coefficients; eigenvalues by bisection (Sturm counts)
+    std::vector<double> d(k), e(k, 0.0);
+    for (int j = 0; j < k; ++j) {
+        d[j] = 1.0 / h->alpha[j] + (j > 0 ? h->beta[j - 1] / h->alpha[j - 1] : 0.0);
+        if (j + 1 < k) e[j] = std::sqrt(h->beta[j]) / h->alpha[j];
+    }
+    double lo = 1e300, hi = -1e300;
+    for (int j = 0; j < k; ++j) {
+        double r = (j > 0 ? std::fabs(e[j - 1]) : 0.0) + std::fabs(e[j]);
+        lo = std::min(lo, d[j] - r);
+        hi = std::max(hi, d[j] + r);
+    }
+    auto less = [&](double x) {
+        int c = 0;
+        double q = d[0] - x;
+        if (std::fabs(q) < 1e-300) q = -1e-300;
+        if (q < 0) ++c;
+        for (int j = 1; j < k; ++j) {
+            q = d[j] - x - e[j - 1] * e[j - 1] / q;
+            if (std::fabs(q) < 1e-300) q = -1e-300;
+            if (q < 0) ++c;
+        }
+        return c;
+    };
+    auto kth = [&](int idx) {
+        double a = lo - 1, b = hi + 1;
+        for (int it = 0; it < 200; ++it) {
+            double m = 0.5 * (a + b);
+            if (less(m) > idx)
+                b = m;
+            else
+                a = m;
+        }
+        return 0.5 * (a + b);
+    };
+    *lmin = kth(0);
+    *lmax = kth(k - 1);
+    return BDDC_OK;
+}
+
+bddc_status bddc_get_sizes(const bddc_handle *h, int64_t *n_free, int64_t *n_interface, int *n_corners, int *n_edges,
+                           int *n_faces, int *n_coarse) {
+    if (!h || !h->have_mesh) return BDDC_ESTATE;
+    if (n_free) *n_free = h->nfree;
+    if (n_interface) *n_interface = h->nG;
+    if (n_corners) *n_corners = (int)h->corners.size();
+    if (n_edges) *n_edges = h->n_edges;
+    if (n_faces) *n_faces = (int)h->faces.size();
+    if (n_coarse) *n_coarse = h->nC;
+    return BDDC_OK;
+}
+
+bddc_status bddc_get_corners(const bddc_handle *h, int64_t *nodes, int cap, int *n) {
+    if (!h || !h->have_mesh) return BDDC_ESTATE;
+    if (n) *n = (int)h->corners.size();
+    for (int k = 0; k < (int)h->corners.size() && k < cap; ++k) nodes[k] = h->corners[k];
+    return BDDC_OK;
+}
+
+bddc_status bddc_get_face_eigs(const bddc_handle *h, int f, int32_t *i, int32_t *j, double *lam, int cap, int *n_lam,
+                               int *n_selected, int *n_kept) {
+    if (!h || !h->have_mesh) return BDDC_ESTATE;
+    if (f < 0 || f >= (int)h->faces.size()) return BDDC_EINVAL;
+    const auto &fp = h->faces[f];
+    if (i) *i = fp.i;
+    if (j) *j = fp.j;
+    if (n_lam) *n_lam = (int)fp.lam.size();
+    if (n_selected) *n_selected = fp.nsel;
+    if (n_kept) *n_kept = fp.nkept;
+    for (int k = 0; k < (int)fp.lam.size() && k < cap; ++k) lam[k] = fp.lam[k];
+    return BDDC_OK;
+}
+
+bddc_status bddc_get_interface_dofs(const bddc_handle *h, int s, int64_t *gdofs, int cap, int *n) {
+    if (!h || !h->have_mesh) return BDDC_ESTATE;
+    if (s < 0 || s >= h->nsub) return BDDC_EINVAL;
+    const auto &sd = h->subs[s];
+    if (n) *n = sd.nG;
+    for (int k = 0; k < sd.nG && k < cap; ++k) gdofs[k] = sd.gG[k];
+    return BDDC_OK;
+}
+
+bddc_status bddc_get_schur(const bddc_handle *h, int s, double *S, int ld, int mem) {
+    if (!h || !h->have_setup) return BDDC_ESTATE;
+    if (s < 0 || s >= h->nsub || ld < h->subs[s].nG) return BDDC_EINVAL;
+    const auto &sd = h->subs[s];
+    cudaError_t e = cudaMemcpy2D(S, (size_t)ld * sizeof(double), sd.S, (size_t)sd.ldS * sizeof(double),
+                                 (size_t)sd.nG * sizeof(double), sd.nG,
+                                 mem == BDDC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? BDDC_OK : BDDC_ECUDA;
+}
+
+static bddc_status apply_op(bddc_handle *h, const double *in, double *out, int mem, int mode) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(h->have_setup, BDDC_ESTATE, "apply before setup");
+        reset_status(h);
+        auto kind = mem == BDDC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        double *dst_in = mode == PCG_APPLY_M ? h->pb.r : h->pb.z;
+        BDDC_CUDA(cudaMemcpyAsync(dst_in, in, h->nG * sizeof(double), kind, h->stream));
+        int nb = 0;
+        cudaError_t e = launch_pcg(h->ops, h->pb, mode, h->opt.tol, h->opt.maxit, h->dst, h->opt.timeout_s, h->stream, &nb);
+        BDDC_REQUIRE(e == cudaSuccess, BDDC_ECUDA, std::string("apply launch: ") + cudaGetErrorString(e));
+        h->launches++;
+        double *src_out = mode == PCG_APPLY_M ? h->pb.z : h->pb.q;
+        auto kind2 = mem == BDDC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        BDDC_CUDA(cudaMemcpyAsync(out, src_out, h->nG * sizeof(double), kind2, h->stream));
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        fail_check(h, "apply");
+    });
+}
+
+bddc_status bddc_apply_preconditioner(bddc_handle *h, const double *r, double *z, int mem) {
+    return apply_op(h, r, z, mem, PCG_APPLY_M);
+}
+
+bddc_status bddc_apply_schur(bddc_handle *h, const double *x, double *y, int mem) {
+    return apply_op(h, x, y, mem, PCG_APPLY_S);
+}
+
+int64_t bddc_launch_count(const bddc_handle *h) { return h ? h->launches : 0; }
+
+bddc_status bddc_get_phase_times(const bddc_handle *h, double *ms, double *flop, int cap, int *n) {
+    if (!h) return BDDC_EINVAL;
+    if (n) *n = bddc_handle::kPhases;
+    for (int k = 0; k < bddc_handle::kPhases && k < cap; ++k) {
+        if (ms) ms[k] = h->phase_ms[k];
+        if (flop) flop[k] = h->phase_flop[k];
+    }
+    return BDDC_OK;
+}
+
+}  // extern "C"

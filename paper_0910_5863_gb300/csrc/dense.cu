@@ -1,0 +1,410 @@
+// Batched variable-size dense kernels (FP64 and FP32) for the substructure
+// and face-pair algebra of adaptive BDDC.
+//
+// The central operation is a *partial* right-looking blocked Cholesky: for a
+// symmetric matrix stored column-major (lower triangle significant) it
+// eliminates the first nstop columns.  Afterwards
+//   A[0:n, 0:nstop]        holds L11 (lower) and L21 = A21 L11^-T,
+//   A[nstop:n, nstop:n]    (lower) holds the Schur complement A22 - L21 L21^T,
+//   the strict upper triangle keeps its original contents.
+// With A = [[A_II, A_IG], [A_GI, A_GG]] and nstop = n_I this is the interior
+// elimination of Section 2 of the paper (S_i = A_GG - A_GI A_II^{-1} A_IG),
+// and with augmented matrices it also yields inverses and coarse operators.
+#include "common.cuh"
+#include "dense.h"
+#include <algorithm>
+
+namespace bddc {
+
+constexpr int NB = 32;          // panel width
+constexpr int PANEL_ROWS = 128; // rows of the panel solved per CTA
+constexpr int TILE = 64;        // trailing-update tile
+
+// ---------------------------------------------------------------------------
+// panel: factor the nb x nb diagonal block (redundantly per CTA) and solve
+// the rows below it: A[r, kb:kb+nb] <- A[r, kb:kb+nb] L_kk^-T.
+template <typename T>
+__global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc<T> *descs, const int2 *items,
+                                                                 int nitems, int kb, DevStatus *st) {
+    int it = blockIdx.x;
+    if (it >= nitems) return;
+    int2 w = items[it];
+    const PcholDesc<T> d = descs[w.x];
+    const int n = d.n, ld = d.ld;
+    const int nb = min(NB, d.nstop - kb);
+    T *A = d.A;
+    __shared__ T Ld[NB][NB + 1];
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+        int i = e % nb, j = e / nb;
+        Ld[i][j] = (i >= j) ? A[(size_t)(kb + j) * ld + kb + i] : T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (tid == 0) {
+            T dj = Ld[j][j];
+            if (!(dj > T(0))) {
+                bad = 1;
+                dj = T(1);
+            }
+            Ld[j][j] = sqrt(dj);
+        }
+        __syncthreads();
+        for (int i = j + 1 + tid; i < nb; i += blockDim.x) Ld[i][j] /= Ld[j][j];
+        __syncthreads();
+        int m = nb - j - 1;
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            int i = j + 1 + e % m, k = j + 1 + e / m;
+            if (i >= k) Ld[i][k] -= Ld[i][j] * Ld[k][j];
+        }
+        __syncthreads();
+    }
+    if (bad && tid == 0 && w.y == 0) dev_fail(st, BDDC_DEV_ERR_NOTSPD, w.x, kb);
+    if (w.y == 0) {
+        for (int e = tid; e < nb * nb; e += blockDim.x) {
+            int i = e % nb, j = e / nb;
+            if (i >= j) A[(size_t)(kb + j) * ld + kb + i] = Ld[i][j];
+        }
+    }
+    int r = kb + nb + w.y * PANEL_ROWS + tid;
+    if (r < n) {
+        T x[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+            if (c < nb) x[c] = A[(size_t)(kb + c) * ld + r];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+            if (c < nb) {
+                T s = x[c];
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (k < c) s -= x[k] * Ld[c][k];
+                x[c] = s / Ld[c][c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+            if (c < nb) A[(size_t)(kb + c) * ld + r] = x[c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// trailing update of one 64x64 lower tile: C -= P_i P_j^T with P = A[:, kb:kb+nb].
+template <typename T>
+__global__ void __launch_bounds__(256) pchol_update_kernel(const PcholDesc<T> *descs, const int4 *items,
+                                                           int nitems, int kb) {
+    int it = blockIdx.x;
+    if (it >= nitems) return;
+    int4 w = items[it];  // x = desc, y = tile row, z = tile col
+    const PcholDesc<T> d = descs[w.x];
+    const int n = d.n, ld = d.ld;
+    const int nb = min(NB, d.nstop - kb);
+    const int t0 = kb + nb;
+    const int i0 = t0 + w.y * TILE, j0 = t0 + w.z * TILE;
+    T *A = d.A;
+    __shared__ T Pa[NB][TILE + 1];
+    __shared__ T Pb[NB][TILE + 1];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NB * TILE; e += 256) {
+        int r = e % TILE, k = e / TILE;
+        T va = 0, vb = 0;
+        if (k < nb) {
+            if (i0 + r < n) va = A[(size_t)(kb + k) * ld + i0 + r];
+            if (j0 + r < n) vb = A[(size_t)(kb + k) * ld + j0 + r];
+        }
+        Pa[k][r] = va;
+        Pb[k][r] = vb;
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    for (int k = 0; k < nb; ++k) {
+        T pa[4], pb[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) pa[a] = Pa[k][tx + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) pb[b] = Pb[k][ty + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += pa[a] * pb[b];
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        int c = j0 + ty + 16 * b;
+        if (c >= n) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            int r = i0 + tx + 16 * a;
+            if (r < n && r >= c) A[(size_t)c * ld + r] -= acc[a][b];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// generic gather: dst[p, q] (+)= scale * src(rmap[p], cmap[q]); maps < 0 give 0.
+// src_sym: src holds a symmetric matrix in its lower triangle.
+// dst_lower: only p >= q is written.
+__global__ void gather_kernel(const GatherOp *ops, const int2 *items, int nitems) {
+    int it = blockIdx.x;
+    if (it >= nitems) return;
+    int2 w = items[it];  // x = op, y = column block of 8
+    const GatherOp o = ops[w.x];
+    int q0 = w.y * 8;
+    for (int qq = 0; qq < 8; ++qq) {
+        int q = q0 + qq;
+        if (q >= o.nc) break;
+        int cq = o.cmap ? o.cmap[q] : q;
+        for (int p = threadIdx.x; p < o.nr; p += blockDim.x) {
+            if (o.dst_lower && p + o.dst_row_off < q + o.dst_col_off) continue;
+            int rp = o.rmap ? o.rmap[p] : p;
+            double v = 0.0;
+            if (rp >= 0 && cq >= 0) {
+                if (!o.src) {
+                    v = (rp == cq) ? 1.0 : 0.0;
+                } else {
+                    int a = rp + o.src_row_off, b = cq + o.src_col_off;
+                    if (o.src_sym && a < b) {
+                        int t = a;
+                        a = b;
+                        b = t;
+                    }
+                    v = o.src[(size_t)b * o.ld_src + a];
+                }
+                if (o.rscale) v *= o.rscale[p];
+                if (o.cscale) v *= o.cscale[q];
+            }
+            double *dp = o.dst + (size_t)(q + o.dst_col_off) * o.ld_dst + p + o.dst_row_off;
+            if (o.accumulate)
+                *dp += o.scale * v;
+            else
+                *dp = o.scale * v;
+        }
+    }
+}
+
+// dst[(off + k), (off2 + k)] = value for k < n (an identity block)
+__global__ void diag_set_kernel(const DiagOp *ops, int nops) {
+    int it = blockIdx.x;
+    if (it >= nops) return;
+    DiagOp o = ops[it];
+    for (int k = threadIdx.x; k < o.n; k += blockDim.x)
+        o.dst[(size_t)(o.col_off + k) * o.ld + o.row_off + k] = o.value;
+}
+
+__global__ void zero_kernel(double *p, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) p[i] = 0.0;
+}
+
+__global__ void scatter_kernel(double *dst, const int64_t *idx, const double *src, int64_t n) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        dst[idx[k]] = src[k];
+}
+__global__ void gatherv_kernel(double *dst, const int64_t *idx, const double *src, int64_t n) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = src[idx[k]];
+}
+__global__ void gatherv_add_kernel(double *dst, const int64_t *idx, const double *src, int64_t n) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] += src[idx[k]];
+}
+__global__ void coarse_assemble_kernel(const CoarseAsmDesc *d, int nsub, double *SC, int nC) {
+    for (int s = 0; s < nsub; ++s) {
+        const CoarseAsmDesc c = d[s];
+        for (int e = threadIdx.x; e < c.nci * c.nci; e += blockDim.x) {
+            int m = e % c.nci, l = e / c.nci;
+            SC[(size_t)c.Rc[l] * nC + c.Rc[m]] += c.SCi[(size_t)l * c.ld + m];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batched GEMM, FP64: C = alpha op(A) op(B) + beta C, 64x64 tiles, k-step 16
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const int4 *items, int nitems) {
+    int it = blockIdx.x;
+    if (it >= nitems) return;
+    int4 w = items[it];
+    const GemmDesc d = descs[w.x];
+    const int m0 = w.y * TILE, n0 = w.z * TILE;
+    __shared__ double As[16][TILE + 1];
+    __shared__ double Bs[16][TILE + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < d.k; k0 += 16) {
+        for (int e = tid; e < 16 * TILE; e += 256) {
+            int r, k;
+            // A tile: rows m0..m0+63, k0..k0+15
+            if (!d.transA) {
+                r = e % TILE;
+                k = e / TILE;
+            } else {
+                k = e % 16;
+                r = e / 16;
+            }
+            double v = 0.0;
+            if (m0 + r < d.m && k0 + k < d.k)
+                v = d.transA ? d.A[(size_t)(m0 + r) * d.lda + k0 + k] : d.A[(size_t)(k0 + k) * d.lda + m0 + r];
+            As[k][r] = v;
+            int c;
+            if (d.transB) {
+                c = e % TILE;
+                k = e / TILE;
+            } else {
+                k = e % 16;
+                c = e / 16;
+            }
+            v = 0.0;
+            if (n0 + c < d.n && k0 + k < d.k)
+                v = d.transB ? d.B[(size_t)(k0 + k) * d.ldb + n0 + c] : d.B[(size_t)(n0 + c) * d.ldb + k0 + k];
+            Bs[k][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[k][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int c = n0 + ty + 16 * j;
+        if (c >= d.n) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int r = m0 + tx + 16 * i;
+            if (r >= d.m) continue;
+            double *cp = d.C + (size_t)c * d.ldc + r;
+            *cp = d.alpha * acc[i][j] + (d.beta == 0.0 ? 0.0 : d.beta * *cp);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batched triangular solves with the factor of a partial Cholesky, one CTA
+// per matrix, one right-hand side:
+//   forward : y = L11^{-1} b        (b, y in x[0:nstop])
+//   backward: x = L11^{-T} y
+template <typename T>
+__global__ void __launch_bounds__(256) trsv_kernel(const TrsvDesc<T> *descs, int nd, int backward) {
+    int it = blockIdx.x;
+    if (it >= nd) return;
+    const TrsvDesc<T> d = descs[it];
+    const int n = d.n, ld = d.ld;
+    const T *L = d.L;
+    double *x = d.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    __shared__ double part[8][32];
+    if (!backward) {
+        for (int jb = 0; jb < n; jb += 32) {
+            int nb = min(32, n - jb);
+            if (wid == 0) {
+                double v = lane < nb ? x[jb + lane] : 0.0;
+                for (int c = 0; c < nb; ++c) {
+                    if (lane == c) v /= (double)L[(size_t)(jb + c) * ld + jb + c];
+                    double yc = __shfl_sync(0xffffffffu, v, c);
+                    if (lane > c && lane < nb) v -= (double)L[(size_t)(jb + c) * ld + jb + lane] * yc;
+                }
+                if (lane < nb) x[jb + lane] = v;
+            }
+            __syncthreads();
+            for (int r = jb + nb + tid; r < n; r += blockDim.x) {
+                double s = 0.0;
+                for (int c = 0; c < nb; ++c) s += (double)L[(size_t)(jb + c) * ld + r] * x[jb + c];
+                x[r] -= s;
+            }
+            __syncthreads();
+        }
+    } else {
+        int nblk = (n + 31) / 32;
+        for (int bi = nblk - 1; bi >= 0; --bi) {
+            int jb = bi * 32, nb = min(32, n - jb);
+            // x[jb+c] -= sum_{r >= jb+nb} L[r, jb+c] x[r]
+            for (int c = wid; c < nb; c += nw) {
+                double s = 0.0;
+                for (int r = jb + nb + lane; r < n; r += 32) s += (double)L[(size_t)(jb + c) * ld + r] * x[r];
+                s = warp_sum(s);
+                if (lane == 0) part[0][c] = s;
+            }
+            __syncthreads();
+            if (wid == 0) {
+                double v = lane < nb ? x[jb + lane] - part[0][lane] : 0.0;
+                for (int c = nb - 1; c >= 0; --c) {
+                    if (lane == c) v /= (double)L[(size_t)(jb + c) * ld + jb + c];
+                    double xc = __shfl_sync(0xffffffffu, v, c);
+                    if (lane < c) v -= (double)L[(size_t)(jb + lane) * ld + jb + c] * xc;
+                }
+                if (lane < nb) x[jb + lane] = v;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+template <typename T>
+void launch_pchol_panel(const PcholDesc<T> *descs, const int2 *items, int nitems, int kb, DevStatus *st,
+                        cudaStream_t s) {
+    if (nitems > 0) pchol_panel_kernel<T><<<nitems, PANEL_ROWS, 0, s>>>(descs, items, nitems, kb, st);
+}
+template <typename T>
+void launch_pchol_update(const PcholDesc<T> *descs, const int4 *items, int nitems, int kb, cudaStream_t s) {
+    if (nitems > 0) pchol_update_kernel<T><<<nitems, 256, 0, s>>>(descs, items, nitems, kb);
+}
+template void launch_pchol_panel<double>(const PcholDesc<double> *, const int2 *, int, int, DevStatus *, cudaStream_t);
+template void launch_pchol_panel<float>(const PcholDesc<float> *, const int2 *, int, int, DevStatus *, cudaStream_t);
+template void launch_pchol_update<double>(const PcholDesc<double> *, const int4 *, int, int, cudaStream_t);
+template void launch_pchol_update<float>(const PcholDesc<float> *, const int4 *, int, int, cudaStream_t);
+
+void launch_gather(const GatherOp *ops, const int2 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) gather_kernel<<<nitems, 256, 0, s>>>(ops, items, nitems);
+}
+void launch_diag_set(const DiagOp *ops, int nops, cudaStream_t s) {
+    if (nops > 0) diag_set_kernel<<<nops, 256, 0, s>>>(ops, nops);
+}
+void launch_zero(double *p, size_t n, cudaStream_t s) {
+    if (n == 0) return;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    zero_kernel<<<blocks, 256, 0, s>>>(p, n);
+}
+void launch_scatter(double *dst, const int64_t *idx, const double *src, int64_t n, cudaStream_t s) {
+    if (n > 0) scatter_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(dst, idx, src, n);
+}
+void launch_gatherv(double *dst, const int64_t *idx, const double *src, int64_t n, cudaStream_t s) {
+    if (n > 0) gatherv_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(dst, idx, src, n);
+}
+void launch_gatherv_add(double *dst, const int64_t *idx, const double *src, int64_t n, cudaStream_t s) {
+    if (n > 0) gatherv_add_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(dst, idx, src, n);
+}
+void launch_coarse_assemble(const CoarseAsmDesc *d, int nsub, double *SC, int nC, cudaStream_t s) {
+    if (nsub > 0) coarse_assemble_kernel<<<1, 1024, 0, s>>>(d, nsub, SC, nC);
+}
+void launch_gemm(const GemmDesc *descs, const int4 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) gemm_kernel<<<nitems, 256, 0, s>>>(descs, items, nitems);
+}
+template <typename T>
+void launch_trsv(const TrsvDesc<T> *descs, int nd, int backward, cudaStream_t s) {
+    if (nd > 0) trsv_kernel<T><<<nd, 256, 0, s>>>(descs, nd, backward);
+}
+template void launch_trsv<double>(const TrsvDesc<double> *, int, int, cudaStream_t);
+template void launch_trsv<float>(const TrsvDesc<float> *, int, int, cudaStream_t);
+
+}  // namespace bddc

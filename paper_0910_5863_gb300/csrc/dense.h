@@ -1,0 +1,89 @@
+// Descriptors and launchers of the batched dense kernels (dense.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include "common.cuh"
+
+namespace bddc {
+
+// One matrix of a batched partial Cholesky: eliminate columns [0, nstop).
+template <typename T>
+struct PcholDesc {
+    T *A;
+    int n;
+    int ld;
+    int nstop;
+    int pad;
+};
+
+// dst[p + dst_row_off, q + dst_col_off] (+)= scale * rscale[p] * cscale[q] * src(rmap[p], cmap[q])
+struct GatherOp {
+    const double *src;    // NULL = identity source (1 where the mapped row equals the mapped column)
+    double *dst;
+    const int *rmap;      // NULL = identity
+    const int *cmap;      // NULL = identity
+    const double *rscale; // NULL = 1
+    const double *cscale; // NULL = 1
+    int ld_src, ld_dst;
+    int nr, nc;
+    int dst_row_off, dst_col_off;
+    int src_row_off, src_col_off;  // added to mapped indices
+    double scale;
+    int src_sym;          // src symmetric, lower triangle stored
+    int dst_lower;        // write only dst rows >= cols
+    int accumulate;
+    int pad;
+};
+
+struct DiagOp {
+    double *dst;
+    int ld, row_off, col_off, n;
+    double value;
+};
+
+struct GemmDesc {
+    const double *A;
+    const double *B;
+    double *C;
+    int lda, ldb, ldc;
+    int m, n, k;
+    int transA, transB;
+    double alpha, beta;
+};
+
+template <typename T>
+struct TrsvDesc {
+    const T *L;
+    double *x;
+    int n, ld;
+};
+
+template <typename T>
+void launch_pchol_panel(const PcholDesc<T> *descs, const int2 *items, int nitems, int kb, DevStatus *st,
+                        cudaStream_t s);
+template <typename T>
+void launch_pchol_update(const PcholDesc<T> *descs, const int4 *items, int nitems, int kb, cudaStream_t s);
+void launch_gather(const GatherOp *ops, const int2 *items, int nitems, cudaStream_t s);
+void launch_diag_set(const DiagOp *ops, int nops, cudaStream_t s);
+void launch_zero(double *p, size_t n, cudaStream_t s);
+// dst[idx[k]] = src[k] (scatter) or dst[k] = src[idx[k]] (gather), k < n
+void launch_scatter(double *dst, const int64_t *idx, const double *src, int64_t n, cudaStream_t s);
+void launch_gatherv(double *dst, const int64_t *idx, const double *src, int64_t n, cudaStream_t s);
+// dst[k] += src[idx[k]]
+void launch_gatherv_add(double *dst, const int64_t *idx, const double *src, int64_t n, cudaStream_t s);
+// S_C[Rc[m], Rc[l]] += SCi[m, l], substructures added in order (deterministic)
+struct CoarseAsmDesc {
+    const double *SCi;
+    const int *Rc;
+    int nci, ld;
+};
+void launch_coarse_assemble(const CoarseAsmDesc *d, int nsub, double *SC, int nC, cudaStream_t s);
+void launch_gemm(const GemmDesc *descs, const int4 *items, int nitems, cudaStream_t s);
+template <typename T>
+void launch_trsv(const TrsvDesc<T> *descs, int nd, int backward, cudaStream_t s);
+
+constexpr int kPanelNB = 32;
+constexpr int kPanelRows = 128;
+constexpr int kTile = 64;
+
+}  // namespace bddc

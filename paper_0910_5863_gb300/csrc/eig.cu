@@ -1,0 +1,381 @@
+// Face-pair eigenproblems of adaptive BDDC (Section 3 of the paper).
+//
+// Each face pair's generalized problem has been reduced, exactly, to a
+// symmetric standard problem C y = lambda y of order n_s (the number of
+// shared non-corner dofs; see the adapt phase for the reduction).  One CTA
+// per pair:
+//   1. Householder reduction of C to tridiagonal T (reflectors kept),
+//   2. Sturm-sequence counts give k = #{lambda > tau} exactly (Algorithm
+//      3.1 selects the smallest k with lambda_{k+1} <= tau) and bisection
+//      gives lambda_1..lambda_{k+1},
+//   3. inverse iteration on T (LU with row interchanges) for the k vectors,
+//      re-orthogonalised inside clusters, and back-transformation,
+//   4. face rows d = (W1 y)|face (the face part of eq. (d-def); edge parts
+//      are dropped as in the paper's Remark), normalised and orthogonalised
+//      with row pivoting; rows whose pivot is below drop_rel are dropped.
+#include "common.cuh"
+#include "eig.h"
+
+namespace bddc {
+
+constexpr int EIG_THREADS = 256;
+
+__device__ int sturm_less(const double *d, const double *e, int n, double x, double pivmin) {
+    int cnt = 0;
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++cnt;
+    for (int i = 1; i < n; ++i) {
+        q = d[i] - x - e[i - 1] * e[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *descs, int np, double tau,
+                                                               double drop_rel, DevStatus *st, int use_smem) {
+    extern __shared__ double sm[];
+    __shared__ double scratch[32];
+    __shared__ double sh_val[4];
+    __shared__ int sh_int[4];
+    if (blockIdx.x >= np) return;
+    const EigDesc D = descs[blockIdx.x];
+    const int n = D.n, tid = threadIdx.x, nt = blockDim.x;
+    int *counts = D.counts;
+    if (n <= 0) {
+        if (tid == 0) counts[0] = counts[1] = counts[2] = counts[3] = counts[4] = 0;
+        return;
+    }
+    double *A;
+    int lda;
+    double *work;
+    if (use_smem) {
+        A = sm;
+        lda = n;
+        work = sm + (size_t)n * n;
+        for (int e = tid; e < n * n; e += nt) A[e] = D.C[(size_t)(e / n) * D.ld + e % n];
+    } else {
+        A = D.C;
+        lda = D.ld;
+        work = D.work;
+    }
+    double *dd = work, *ee = work + n, *bet = work + 2 * n, *P = work + 3 * n, *Wv = work + 4 * n;
+    __syncthreads();
+    // ---- 1. Householder tridiagonalisation: A = Q T Q^T ----
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        double *x = A + (size_t)k * lda + k + 1;   // column k below the diagonal
+        double s = 0.0;
+        for (int i = tid; i < m; i += nt) s += x[i] * x[i];
+        s = block_sum(s, scratch);
+        const double x0 = x[0];
+        const double rest = s - x0 * x0;
+        if (rest <= 1e-300 * (s + 1e-300)) {
+            if (tid == 0) {
+                bet[k] = 0.0;
+                ee[k] = x0;
+            }
+            __syncthreads();
+            continue;
+        }
+        const double nrm = sqrt(s);
+        const double alpha = x0 > 0 ? -nrm : nrm;
+        const double v0 = x0 - alpha;
+        const double beta = 2.0 / (rest + v0 * v0);
+        __syncthreads();
+        if (tid == 0) {
+            x[0] = v0;
+            bet[k] = beta;
+            ee[k] = alpha;
+        }
+        __syncthreads();
+        double *B = A + (size_t)(k + 1) * lda + k + 1;
+        for (int i = tid; i < m; i += nt) {
+            double acc = 0.0;
+            for (int j = 0; j < m; ++j) acc += B[(size_t)j * lda + i] * x[j];
+            P[i] = beta * acc;
+        }
+        __syncthreads();
+        double pv = 0.0;
+        for (int i = tid; i < m; i += nt) pv += P[i] * x[i];
+        pv = block_sum(pv, scratch);
+        const double K = 0.5 * beta * pv;
+        for (int i = tid; i < m; i += nt) Wv[i] = P[i] - K * x[i];
+        __syncthreads();
+        for (int e = tid; e < m * m; e += nt) {
+            int i = e % m, j = e / m;
+            B[(size_t)j * lda + i] -= x[i] * Wv[j] + Wv[i] * x[j];
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += nt) dd[i] = A[(size_t)i * lda + i];
+    if (tid == 0) {
+        if (n >= 2) {
+            ee[n - 2] = A[(size_t)(n - 2) * lda + n - 1];
+            bet[n - 2] = 0.0;
+        }
+        bet[n - 1] = 0.0;
+        ee[n - 1] = 0.0;
+    }
+    __syncthreads();
+    // ---- 2. counts and bisection ----
+    double tnorm = 0.0, emax2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double r = fabs(dd[i]) + (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i + 1 < n ? fabs(ee[i]) : 0.0);
+        tnorm = fmax(tnorm, r);
+        if (i + 1 < n) emax2 = fmax(emax2, ee[i] * ee[i]);
+    }
+    const double pivmin = fmax(1e-300, 1e-290 * fmax(emax2, 1.0));
+    if (tid == 0) {
+        int less = sturm_less(dd, ee, n, tau, pivmin);
+        int nsel = n - less;
+        int ties = sturm_less(dd, ee, n, tau * (1 + 1e-6), pivmin) - sturm_less(dd, ee, n, tau * (1 - 1e-6), pivmin);
+        int over = 0;
+        if (nsel > kEigCap) {
+            nsel = kEigCap;
+            over = 1;
+        }
+        sh_int[0] = nsel;
+        sh_int[1] = ties;
+        sh_int[2] = over;
+        sh_int[3] = min(nsel + 1, n);
+    }
+    __syncthreads();
+    const int nsel = sh_int[0], nval = sh_int[3];
+    double *lam = D.lam;
+    for (int t = tid; t < nval; t += nt) {
+        const int j = n - 1 - t;  // index among ascending eigenvalues
+        double lo = -tnorm - 1.0, hi = tnorm + 1.0;
+        for (int itb = 0; itb < 400; ++itb) {
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (sturm_less(dd, ee, n, mid, pivmin) > j)
+                hi = mid;
+            else
+                lo = mid;
+            if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
+        }
+        lam[t] = 0.5 * (lo + hi);
+    }
+    __syncthreads();
+    // ---- 3. inverse iteration on T, back-transformation ----
+    double *dl = P, *du = Wv, *dv = work + 5 * n, *du2 = work + 6 * n, *xv = work + 7 * n;
+    int *piv = (int *)(work + 8 * n);
+    for (int mI = 0; mI < nsel; ++mI) {
+        const double lm = lam[mI];
+        if (tid == 0) {
+            // LU with row interchanges of T - lm I
+            const double small = 2.2e-16 * fmax(tnorm, 1e-300);
+            for (int i = 0; i < n; ++i) {
+                dv[i] = dd[i] - lm;
+                du[i] = (i + 1 < n) ? ee[i] : 0.0;
+                dl[i] = (i + 1 < n) ? ee[i] : 0.0;
+                du2[i] = 0.0;
+            }
+            for (int i = 0; i + 1 < n; ++i) {
+                if (fabs(dv[i]) >= fabs(dl[i])) {
+                    piv[i] = 0;
+                    if (dv[i] == 0.0) dv[i] = small;
+                    double f = dl[i] / dv[i];
+                    dl[i] = f;
+                    dv[i + 1] -= f * du[i];
+                } else {
+                    piv[i] = 1;
+                    double f = dv[i] / dl[i];
+                    dv[i] = dl[i];
+                    dl[i] = f;
+                    double t = du[i];
+                    du[i] = dv[i + 1];
+                    dv[i + 1] = t - f * dv[i + 1];
+                    if (i + 2 < n) {
+                        du2[i] = du[i + 1];
+                        du[i + 1] = -f * du[i + 1];
+                    }
+                }
+            }
+            if (dv[n - 1] == 0.0) dv[n - 1] = small;
+            for (int i = 0; i < n; ++i) xv[i] = 1.0 + 0.1 * (double)((i * 7919 + mI * 104729) % 17) / 17.0;
+        }
+        __syncthreads();
+        for (int itr = 0; itr < 4; ++itr) {
+            if (tid == 0) {
+                // solve L U x = b (row interchanges recorded in piv)
+                for (int i = 0; i + 1 < n; ++i) {
+                    if (piv[i] == 0) {
+                        xv[i + 1] -= dl[i] * xv[i];
+                    } else {
+                        double t = xv[i];
+                        xv[i] = xv[i + 1];
+                        xv[i + 1] = t - dl[i] * xv[i + 1];
+                    }
+                }
+                xv[n - 1] /= dv[n - 1];
+                if (n >= 2) xv[n - 2] = (xv[n - 2] - du[n - 2] * xv[n - 1]) / dv[n - 2];
+                for (int i = n - 3; i >= 0; --i) xv[i] = (xv[i] - du[i] * xv[i + 1] - du2[i] * xv[i + 2]) / dv[i];
+            }
+            __syncthreads();
+            // orthogonalise against earlier vectors of the same cluster
+            for (int q = 0; q < mI; ++q) {
+                if (fabs(lam[q] - lm) > 1e-5 * fabs(lm)) continue;
+                const double *vq = D.vec + (size_t)q * n;
+                double dot = 0.0;
+                for (int i = tid; i < n; i += nt) dot += vq[i] * xv[i];
+                dot = block_sum(dot, scratch);
+                for (int i = tid; i < n; i += nt) xv[i] -= dot * vq[i];
+                __syncthreads();
+            }
+            double s2 = 0.0;
+            for (int i = tid; i < n; i += nt) s2 += xv[i] * xv[i];
+            s2 = block_sum(s2, scratch);
+            double inv = s2 > 0 ? 1.0 / sqrt(s2) : 0.0;
+            for (int i = tid; i < n; i += nt) xv[i] *= inv;
+            __syncthreads();
+        }
+        double *vout = D.vec + (size_t)mI * n;
+        for (int i = tid; i < n; i += nt) vout[i] = xv[i];
+        __syncthreads();
+    }
+    // back-transformation y = H_0 H_1 ... H_{n-3} x for every selected vector
+    for (int mI = 0; mI < nsel; ++mI) {
+        double *y = D.vec + (size_t)mI * n;
+        for (int k = n - 3; k >= 0; --k) {
+            const double b = bet[k];
+            if (b == 0.0) continue;
+            const double *v = A + (size_t)k * lda + k + 1;
+            double dot = 0.0;
+            for (int i = tid; i < n - k - 1; i += nt) dot += v[i] * y[k + 1 + i];
+            dot = block_sum(dot, scratch);
+            for (int i = tid; i < n - k - 1; i += nt) y[k + 1 + i] -= b * dot * v[i];
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // ---- 4. face rows and their pivoted orthonormalisation ----
+    const int nf = D.nface;
+    double *R = D.rows;
+    for (int e = tid; e < nsel * nf; e += nt) {
+        int l = e / nf, f = e % nf;
+        const double *y = D.vec + (size_t)l * n;
+        const double *wr = D.W1 + D.face_pos[f];
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += wr[(size_t)j * D.ldw] * y[j];
+        R[(size_t)l * nf + f] = acc;
+    }
+    __syncthreads();
+    // normalise every row
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int l = wid; l < nsel; l += nw) {
+        double s = 0.0;
+        for (int f = lane; f < nf; f += 32) s += R[(size_t)l * nf + f] * R[(size_t)l * nf + f];
+        s = warp_sum(s);
+        double inv = s > 0 ? 1.0 / sqrt(s) : 0.0;
+        for (int f = lane; f < nf; f += 32) R[(size_t)l * nf + f] *= inv;
+    }
+    __syncthreads();
+    // Gram-Schmidt with row pivoting: rows [0, kept) are final
+    int kept = 0;
+    double first = -1.0;
+    double *nrm = xv;  // nsel <= n
+    for (int step = 0; step < nsel; ++step) {
+        for (int l = step + wid; l < nsel; l += nw) {
+            double s = 0.0;
+            for (int f = lane; f < nf; f += 32) s += R[(size_t)l * nf + f] * R[(size_t)l * nf + f];
+            s = warp_sum(s);
+            if (lane == 0) nrm[l] = sqrt(s);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int best = step;
+            for (int l = step + 1; l < nsel; ++l)
+                if (nrm[l] > nrm[best]) best = l;
+            sh_int[0] = best;
+            sh_val[0] = nrm[best];
+        }
+        __syncthreads();
+        const int best = sh_int[0];
+        const double pn = sh_val[0];
+        if (first < 0) first = pn;
+        if (!(pn > drop_rel * first) || pn == 0.0) break;
+        // swap rows best <-> step, normalise
+        for (int f = tid; f < nf; f += nt) {
+            double a = R[(size_t)best * nf + f], b = R[(size_t)step * nf + f];
+            R[(size_t)step * nf + f] = a / pn;
+            R[(size_t)best * nf + f] = b;
+        }
+        __syncthreads();
+        for (int l = step + 1 + wid; l < nsel; l += nw) {
+            double s = 0.0;
+            for (int f = lane; f < nf; f += 32) s += R[(size_t)l * nf + f] * R[(size_t)step * nf + f];
+            s = warp_sum(s);
+            for (int f = lane; f < nf; f += 32) R[(size_t)l * nf + f] -= s * R[(size_t)step * nf + f];
+        }
+        __syncthreads();
+        kept = step + 1;
+    }
+    if (tid == 0) {
+        counts[0] = nsel;
+        counts[1] = kept;
+        counts[2] = nval;
+        counts[3] = sh_int[1];
+        counts[4] = sh_int[2];
+    }
+}
+
+void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, DevStatus *st,
+                       cudaStream_t s) {
+    if (npairs <= 0) return;
+    size_t need = sizeof(double) * ((size_t)nmax * nmax + 10 * (size_t)nmax);
+    int use_smem = need <= 200 * 1024;
+    size_t smem = use_smem ? need : 0;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(face_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    face_eig_kernel<<<npairs, EIG_THREADS, smem, s>>>(descs, npairs, tau, drop_rel, st, use_smem);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void deflate_kernel(const DeflateDesc *dd, int np) {
+    __shared__ double scratch[32];
+    const DeflateDesc d = dd[blockIdx.x];
+    const int ns = d.ns, tid = threadIdx.x;
+    if (d.nnull == 0 || ns == 0) return;
+    double mx = 0.0;
+    for (int p = tid; p < 2 * ns; p += blockDim.x) mx = fmax(mx, d.Shat[(size_t)p * d.ld_s + p]);
+    // block max via shared
+    __syncthreads();
+    double m = mx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) scratch[tid >> 5] = m;
+    __syncthreads();
+    double sigma = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sigma = fmax(sigma, scratch[w]);
+    for (int e = tid; e < ns * ns; e += blockDim.x) {
+        int p = e % ns, q = e / ns;
+        double v = 0.0;
+        for (int l = 0; l < d.nnull; ++l) v += d.N0[(size_t)l * ns + p] * d.N0[(size_t)l * ns + q];
+        v *= sigma;
+        // blocks in order (w2, b, id): (w2,w2) += 4v (lower), (b,w2) += 2v, (b,b) += v (lower)
+        if (p >= q) d.M3[(size_t)q * d.ld_m + p] += 4.0 * v;
+        d.M3[(size_t)q * d.ld_m + ns + p] += 2.0 * v;
+        if (p >= q) d.M3[(size_t)(ns + q) * d.ld_m + ns + p] += v;
+    }
+}
+
+void launch_deflate(const DeflateDesc *d, int npairs, cudaStream_t s) {
+    if (npairs > 0) deflate_kernel<<<npairs, 256, 0, s>>>(d, npairs);
+}
+
+__global__ void pair_weights_kernel(const PairWeightDesc *dd, int np) {
+    const PairWeightDesc d = dd[blockIdx.x];
+    for (int k = threadIdx.x; k < d.ns; k += blockDim.x) {
+        double a = d.diag_i[d.pos_i[k]], b = d.diag_j[d.pos_j[k]];
+        d.di[k] = a / (a + b);
+        d.dj[k] = b / (a + b);
+    }
+}
+
+void launch_pair_weights(const PairWeightDesc *d, int npairs, cudaStream_t s) {
+    if (npairs > 0) pair_weights_kernel<<<npairs, 128, 0, s>>>(d, npairs);
+}
+
+}  // namespace bddc

@@ -1,0 +1,300 @@
+// PCG on the reduced interface problem with the BDDC preconditioner, as one
+// persistent cooperative kernel (Section 2 of the paper: PCG on the reduced
+// problem, preconditioner of Lemma 2.1 / eq. (BDDC-prec); the (I-P)^T r step
+// is omitted because the residual vanishes in the interiors).
+//
+// The preconditioner is applied in its primal (local + coarse) form, which
+// the paper's Remark 5.1 states is equivalent once every constraint is a
+// coarse degree of freedom:
+//     r_i = R_i r,  z_i = P~_i r_i,  c_i = Phi~_i^T r_i,
+//     u_c = S_C^{-1} sum_i R_ci^T c_i,
+//     z   = sum_i R_i^T (z_i + Phi~_i R_ci u_c)
+// with the averaging weights folded into P~ = D P D and Phi~ = D Phi.
+// All reductions are deterministic: fixed per-block partial sums reduced in
+// block order by every block.
+#include <cooperative_groups.h>
+#include "common.cuh"
+#include "pcg.h"
+
+namespace bddc {
+
+constexpr int PCG_THREADS = 256;
+
+// Data written by other blocks of this launch is read through L2 only
+// (ld.global.cg), so no block can see a stale L1 line after a grid barrier.
+__device__ __forceinline__ double ldx(const double *p) { return __ldcg(p); }
+
+struct PcgParams {
+    IfaceOps o;
+    PcgBuffers b;
+    int mode;
+    double tol;
+    int maxit;
+    DevStatus *st;
+    uint64_t timeout_ns;
+};
+
+// y_i = Mats_i * v_i for every (substructure, 64-row block); v gathered through RG.
+// If pold != nullptr, v[g] = z[g] + beta * pold[g] (the new search direction).
+__device__ void local_gemv(const PcgParams &P, double *const *Mats, const double *vin, const double *pold,
+                           double beta, double *yout, double *red) {
+    const IfaceOps &o = P.o;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int it = blockIdx.x; it < o.nrowblk; it += gridDim.x) {
+        int2 w = o.rowblk[it];
+        int s = w.x, r0 = w.y;
+        int n = o.nGi[s], ld = o.ldS[s];
+        const double *A = Mats[s];
+        const int *RG = o.RG + o.off[s];
+        int ra = r0 + lane, rb = r0 + lane + 32;
+        double acc0 = 0.0, acc1 = 0.0;
+        for (int c = wid; c < n; c += 8) {
+            int g = RG[c];
+            double v = pold ? ldx(vin + g) + beta * ldx(pold + g) : ldx(vin + g);
+            const double *col = A + (size_t)c * ld;
+            if (ra < n) acc0 += col[ra] * v;
+            if (rb < n) acc1 += col[rb] * v;
+        }
+        red[wid * 64 + lane] = acc0;
+        red[wid * 64 + lane + 32] = acc1;
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            int r = r0 + threadIdx.x;
+            double sum = 0.0;
+            for (int k = 0; k < 8; ++k) sum += red[k * 64 + threadIdx.x];
+            if (r < n) yout[o.off[s] + r] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// c_i[m] = Phi~_i[:, m] . r_i
+__device__ void coarse_dots(const PcgParams &P, const double *rin) {
+    const IfaceOps &o = P.o;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int it = blockIdx.x; it < o.ncdot; it += gridDim.x) {
+        int2 w = o.cdot[it];
+        int s = w.x, m = w.y + wid;
+        if (m < o.nci[s]) {
+            int n = o.nGi[s], ld = o.ldS[s];
+            const double *col = o.Phi[s] + (size_t)m * ld;
+            const int *RG = o.RG + o.off[s];
+            double acc = 0.0;
+            for (int k = lane; k < n; k += 32) acc += col[k] * ldx(rin + RG[k]);
+            acc = warp_sum(acc);
+            if (lane == 0) P.b.cl[o.offc[s] + m] = acc;
+        }
+    }
+}
+
+// u_c = S_C^{-1} r_c; r_c is assembled redundantly in every block (shared memory)
+__device__ void coarse_solve(const PcgParams &P, double *rc) {
+    const IfaceOps &o = P.o;
+    for (int c = threadIdx.x; c < o.nC; c += blockDim.x) {
+        double s = 0.0;
+        for (int e = o.cptr[c]; e < o.cptr[c + 1]; ++e) s += ldx(P.b.cl + o.cent[e]);
+        rc[c] = s;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int row = blockIdx.x * 8 + wid; row < o.nC; row += gridDim.x * 8) {
+        const double *col = o.SCinv + (size_t)row * o.nC;
+        double acc = 0.0;
+        for (int c = lane; c < o.nC; c += 32) acc += col[c] * rc[c];
+        acc = warp_sum(acc);
+        if (lane == 0) P.b.uc[row] = acc;
+    }
+}
+
+// z[x] = sum over entries (z_i[k] + Phi~_i[k, :] u_c[R_ci]); returns this thread's part of r . z
+__device__ double assemble_z(const PcgParams &P, const double *rin, double *zout) {
+    const IfaceOps &o = P.o;
+    double part = 0.0;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < o.nG; x += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int e = o.gptr[x]; e < o.gptr[x + 1]; ++e) {
+            int64_t pe = o.gent[e];
+            int s = o.gsub[e];
+            int k = (int)(pe - o.off[s]);
+            double w = ldx(P.b.zl + pe);
+            int nc = o.nci[s], ld = o.ldS[s];
+            const double *Ph = o.Phi[s];
+            const int *Rc = o.Rc + o.offc[s];
+            for (int m = 0; m < nc; ++m) w += Ph[(size_t)m * ld + k] * ldx(P.b.uc + Rc[m]);
+            v += w;
+        }
+        zout[x] = v;
+        part += rin[x] * v;
+    }
+    return part;
+}
+
+__device__ double reduce_partials(const double *partial, int nb) {
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += ldx(partial + i);
+    return s;
+}
+
+__global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(PcgParams P) {
+    extern __shared__ double smem[];
+    double *red = smem;            // 8 * 64
+    double *rc = smem + 8 * 64;    // nC
+    __shared__ double scratch[32];
+    const IfaceOps &o = P.o;
+    PcgBuffers &b = P.b;
+    const unsigned nb = gridDim.x;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+
+    if (P.mode == PCG_APPLY_M) {
+        local_gemv(P, o.P, b.r, nullptr, 0.0, b.zl, red);
+        coarse_dots(P, b.r);
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        coarse_solve(P, rc);
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        assemble_z(P, b.r, b.z);
+        return;
+    }
+    if (P.mode == PCG_APPLY_S) {
+        local_gemv(P, o.S, b.z, nullptr, 0.0, b.yl, red);
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        for (int x = gtid; x < o.nG; x += gstride) {
+            double v = 0.0;
+            for (int e = o.gptr[x]; e < o.gptr[x + 1]; ++e) v += ldx(b.yl + o.gent[e]);
+            b.q[x] = v;
+        }
+        return;
+    }
+
+    // ---- PCG ----
+    double part = 0.0;
+    for (int x = gtid; x < o.nG; x += gstride) {
+        b.x[x] = 0.0;
+        b.p0[x] = 0.0;
+        part += b.r[x] * b.r[x];
+    }
+    part = block_sum(part, scratch);
+    if (threadIdx.x == 0) b.partial[blockIdx.x] = part;
+    if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+    const double r0 = sqrt(reduce_partials(b.partial, nb));
+    double rz_old = 1.0, rr = r0 * r0;
+    int k = 0;
+    bool conv = (r0 == 0.0);
+    double *pold = b.p0, *pnew = b.p1;
+    while (!conv && k < P.maxit) {
+        ++k;
+        // z = M r
+        local_gemv(P, o.P, b.r, nullptr, 0.0, b.zl, red);
+        coarse_dots(P, b.r);
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        coarse_solve(P, rc);
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        part = assemble_z(P, b.r, b.z);
+        part = block_sum(part, scratch);
+        if (threadIdx.x == 0) b.partial[blockIdx.x] = part;
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        // beta, p = z + beta p, y_i = S_i p_i
+        const double rz = reduce_partials(b.partial, nb);
+        const double beta = (k == 1) ? 0.0 : rz / rz_old;
+        for (int x = gtid; x < o.nG; x += gstride) pnew[x] = b.z[x] + beta * pold[x];
+        local_gemv(P, o.S, b.z, pold, beta, b.yl, red);
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        // q = sum R_i^T y_i, p . q
+        part = 0.0;
+        for (int x = gtid; x < o.nG; x += gstride) {
+            double v = 0.0;
+            for (int e = o.gptr[x]; e < o.gptr[x + 1]; ++e) v += ldx(b.yl + o.gent[e]);
+            b.q[x] = v;
+            part += pnew[x] * v;
+        }
+        part = block_sum(part, scratch);
+        if (threadIdx.x == 0) b.partial[blockIdx.x] = part;
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        const double pq = reduce_partials(b.partial, nb);
+        if (!(pq > 0.0)) {
+            --k;
+            break;
+        }
+        const double alpha = rz / pq;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            b.alpha[k - 1] = alpha;
+            if (k > 1) b.beta[k - 2] = beta;
+        }
+        part = 0.0;
+        for (int x = gtid; x < o.nG; x += gstride) {
+            b.x[x] += alpha * pnew[x];
+            double rv = b.r[x] - alpha * b.q[x];
+            b.r[x] = rv;
+            part += rv * rv;
+        }
+        part = block_sum(part, scratch);
+        if (threadIdx.x == 0) b.partial[blockIdx.x] = part;
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        rr = reduce_partials(b.partial, nb);
+        conv = sqrt(rr) <= P.tol * r0;
+        rz_old = rz;
+        double *t = pold;
+        pold = pnew;
+        pnew = t;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *b.iters = k;
+        *b.converged = conv ? 1 : 0;
+        *b.relres = r0 > 0.0 ? sqrt(rr) / r0 : 0.0;
+    }
+}
+
+cudaError_t launch_pcg(const IfaceOps &ops, const PcgBuffers &buf, int mode, double tol, int maxit,
+                       DevStatus *st, double timeout_s, cudaStream_t s, int *nblocks_out) {
+    PcgParams P;
+    P.o = ops;
+    P.b = buf;
+    P.mode = mode;
+    P.tol = tol;
+    P.maxit = maxit;
+    P.st = st;
+    P.timeout_ns = (uint64_t)(timeout_s * 1e9);
+    size_t smem = sizeof(double) * (8 * 64 + (size_t)(ops.nC > 0 ? ops.nC : 1));
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(pcg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel, PCG_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (per_sm > 2) per_sm = 2;
+    int nblocks = nsm * per_sm;
+    if (nblocks_out) *nblocks_out = nblocks;
+    void *args[] = {&P};
+    return cudaLaunchCooperativeKernel((void *)pcg_kernel, dim3(nblocks), dim3(PCG_THREADS), args, smem, s);
+}
+
+__global__ void iface_assemble_kernel(IfaceOps o, const double *packed, double *out) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < o.nG; x += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int e = o.gptr[x]; e < o.gptr[x + 1]; ++e) v += packed[o.gent[e]];
+        out[x] = v;
+    }
+}
+
+__global__ void weights_kernel(IfaceOps o, const double *diag, const double *total, double *delta) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < o.nG; x += gridDim.x * blockDim.x) {
+        for (int e = o.gptr[x]; e < o.gptr[x + 1]; ++e) delta[o.gent[e]] = diag[o.gent[e]] / total[x];
+    }
+}
+
+void launch_iface_assemble(const IfaceOps &ops, const double *packed, double *out, cudaStream_t s) {
+    int blocks = (ops.nG + 255) / 256;
+    if (blocks > 0) iface_assemble_kernel<<<blocks, 256, 0, s>>>(ops, packed, out);
+}
+
+void launch_weights(const IfaceOps &ops, const double *diag_packed, double *total, double *delta_packed,
+                    cudaStream_t s) {
+    launch_iface_assemble(ops, diag_packed, total, s);
+    int blocks = (ops.nG + 255) / 256;
+    if (blocks > 0) weights_kernel<<<blocks, 256, 0, s>>>(ops, diag_packed, total, delta_packed);
+}
+
+}  // namespace bddc

@@ -1,0 +1,60 @@
+// Interface operators of the reduced problem and the persistent PCG (pcg.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+
+namespace bddc {
+
+// Everything the operator S = sum R_i^T S_i R_i and the BDDC preconditioner
+// M r = sum R_i^T D_i (P_i D_i R_i r + Phi_i R_ci u_c), S_C u_c = sum R_ci^T Phi_i^T D_i R_i r
+// need, packed per substructure.  P~ = D P D and Phi~ = D Phi are stored
+// with the weights folded in.
+struct IfaceOps {
+    int nsub, nG, nC;
+    const int *nGi;          // (nsub) interface size
+    const int *ldS;          // (nsub) leading dimension of S_i and P~_i
+    const int64_t *off;      // (nsub) offset of the substructure's packed local vector
+    const int *RG;           // (sum nGi) global interface index of each local interface dof
+    double *const *S;        // (nsub) S_i, full symmetric column-major
+    double *const *P;        // (nsub) P~_i, full symmetric column-major
+    double *const *Phi;      // (nsub) Phi~_i, nGi x nci column-major (ld = ldS)
+    const int *nci;          // (nsub) local coarse count
+    const int64_t *offc;     // (nsub) offset of the local coarse vector
+    const int *Rc;           // (sum nci) global coarse index of each local coarse dof
+    const double *SCinv;     // nC x nC inverse coarse matrix (full)
+    const int *gptr;         // (nG+1) local entries of each interface dof
+    const int64_t *gent;     // packed local index of each entry
+    const int *gsub;         // substructure of each entry
+    const int *cptr;         // (nC+1)
+    const int64_t *cent;     // packed local coarse index of each entry
+    const int2 *rowblk;      // (sub, first row) GEMV work items, 64 rows each
+    int nrowblk;
+    const int2 *cdot;        // (sub, first coarse column) items, 8 columns each
+    int ncdot;
+};
+
+struct PcgBuffers {
+    double *x, *r, *z, *p0, *p1, *q;  // nG
+    double *zl, *yl;                  // sum nGi
+    double *cl;                       // sum nci
+    double *uc;                       // nC
+    double *partial;                  // nblocks
+    double *alpha, *beta;             // maxit
+    int *iters, *converged;
+    double *relres;
+};
+
+enum PcgMode { PCG_SOLVE = 0, PCG_APPLY_M = 1, PCG_APPLY_S = 2 };
+
+// Launches the persistent cooperative kernel.  Returns the cudaError of the launch.
+cudaError_t launch_pcg(const IfaceOps &ops, const PcgBuffers &buf, int mode, double tol, int maxit,
+                       DevStatus *st, double timeout_s, cudaStream_t s, int *nblocks_out);
+
+// Weights: delta(k) = diag_i(k) / sum over the substructures sharing the dof.
+void launch_weights(const IfaceOps &ops, const double *diag_packed, double *total, double *delta_packed,
+                    cudaStream_t s);
+// Deterministic assembly of a packed local interface vector: out[x] = sum over entries.
+void launch_iface_assemble(const IfaceOps &ops, const double *packed, double *out, cudaStream_t s);
+
+}  // namespace bddc
