@@ -189,6 +189,30 @@ BDDC_API bddc_status bddc_get_phase_times(const bddc_handle *h, double *ms, doub
 /* Number of kernel launches made by the handle so far (all phases). */
 BDDC_API int64_t bddc_launch_count(const bddc_handle *h);
 
+/* Schur complement of ONE dense symmetric matrix, for callers that cannot
+ * allocate device memory (the paper has no counterpart; it is a service
+ * entry point).  Callers that run under a fixed memory budget, own the device
+ * memory through their own allocator, or must not allocate after start-up can
+ * still use the interior elimination kernels through this call: it makes no
+ * cudaMalloc, cudaFree or other allocating call.  Its scratch (a working copy
+ * of A plus the kernels' work lists) is a static device array of about 8.5 MB
+ * that every GPU loading the library holds until the process exits.
+ *   n, n_int  order of A and number of leading (interior) rows to eliminate,
+ *             0 <= n_int < n <= 1024 (larger n is rejected with BDDC_EINVAL)
+ *   A, lda    device pointer, column-major, lower triangle read, not modified
+ *   S, lds    device pointer: S = A_GG - A_GI A_II^{-1} A_IG written in full
+ *             ((n - n_int) x (n - n_int), column-major, lds >= n - n_int)
+ *   stream    cudaStream_t (NULL = default stream); the call synchronizes it
+ *   msg       optional buffer (msg_cap bytes) for a one-line error reason
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the one array:
+ * calls whose work overlaps on the GPU (other threads or streams) race and
+ * must be serialized by the caller.  Errors: BDDC_EINVAL (sizes, null
+ * pointers, n > 1024), BDDC_ENOTSPD (A_II not positive definite), BDDC_ECUDA. */
+BDDC_API bddc_status bddc_schur_dense_static(int n, int n_int, const double *A, int lda, double *S, int lds,
+                                             void *stream, char *msg, int msg_cap);
+
 BDDC_API const char *bddc_status_str(bddc_status s);
 BDDC_API const char *bddc_last_error(const bddc_handle *h);
 
