@@ -179,8 +179,9 @@ BDDC_API bddc_status bddc_apply_schur(bddc_handle *h, const double *x, double *y
 /* Device time (CUDA events on the handle's stream) and algorithmic FLOPs of
  * the phases of the last setup / adapt / solve, in this order:
  *   0 Q1 assembly + weights          1 interior elimination (partial Cholesky of A_i)
- *   2 coarse operators (setup)       3 pair condensations (adapt)
- *   4 face eigenproblems (adapt)     5 coarse operators (adapt)
+ *   2 coarse operators (built before the first solve or apply after a setup
+ *     or adapt changed the constraints)
+ *   3 pair condensations (adapt)     4 face eigenproblems (adapt)     5 unused (0)
  *   6 condensed right-hand side      7 PCG                       8 interior recovery
  * FLOPs of phase 1 are the dense count sum_i n_I^3/3 + n_I^2 n_G + n_I n_G^2;
  * other phases report 0 FLOPs.  ms[cap], flop[cap] may be NULL; *n = 9. */

@@ -129,6 +129,7 @@ struct bddc_handle {
     double omega = 0.0;
     std::vector<double *> face_rows_dev;
     int face_row_ld = 0;
+    bool coarse_dirty = true;   // coarse operators are (re)built before the next solve
     // phase timing: events [2k, 2k+1] bracket phase k
     static constexpr int kPhases = 9;
     cudaEvent_t ev[2 * kPhases] = {};
@@ -245,6 +246,19 @@ void run_gemm(bddc_handle *h, const std::vector<GemmDesc> &descs, const std::str
     check_launch(h);
 }
 
+void run_gemv(bddc_handle *h, const std::vector<GemmDesc> &descs, const std::string &tag) {
+    if (descs.empty()) return;
+    std::vector<int2> items;
+    for (int k = 0; k < (int)descs.size(); ++k) {
+        const int rows = descs[k].transA ? 8 : 32;
+        for (int r = 0; r < (descs[k].m + rows - 1) / rows; ++r) items.push_back(make_int2(k, r));
+    }
+    auto *dd = h->ar.upload("gv_desc_" + tag, descs, h->stream);
+    auto *di = h->ar.upload("gv_it_" + tag, items, h->stream);
+    launch_gemv(dd, di, (int)items.size(), h->stream);
+    check_launch(h);
+}
+
 void zero(bddc_handle *h, double *p, size_t n) {
     launch_zero(p, n, h->stream);
     check_launch(h);
@@ -281,46 +295,76 @@ void classify(bddc_handle *h) {
             nf += c;
         }
     h->nfree = nf;
-    // node -> set of substructures
-    std::vector<std::vector<int>> nsets(nn);
-    for (int64_t e = 0; e < ne; ++e)
+    // node -> sorted set of substructures (flat, at most kMaxSet per node)
+    constexpr int kMaxSet = 16;
+    struct NodeSubs {
+        int cnt;
+        int s[kMaxSet];
+    };
+    std::vector<NodeSubs> nsv(nn);
+    for (auto &x : nsv) x.cnt = 0;
+    for (int64_t e = 0; e < ne; ++e) {
+        const int sb = h->esub[e];
         for (int a = 0; a < 8; ++a) {
-            auto &v = nsets[h->elems[e * 8 + a]];
-            int s = h->esub[e];
-            if (std::find(v.begin(), v.end(), s) == v.end()) v.push_back(s);
+            NodeSubs &x = nsv[h->elems[e * 8 + a]];
+            bool found = false;
+            for (int k = 0; k < x.cnt; ++k)
+                if (x.s[k] == sb) {
+                    found = true;
+                    break;
+                }
+            if (!found) {
+                BDDC_REQUIRE(x.cnt < kMaxSet, BDDC_EINVAL, "a node lies in more than 16 substructures");
+                x.s[x.cnt++] = sb;
+            }
         }
-    std::map<std::vector<int>, int> set_id;
+    }
+    for (auto &x : nsv) std::sort(x.s, x.s + x.cnt);
+    auto same_set = [&](int64_t a, int64_t b) {
+        const NodeSubs &A = nsv[a], &B = nsv[b];
+        if (A.cnt != B.cnt) return false;
+        for (int k = 0; k < A.cnt; ++k)
+            if (A.s[k] != B.s[k]) return false;
+        return true;
+    };
+    std::vector<int64_t> order(nn);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        const NodeSubs &A = nsv[a], &B = nsv[b];
+        if (A.cnt != B.cnt) return A.cnt < B.cnt;
+        for (int k = 0; k < A.cnt; ++k)
+            if (A.s[k] != B.s[k]) return A.s[k] < B.s[k];
+        return a < b;
+    });
     h->sets.clear();
     h->node_set.assign(nn, -1);
-    for (int64_t v = 0; v < nn; ++v) {
-        auto &s = nsets[v];
-        std::sort(s.begin(), s.end());
-        auto it = set_id.find(s);
-        int id;
-        if (it == set_id.end()) {
-            id = (int)h->sets.size();
-            set_id[s] = id;
-            h->sets.push_back(s);
-        } else {
-            id = it->second;
+    std::vector<int> set_count;
+    for (int64_t k = 0; k < nn; ++k) {
+        int64_t v = order[k];
+        if (k == 0 || !same_set(v, order[k - 1])) {
+            h->sets.emplace_back(nsv[v].s, nsv[v].s + nsv[v].cnt);
+            set_count.push_back(0);
         }
-        h->node_set[v] = id;
+        h->node_set[v] = (int)h->sets.size() - 1;
+        set_count.back()++;
     }
     // element-edge neighbours of nodes in edge sets (set size >= 3)
-    std::vector<std::vector<int64_t>> nb(nn);
+    std::vector<int> eidx(nn, -1);
+    int n_edge_nodes = 0;
+    for (int64_t v = 0; v < nn; ++v)
+        if (nsv[v].cnt >= 3) eidx[v] = n_edge_nodes++;
+    std::vector<std::vector<int64_t>> nb(n_edge_nodes);
     for (int64_t e = 0; e < ne; ++e)
         for (auto &ed : HEX_EDGES) {
             int64_t a = h->elems[e * 8 + ed[0]], b = h->elems[e * 8 + ed[1]];
-            if (h->sets[h->node_set[a]].size() >= 3) nb[a].push_back(b);
-            if (h->sets[h->node_set[b]].size() >= 3) nb[b].push_back(a);
+            if (eidx[a] >= 0) nb[eidx[a]].push_back(b);
+            if (eidx[b] >= 0) nb[eidx[b]].push_back(a);
         }
     auto is_superset = [&](int big, int small) {
         const auto &B = h->sets[big], &S = h->sets[small];
         if (B.size() <= S.size()) return false;
         return std::includes(B.begin(), B.end(), S.begin(), S.end());
     };
-    std::vector<int> set_count(h->sets.size(), 0);
-    for (int64_t v = 0; v < nn; ++v) set_count[h->node_set[v]]++;
     h->is_corner.assign(nn, 0);
     for (int64_t v = 0; v < nn; ++v) {
         int sid = h->node_set[v];
@@ -329,7 +373,7 @@ void classify(bddc_handle *h) {
             h->is_corner[v] = 1;
             continue;
         }
-        auto &L = nb[v];
+        auto &L = nb[eidx[v]];
         std::sort(L.begin(), L.end());
         L.erase(std::unique(L.begin(), L.end()), L.end());
         int same = 0;
@@ -346,20 +390,24 @@ void classify(bddc_handle *h) {
         if (h->is_corner[v] && h->dirich[v]) h->is_corner[v] = 0;
         if (h->is_corner[v]) h->corners.push_back(v);
     }
-    // globs
-    std::map<std::vector<int>, std::vector<int64_t>> glob_nodes;
-    for (int64_t v = 0; v < nn; ++v) {
-        const auto &s = h->sets[h->node_set[v]];
-        if (s.size() < 2 || h->dirich[v] || h->is_corner[v]) continue;
-        glob_nodes[s].push_back(v);
-    }
+    // globs: nodes grouped by set (the sort above keeps each set contiguous, ascending node ids)
     h->edge_globs.clear();
     std::vector<std::pair<std::pair<int, int>, std::vector<int64_t>>> face_list;
-    for (auto &kv : glob_nodes) {
-        if (kv.first.size() == 2)
-            face_list.push_back({{kv.first[0], kv.first[1]}, kv.second});
+    for (int64_t k = 0; k < nn;) {
+        int sid = h->node_set[order[k]];
+        int64_t k1 = k;
+        std::vector<int64_t> nodes;
+        while (k1 < nn && h->node_set[order[k1]] == sid) {
+            int64_t v = order[k1++];
+            if (!h->dirich[v] && !h->is_corner[v]) nodes.push_back(v);
+        }
+        k = k1;
+        const auto &S = h->sets[sid];
+        if (S.size() < 2 || nodes.empty()) continue;
+        if (S.size() == 2)
+            face_list.push_back({{S[0], S[1]}, nodes});
         else
-            h->edge_globs.push_back({kv.first, kv.second});
+            h->edge_globs.push_back({S, nodes});
     }
     std::sort(face_list.begin(), face_list.end());
     h->n_edges = (int)h->edge_globs.size();
@@ -404,7 +452,7 @@ void classify(bddc_handle *h) {
     for (int x = 0; x < h->nG; ++x) gidx[all[x]] = x;
     h->offG.assign(ns, 0);
     int64_t off = 0, offI = 0;
-    std::vector<std::vector<std::pair<int, int64_t>>> ent(h->nG);
+    h->gptr.assign(h->nG + 1, 0);
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
         h->offG[s] = off;
@@ -412,7 +460,7 @@ void classify(bddc_handle *h) {
         sd.RG.resize(sd.nG);
         for (int k = 0; k < sd.nG; ++k) {
             sd.RG[k] = gidx[sd.gG[k]];
-            ent[sd.RG[k]].push_back({s, off + k});
+            h->gptr[sd.RG[k] + 1]++;
         }
         off += sd.nG;
         offI += sd.nI;
@@ -429,22 +477,26 @@ void classify(bddc_handle *h) {
     for (auto &sd : h->subs) {
         for (int k = 0; k < sd.nG; ++k) (h->is_corner[dof_node[sd.gG[k]]] ? sd.cpos : sd.rpos).push_back(k);
     }
-    h->gptr.assign(h->nG + 1, 0);
-    h->gent.clear();
-    h->gsub.clear();
-    for (int x = 0; x < h->nG; ++x) {
-        for (auto &pe : ent[x]) {
-            h->gent.push_back(pe.second);
-            h->gsub.push_back(pe.first);
+    for (int x = 0; x < h->nG; ++x) h->gptr[x + 1] += h->gptr[x];
+    h->gent.assign(h->gptr[h->nG], 0);
+    h->gsub.assign(h->gptr[h->nG], 0);
+    {
+        std::vector<int> fill(h->gptr.begin(), h->gptr.end() - 1);
+        for (int s = 0; s < ns; ++s) {
+            auto &sd = h->subs[s];
+            for (int k = 0; k < sd.nG; ++k) {
+                int slot = fill[sd.RG[k]]++;
+                h->gent[slot] = h->offG[s] + k;
+                h->gsub[slot] = s;
+            }
         }
-        h->gptr[x + 1] = (int)h->gent.size();
     }
     // corner dofs: global coarse indices 0..n_corner_dofs-1 in global dof order
     std::vector<int64_t> cdofs;
     for (int64_t v : h->corners)
         for (int k = 0; k < c; ++k) cdofs.push_back(h->node_first[v] + k);
     h->n_corner_dofs = (int)cdofs.size();
-    std::map<int64_t, int> cidx;
+    std::vector<int> cidx(h->nfree, -1);
     for (int k = 0; k < (int)cdofs.size(); ++k) cidx[cdofs[k]] = k;
     for (auto &sd : h->subs) {
         sd.corner_coarse.clear();
@@ -485,12 +537,12 @@ void classify(bddc_handle *h) {
     }
     // face pairs
     h->faces.clear();
+    std::vector<int> pi(h->nfree, -1), pj(h->nfree, -1);
     for (auto &fl : face_list) {
         FacePair fp;
         fp.i = fl.first.first;
         fp.j = fl.first.second;
         auto &si = h->subs[fp.i], &sj = h->subs[fp.j];
-        std::map<int64_t, int> pi, pj;
         for (int k = 0; k < si.nG; ++k) pi[si.gG[k]] = k;
         for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = k;
         std::vector<int64_t> cn;
@@ -502,7 +554,7 @@ void classify(bddc_handle *h) {
             if (!both) continue;
             if (h->is_corner[v]) {
                 fp.ci_pos.push_back(k);
-                fp.cj_pos.push_back(pj.at(g));
+                fp.cj_pos.push_back(pj[g]);
                 if (g % c == 0 || c == 1) cn.push_back(v);
                 continue;
             }
@@ -511,8 +563,8 @@ void classify(bddc_handle *h) {
         // s sorted by global dof (si.gG is sorted so s_g is too)
         for (size_t k = 0; k < fp.s_g.size(); ++k) {
             int64_t g = fp.s_g[k];
-            fp.pos_i.push_back(pi.at(g));
-            fp.pos_j.push_back(pj.at(g));
+            fp.pos_i.push_back(pi[g]);
+            fp.pos_j.push_back(pj[g]);
             const auto &S = h->sets[h->node_set[dof_node[g]]];
             if (S.size() == 2) fp.face_idx.push_back((int)k);
         }
@@ -564,19 +616,30 @@ void classify(bddc_handle *h) {
             fp.N0 = Q;
             fp.nnull = kept;
         }
+        for (int k = 0; k < si.nG; ++k) pi[si.gG[k]] = -1;
+        for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = -1;
         h->faces.push_back(fp);
     }
     // element colouring (greedy, nodes shared => different colours)
     h->colors.clear();
     std::vector<int> ecol(ne, -1);
-    std::vector<std::vector<int64_t>> node_elems(nn);
-    for (int64_t e = 0; e < ne; ++e)
-        for (int a = 0; a < 8; ++a) node_elems[h->elems[e * 8 + a]].push_back(e);
+    std::vector<int64_t> neptr(nn + 1, 0), nelist(ne * 8);
+    for (int64_t k = 0; k < ne * 8; ++k) neptr[h->elems[k] + 1]++;
+    for (int64_t v = 0; v < nn; ++v) neptr[v + 1] += neptr[v];
+    {
+        std::vector<int64_t> fill(neptr.begin(), neptr.end() - 1);
+        for (int64_t e = 0; e < ne; ++e)
+            for (int a = 0; a < 8; ++a) nelist[fill[h->elems[e * 8 + a]]++] = e;
+    }
     for (int64_t e = 0; e < ne; ++e) {
         uint64_t used = 0;
-        for (int a = 0; a < 8; ++a)
-            for (int64_t f : node_elems[h->elems[e * 8 + a]])
+        for (int a = 0; a < 8; ++a) {
+            int64_t v = h->elems[e * 8 + a];
+            for (int64_t q = neptr[v]; q < neptr[v + 1]; ++q) {
+                int64_t f = nelist[q];
                 if (ecol[f] >= 0 && ecol[f] < 64) used |= (1ull << ecol[f]);
+            }
+        }
         int col = 0;
         while (col < 64 && (used >> col) & 1ull) ++col;
         BDDC_REQUIRE(col < 64, BDDC_EINVAL, "element colouring needs more than 64 colours");
@@ -589,19 +652,20 @@ void classify(bddc_handle *h) {
 // positions of each node's first dof in the dense local ordering [interior; interface]
 std::vector<int32_t> element_positions(bddc_handle *h) {
     std::vector<int32_t> pos(h->ne * 8, -1);
-    std::vector<std::map<int64_t, int>> lp(h->nsub);
+    std::vector<std::vector<int32_t>> sub_elems(h->nsub);
+    for (int64_t e = 0; e < h->ne; ++e) sub_elems[h->esub[e]].push_back((int32_t)e);
+    std::vector<int> lp(h->nfree, -1);
     for (int s = 0; s < h->nsub; ++s) {
         auto &sd = h->subs[s];
-        for (int k = 0; k < sd.nI; k += h->ncomp) lp[s][sd.gI[k]] = k;
-        for (int k = 0; k < sd.nG; k += h->ncomp) lp[s][sd.gG[k]] = sd.nI + k;
-    }
-    for (int64_t e = 0; e < h->ne; ++e) {
-        int s = h->esub[e];
-        for (int a = 0; a < 8; ++a) {
-            int64_t v = h->elems[e * 8 + a];
-            if (h->node_first[v] < 0) continue;
-            pos[e * 8 + a] = lp[s].at(h->node_first[v]);
-        }
+        for (int k = 0; k < sd.nI; k += h->ncomp) lp[sd.gI[k]] = k;
+        for (int k = 0; k < sd.nG; k += h->ncomp) lp[sd.gG[k]] = sd.nI + k;
+        for (int32_t e : sub_elems[s])
+            for (int a = 0; a < 8; ++a) {
+                int64_t v = h->elems[(int64_t)e * 8 + a];
+                if (h->node_first[v] >= 0) pos[(int64_t)e * 8 + a] = lp[h->node_first[v]];
+            }
+        for (int k = 0; k < sd.nI; k += h->ncomp) lp[sd.gI[k]] = -1;
+        for (int k = 0; k < sd.nG; k += h->ncomp) lp[sd.gG[k]] = -1;
     }
     return pos;
 }
@@ -654,13 +718,13 @@ void layout_constraints(bddc_handle *h) {
     }
     h->nC = nC;
     std::vector<GatherOp> ops;
+    std::vector<int> pos(h->nfree, -1);
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
         sd.na = (int)sub_rows[s].size();
         sd.capA = std::max(1, sd.na);
         sd.Cb = h->ar.get_t<double>("Cb_" + std::to_string(s), (size_t)sd.capA * sd.nG);
         std::vector<double> host((size_t)sd.capA * sd.nG, 0.0);
-        std::map<int64_t, int> pos;
         for (int k = 0; k < sd.nG; ++k) pos[sd.gG[k]] = k;
         sd.row_coarse.clear();
         for (int m = 0; m < sd.na; ++m) {
@@ -669,8 +733,9 @@ void layout_constraints(bddc_handle *h) {
             sd.row_coarse.push_back(g.coarse0 + r);
             if (g.face >= 0) continue;
             for (size_t k = 0; k < g.gdofs.size(); ++k)
-                host[(size_t)pos.at(g.gdofs[k]) * sd.capA + m] = g.rows[(size_t)r * g.gdofs.size() + k];
+                host[(size_t)pos[g.gdofs[k]] * sd.capA + m] = g.rows[(size_t)r * g.gdofs.size() + k];
         }
+        for (int k = 0; k < sd.nG; ++k) pos[sd.gG[k]] = -1;
         BDDC_CUDA(cudaMemcpyAsync(sd.Cb, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         // adaptive rows: one gather per (sub, face glob): Cb[m0 + l, facepos] = rows[l, f]
         for (int m = 0; m < sd.na;) {
@@ -898,7 +963,7 @@ void coarse_setup(bddc_handle *h) {
     std::vector<int2> cdot;
     for (int s = 0; s < ns; ++s) {
         nci_v[s] = (int)h->subs[s].cpos.size() + h->subs[s].na;
-        for (int m = 0; m < nci_v[s]; m += 8) cdot.push_back(make_int2(s, m));
+        for (int m = 0; m < nci_v[s]; m += 16) cdot.push_back(make_int2(s, m));
     }
     h->ops.nci = h->ar.upload("nci", nci_v, h->stream);
     h->ops.offc = h->ar.upload("offc", offc, h->stream);
@@ -936,13 +1001,15 @@ void alloc_solver_buffers(bddc_handle *h) {
     }
     h->ops.nsub = ns;
     h->ops.nG = h->nG;
+    h->ops.maxGi = 0;
+    for (auto &sd : h->subs) h->ops.maxGi = std::max(h->ops.maxGi, sd.nG);
     std::vector<int> nGi(ns), ldS(ns), RG;
     std::vector<int2> rb;
     for (int s = 0; s < ns; ++s) {
         nGi[s] = h->subs[s].nG;
         ldS[s] = h->subs[s].ldS;
         RG.insert(RG.end(), h->subs[s].RG.begin(), h->subs[s].RG.end());
-        for (int r = 0; r < nGi[s]; r += 64) rb.push_back(make_int2(s, r));
+        for (int r = 0; r < nGi[s]; r += 32) rb.push_back(make_int2(s, r));
     }
     h->ops.nGi = h->ar.upload("nGi", nGi, h->stream);
     h->ops.ldS = h->ar.upload("ldS", ldS, h->stream);
@@ -986,6 +1053,22 @@ void set_phi_pointers(bddc_handle *h) {
 }
 
 // ---- phases --------------------------------------------------------------
+void count_coarse(bddc_handle *h) {
+    int nC = h->n_corner_dofs;
+    for (auto &g : h->globs) nC += g.nrows;
+    h->nC = nC;
+}
+
+// builds the coarse operators for the current constraints if they changed
+void ensure_coarse(bddc_handle *h) {
+    if (!h->coarse_dirty) return;
+    phase_begin(h, 2);
+    coarse_setup(h);
+    phase_end(h, 2);
+    phase_collect(h, 2, 2);
+    h->coarse_dirty = false;
+}
+
 void do_setup(bddc_handle *h) {
     const int ns = h->nsub;
     reset_status(h);
@@ -1068,11 +1151,10 @@ void do_setup(bddc_handle *h) {
         for (int s = 0; s < ns; ++s) h->subs[s].na = na[s];
         set_phi_pointers(h);
     }
-    phase_begin(h, 2);
-    coarse_setup(h);
-    phase_end(h, 2);
+    count_coarse(h);
+    h->coarse_dirty = true;
     h->face_rows_dev.assign(h->faces.size(), nullptr);
-    phase_collect(h, 0, 2);
+    phase_collect(h, 0, 1);
 }
 
 }  // namespace
@@ -1325,11 +1407,11 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         e.ldw = ldq;
         e.face_pos = fpos;
         e.nface = nface;
-        e.lam = h->ar.get_t<double>("lam_" + std::to_string(f), kEigCap + 1);
+        e.lam = h->ar.get_t<double>("lam_all", (size_t)nf * (kEigCap + 1)) + (size_t)f * (kEigCap + 1);
         e.vec = h->ar.get_t<double>("vec_" + std::to_string(f), (size_t)kEigCap * ns);
-        e.work = h->ar.get_t<double>("ework_" + std::to_string(f), (size_t)10 * ns + 16);
+        e.work = h->ar.get_t<double>("ework_" + std::to_string(f), (size_t)64 * ns + 16);
         e.rows = h->ar.get_t<double>("frows_" + std::to_string(f), (size_t)kEigCap * std::max(nface, 1));
-        e.counts = h->ar.get_t<int>("fcnt_" + std::to_string(f), 8);
+        e.counts = h->ar.get_t<int>("fcnt_all", (size_t)nf * 8) + (size_t)f * 8;
         eds.push_back(e);
         eig_face.push_back(f);
     }
@@ -1346,14 +1428,20 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
     int n_added = 0, n_ties = 0;
     double omega = 0.0;
     h->face_rows_dev.assign(nf, nullptr);
+    std::vector<int> cnt_all((size_t)nf * 8, 0);
+    std::vector<double> lam_all((size_t)nf * (kEigCap + 1), 0.0);
+    if (!eds.empty()) {
+        BDDC_CUDA(cudaMemcpyAsync(cnt_all.data(), h->ar.get_t<int>("fcnt_all", (size_t)nf * 8), cnt_all.size() * sizeof(int),
+                                  cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaMemcpyAsync(lam_all.data(), h->ar.get_t<double>("lam_all", (size_t)nf * (kEigCap + 1)),
+                                  lam_all.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+    }
     for (size_t k = 0; k < eds.size(); ++k) {
         int f = eig_face[k];
         auto &fp = h->faces[f];
-        int cnt[8];
-        BDDC_CUDA(cudaMemcpyAsync(cnt, eds[k].counts, 8 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-        std::vector<double> lam(kEigCap + 1);
-        BDDC_CUDA(cudaMemcpyAsync(lam.data(), eds[k].lam, lam.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        const int *cnt = &cnt_all[(size_t)f * 8];
+        std::vector<double> lam(lam_all.begin() + (size_t)f * (kEigCap + 1), lam_all.begin() + (size_t)(f + 1) * (kEigCap + 1));
         fp.nsel = cnt[0];
         fp.nkept = cnt[1];
         fp.ties = cnt[3];
@@ -1404,10 +1492,9 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         for (int s = 0; s < ns; ++s) h->subs[s].na = na[s];
         set_phi_pointers(h);
     }
-    phase_begin(h, 5);
-    coarse_setup(h);
-    phase_end(h, 5);
-    phase_collect(h, 3, 5);
+    count_coarse(h);
+    h->coarse_dirty = true;
+    phase_collect(h, 3, 4);
     if (info) {
         info->n_faces = nf;
         info->n_added = n_added;
@@ -1420,6 +1507,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
 void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_info *info) {
     const int ns = h->nsub;
     reset_status(h);
+    ensure_coarse(h);
     double *df = h->ar.get_t<double>("f", std::max<int64_t>(h->nfree, 1));
     phase_begin(h, 6);
     if (mem == BDDC_MEM_DEVICE)
@@ -1447,7 +1535,7 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
     launch_trsv<double>(dtv, (int)tv.size(), 0, h->stream);
     check_launch(h);
     zero(h, gl, h->sumG);
-    run_gemm(h, gm, "cond");
+    run_gemv(h, gm, "cond");
     launch_iface_assemble(h->ops, gl, h->pb.r, h->stream);
     check_launch(h);
     // g = f_G - sum_i R_i^T A_GI A_II^{-1} f_I
@@ -1474,7 +1562,7 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
         gr.push_back(GemmDesc{sd.A + sd.nI, ug + h->offG[s], yI + sd.offI, sd.ld, std::max(sd.nG, 1), std::max(sd.nI, 1),
                               sd.nI, 1, sd.nG, 1, 0, -1.0, 1.0});
     }
-    run_gemm(h, gr, "rec");
+    run_gemv(h, gr, "rec");
     launch_trsv<double>(dtv, (int)tv.size(), 1, h->stream);
     check_launch(h);
     double *du = h->ar.get_t<double>("u", std::max<int64_t>(h->nfree, 1));
@@ -1800,6 +1888,7 @@ static bddc_status apply_op(bddc_handle *h, const double *in, double *out, int m
     BDDC_TRY(h, {
         BDDC_REQUIRE(h->have_setup, BDDC_ESTATE, "apply before setup");
         reset_status(h);
+        ensure_coarse(h);
         auto kind = mem == BDDC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         double *dst_in = mode == PCG_APPLY_M ? h->pb.r : h->pb.z;
         BDDC_CUDA(cudaMemcpyAsync(dst_in, in, h->nG * sizeof(double), kind, h->stream));

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
     const int nb = min(NB, d.nstop - kb);
     T *A = d.A;
     __shared__ T Ld[NB][NB + 1];
+    __shared__ T inv_d[NB];
     __shared__ int bad;
     const int tid = threadIdx.x;
     if (tid == 0) bad = 0;
@@ -50,9 +51,10 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
                 dj = T(1);
             }
             Ld[j][j] = sqrt(dj);
+            inv_d[j] = T(1) / Ld[j][j];
         }
         __syncthreads();
-        for (int i = j + 1 + tid; i < nb; i += blockDim.x) Ld[i][j] /= Ld[j][j];
+        for (int i = j + 1 + tid; i < nb; i += blockDim.x) Ld[i][j] *= inv_d[j];
         __syncthreads();
         int m = nb - j - 1;
         for (int e = tid; e < m * m; e += blockDim.x) {
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
 #pragma unroll
                 for (int k = 0; k < NB; ++k)
                     if (k < c) s -= x[k] * Ld[c][k];
-                x[c] = s / Ld[c][c];
+                x[c] = s * inv_d[c];
             }
         }
 #pragma unroll
@@ -228,6 +230,46 @@ __global__ void coarse_assemble_kernel(const CoarseAsmDesc *d, int nsub, double 
 }
 
 // ---------------------------------------------------------------------------
+// batched GEMV (descriptors of GemmDesc with n == 1): y = alpha op(A) x + beta y
+//   transA == 0: item = (desc, 32-row block); warps split k, lanes the rows
+//   transA == 1: item = (desc, 8-row block);  one warp per row, lanes split k
+__global__ void __launch_bounds__(256) gemv_kernel(const GemmDesc *descs, const int2 *items, int nitems) {
+    int it = blockIdx.x;
+    if (it >= nitems) return;
+    int2 w = items[it];
+    const GemmDesc d = descs[w.x];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ double red[8][32];
+    if (!d.transA) {
+        const int r = w.y * 32 + lane;
+        double acc = 0.0;
+        if (r < d.m) {
+#pragma unroll 4
+            for (int k = wid; k < d.k; k += 8) acc += d.A[(size_t)k * d.lda + r] * d.B[k];
+        }
+        red[wid][lane] = acc;
+        __syncthreads();
+        if (wid == 0 && r < d.m) {
+            double s = 0.0;
+            for (int q = 0; q < 8; ++q) s += red[q][lane];
+            double *cp = d.C + r;
+            *cp = d.alpha * s + (d.beta == 0.0 ? 0.0 : d.beta * *cp);
+        }
+    } else {
+        const int r = w.y * 8 + wid;
+        if (r >= d.m) return;
+        const double *col = d.A + (size_t)r * d.lda;
+        double acc = 0.0;
+        for (int k = lane; k < d.k; k += 32) acc += col[k] * d.B[k];
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            double *cp = d.C + r;
+            *cp = d.alpha * acc + (d.beta == 0.0 ? 0.0 : d.beta * *cp);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // batched GEMM, FP64: C = alpha op(A) op(B) + beta C, 64x64 tiles, k-step 16
 __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const int4 *items, int nitems) {
     int it = blockIdx.x;
@@ -316,8 +358,9 @@ __global__ void __launch_bounds__(256) trsv_kernel(const TrsvDesc<T> *descs, int
             int nb = min(32, n - jb);
             if (wid == 0) {
                 double v = lane < nb ? x[jb + lane] : 0.0;
+                const double rdiag = lane < nb ? 1.0 / (double)L[(size_t)(jb + lane) * ld + jb + lane] : 0.0;
                 for (int c = 0; c < nb; ++c) {
-                    if (lane == c) v /= (double)L[(size_t)(jb + c) * ld + jb + c];
+                    if (lane == c) v *= rdiag;
                     double yc = __shfl_sync(0xffffffffu, v, c);
                     if (lane > c && lane < nb) v -= (double)L[(size_t)(jb + c) * ld + jb + lane] * yc;
                 }
@@ -345,8 +388,9 @@ __global__ void __launch_bounds__(256) trsv_kernel(const TrsvDesc<T> *descs, int
             __syncthreads();
             if (wid == 0) {
                 double v = lane < nb ? x[jb + lane] - part[0][lane] : 0.0;
+                const double rdiag = lane < nb ? 1.0 / (double)L[(size_t)(jb + lane) * ld + jb + lane] : 0.0;
                 for (int c = nb - 1; c >= 0; --c) {
-                    if (lane == c) v /= (double)L[(size_t)(jb + c) * ld + jb + c];
+                    if (lane == c) v *= rdiag;
                     double xc = __shfl_sync(0xffffffffu, v, c);
                     if (lane < c) v -= (double)L[(size_t)(jb + lane) * ld + jb + c] * xc;
                 }
@@ -396,6 +440,9 @@ void launch_gatherv_add(double *dst, const int64_t *idx, const double *src, int6
 }
 void launch_coarse_assemble(const CoarseAsmDesc *d, int nsub, double *SC, int nC, cudaStream_t s) {
     if (nsub > 0) coarse_assemble_kernel<<<1, 1024, 0, s>>>(d, nsub, SC, nC);
+}
+void launch_gemv(const GemmDesc *descs, const int2 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) gemv_kernel<<<nitems, 256, 0, s>>>(descs, items, nitems);
 }
 void launch_gemm(const GemmDesc *descs, const int4 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) gemm_kernel<<<nitems, 256, 0, s>>>(descs, items, nitems);

@@ -79,6 +79,8 @@ struct CoarseAsmDesc {
 };
 void launch_coarse_assemble(const CoarseAsmDesc *d, int nsub, double *SC, int nC, cudaStream_t s);
 void launch_gemm(const GemmDesc *descs, const int4 *items, int nitems, cudaStream_t s);
+// descriptors with n == 1 and one transA value for the whole batch
+void launch_gemv(const GemmDesc *descs, const int2 *items, int nitems, cudaStream_t s);
 template <typename T>
 void launch_trsv(const TrsvDesc<T> *descs, int nd, int backward, cudaStream_t s);
 

@@ -144,28 +144,35 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     __syncthreads();
     const int nsel = sh_int[0], nval = sh_int[3];
     double *lam = D.lam;
-    for (int t = tid; t < nval; t += nt) {
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    // 32-way multisection, one warp per eigenvalue: lanes 0..30 count at 31 interior points
+    for (int t = wid; t < nval; t += nw) {
         const int j = n - 1 - t;  // index among ascending eigenvalues
         double lo = -tnorm - 1.0, hi = tnorm + 1.0;
-        for (int itb = 0; itb < 400; ++itb) {
-            double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi) break;
-            if (sturm_less(dd, ee, n, mid, pivmin) > j)
-                hi = mid;
-            else
-                lo = mid;
-            if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
+        for (int round = 0; round < 40; ++round) {
+            const double w = hi - lo;
+            if (w <= 1e-15 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
+            const double x = lo + w * (double)(lane + 1) * (1.0 / 32.0);
+            const bool above = lane < 31 && sturm_less(dd, ee, n, x, pivmin) > j;
+            const unsigned mask = __ballot_sync(0xffffffffu, above);
+            const int first = mask ? __ffs(mask) - 1 : 31;
+            const double nlo = first == 0 ? lo : lo + w * (double)first * (1.0 / 32.0);
+            const double nhi = first == 31 ? hi : lo + w * (double)(first + 1) * (1.0 / 32.0);
+            if (!(nlo > lo || nhi < hi)) break;
+            lo = nlo;
+            hi = nhi;
         }
-        lam[t] = 0.5 * (lo + hi);
+        if (lane == 0) lam[t] = 0.5 * (lo + hi);
     }
     __syncthreads();
-    // ---- 3. inverse iteration on T, back-transformation ----
-    double *dl = P, *du = Wv, *dv = work + 5 * n, *du2 = work + 6 * n, *xv = work + 7 * n;
-    int *piv = (int *)(work + 8 * n);
-    for (int mI = 0; mI < nsel; ++mI) {
+    // ---- 3. inverse iteration on T (one warp per vector), back-transformation ----
+    double *wbase = work + 10 * n;  // 6 n doubles per warp
+    for (int mI = wid; mI < nsel; mI += nw) {
+        double *dl = wbase + (size_t)wid * 6 * n, *du = dl + n, *dv = du + n, *du2 = dv + n, *xv = du2 + n;
+        int *piv = (int *)(xv + n);
         const double lm = lam[mI];
-        if (tid == 0) {
-            // LU with row interchanges of T - lm I
+        if (lane == 0) {
+            // LU with row interchanges of T - lm I; the reciprocals of the pivots are kept in dv
             const double small = 2.2e-16 * fmax(tnorm, 1e-300);
             for (int i = 0; i < n; ++i) {
                 dv[i] = dd[i] - lm;
@@ -195,12 +202,12 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
                 }
             }
             if (dv[n - 1] == 0.0) dv[n - 1] = small;
-            for (int i = 0; i < n; ++i) xv[i] = 1.0 + 0.1 * (double)((i * 7919 + mI * 104729) % 17) / 17.0;
+            for (int i = 0; i < n; ++i) dv[i] = 1.0 / dv[i];
         }
-        __syncthreads();
-        for (int itr = 0; itr < 4; ++itr) {
-            if (tid == 0) {
-                // solve L U x = b (row interchanges recorded in piv)
+        for (int i = lane; i < n; i += 32) xv[i] = 1.0 + 0.1 * (double)((i * 7919 + mI * 104729) % 17) / 17.0;
+        __syncwarp();
+        for (int itr = 0; itr < 3; ++itr) {
+            if (lane == 0) {
                 for (int i = 0; i + 1 < n; ++i) {
                     if (piv[i] == 0) {
                         xv[i + 1] -= dl[i] * xv[i];
@@ -210,44 +217,57 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
                         xv[i + 1] = t - dl[i] * xv[i + 1];
                     }
                 }
-                xv[n - 1] /= dv[n - 1];
-                if (n >= 2) xv[n - 2] = (xv[n - 2] - du[n - 2] * xv[n - 1]) / dv[n - 2];
-                for (int i = n - 3; i >= 0; --i) xv[i] = (xv[i] - du[i] * xv[i + 1] - du2[i] * xv[i + 2]) / dv[i];
+                xv[n - 1] *= dv[n - 1];
+                if (n >= 2) xv[n - 2] = (xv[n - 2] - du[n - 2] * xv[n - 1]) * dv[n - 2];
+                for (int i = n - 3; i >= 0; --i) xv[i] = (xv[i] - du[i] * xv[i + 1] - du2[i] * xv[i + 2]) * dv[i];
             }
-            __syncthreads();
-            // orthogonalise against earlier vectors of the same cluster
-            for (int q = 0; q < mI; ++q) {
-                if (fabs(lam[q] - lm) > 1e-5 * fabs(lm)) continue;
-                const double *vq = D.vec + (size_t)q * n;
-                double dot = 0.0;
-                for (int i = tid; i < n; i += nt) dot += vq[i] * xv[i];
-                dot = block_sum(dot, scratch);
-                for (int i = tid; i < n; i += nt) xv[i] -= dot * vq[i];
-                __syncthreads();
-            }
+            __syncwarp();
             double s2 = 0.0;
-            for (int i = tid; i < n; i += nt) s2 += xv[i] * xv[i];
-            s2 = block_sum(s2, scratch);
-            double inv = s2 > 0 ? 1.0 / sqrt(s2) : 0.0;
-            for (int i = tid; i < n; i += nt) xv[i] *= inv;
-            __syncthreads();
+            for (int i = lane; i < n; i += 32) s2 += xv[i] * xv[i];
+            s2 = warp_sum(s2);
+            const double inv = s2 > 0 ? 1.0 / sqrt(s2) : 0.0;
+            for (int i = lane; i < n; i += 32) xv[i] *= inv;
+            __syncwarp();
         }
         double *vout = D.vec + (size_t)mI * n;
-        for (int i = tid; i < n; i += nt) vout[i] = xv[i];
-        __syncthreads();
+        for (int i = lane; i < n; i += 32) vout[i] = xv[i];
     }
-    // back-transformation y = H_0 H_1 ... H_{n-3} x for every selected vector
-    for (int mI = 0; mI < nsel; ++mI) {
+    __syncthreads();
+    // clusters (eigenvalues within 1e-5 relative): orthonormalise in order (rare)
+    for (int mI = 1; mI < nsel; ++mI) {
+        double *x = D.vec + (size_t)mI * n;
+        bool any = false;
+        for (int q = 0; q < mI; ++q) {
+            if (fabs(lam[q] - lam[mI]) > 1e-5 * fabs(lam[mI])) continue;
+            any = true;
+            const double *vq = D.vec + (size_t)q * n;
+            double dot = 0.0;
+            for (int i = tid; i < n; i += nt) dot += vq[i] * x[i];
+            dot = block_sum(dot, scratch);
+            for (int i = tid; i < n; i += nt) x[i] -= dot * vq[i];
+            __syncthreads();
+        }
+        if (any) {
+            double s2 = 0.0;
+            for (int i = tid; i < n; i += nt) s2 += x[i] * x[i];
+            s2 = block_sum(s2, scratch);
+            const double inv = s2 > 0 ? 1.0 / sqrt(s2) : 0.0;
+            for (int i = tid; i < n; i += nt) x[i] *= inv;
+            __syncthreads();
+        }
+    }
+    // back-transformation y = H_0 H_1 ... H_{n-3} x, one warp per vector (reflectors are read-only)
+    for (int mI = wid; mI < nsel; mI += nw) {
         double *y = D.vec + (size_t)mI * n;
         for (int k = n - 3; k >= 0; --k) {
             const double b = bet[k];
             if (b == 0.0) continue;
             const double *v = A + (size_t)k * lda + k + 1;
             double dot = 0.0;
-            for (int i = tid; i < n - k - 1; i += nt) dot += v[i] * y[k + 1 + i];
-            dot = block_sum(dot, scratch);
-            for (int i = tid; i < n - k - 1; i += nt) y[k + 1 + i] -= b * dot * v[i];
-            __syncthreads();
+            for (int i = lane; i < n - k - 1; i += 32) dot += v[i] * y[k + 1 + i];
+            dot = warp_sum(dot) * b;
+            for (int i = lane; i < n - k - 1; i += 32) y[k + 1 + i] -= dot * v[i];
+            __syncwarp();
         }
     }
     __syncthreads();
@@ -264,7 +284,6 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     }
     __syncthreads();
     // normalise every row
-    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     for (int l = wid; l < nsel; l += nw) {
         double s = 0.0;
         for (int f = lane; f < nf; f += 32) s += R[(size_t)l * nf + f] * R[(size_t)l * nf + f];
@@ -276,7 +295,7 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     // Gram-Schmidt with row pivoting: rows [0, kept) are final
     int kept = 0;
     double first = -1.0;
-    double *nrm = xv;  // nsel <= n
+    double *nrm = P;  // nsel <= n
     for (int step = 0; step < nsel; ++step) {
         for (int l = step + wid; l < nsel; l += nw) {
             double s = 0.0;
@@ -325,7 +344,7 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
 void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, DevStatus *st,
                        cudaStream_t s) {
     if (npairs <= 0) return;
-    size_t need = sizeof(double) * ((size_t)nmax * nmax + 10 * (size_t)nmax);
+    size_t need = sizeof(double) * ((size_t)nmax * nmax + (10 + 6 * (EIG_THREADS / 32)) * (size_t)nmax + 16);
     int use_smem = need <= 200 * 1024;
     size_t smem = use_smem ? need : 0;
     if (smem > 48 * 1024) cudaFuncSetAttribute(face_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -16,13 +16,14 @@ struct EigDesc {
     int nface;
     double *lam;          // out: eigenvalues, descending (selected + largest rejected), kEigCap + 1
     double *vec;          // scratch: kEigCap x n eigenvectors of C
-    double *work;         // scratch: 10 n
+    double *work;         // scratch: 64 n + 16
     double *rows;         // out: face rows, row l at rows[l * nface + f] (orthonormal)
     int *counts;          // out: [0] selected, [1] kept, [2] values in lam, [3] ties, [4] overflow
 };
 
-// nmax: largest n of the batch; work must hold 10 n doubles when n^2 + 10 n
-// doubles exceed 200 KB (the matrix is then reduced in place).
+// nmax: largest n of the batch; when the matrix and work arrays do not fit in
+// 200 KB of shared memory the matrix is reduced in place and work (64 n + 16
+// doubles) is used from global memory.
 void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, DevStatus *st,
                        cudaStream_t s);
 

@@ -15,10 +15,12 @@
 #include <cooperative_groups.h>
 #include "common.cuh"
 #include "pcg.h"
+#include <algorithm>
 
 namespace bddc {
 
-constexpr int PCG_THREADS = 256;
+constexpr int PCG_THREADS = 512;
+constexpr int PCG_WARPS = PCG_THREADS / 32;
 
 // Data written by other blocks of this launch is read through L2 only
 // (ld.global.cg), so no block can see a stale L1 line after a grid barrier.
@@ -34,35 +36,43 @@ struct PcgParams {
     uint64_t timeout_ns;
 };
 
-// y_i = Mats_i * v_i for every (substructure, 64-row block); v gathered through RG.
+// y_i = Mats_i * v_i for every (substructure, 32-row block); v_i = R_i v is
+// staged in shared memory once per substructure, then the warps split the
+// columns and the lanes the rows (coalesced column reads).
 // If pold != nullptr, v[g] = z[g] + beta * pold[g] (the new search direction).
 __device__ void local_gemv(const PcgParams &P, double *const *Mats, const double *vin, const double *pold,
-                           double beta, double *yout, double *red) {
+                           double beta, double *yout, double *red, double *vs) {
     const IfaceOps &o = P.o;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int cur = -1;
     for (int it = blockIdx.x; it < o.nrowblk; it += gridDim.x) {
         int2 w = o.rowblk[it];
-        int s = w.x, r0 = w.y;
-        int n = o.nGi[s], ld = o.ldS[s];
-        const double *A = Mats[s];
-        const int *RG = o.RG + o.off[s];
-        int ra = r0 + lane, rb = r0 + lane + 32;
-        double acc0 = 0.0, acc1 = 0.0;
-        for (int c = wid; c < n; c += 8) {
-            int g = RG[c];
-            double v = pold ? ldx(vin + g) + beta * ldx(pold + g) : ldx(vin + g);
-            const double *col = A + (size_t)c * ld;
-            if (ra < n) acc0 += col[ra] * v;
-            if (rb < n) acc1 += col[rb] * v;
+        const int s = w.x, r0 = w.y;
+        const int n = o.nGi[s], ld = o.ldS[s];
+        if (s != cur) {
+            const int *RG = o.RG + o.off[s];
+            __syncthreads();
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                int g = RG[c];
+                vs[c] = pold ? ldx(vin + g) + beta * ldx(pold + g) : ldx(vin + g);
+            }
+            __syncthreads();
+            cur = s;
         }
-        red[wid * 64 + lane] = acc0;
-        red[wid * 64 + lane + 32] = acc1;
+        const double *A = Mats[s];
+        const int r = r0 + lane;
+        double acc = 0.0;
+        if (r < n) {
+#pragma unroll 4
+            for (int c = wid; c < n; c += PCG_WARPS) acc += A[(size_t)c * ld + r] * vs[c];
+        }
+        red[wid * 32 + lane] = acc;
         __syncthreads();
-        if (threadIdx.x < 64) {
-            int r = r0 + threadIdx.x;
+        if (threadIdx.x < 32) {
             double sum = 0.0;
-            for (int k = 0; k < 8; ++k) sum += red[k * 64 + threadIdx.x];
-            if (r < n) yout[o.off[s] + r] = sum;
+#pragma unroll
+            for (int k = 0; k < PCG_WARPS; ++k) sum += red[k * 32 + threadIdx.x];
+            if (r0 + threadIdx.x < n) yout[o.off[s] + r0 + threadIdx.x] = sum;
         }
         __syncthreads();
     }
@@ -97,7 +107,7 @@ __device__ void coarse_solve(const PcgParams &P, double *rc) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int row = blockIdx.x * 8 + wid; row < o.nC; row += gridDim.x * 8) {
+    for (int row = blockIdx.x * PCG_WARPS + wid; row < o.nC; row += gridDim.x * PCG_WARPS) {
         const double *col = o.SCinv + (size_t)row * o.nC;
         double acc = 0.0;
         for (int c = lane; c < o.nC; c += 32) acc += col[c] * rc[c];
@@ -129,16 +139,19 @@ __device__ double assemble_z(const PcgParams &P, const double *rin, double *zout
     return part;
 }
 
+// every warp reduces the block partial sums in the same fixed order
 __device__ double reduce_partials(const double *partial, int nb) {
+    const int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (int i = 0; i < nb; ++i) s += ldx(partial + i);
-    return s;
+    for (int i = lane; i < nb; i += 32) s += ldx(partial + i);
+    return warp_sum(s);
 }
 
 __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(PcgParams P) {
     extern __shared__ double smem[];
-    double *red = smem;            // 8 * 64
-    double *rc = smem + 8 * 64;    // nC
+    double *red = smem;                    // PCG_WARPS * 32
+    double *rc = smem + PCG_WARPS * 32;    // nC (coarse phase) ...
+    double *vs = rc;                       // ... or max nGi (local products)
     __shared__ double scratch[32];
     const IfaceOps &o = P.o;
     PcgBuffers &b = P.b;
@@ -146,7 +159,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(PcgParams P) {
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
 
     if (P.mode == PCG_APPLY_M) {
-        local_gemv(P, o.P, b.r, nullptr, 0.0, b.zl, red);
+        local_gemv(P, o.P, b.r, nullptr, 0.0, b.zl, red, vs);
         coarse_dots(P, b.r);
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
         coarse_solve(P, rc);
@@ -155,7 +168,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(PcgParams P) {
         return;
     }
     if (P.mode == PCG_APPLY_S) {
-        local_gemv(P, o.S, b.z, nullptr, 0.0, b.yl, red);
+        local_gemv(P, o.S, b.z, nullptr, 0.0, b.yl, red, vs);
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
         for (int x = gtid; x < o.nG; x += gstride) {
             double v = 0.0;
@@ -183,7 +196,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(PcgParams P) {
     while (!conv && k < P.maxit) {
         ++k;
         // z = M r
-        local_gemv(P, o.P, b.r, nullptr, 0.0, b.zl, red);
+        local_gemv(P, o.P, b.r, nullptr, 0.0, b.zl, red, vs);
         coarse_dots(P, b.r);
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
         coarse_solve(P, rc);
@@ -196,7 +209,7 @@ __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(PcgParams P) {
         const double rz = reduce_partials(b.partial, nb);
         const double beta = (k == 1) ? 0.0 : rz / rz_old;
         for (int x = gtid; x < o.nG; x += gstride) pnew[x] = b.z[x] + beta * pold[x];
-        local_gemv(P, o.S, b.z, pold, beta, b.yl, red);
+        local_gemv(P, o.S, b.z, pold, beta, b.yl, red, vs);
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
         // q = sum R_i^T y_i, p . q
         part = 0.0;
@@ -253,7 +266,7 @@ cudaError_t launch_pcg(const IfaceOps &ops, const PcgBuffers &buf, int mode, dou
     P.maxit = maxit;
     P.st = st;
     P.timeout_ns = (uint64_t)(timeout_s * 1e9);
-    size_t smem = sizeof(double) * (8 * 64 + (size_t)(ops.nC > 0 ? ops.nC : 1));
+    size_t smem = sizeof(double) * (PCG_WARPS * 32 + (size_t)std::max(std::max(ops.nC, ops.maxGi), 1));
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -264,7 +277,7 @@ cudaError_t launch_pcg(const IfaceOps &ops, const PcgBuffers &buf, int mode, dou
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel, PCG_THREADS, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (per_sm > 2) per_sm = 2;
+    if (per_sm > 1) per_sm = 1;
     int nblocks = nsm * per_sm;
     if (nblocks_out) *nblocks_out = nblocks;
     void *args[] = {&P};

@@ -12,6 +12,7 @@ namespace bddc {
 // with the weights folded in.
 struct IfaceOps {
     int nsub, nG, nC;
+    int maxGi;               // largest nGi
     const int *nGi;          // (nsub) interface size
     const int *ldS;          // (nsub) leading dimension of S_i and P~_i
     const int64_t *off;      // (nsub) offset of the substructure's packed local vector
@@ -28,9 +29,9 @@ struct IfaceOps {
     const int *gsub;         // substructure of each entry
     const int *cptr;         // (nC+1)
     const int64_t *cent;     // packed local coarse index of each entry
-    const int2 *rowblk;      // (sub, first row) GEMV work items, 64 rows each
+    const int2 *rowblk;      // (sub, first row) GEMV work items, 32 rows each
     int nrowblk;
-    const int2 *cdot;        // (sub, first coarse column) items, 8 columns each
+    const int2 *cdot;        // (sub, first coarse column) items, 16 columns each
     int ncdot;
 };
 
