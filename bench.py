@@ -99,6 +99,17 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, world):
+    """The slowest rank's value (replicas run concurrently; the job takes the max)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_0910_5863_gb300 import problems as P
@@ -153,12 +164,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = solver.launch_count() - launches0
-    t_step = sum(times) / len(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_step], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(sum(times) / len(times), world)
 
     # end-to-end through the C ABI with host buffers (mesh and f from host, u back to host)
     mesh_host = [np.ascontiguousarray(prob.xyz), np.ascontiguousarray(prob.elems, dtype=np.int64),
