@@ -110,26 +110,18 @@ def max_over_ranks(value, world):
     return float(t.item())
 
 
-def run_gpu(args, rank, world, local_rank):
+def _arm(args, precision, prob, dev_arrays, f_host, world, local_rank):
+    """Times K steps of one precision arm; returns (seconds per step, phase stats, info, launches, clocks)."""
     import torch
-    from paper_0910_5863_gb300 import problems as P
     from paper_0910_5863_gb300 import bddc as B
 
-    torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    prob = P.config_adaptive_poisson(seed=args.seed)
-    # inputs resident in HBM
-    d_xyz = torch.from_numpy(np.ascontiguousarray(prob.xyz)).to(dev)
-    d_el = torch.from_numpy(np.ascontiguousarray(prob.elems, dtype=np.int64)).to(dev)
-    d_coef = torch.from_numpy(np.ascontiguousarray(prob.coef)).to(dev)
-    d_sub = torch.from_numpy(np.ascontiguousarray(prob.elem_sub, dtype=np.int32)).to(dev)
-    d_dir = torch.from_numpy(np.ascontiguousarray(prob.dirichlet, dtype=np.uint8)).to(dev)
-    f_host = B.free_load_vector(prob)
+    d_xyz, d_el, d_coef, d_sub, d_dir = dev_arrays
     d_f = torch.from_numpy(f_host).to(dev)
     d_u = torch.zeros_like(d_f)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    solver = B.Solver(tol=1e-8, stream=stream.cuda_stream)
+    solver = B.Solver(precision=precision, tol=1e-8, stream=stream.cuda_stream)
 
     def step():
         solver.set_mesh(prob.ncomp, d_xyz, d_el, d_coef, prob.nu, d_sub, prob.nsub, d_dir)
@@ -165,8 +157,45 @@ def run_gpu(args, rank, world, local_rank):
     clk = clocks.stop()
     launches = solver.launch_count() - launches0
     t_step = max_over_ranks(sum(times) / len(times), world)
+    return solver, t_step, phases, ad, info, launches, clk
 
-    # end-to-end through the C ABI with host buffers (mesh and f from host, u back to host)
+
+def _phase_summary(phases):
+    return {k: round(sum(m for m, _ in v) / len(v), 4) for k, v in phases.items()}
+
+
+def _roofline(phases, phase, kernel, fp64_peak, src, bf16):
+    ph = phases[phase]
+    ms = sum(m for m, _ in ph) / len(ph)
+    flop = ph[-1][1]
+    achieved = flop / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "traffic": None,
+            "peak_source": f"{src} bf16 {bf16} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250 (of {src})",
+            "flop_per_launch": flop, "ms_per_launch": ms}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_0910_5863_gb300 import problems as P
+    from paper_0910_5863_gb300 import bddc as B
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = P.config_adaptive_poisson(seed=args.seed)
+    # inputs resident in HBM
+    dev_arrays = (torch.from_numpy(np.ascontiguousarray(prob.xyz)).to(dev),
+                  torch.from_numpy(np.ascontiguousarray(prob.elems, dtype=np.int64)).to(dev),
+                  torch.from_numpy(np.ascontiguousarray(prob.coef)).to(dev),
+                  torch.from_numpy(np.ascontiguousarray(prob.elem_sub, dtype=np.int32)).to(dev),
+                  torch.from_numpy(np.ascontiguousarray(prob.dirichlet, dtype=np.uint8)).to(dev))
+    f_host = B.free_load_vector(prob)
+    solver, t_mixed, ph_mixed, ad, info, launches, clk = _arm(args, B.MIXED, prob, dev_arrays, f_host, world,
+                                                              local_rank)
+    _, t_fp64, ph_fp64, ad64, info64, launches64, clk64 = _arm(args, B.FP64, prob, dev_arrays, f_host, world,
+                                                              local_rank)
+
+    # end-to-end through the C ABI with host buffers (mesh and f from host, u back to host), mixed arm
     mesh_host = [np.ascontiguousarray(prob.xyz), np.ascontiguousarray(prob.elems, dtype=np.int64),
                  np.ascontiguousarray(prob.coef), np.ascontiguousarray(prob.elem_sub, dtype=np.int32),
                  np.ascontiguousarray(prob.dirichlet, dtype=np.uint8)]
@@ -186,31 +215,31 @@ def run_gpu(args, rank, world, local_rank):
     h2d = sum(a.nbytes for a in mesh_host) + f_host.nbytes
     d2h = u_host.nbytes
 
-    # roofline: the batched partial Cholesky of the interior elimination (FP64)
     bf16, hbm, src = _peaks()
     fp64_peak = bf16 * NOMINAL_FP64_OVER_BF16
-    ie = phases["interior_elimination"]
-    ie_ms = sum(m for m, _ in ie) / len(ie)
-    ie_flop = ie[-1][1]
-    achieved = ie_flop / (ie_ms / 1e3) / 1e12
-    phase_ms = {k: round(sum(m for m, _ in v) / len(v), 4) for k, v in phases.items()}
-    dominant = max(phase_ms, key=phase_ms.get)
+    pm, pf = _phase_summary(ph_mixed), _phase_summary(ph_fp64)
     line = {
-        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(prob, args.seed),
-        "roofline": {"bound": "tensor", "kernel": "pchol_panel+pchol_update (interior elimination, FP64)",
-                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                     "traffic": None,
-                     "peak_source": f"{src} bf16 {bf16} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250",
-                     "flop_per_launch": ie_flop, "ms_per_launch": ie_ms},
+        "metric": METRIC, "value": t_mixed, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_mixed * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": _config(prob, args.seed),
+        "roofline": _roofline(ph_mixed, "pair_condensation",
+                              "pchol_panel+pchol_update <double> (pair condensations, the FP64 part of the mixed path)",
+                              fp64_peak, src, bf16),
         "e2e": {"value": statistics.median(e2e_times), "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clk,
-        "phase_ms": phase_ms, "dominant_phase": dominant,
+        "phase_ms": pm, "dominant_phase": max(pm, key=pm.get),
         "iters": info["iters"], "kappa": info["kappa"], "n_added": ad["n_added"], "omega": ad["omega"],
+        "fp64": {"value": t_fp64, "unit": "s", "ms_per_step": t_fp64 * 1e3, "phase_ms": pf,
+                 "iters": info64["iters"], "kappa": info64["kappa"], "n_added": ad64["n_added"],
+                 "gpu_launches": int(launches64), "clocks": clk64,
+                 "roofline": _roofline(ph_fp64, "interior_elimination",
+                                       "pchol_panel+pchol_update <double> (interior elimination)", fp64_peak, src,
+                                       bf16)},
+        "mixed_over_fp64_speedup": t_fp64 / t_mixed,
     }
+    line["config"]["precision"] = "mixed (FP32 factorizations + FP64 refinement, FP64 pair problems/coarse/PCG)"
     return line
 
 

@@ -181,10 +181,13 @@ BDDC_API bddc_status bddc_apply_schur(bddc_handle *h, const double *x, double *y
  *   0 Q1 assembly + weights          1 interior elimination (partial Cholesky of A_i)
  *   2 coarse operators (built before the first solve or apply after a setup
  *     or adapt changed the constraints)
- *   3 pair condensations (adapt)     4 face eigenproblems (adapt)     5 unused (0)
+ *   3 pair condensations (adapt)     4 face eigenproblems (adapt)
+ *   5 analysis of bddc_set_mesh_q1 (host wall time: classification, index maps, uploads)
  *   6 condensed right-hand side      7 PCG                       8 interior recovery
  * FLOPs of phase 1 are the dense count sum_i n_I^3/3 + n_I^2 n_G + n_I n_G^2;
- * other phases report 0 FLOPs.  ms[cap], flop[cap] may be NULL; *n = 9. */
+ * phase 3 reports m^3/3 + m^2 (n-m) + m (n-m)^2 summed over its partial
+ * Cholesky factorizations (order n, m columns eliminated); other phases
+ * report 0 FLOPs.  ms[cap], flop[cap] may be NULL; *n = 9. */
 BDDC_API bddc_status bddc_get_phase_times(const bddc_handle *h, double *ms, double *flop, int cap, int *n);
 
 /* Number of kernel launches made by the handle so far (all phases). */

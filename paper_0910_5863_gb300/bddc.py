@@ -27,7 +27,7 @@ EXPORTS = ["bddc_default_options", "bddc_create", "bddc_destroy", "bddc_set_mesh
            "bddc_apply_preconditioner", "bddc_apply_schur", "bddc_launch_count", "bddc_status_str",
            "bddc_last_error", "bddc_get_phase_times"]
 PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
-          "unused", "condensed_rhs", "pcg", "recovery"]
+          "analysis_host", "condensed_rhs", "pcg", "recovery"]
 
 
 class Options(C.Structure):

@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -29,6 +30,7 @@
 #include "dense.h"
 #include "eig.h"
 #include "host_util.h"
+#include "mixed.h"
 #include "pcg.h"
 
 using namespace bddc;
@@ -130,6 +132,8 @@ struct bddc_handle {
     std::vector<double *> face_rows_dev;
     int face_row_ld = 0;
     bool coarse_dirty = true;   // coarse operators are (re)built before the next solve
+    int mixed_iters = 0;        // refinement steps the interior elimination needed (mixed mode)
+    double mixed_relres = 0.0;  // largest relative residual of the refined A_II X = A_IG
     // phase timing: events [2k, 2k+1] bracket phase k
     static constexpr int kPhases = 9;
     cudaEvent_t ev[2 * kPhases] = {};
@@ -264,6 +268,28 @@ void zero(bddc_handle *h, double *p, size_t n) {
     check_launch(h);
 }
 
+// buffers to clear with a single launch
+struct ZeroList {
+    std::vector<double *> p;
+    std::vector<int64_t> n;
+    void add(double *ptr, size_t count) {
+        p.push_back(ptr);
+        n.push_back((int64_t)count);
+    }
+};
+
+void zero_all(bddc_handle *h, const ZeroList &z, const std::string &tag) {
+    if (z.p.empty()) return;
+    std::vector<int2> items;
+    for (int k = 0; k < (int)z.p.size(); ++k)
+        for (int64_t c = 0; c < (z.n[k] + 8191) / 8192; ++c) items.push_back(make_int2(k, (int)c));
+    auto *dp = h->ar.upload("z_p_" + tag, z.p, h->stream);
+    auto *dn = h->ar.upload("z_n_" + tag, z.n, h->stream);
+    auto *di = h->ar.upload("z_i_" + tag, items, h->stream);
+    launch_zero_many(dp, dn, di, (int)items.size(), h->stream);
+    check_launch(h);
+}
+
 GatherOp gop(const double *src, int ld_src, double *dst, int ld_dst, int nr, int nc) {
     GatherOp o;
     memset(&o, 0, sizeof(o));
@@ -284,6 +310,7 @@ const int HEX_EDGES[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
                               {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
 
 void classify(bddc_handle *h) {
+    const auto tc0 = std::chrono::steady_clock::now();
     const int64_t nn = h->nn, ne = h->ne;
     const int c = h->ncomp;
     // free dofs
@@ -320,32 +347,50 @@ void classify(bddc_handle *h) {
         }
     }
     for (auto &x : nsv) std::sort(x.s, x.s + x.cnt);
-    auto same_set = [&](int64_t a, int64_t b) {
-        const NodeSubs &A = nsv[a], &B = nsv[b];
-        if (A.cnt != B.cnt) return false;
-        for (int k = 0; k < A.cnt; ++k)
-            if (A.s[k] != B.s[k]) return false;
+    // set ids: {s} -> s for the one-substructure sets; interface sets are sorted by key
+    h->sets.clear();
+    for (int sb = 0; sb < h->nsub; ++sb) h->sets.push_back({sb});
+    std::vector<int> set_count(h->nsub, 0);
+    h->node_set.assign(nn, -1);
+    struct Key {
+        int cnt;
+        int s[kMaxSet];
+        int64_t node;
+    };
+    std::vector<Key> keys;
+    for (int64_t v = 0; v < nn; ++v) {
+        const NodeSubs &x = nsv[v];
+        BDDC_REQUIRE(x.cnt >= 1, BDDC_EINVAL, "a node belongs to no element");
+        if (x.cnt == 1) {
+            h->node_set[v] = x.s[0];
+            set_count[x.s[0]]++;
+            continue;
+        }
+        Key k;
+        k.cnt = x.cnt;
+        for (int q = 0; q < kMaxSet; ++q) k.s[q] = q < x.cnt ? x.s[q] : -1;
+        k.node = v;
+        keys.push_back(k);
+    }
+    auto key_less = [](const Key &a, const Key &b) {
+        if (a.cnt != b.cnt) return a.cnt < b.cnt;
+        for (int q = 0; q < a.cnt; ++q)
+            if (a.s[q] != b.s[q]) return a.s[q] < b.s[q];
+        return a.node < b.node;
+    };
+    auto key_same = [](const Key &a, const Key &b) {
+        if (a.cnt != b.cnt) return false;
+        for (int q = 0; q < a.cnt; ++q)
+            if (a.s[q] != b.s[q]) return false;
         return true;
     };
-    std::vector<int64_t> order(nn);
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-        const NodeSubs &A = nsv[a], &B = nsv[b];
-        if (A.cnt != B.cnt) return A.cnt < B.cnt;
-        for (int k = 0; k < A.cnt; ++k)
-            if (A.s[k] != B.s[k]) return A.s[k] < B.s[k];
-        return a < b;
-    });
-    h->sets.clear();
-    h->node_set.assign(nn, -1);
-    std::vector<int> set_count;
-    for (int64_t k = 0; k < nn; ++k) {
-        int64_t v = order[k];
-        if (k == 0 || !same_set(v, order[k - 1])) {
-            h->sets.emplace_back(nsv[v].s, nsv[v].s + nsv[v].cnt);
+    std::sort(keys.begin(), keys.end(), key_less);
+    for (size_t q = 0; q < keys.size(); ++q) {
+        if (q == 0 || !key_same(keys[q], keys[q - 1])) {
+            h->sets.emplace_back(keys[q].s, keys[q].s + keys[q].cnt);
             set_count.push_back(0);
         }
-        h->node_set[v] = (int)h->sets.size() - 1;
+        h->node_set[keys[q].node] = (int)h->sets.size() - 1;
         set_count.back()++;
     }
     // element-edge neighbours of nodes in edge sets (set size >= 3)
@@ -390,20 +435,20 @@ void classify(bddc_handle *h) {
         if (h->is_corner[v] && h->dirich[v]) h->is_corner[v] = 0;
         if (h->is_corner[v]) h->corners.push_back(v);
     }
-    // globs: nodes grouped by set (the sort above keeps each set contiguous, ascending node ids)
+    // globs: interface nodes grouped by set (the key sort keeps each set contiguous, ascending node ids)
     h->edge_globs.clear();
     std::vector<std::pair<std::pair<int, int>, std::vector<int64_t>>> face_list;
-    for (int64_t k = 0; k < nn;) {
-        int sid = h->node_set[order[k]];
-        int64_t k1 = k;
+    for (size_t q = 0; q < keys.size();) {
+        const int sid = h->node_set[keys[q].node];
+        size_t q1 = q;
         std::vector<int64_t> nodes;
-        while (k1 < nn && h->node_set[order[k1]] == sid) {
-            int64_t v = order[k1++];
+        while (q1 < keys.size() && h->node_set[keys[q1].node] == sid) {
+            int64_t v = keys[q1++].node;
             if (!h->dirich[v] && !h->is_corner[v]) nodes.push_back(v);
         }
-        k = k1;
+        q = q1;
         const auto &S = h->sets[sid];
-        if (S.size() < 2 || nodes.empty()) continue;
+        if (nodes.empty()) continue;
         if (S.size() == 2)
             face_list.push_back({{S[0], S[1]}, nodes});
         else
@@ -415,16 +460,22 @@ void classify(bddc_handle *h) {
     // substructures
     const int ns = h->nsub;
     h->subs.assign(ns, SubData());
+    // local nodes of every substructure, ascending (each node appended to the substructures of its set)
     std::vector<std::vector<int64_t>> snodes(ns);
-    for (int64_t e = 0; e < ne; ++e)
-        for (int a = 0; a < 8; ++a) snodes[h->esub[e]].push_back(h->elems[e * 8 + a]);
+    {
+        std::vector<int64_t> cnt(ns, 0);
+        for (int64_t v = 0; v < nn; ++v)
+            for (int q = 0; q < nsv[v].cnt; ++q) cnt[nsv[v].s[q]]++;
+        for (int sb = 0; sb < ns; ++sb) snodes[sb].reserve(cnt[sb]);
+        for (int64_t v = 0; v < nn; ++v)
+            for (int q = 0; q < nsv[v].cnt; ++q) snodes[nsv[v].s[q]].push_back(v);
+    }
+    const auto tc_sub = std::chrono::steady_clock::now();
     std::vector<char> is_iface_node(nn, 0);
     for (int64_t v = 0; v < nn; ++v) is_iface_node[v] = h->sets[h->node_set[v]].size() >= 2 && !h->dirich[v];
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
         auto &L = snodes[s];
-        std::sort(L.begin(), L.end());
-        L.erase(std::unique(L.begin(), L.end()), L.end());
         sd.nodes = L;
         bool touches_dirichlet = false;
         for (int64_t v : L) {
@@ -535,6 +586,7 @@ void classify(bddc_handle *h) {
             throw Error{BDDC_EASSUMPTION, "Assumption 1: floating substructure " + std::to_string(s) +
                                               " has too few corners to fix its rigid body modes"};
     }
+    const auto tc_faces = std::chrono::steady_clock::now();
     // face pairs
     h->faces.clear();
     std::vector<int> pi(h->nfree, -1), pj(h->nfree, -1);
@@ -620,32 +672,28 @@ void classify(bddc_handle *h) {
         for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = -1;
         h->faces.push_back(fp);
     }
+    const auto tc_color = std::chrono::steady_clock::now();
     // element colouring (greedy, nodes shared => different colours)
     h->colors.clear();
     std::vector<int> ecol(ne, -1);
-    std::vector<int64_t> neptr(nn + 1, 0), nelist(ne * 8);
-    for (int64_t k = 0; k < ne * 8; ++k) neptr[h->elems[k] + 1]++;
-    for (int64_t v = 0; v < nn; ++v) neptr[v + 1] += neptr[v];
-    {
-        std::vector<int64_t> fill(neptr.begin(), neptr.end() - 1);
-        for (int64_t e = 0; e < ne; ++e)
-            for (int a = 0; a < 8; ++a) nelist[fill[h->elems[e * 8 + a]]++] = e;
-    }
+    // greedy: an element takes the lowest colour not yet used by an element sharing one of its nodes
+    std::vector<uint64_t> node_mask(nn, 0);
     for (int64_t e = 0; e < ne; ++e) {
         uint64_t used = 0;
-        for (int a = 0; a < 8; ++a) {
-            int64_t v = h->elems[e * 8 + a];
-            for (int64_t q = neptr[v]; q < neptr[v + 1]; ++q) {
-                int64_t f = nelist[q];
-                if (ecol[f] >= 0 && ecol[f] < 64) used |= (1ull << ecol[f]);
-            }
-        }
+        for (int a = 0; a < 8; ++a) used |= node_mask[h->elems[e * 8 + a]];
         int col = 0;
         while (col < 64 && (used >> col) & 1ull) ++col;
         BDDC_REQUIRE(col < 64, BDDC_EINVAL, "element colouring needs more than 64 colours");
         ecol[e] = col;
+        for (int a = 0; a < 8; ++a) node_mask[h->elems[e * 8 + a]] |= (1ull << col);
         if ((int)h->colors.size() <= col) h->colors.resize(col + 1);
         h->colors[col].push_back((int32_t)e);
+    }
+    if (getenv("BDDC_DEBUG_TIMING")) {
+        auto ms = [](auto x, auto y) { return std::chrono::duration<double, std::milli>(y - x).count(); };
+        const auto tc_end = std::chrono::steady_clock::now();
+        fprintf(stderr, "classify: sets+globs %.3f subs+maps %.3f faces %.3f colours %.3f ms\n", ms(tc0, tc_sub),
+                ms(tc_sub, tc_faces), ms(tc_faces, tc_color), ms(tc_color, tc_end));
     }
 }
 
@@ -774,13 +822,48 @@ void layout_constraints(bddc_handle *h) {
 // with K = S_rr^-1, Z = K [S_rc, C_r^T], G = C_r K C_r^T, H = C_r K S_rc, J = S_cr K S_rc.
 void coarse_setup(bddc_handle *h) {
     const int ns = h->nsub;
+    const bool mixed = h->opt.precision == BDDC_MIXED;
     layout_constraints(h);
+    // mixed: M1 in FP32 with the symmetric equilibration d = diag(S)^-1/2 of the remaining dofs
+    double *eqS = nullptr, *dr = nullptr, *s2 = nullptr;
+    std::vector<int64_t> off_r(ns, 0), off_s2(ns, 0);
+    if (mixed) {
+        std::vector<MixedSub> ms(ns);
+        std::vector<int64_t> idx_r, idx_s2;
+        eqS = h->ar.get_t<double>("eqS", h->sumG + 1);
+        for (int s = 0; s < ns; ++s) {
+            auto &sd = h->subs[s];
+            ms[s] = MixedSub{sd.S, sd.nG, 0, sd.ldS, eqS + h->offG[s], nullptr, nullptr, nullptr, 0};
+            off_r[s] = (int64_t)idx_r.size();
+            for (int p : sd.rpos) idx_r.push_back(h->offG[s] + p);
+            off_s2[s] = (int64_t)idx_s2.size();
+            for (int k = 0; k < sd.na; ++k) idx_s2.push_back(h->sumG);  // the constant 1
+            for (int p : sd.rpos) idx_s2.push_back(h->offG[s] + p);
+            for (size_t k = 0; k < sd.cpos.size(); ++k) idx_s2.push_back(h->sumG);
+        }
+        auto *dms = h->ar.upload("ms_S", ms, h->stream);
+        launch_equilibrate(dms, ns, h->stream);
+        check_launch(h);
+        const double one = 1.0;
+        BDDC_CUDA(cudaMemcpyAsync(eqS + h->sumG, &one, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        dr = h->ar.get_t<double>("dr", idx_r.size() + 1);
+        s2 = h->ar.get_t<double>("s2", idx_s2.size() + 1);
+        auto *di = h->ar.upload("idx_r", idx_r, h->stream);
+        auto *d2i = h->ar.upload("idx_s2", idx_s2, h->stream);
+        launch_gatherv(dr, di, eqS, (int64_t)idx_r.size(), h->stream);
+        check_launch(h);
+        launch_gatherv(s2, d2i, eqS, (int64_t)idx_s2.size(), h->stream);
+        check_launch(h);
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));  // 'one' lives on the host stack
+    }
     std::vector<PcholDesc<double>> d1, d2;
+    std::vector<PcholDesc<float>> d1f;
     std::vector<GatherOp> g1, g2, g3;
     std::vector<DiagOp> id1, id2;
     std::vector<double *> M1(ns), M2(ns), SCi(ns);
     std::vector<int> N1(ns), N2(ns), ld1(ns), ld2(ns);
     // map arrays uploaded per sub
+    ZeroList zl;
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
         const int nr = (int)sd.rpos.size(), nc = (int)sd.cpos.size(), na = sd.na;
@@ -790,20 +873,27 @@ void coarse_setup(bddc_handle *h) {
         ld2[s] = round_up(std::max(N2[s], 1), 8);
         M1[s] = h->ar.get_t<double>("M1_" + std::to_string(s), (size_t)ld1[s] * N1[s]);
         M2[s] = h->ar.get_t<double>("M2_" + std::to_string(s), (size_t)ld2[s] * std::max(N2[s], 1));
-        zero(h, M1[s], (size_t)ld1[s] * N1[s]);
-        zero(h, M2[s], (size_t)ld2[s] * std::max(N2[s], 1));
+        // in mixed mode M1 holds floats (ld1 is a multiple of 8, so half the doubles cover it)
+        zl.add(M1[s], mixed ? (size_t)ld1[s] * N1[s] / 2 : (size_t)ld1[s] * N1[s]);
+        zl.add(M2[s], (size_t)ld2[s] * std::max(N2[s], 1));
         int *drpos = h->ar.upload("rpos_" + std::to_string(s), sd.rpos, h->stream);
         int *dcpos = h->ar.upload("cpos_" + std::to_string(s), sd.cpos, h->stream);
-        // M1 blocks
+        // M1 blocks (mixed: FP32, columns of the remaining dofs scaled by d)
+        const double *dsc = mixed ? dr + off_r[s] : nullptr;
         GatherOp o = gop(sd.S, sd.ldS, M1[s], ld1[s], nr, nr);
         o.rmap = drpos;
         o.cmap = drpos;
         o.dst_lower = 1;
+        o.rscale = dsc;
+        o.cscale = dsc;
+        o.dst_f32 = mixed;
         g1.push_back(o);
         if (na > 0) {
             o = gop(sd.Cb, sd.capA, M1[s], ld1[s], na, nr);
             o.cmap = drpos;
             o.dst_row_off = 2 * nr;
+            o.cscale = dsc;
+            o.dst_f32 = mixed;
             g1.push_back(o);
         }
         if (nc > 0) {
@@ -811,14 +901,24 @@ void coarse_setup(bddc_handle *h) {
             o.rmap = dcpos;
             o.cmap = drpos;
             o.dst_row_off = 2 * nr + na;
+            o.cscale = dsc;
+            o.dst_f32 = mixed;
             g1.push_back(o);
         }
-        id1.push_back(DiagOp{M1[s], ld1[s], nr, 0, nr, 1.0});
-        d1.push_back(PcholDesc<double>{M1[s], N1[s], ld1[s], nr, 0});
+        DiagOp dop{M1[s], ld1[s], nr, 0, nr, 1.0, mixed ? 1 : 0, 0};
+        id1.push_back(dop);
+        if (mixed)
+            d1f.push_back(PcholDesc<float>{reinterpret_cast<float *>(M1[s]), N1[s], ld1[s], nr, 0});
+        else
+            d1.push_back(PcholDesc<double>{M1[s], N1[s], ld1[s], nr, 0});
     }
+    zero_all(h, zl, "M12");
     run_gathers(h, g1, "M1");
     run_diag(h, id1, "M1");
-    run_pchol<double>(h, d1, "M1");
+    if (mixed)
+        run_pchol<float>(h, d1f, "M1f");
+    else
+        run_pchol<double>(h, d1, "M1");
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
         const int nr = (int)sd.rpos.size(), nc = (int)sd.cpos.size(), na = sd.na;
@@ -836,6 +936,11 @@ void coarse_setup(bddc_handle *h) {
             o.src_sym = 1;
             o.dst_lower = 1;
             o.scale = -1.0;
+            if (mixed) {  // undo the equilibration on the (id) block: K = D K_s D, Z = D (K_s D C^T) ...
+                o.src_f32 = 1;
+                o.rscale = s2 + off_s2[s];
+                o.cscale = s2 + off_s2[s];
+            }
             g2.push_back(o);
         }
         if (na > 0) id2.push_back(DiagOp{M2[s], ld2[s], K, 0, na, 1.0});
@@ -937,14 +1042,18 @@ void coarse_setup(bddc_handle *h) {
     BDDC_REQUIRE(nC > 0, BDDC_EASSUMPTION, "no coarse degrees of freedom");
     BDDC_REQUIRE(nC <= 12000, BDDC_EINVAL, "coarse problem larger than 12000 dofs");
     double *SC = h->ar.get_t<double>("SC", (size_t)nC * nC);
-    zero(h, SC, (size_t)nC * nC);
+    int ldm = round_up(2 * nC, 8);
+    double *MC = h->ar.get_t<double>("MC", (size_t)ldm * 2 * nC);
+    {
+        ZeroList zc;
+        zc.add(SC, (size_t)nC * nC);
+        zc.add(MC, (size_t)ldm * 2 * nC);
+        zero_all(h, zc, "SC");
+    }
     auto *dcad = h->ar.upload("cad", cad, h->stream);
     launch_coarse_assemble(dcad, ns, SC, nC, h->stream);
     check_launch(h);
     // inverse by partial Cholesky of [[S_C, .]; [I, 0]]
-    int ldm = round_up(2 * nC, 8);
-    double *MC = h->ar.get_t<double>("MC", (size_t)ldm * 2 * nC);
-    zero(h, MC, (size_t)ldm * 2 * nC);
     std::vector<GatherOp> g5{gop(SC, nC, MC, ldm, nC, nC)};
     g5[0].dst_lower = 1;
     run_gathers(h, g5, "MC");
@@ -1052,6 +1161,210 @@ void set_phi_pointers(bddc_handle *h) {
     h->ops.Phi = h->ar.upload("Phiptr", Phi, h->stream);
 }
 
+// ---- mixed precision: FP32 factorization, FP64 refinement ---------------------
+constexpr int kEllPerComp = 32;  // ELL width per component (27-point stencil + slack)
+
+struct RefineJob {  // A_II X = B for one substructure, X starts at zero
+    int s;
+    const double *B;
+    int ldb;
+    double *X;
+    int ldx;
+    double *R;
+    int ldr;
+    int ncol;
+};
+
+void run_ell(bddc_handle *h, const std::vector<EllProduct> &ps, const std::string &tag) {
+    if (ps.empty()) return;
+    std::vector<int2> items;
+    for (int k = 0; k < (int)ps.size(); ++k) {
+        const int64_t cnt = (int64_t)ps[k].m * ps[k].ncol;
+        for (int64_t b = 0; b < (cnt + 255) / 256; ++b) items.push_back(make_int2(k, (int)b));
+    }
+    auto *dp = h->ar.upload("ell_p_" + tag, ps, h->stream);
+    auto *di = h->ar.upload("ell_i_" + tag, items, h->stream);
+    launch_ell_residual(dp, di, (int)items.size(), h->stream);
+    check_launch(h);
+}
+
+EllProduct ell_of(bddc_handle *h, int s) {
+    auto &sd = h->subs[s];
+    const std::string t = std::to_string(s);
+    const int W = kEllPerComp * h->ncomp;
+    EllProduct p;
+    memset(&p, 0, sizeof(p));
+    p.ell_cnt = h->ar.get_t<int>("ellc_" + t, sd.n);
+    p.ell_col = h->ar.get_t<int>("ellj_" + t, (size_t)sd.n * W);
+    p.ell_val = h->ar.get_t<double>("ellv_" + t, (size_t)sd.n * W);
+    p.ell_w = W;
+    return p;
+}
+
+// Refinement for A_II X = B from X = 0: the first correction is X = D K_s D B, then
+// R = B - A_II X (FP64) and X += D K_s D R.  With check, stops at the first residual
+// whose relative norm is below tol for every job (R then holds that residual);
+// without, stops after exactly `corrections` corrections.  Returns the corrections made.
+int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, int max_corr, double tol, bool check,
+           const std::string &tag) {
+    if (jobs.empty()) return 0;
+    std::vector<EllProduct> ps;
+    std::vector<MixedUpdate> us, us0;
+    std::vector<int4> uitems;
+    ZeroList zx;
+    for (int k = 0; k < (int)jobs.size(); ++k) {
+        const auto &j = jobs[k];
+        auto &sd = h->subs[j.s];
+        const std::string t = std::to_string(j.s);
+        EllProduct p = ell_of(h, j.s);
+        p.r0 = 0;
+        p.m = sd.nI;
+        p.ncol = j.ncol;
+        p.X = j.X;
+        p.ldx = j.ldx;
+        p.B = j.B;
+        p.ldb = j.ldb;
+        p.out = j.R;
+        p.ldo = j.ldr;
+        ps.push_back(p);
+        const int ldk = round_up(std::max(sd.nI, 1), 8);
+        const float *K = reinterpret_cast<const float *>(h->ar.get("Kinv_" + t, (size_t)ldk * sd.nI * 4 + 16));
+        const double *eq = h->ar.get_t<double>("eq_" + t, sd.n);
+        us.push_back(MixedUpdate{K, ldk, eq, j.R, j.ldr, j.X, j.ldx, sd.nI, j.ncol});
+        us0.push_back(MixedUpdate{K, ldk, eq, j.B, j.ldb, j.X, j.ldx, sd.nI, j.ncol});
+        for (int a = 0; a < (sd.nI + 63) / 64; ++a)
+            for (int b = 0; b < (j.ncol + 63) / 64; ++b) uitems.push_back(make_int4(k, a, b, 0));
+        zx.add(j.X, (size_t)j.ldx * j.ncol);
+    }
+    zero_all(h, zx, "X_" + tag);
+    auto *dus = h->ar.upload("mu_" + tag, us, h->stream);
+    auto *dus0 = h->ar.upload("mu0_" + tag, us0, h->stream);
+    auto *dui = h->ar.upload("mui_" + tag, uitems, h->stream);
+    auto *dps = h->ar.upload("mps_" + tag, ps, h->stream);
+    double *norms = h->ar.get_t<double>("rnorm_" + tag, 2 * jobs.size());
+    std::vector<double> hn(2 * jobs.size());
+    launch_mixed_update(dus0, dui, (int)uitems.size(), h->stream);
+    check_launch(h);
+    int done = 1;
+    for (;;) {
+        if (!check && done >= corrections) break;
+        run_ell(h, ps, tag);
+        if (check) {
+            launch_residual_norms(dps, (int)ps.size(), norms, h->stream);
+            check_launch(h);
+            BDDC_CUDA(cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            BDDC_CUDA(cudaStreamSynchronize(h->stream));
+            double worst = 0.0;
+            for (size_t k = 0; k < jobs.size(); ++k)
+                worst = std::max(worst, std::sqrt(hn[2 * k] / std::max(hn[2 * k + 1], 1e-300)));
+            h->mixed_relres = worst;
+            if (worst <= tol && done >= corrections) break;
+            BDDC_REQUIRE(done < max_corr, BDDC_ENOCONV,
+                         "mixed-precision refinement of the interior solves did not converge (relative residual " +
+                             std::to_string(worst) + "); use BDDC_FP64");
+        }
+        launch_mixed_update(dus, dui, (int)uitems.size(), h->stream);
+        check_launch(h);
+        ++done;
+    }
+    return done;
+}
+
+// Interior elimination in mixed precision (see mixed.cu): FP32 explicit inverse of the
+// equilibrated A_II, FP64-refined X = A_II^-1 A_IG, S_i = A_GG - A_GI X in FP64.
+void interior_mixed(bddc_handle *h) {
+    const int ns = h->nsub, W = kEllPerComp * h->ncomp;
+    std::vector<MixedSub> ms(ns);
+    std::vector<int2> eitems;
+    ZeroList zl;
+    std::vector<GatherOp> gF, gK;
+    std::vector<DiagOp> dI;
+    std::vector<PcholDesc<float>> pd;
+    std::vector<RefineJob> jobs;
+    for (int s = 0; s < ns; ++s) {
+        auto &sd = h->subs[s];
+        const int n = sd.n, nI = sd.nI, nG = sd.nG;
+        const std::string t = std::to_string(s);
+        double *eq = h->ar.get_t<double>("eq_" + t, n);
+        EllProduct e = ell_of(h, s);
+        ms[s] = MixedSub{sd.A, n, nI, sd.ld, eq, const_cast<int *>(e.ell_cnt), const_cast<int *>(e.ell_col),
+                         const_cast<double *>(e.ell_val), W};
+        for (int r = 0; r < n; ++r) eitems.push_back(make_int2(s, r));
+        if (nI == 0) continue;
+        const int ldF = round_up(2 * nI, 8);
+        double *F = static_cast<double *>(h->ar.get("F_" + t, (size_t)ldF * 2 * nI * sizeof(float) + 16));
+        zl.add(F, (size_t)ldF * nI);
+        GatherOp o = gop(sd.A, sd.ld, F, ldF, nI, nI);
+        o.dst_lower = 1;
+        o.rscale = eq;
+        o.cscale = eq;
+        o.dst_f32 = 1;
+        gF.push_back(o);
+        dI.push_back(DiagOp{F, ldF, nI, 0, nI, 1.0, 1, 0});
+        pd.push_back(PcholDesc<float>{reinterpret_cast<float *>(F), 2 * nI, ldF, nI, 0});
+        const int ldk = round_up(nI, 8);
+        double *K = static_cast<double *>(h->ar.get("Kinv_" + t, (size_t)ldk * nI * sizeof(float) + 16));
+        GatherOp k = gop(F, ldF, K, ldk, nI, nI);
+        k.src_row_off = nI;
+        k.src_col_off = nI;
+        k.src_sym = 1;
+        k.src_f32 = 1;
+        k.dst_f32 = 1;
+        k.scale = -1.0;
+        gK.push_back(k);
+        const int ldx = round_up(nI, 8);
+        double *X = h->ar.get_t<double>("X_" + t, (size_t)ldx * std::max(nG, 1));
+        double *R = h->ar.get_t<double>("R_" + t, (size_t)ldx * std::max(nG, 1));
+        jobs.push_back(RefineJob{s, sd.A + (size_t)nI * sd.ld, sd.ld, X, ldx, R, ldx, nG});
+    }
+    auto *dms = h->ar.upload("ms_A", ms, h->stream);
+    launch_equilibrate(dms, ns, h->stream);
+    check_launch(h);
+    auto *dei = h->ar.upload("ell_items", eitems, h->stream);
+    launch_ell_build(dms, dei, (int)eitems.size(), h->dst, h->stream);
+    check_launch(h);
+    zero_all(h, zl, "F");
+    run_gathers(h, gF, "F");
+    run_diag(h, dI, "F");
+    run_pchol<float>(h, pd, "F");
+    run_gathers(h, gK, "Kinv");
+    fail_check(h, "mixed interior factorization");
+    // refine until ||A_IG - A_II X|| <= 1e-8 ||A_IG||; the energy form below squares that error
+    h->mixed_iters = refine(h, jobs, 1, 12, 1e-8, true, "X");
+    // S_i = A_GG - A_GI X - X^T R  (R = A_IG - A_II X, the residual of the accepted X)
+    std::vector<EllProduct> ps;
+    for (const auto &j : jobs) {
+        auto &sd = h->subs[j.s];
+        EllProduct p = ell_of(h, j.s);
+        p.r0 = sd.nI;
+        p.m = sd.nG;
+        p.ncol = sd.nG;
+        p.X = j.X;
+        p.ldx = j.ldx;
+        p.B = sd.A + (size_t)sd.nI * sd.ld + sd.nI;
+        p.ldb = sd.ld;
+        p.out = sd.S;
+        p.ldo = sd.ldS;
+        ps.push_back(p);
+    }
+    run_ell(h, ps, "S");
+    std::vector<GramCorrect> gc;
+    std::vector<int4> gitems;
+    for (const auto &j : jobs) {
+        auto &sd = h->subs[j.s];
+        const int k = (int)gc.size();
+        gc.push_back(GramCorrect{j.X, j.ldx, j.R, j.ldr, sd.S, sd.ldS, sd.nI, sd.nG});
+        for (int a = 0; a < (sd.nG + 63) / 64; ++a)
+            for (int b = 0; b < (sd.nG + 63) / 64; ++b) gitems.push_back(make_int4(k, a, b, 0));
+    }
+    auto *dgc = h->ar.upload("gc", gc, h->stream);
+    auto *dgi = h->ar.upload("gci", gitems, h->stream);
+    launch_gram_correct(dgc, dgi, (int)gitems.size(), h->stream);
+    check_launch(h);
+    launch_symmetrize(h->ops.S, h->ops.nGi, h->ops.ldS, ns, h->stream);
+    check_launch(h);
+}
+
 // ---- phases --------------------------------------------------------------
 void count_coarse(bddc_handle *h) {
     int nC = h->n_corner_dofs;
@@ -1082,12 +1395,14 @@ void do_setup(bddc_handle *h) {
     check_launch(h);
     std::vector<double *> Aptr(ns);
     std::vector<int> lds(ns);
+    ZeroList zl;
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
-        zero(h, sd.A, (size_t)sd.ld * sd.n);
+        zl.add(sd.A, (size_t)sd.ld * sd.n);
         Aptr[s] = sd.A;
         lds[s] = sd.ld;
     }
+    zero_all(h, zl, "A");
     AssemblyArgs aa;
     aa.grads = grads;
     aa.wdet = wdet;
@@ -1124,20 +1439,25 @@ void do_setup(bddc_handle *h) {
     for (auto &sd : h->subs)
         fl += (double)sd.nI * sd.nI * sd.nI / 3.0 + (double)sd.nI * sd.nI * sd.nG + (double)sd.nI * sd.nG * sd.nG;
     h->phase_flop[1] = fl;
-    std::vector<PcholDesc<double>> d;
-    for (int s = 0; s < ns; ++s) d.push_back(PcholDesc<double>{h->subs[s].A, h->subs[s].n, h->subs[s].ld, h->subs[s].nI, 0});
-    run_pchol<double>(h, d, "AII");
-    // S_i full from the trailing lower block
-    std::vector<GatherOp> gs;
-    for (int s = 0; s < ns; ++s) {
-        auto &sd = h->subs[s];
-        GatherOp o = gop(sd.A, sd.ld, sd.S, sd.ldS, sd.nG, sd.nG);
-        o.src_row_off = sd.nI;
-        o.src_col_off = sd.nI;
-        o.src_sym = 1;
-        gs.push_back(o);
+    if (h->opt.precision == BDDC_MIXED) {
+        interior_mixed(h);
+    } else {
+        std::vector<PcholDesc<double>> d;
+        for (int s = 0; s < ns; ++s)
+            d.push_back(PcholDesc<double>{h->subs[s].A, h->subs[s].n, h->subs[s].ld, h->subs[s].nI, 0});
+        run_pchol<double>(h, d, "AII");
+        // S_i full from the trailing lower block
+        std::vector<GatherOp> gs;
+        for (int s = 0; s < ns; ++s) {
+            auto &sd = h->subs[s];
+            GatherOp o = gop(sd.A, sd.ld, sd.S, sd.ldS, sd.nG, sd.nG);
+            o.src_row_off = sd.nI;
+            o.src_col_off = sd.nI;
+            o.src_sym = 1;
+            gs.push_back(o);
+        }
+        run_gathers(h, gs, "S");
     }
-    run_gathers(h, gs, "S");
     phase_end(h, 1);
     fail_check(h, "interior factorization");
     build_average_globs(h);
@@ -1227,14 +1547,20 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
     }
     run_gathers(h, gE1, "E1");
     run_pchol<double>(h, dE1, "E1");
+    // algorithmic FP64 flops of the condensations: partial Cholesky of n with nstop = m
+    // (m^3/3 + m^2 (n - m) + m (n - m)^2), for the E1 matrices here and E2, E3 below
+    auto pchol_flop = [](double n, double m) { return m * m * m / 3.0 + m * m * (n - m) + m * (n - m) * (n - m); };
+    double cflop = 0.0;
+    for (auto &dd : dE1) cflop += pchol_flop(dd.n, dd.nstop);
     // E2: pair matrix [C; s_i; s_j], eliminate C -> S^ (2 ns)
+    ZeroList zy;
     for (int f = 0; f < nf; ++f) {
         auto &B = pbufs[f];
         const int ns = B.ns, nc = B.nc;
         B.nY = nc + 2 * ns;
         B.ldY = round_up(std::max(B.nY, 1), 8);
         B.Y = h->ar.get_t<double>("E2_" + std::to_string(f), (size_t)B.ldY * std::max(B.nY, 1));
-        zero(h, B.Y, (size_t)B.ldY * std::max(B.nY, 1));
+        zy.add(B.Y, (size_t)B.ldY * std::max(B.nY, 1));
         for (int side = 0; side < 2; ++side) {
             const int o0 = B.no[side];  // trailing offset: [s (ns); C (nc)]
             // C block (accumulate both sides)
@@ -1264,13 +1590,16 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         }
         dE2.push_back(PcholDesc<double>{B.Y, B.nY, B.ldY, nc, 0});
     }
+    zero_all(h, zy, "E2");
     run_gathers(h, gE2, "E2a");
     run_gathers(h, gE3, "E2b");
     gE3.clear();
     run_pchol<double>(h, dE2, "E2");
+    for (auto &dd : dE2) cflop += pchol_flop(dd.n, dd.nstop);
     // E3: M3 = [[Mww, ., .], [Mbw, Mbb, .], [0, I, 0]] from S^ blocks, + deflation, eliminate 2 ns
     std::vector<DeflateDesc> defl;
     std::vector<PairWeightDesc> pw;
+    ZeroList zm;
     for (int f = 0; f < nf; ++f) {
         auto &fp = h->faces[f];
         auto &B = pbufs[f];
@@ -1278,7 +1607,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         int n3 = 3 * ns;
         B.ldM3 = round_up(std::max(n3, 1), 8);
         B.M3 = h->ar.get_t<double>("M3_" + std::to_string(f), (size_t)B.ldM3 * std::max(n3, 1));
-        zero(h, B.M3, (size_t)B.ldM3 * std::max(n3, 1));
+        zm.add(B.M3, (size_t)B.ldM3 * std::max(n3, 1));
         if (ns == 0) continue;
         // S^ blocks live in Y at offset nc: S11 at (nc, nc), S21 at (nc+ns, nc), S22 at (nc+ns, nc+ns)
         auto blk = [&](int bi, int bj, int dro, int dco, double scale, int lower, std::vector<GatherOp> &dst) {
@@ -1314,6 +1643,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         double *diag = h->ar.get_t<double>("diag", h->sumG);
         pw.push_back(PairWeightDesc{diag + h->offG[fp.i], diag + h->offG[fp.j], pi, pj, di, dj, ns});
     }
+    zero_all(h, zm, "E3");
     run_gathers(h, gE3, "E3a");
     run_gathers(h, gQ, "E3b");
     // pass 3: S21 into (w2,w2) and S22 into (w2,w2)
@@ -1354,6 +1684,8 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         check_launch(h);
     }
     run_pchol<double>(h, dE3, "E3");
+    for (auto &dd : dE3) cflop += pchol_flop(dd.n, dd.nstop);
+    h->phase_flop[3] = cflop;
     {
         auto *dpw = h->ar.upload("pw", pw, h->stream);
         launch_pair_weights(dpw, (int)pw.size(), h->stream);
@@ -1521,21 +1853,47 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
     launch_gatherv(yI, gIall, df, h->sumI, h->stream);
     check_launch(h);
     (void)gGall;
+    const bool mixed = h->opt.precision == BDDC_MIXED;
+    // mixed: y = A_II^{-1} f_I by refinement (yI keeps f_I), g_i = -A_GI y (sparse)
+    double *yx = h->ar.get_t<double>("yIx", std::max<int64_t>(h->sumI, 1));
+    double *yr = h->ar.get_t<double>("yIr", std::max<int64_t>(h->sumI, 1));
     std::vector<TrsvDesc<double>> tv;
     std::vector<GemmDesc> gm;
+    std::vector<RefineJob> rj;
+    std::vector<EllProduct> gp;
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
         if (sd.nI == 0) continue;
+        if (mixed) {
+            rj.push_back(RefineJob{s, yI + sd.offI, sd.nI, yx + sd.offI, sd.nI, yr + sd.offI, sd.nI, 1});
+            EllProduct p = ell_of(h, s);
+            p.r0 = sd.nI;
+            p.m = sd.nG;
+            p.ncol = 1;
+            p.X = yx + sd.offI;
+            p.ldx = sd.nI;
+            p.B = nullptr;
+            p.ldb = 1;
+            p.out = gl + h->offG[s];
+            p.ldo = std::max(sd.nG, 1);
+            gp.push_back(p);
+            continue;
+        }
         tv.push_back(TrsvDesc<double>{sd.A, yI + sd.offI, sd.nI, sd.ld});
         // g_i = -L21 y = -A_GI A_II^{-1} f_I  (f_G is added once after assembly)
         gm.push_back(GemmDesc{sd.A + sd.nI, yI + sd.offI, gl + h->offG[s], sd.ld, std::max(sd.nI, 1), std::max(sd.nG, 1),
                               sd.nG, 1, sd.nI, 0, 0, -1.0, 0.0});
     }
     auto *dtv = h->ar.upload("trsv", tv, h->stream);
-    launch_trsv<double>(dtv, (int)tv.size(), 0, h->stream);
-    check_launch(h);
     zero(h, gl, h->sumG);
-    run_gemv(h, gm, "cond");
+    if (mixed) {
+        refine(h, rj, 2 * h->mixed_iters + 1, 64, 0.0, false, "y");
+        run_ell(h, gp, "g");
+    } else {
+        launch_trsv<double>(dtv, (int)tv.size(), 0, h->stream);
+        check_launch(h);
+        run_gemv(h, gm, "cond");
+    }
     launch_iface_assemble(h->ops, gl, h->pb.r, h->stream);
     check_launch(h);
     // g = f_G - sum_i R_i^T A_GI A_II^{-1} f_I
@@ -1559,14 +1917,24 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
         if (sd.nI == 0 || sd.nG == 0) continue;
-        gr.push_back(GemmDesc{sd.A + sd.nI, ug + h->offG[s], yI + sd.offI, sd.ld, std::max(sd.nG, 1), std::max(sd.nI, 1),
-                              sd.nI, 1, sd.nG, 1, 0, -1.0, 1.0});
+        if (mixed)  // b = f_I - A_IG u_G (dense FP64 block of the unfactored A_i), in yI
+            gr.push_back(GemmDesc{sd.A + (size_t)sd.nI * sd.ld, ug + h->offG[s], yI + sd.offI, sd.ld, std::max(sd.nG, 1),
+                                  std::max(sd.nI, 1), sd.nI, 1, sd.nG, 0, 0, -1.0, 1.0});
+        else
+            gr.push_back(GemmDesc{sd.A + sd.nI, ug + h->offG[s], yI + sd.offI, sd.ld, std::max(sd.nG, 1),
+                                  std::max(sd.nI, 1), sd.nI, 1, sd.nG, 1, 0, -1.0, 1.0});
     }
     run_gemv(h, gr, "rec");
-    launch_trsv<double>(dtv, (int)tv.size(), 1, h->stream);
-    check_launch(h);
+    double *uI = yI;
+    if (mixed) {
+        refine(h, rj, 2 * h->mixed_iters + 1, 64, 0.0, false, "u");  // u_I = A_II^{-1} b, in yIx
+        uI = yx;
+    } else {
+        launch_trsv<double>(dtv, (int)tv.size(), 1, h->stream);
+        check_launch(h);
+    }
     double *du = h->ar.get_t<double>("u", std::max<int64_t>(h->nfree, 1));
-    launch_scatter(du, gIall, yI, h->sumI, h->stream);
+    launch_scatter(du, gIall, uI, h->sumI, h->stream);
     check_launch(h);
     const int64_t *ifg = h->ar.get_t<int64_t>("ifgdof", std::max(h->nG, 1));
     launch_scatter(du, ifg, h->pb.x, h->nG, h->stream);
@@ -1695,6 +2063,7 @@ bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double
         BDDC_REQUIRE(ncomp == 1 || ncomp == 3, BDDC_EINVAL, "ncomp must be 1 or 3");
         BDDC_REQUIRE(nn > 0 && ne > 0 && nsub > 0, BDDC_EINVAL, "empty mesh");
         BDDC_REQUIRE(xyz && elems && coef && elem_sub && dirichlet, BDDC_EINVAL, "null array");
+        const auto t_host0 = std::chrono::steady_clock::now();
         h->have_mesh = h->have_setup = false;
         h->ncomp = ncomp;
         h->nn = nn;
@@ -1714,11 +2083,13 @@ bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double
         cp(h->coef.data(), coef, ne * sizeof(double));
         cp(h->esub.data(), elem_sub, ne * sizeof(int32_t));
         cp(h->dirich.data(), dirichlet, nn);
+        const auto t_copy = std::chrono::steady_clock::now();
         for (int64_t k = 0; k < ne * 8; ++k)
             BDDC_REQUIRE(h->elems[k] >= 0 && h->elems[k] < nn, BDDC_EINVAL, "element node id out of range");
         for (int64_t e = 0; e < ne; ++e)
             BDDC_REQUIRE(h->esub[e] >= 0 && h->esub[e] < nsub, BDDC_EINVAL, "substructure id out of range");
         classify(h);
+        const auto t_class = std::chrono::steady_clock::now();
         for (auto &sd : h->subs) BDDC_REQUIRE(sd.n > 0, BDDC_EINVAL, "substructure without free dofs");
         h->avg_flags = 0;
         // device copies of the mesh and index maps
@@ -1739,8 +2110,16 @@ bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double
         h->ar.upload("gGall", gGall, h->stream);
         h->ar.upload("RG64", RG64, h->stream);
         h->ar.upload("ifgdof", h->iface_gdof, h->stream);
+        const auto t_up = std::chrono::steady_clock::now();
         alloc_solver_buffers(h);
         BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        const auto t_end = std::chrono::steady_clock::now();
+        h->phase_ms[5] = std::chrono::duration<double, std::milli>(t_end - t_host0).count();
+        if (getenv("BDDC_DEBUG_TIMING")) {
+            auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
+            fprintf(stderr, "set_mesh: copy %.3f classify %.3f uploads %.3f buffers %.3f ms\n", ms(t_host0, t_copy),
+                    ms(t_copy, t_class), ms(t_class, t_up), ms(t_up, t_end));
+        }
         h->have_mesh = true;
     });
 }

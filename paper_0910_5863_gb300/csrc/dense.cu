@@ -21,8 +21,10 @@ constexpr int PANEL_ROWS = 128; // rows of the panel solved per CTA
 constexpr int TILE = 64;        // trailing-update tile
 
 // ---------------------------------------------------------------------------
-// panel: factor the nb x nb diagonal block (redundantly per CTA) and solve
-// the rows below it: A[r, kb:kb+nb] <- A[r, kb:kb+nb] L_kk^-T.
+// panel: factor the nb x nb diagonal block in shared memory (redundantly per
+// CTA) and solve the rows below it: A[r, kb:kb+nb] <- A[r, kb:kb+nb] L_kk^-T.
+// Column j of the diagonal block is scaled after the loop, so each column
+// costs one reciprocal square root and two block barriers.
 template <typename T>
 __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc<T> *descs, const int2 *items,
                                                                  int nitems, int kb, DevStatus *st) {
@@ -49,20 +51,26 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
             if (!(dj > T(0))) {
                 bad = 1;
                 dj = T(1);
+                Ld[j][j] = dj;
             }
-            Ld[j][j] = sqrt(dj);
-            inv_d[j] = T(1) / Ld[j][j];
+            inv_d[j] = rsqrt(dj);
         }
         __syncthreads();
-        for (int i = j + 1 + tid; i < nb; i += blockDim.x) Ld[i][j] *= inv_d[j];
-        __syncthreads();
-        int m = nb - j - 1;
+        // trailing update with the unscaled column: a_ik -= a_ij a_kj / a_jj
+        const T inv2 = inv_d[j] * inv_d[j];
+        const int m = nb - j - 1;
         for (int e = tid; e < m * m; e += blockDim.x) {
             int i = j + 1 + e % m, k = j + 1 + e / m;
-            if (i >= k) Ld[i][k] -= Ld[i][j] * Ld[k][j];
+            if (i >= k) Ld[i][k] -= Ld[i][j] * Ld[k][j] * inv2;
         }
         __syncthreads();
     }
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+        int i = e % nb, j = e / nb;
+        if (i > j) Ld[i][j] *= inv_d[j];
+        else if (i == j) Ld[j][j] *= inv_d[j];  // a_jj / sqrt(a_jj)
+    }
+    __syncthreads();
     if (bad && tid == 0 && w.y == 0) dev_fail(st, BDDC_DEV_ERR_NOTSPD, w.x, kb);
     if (w.y == 0) {
         for (int e = tid; e < nb * nb; e += blockDim.x) {
@@ -79,11 +87,13 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
 #pragma unroll
         for (int c = 0; c < NB; ++c) {
             if (c < nb) {
-                T s = x[c];
+                T s0 = x[c], s1 = T(0);
 #pragma unroll
-                for (int k = 0; k < NB; ++k)
-                    if (k < c) s -= x[k] * Ld[c][k];
-                x[c] = s * inv_d[c];
+                for (int k = 0; k < NB; k += 2) {
+                    if (k < c) s0 -= x[k] * Ld[c][k];
+                    if (k + 1 < c) s1 -= x[k + 1] * Ld[c][k + 1];
+                }
+                x[c] = (s0 + s1) * inv_d[c];
             }
         }
 #pragma unroll
@@ -177,16 +187,26 @@ __global__ void gather_kernel(const GatherOp *ops, const int2 *items, int nitems
                         a = b;
                         b = t;
                     }
-                    v = o.src[(size_t)b * o.ld_src + a];
+                    v = o.src_f32 ? (double)reinterpret_cast<const float *>(o.src)[(size_t)b * o.ld_src + a]
+                                  : o.src[(size_t)b * o.ld_src + a];
                 }
                 if (o.rscale) v *= o.rscale[p];
                 if (o.cscale) v *= o.cscale[q];
             }
-            double *dp = o.dst + (size_t)(q + o.dst_col_off) * o.ld_dst + p + o.dst_row_off;
-            if (o.accumulate)
-                *dp += o.scale * v;
-            else
-                *dp = o.scale * v;
+            const size_t di = (size_t)(q + o.dst_col_off) * o.ld_dst + p + o.dst_row_off;
+            if (o.dst_f32) {
+                float *dp = reinterpret_cast<float *>(o.dst) + di;
+                if (o.accumulate)
+                    *dp += (float)(o.scale * v);
+                else
+                    *dp = (float)(o.scale * v);
+            } else {
+                double *dp = o.dst + di;
+                if (o.accumulate)
+                    *dp += o.scale * v;
+                else
+                    *dp = o.scale * v;
+            }
         }
     }
 }
@@ -196,8 +216,24 @@ __global__ void diag_set_kernel(const DiagOp *ops, int nops) {
     int it = blockIdx.x;
     if (it >= nops) return;
     DiagOp o = ops[it];
-    for (int k = threadIdx.x; k < o.n; k += blockDim.x)
-        o.dst[(size_t)(o.col_off + k) * o.ld + o.row_off + k] = o.value;
+    for (int k = threadIdx.x; k < o.n; k += blockDim.x) {
+        const size_t di = (size_t)(o.col_off + k) * o.ld + o.row_off + k;
+        if (o.f32)
+            reinterpret_cast<float *>(o.dst)[di] = (float)o.value;
+        else
+            o.dst[di] = o.value;
+    }
+}
+
+// zero many buffers in one launch: item = (segment, chunk of 8192 elements)
+__global__ void zero_many_kernel(double *const *ptrs, const int64_t *sizes, const int2 *items, int nitems) {
+    int it = blockIdx.x;
+    if (it >= nitems) return;
+    int2 w = items[it];
+    double *p = ptrs[w.x];
+    const int64_t n = sizes[w.x];
+    const int64_t base = (int64_t)w.y * 8192;
+    for (int64_t k = base + threadIdx.x; k < base + 8192 && k < n; k += blockDim.x) p[k] = 0.0;
 }
 
 __global__ void zero_kernel(double *p, size_t n) {
@@ -428,6 +464,9 @@ void launch_zero(double *p, size_t n, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     zero_kernel<<<blocks, 256, 0, s>>>(p, n);
+}
+void launch_zero_many(double *const *ptrs, const int64_t *sizes, const int2 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) zero_many_kernel<<<nitems, 256, 0, s>>>(ptrs, sizes, items, nitems);
 }
 void launch_scatter(double *dst, const int64_t *idx, const double *src, int64_t n, cudaStream_t s) {
     if (n > 0) scatter_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(dst, idx, src, n);

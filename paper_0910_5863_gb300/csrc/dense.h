@@ -32,13 +32,17 @@ struct GatherOp {
     int src_sym;          // src symmetric, lower triangle stored
     int dst_lower;        // write only dst rows >= cols
     int accumulate;
+    int src_f32;          // src points to float
+    int dst_f32;          // dst points to float
     int pad;
 };
 
 struct DiagOp {
-    double *dst;
+    double *dst;          // float * when f32
     int ld, row_off, col_off, n;
     double value;
+    int f32;
+    int pad;
 };
 
 struct GemmDesc {
@@ -66,6 +70,8 @@ void launch_pchol_update(const PcholDesc<T> *descs, const int4 *items, int nitem
 void launch_gather(const GatherOp *ops, const int2 *items, int nitems, cudaStream_t s);
 void launch_diag_set(const DiagOp *ops, int nops, cudaStream_t s);
 void launch_zero(double *p, size_t n, cudaStream_t s);
+// zero many buffers in one launch; items = (segment, 8192-element chunk)
+void launch_zero_many(double *const *ptrs, const int64_t *sizes, const int2 *items, int nitems, cudaStream_t s);
 // dst[idx[k]] = src[k] (scatter) or dst[k] = src[idx[k]] (gather), k < n
 void launch_scatter(double *dst, const int64_t *idx, const double *src, int64_t n, cudaStream_t s);
 void launch_gatherv(double *dst, const int64_t *idx, const double *src, int64_t n, cudaStream_t s);

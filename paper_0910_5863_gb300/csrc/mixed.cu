@@ -1,0 +1,236 @@
+// Mixed-precision interior elimination: FP32 factorization, FP64 refinement.
+//
+// For each substructure, with the equilibration D = diag(A)^-1/2:
+//   1. an FP32 partial Cholesky of [[D A_II D, .], [I, 0]] leaves -(D A_II D)^-1
+//      in its trailing block (the explicit FP32 inverse K_s);
+//   2. X = A_II^-1 A_IG is refined in FP64:  R = A_IG - A_II X  (FP64, the
+//      sparse interior columns of A_i in ELL form),  X += D K_s D R  (FP32
+//      product, FP64 accumulation of X);
+//   3. S_i = A_GG - A_GI X  in FP64 (the same sparse product over the
+//      interface rows) -- the Schur complement of Section 2 of the paper.
+// The same refinement solves A_II y = f_I for the condensed right-hand side
+// and the interior recovery.
+#include "common.cuh"
+#include "mixed.h"
+
+namespace bddc {
+
+// eq[k] = 1 / sqrt(A_kk) for every local dof of every substructure
+__global__ void equilibrate_kernel(const MixedSub *subs, int nsub) {
+    const MixedSub s = subs[blockIdx.x];
+    for (int k = threadIdx.x; k < s.n; k += blockDim.x) s.eq[k] = rsqrt(s.A[(size_t)k * s.ld + k]);
+}
+
+// ELL copy of the interior columns of A: row r keeps (c, a_rc) for c < nI and a_rc != 0.
+// A is symmetric, so row r is read as column r (contiguous).  One warp per row.
+__global__ void ell_build_kernel(const MixedSub *subs, const int2 *items, int nitems, DevStatus *st) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int it = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (it >= nitems) return;
+    const int2 w = items[it];
+    const MixedSub s = subs[w.x];
+    const int r = w.y;
+    const double *col = s.A + (size_t)r * s.ld;
+    int cnt = 0;
+    for (int c0 = 0; c0 < s.nI; c0 += 32) {
+        const int c = c0 + lane;
+        const double v = c < s.nI ? col[c] : 0.0;
+        const unsigned m = __ballot_sync(0xffffffffu, v != 0.0);
+        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+        if (v != 0.0 && pos < s.ell_w) {
+            s.ell_col[(size_t)r * s.ell_w + pos] = c;
+            s.ell_val[(size_t)r * s.ell_w + pos] = v;
+        }
+        cnt += __popc(m);
+    }
+    if (cnt > s.ell_w) {
+        if (lane == 0) dev_fail(st, BDDC_DEV_ERR_BOUNDS, w.x, r);
+        cnt = s.ell_w;
+    }
+    if (lane == 0) s.ell_cnt[r] = cnt;
+}
+
+// out[r, c] = B[r, c] - sum_q val[r, q] X[col[r, q], c]   for r in [r0, r0 + m), c < ncol
+// (B may be null = 0).  Thread per (r, c), r fastest.
+__global__ void ell_residual_kernel(const EllProduct *ps, const int2 *items, int nitems) {
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const int2 w = items[it];
+    const EllProduct p = ps[w.x];
+    const int64_t e = (int64_t)w.y * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)p.m * p.ncol) return;
+    const int i = (int)(e % p.m), c = (int)(e / p.m);
+    const int r = p.r0 + i;
+    const int cnt = p.ell_cnt[r];
+    const int *cols = p.ell_col + (size_t)r * p.ell_w;
+    const double *vals = p.ell_val + (size_t)r * p.ell_w;
+    const double *x = p.X + (size_t)c * p.ldx;
+    double acc = 0.0;
+    for (int q = 0; q < cnt; ++q) acc += vals[q] * x[cols[q]];
+    const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
+    p.out[(size_t)c * p.ldo + i] = b - acc;
+}
+
+// X[r, c] += d[r] * sum_k K[r, k] * float(d[k] R[k, c])   (64 x 64 tiles, k-step 32, FP32 products)
+__global__ void __launch_bounds__(256) mixed_update_kernel(const MixedUpdate *us, const int4 *items, int nitems) {
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const int4 w = items[it];
+    const MixedUpdate u = us[w.x];
+    const int m0 = w.y * 64, n0 = w.z * 64;
+    __shared__ float Ks[32][65];
+    __shared__ float Rs[32][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < u.n; k0 += 32) {
+        for (int e = tid; e < 32 * 64; e += 256) {
+            const int rr = e % 64, kk = e / 64;
+            // K[m0 + rr, k0 + kk], column-major (contiguous in rr)
+            float kv = 0.f;
+            if (m0 + rr < u.n && k0 + kk < u.n) kv = u.K[(size_t)(k0 + kk) * u.ldk + m0 + rr];
+            Ks[kk][rr] = kv;
+        }
+        for (int e = tid; e < 32 * 64; e += 256) {
+            const int kk = e % 32, cc = e / 32;
+            float rv = 0.f;
+            if (k0 + kk < u.n && n0 + cc < u.ncol)
+                rv = (float)(u.d[k0 + kk] * u.R[(size_t)(n0 + cc) * u.ldr + k0 + kk]);
+            Rs[kk][cc] = rv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Ks[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Rs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = n0 + ty + 16 * j;
+        if (c >= u.ncol) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = m0 + tx + 16 * i;
+            if (r < u.n) u.X[(size_t)c * u.ldx + r] += u.d[r] * (double)acc[i][j];
+        }
+    }
+}
+
+// S[i, j] -= sum_k X[k, i] R[k, j]  (i, j < m, k < n): the energy correction of the
+// Schur complement, S(X) = A_GG - A_GI X - X^T (A_IG - A_II X) = S + E^T A_II E for
+// X = A_II^-1 A_IG + E.  The term is small, so FP32 products suffice.
+__global__ void __launch_bounds__(256) gram_correct_kernel(const GramCorrect *gs, const int4 *items, int nitems) {
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const int4 w = items[it];
+    const GramCorrect g = gs[w.x];
+    const int i0 = w.y * 64, j0 = w.z * 64;
+    __shared__ float Xs[32][65];
+    __shared__ float Rs[32][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < g.n; k0 += 32) {
+        for (int e = tid; e < 32 * 64; e += 256) {
+            const int kk = e % 32, cc = e / 32;
+            float xv = 0.f, rv = 0.f;
+            if (k0 + kk < g.n) {
+                if (i0 + cc < g.m) xv = (float)g.X[(size_t)(i0 + cc) * g.ldx + k0 + kk];
+                if (j0 + cc < g.m) rv = (float)g.R[(size_t)(j0 + cc) * g.ldr + k0 + kk];
+            }
+            Xs[kk][cc] = xv;
+            Rs[kk][cc] = rv;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Xs[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Rs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = j0 + ty + 16 * j;
+        if (c >= g.m) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = i0 + tx + 16 * i;
+            if (r < g.m) g.S[(size_t)c * g.lds + r] -= (double)acc[i][j];
+        }
+    }
+}
+
+// per substructure: sums of R^2 and B^2 (for the refinement check)
+__global__ void residual_norms_kernel(const EllProduct *ps, int np, double *out) {
+    __shared__ double scratch[32];
+    const EllProduct p = ps[blockIdx.x];
+    double rr = 0.0, bb = 0.0;
+    for (int64_t e = threadIdx.x; e < (int64_t)p.m * p.ncol; e += blockDim.x) {
+        const int i = (int)(e % p.m), c = (int)(e / p.m);
+        const double r = p.out[(size_t)c * p.ldo + i];
+        const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
+        rr += r * r;
+        bb += b * b;
+    }
+    rr = block_sum(rr, scratch);
+    bb = block_sum(bb, scratch);
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = rr;
+        out[2 * blockIdx.x + 1] = bb;
+    }
+}
+
+// S <- (S + S^T) / 2 for n x n column-major blocks
+__global__ void symmetrize_kernel(double *const *S, const int *n, const int *ld, int ns) {
+    const int s = blockIdx.y;
+    if (s >= ns) return;
+    double *A = S[s];
+    const int nn = n[s], l = ld[s];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nn * nn;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % nn), j = (int)(e / nn);
+        if (i <= j) continue;
+        const double v = 0.5 * (A[(size_t)j * l + i] + A[(size_t)i * l + j]);
+        A[(size_t)j * l + i] = v;
+        A[(size_t)i * l + j] = v;
+    }
+}
+
+void launch_equilibrate(const MixedSub *subs, int nsub, cudaStream_t s) {
+    if (nsub > 0) equilibrate_kernel<<<nsub, 256, 0, s>>>(subs, nsub);
+}
+void launch_ell_build(const MixedSub *subs, const int2 *items, int nitems, DevStatus *st, cudaStream_t s) {
+    if (nitems > 0) ell_build_kernel<<<(nitems + 7) / 8, 256, 0, s>>>(subs, items, nitems, st);
+}
+void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) ell_residual_kernel<<<nitems, 256, 0, s>>>(ps, items, nitems);
+}
+void launch_mixed_update(const MixedUpdate *us, const int4 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) mixed_update_kernel<<<nitems, 256, 0, s>>>(us, items, nitems);
+}
+void launch_gram_correct(const GramCorrect *gs, const int4 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) gram_correct_kernel<<<nitems, 256, 0, s>>>(gs, items, nitems);
+}
+void launch_residual_norms(const EllProduct *ps, int np, double *out, cudaStream_t s) {
+    if (np > 0) residual_norms_kernel<<<np, 256, 0, s>>>(ps, np, out);
+}
+void launch_symmetrize(double *const *S, const int *n, const int *ld, int ns, cudaStream_t s) {
+    if (ns > 0) symmetrize_kernel<<<dim3(64, ns), 256, 0, s>>>(S, n, ld, ns);
+}
+
+}  // namespace bddc

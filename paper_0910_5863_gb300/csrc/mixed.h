@@ -1,0 +1,68 @@
+// Kernels of the mixed-precision interior elimination (mixed.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+
+namespace bddc {
+
+struct MixedSub {
+    const double *A;   // dense local matrix (n x n, ld), FP64, unfactored
+    int n, nI, ld;
+    double *eq;        // (n) equilibration 1/sqrt(A_kk)
+    int *ell_cnt;      // (n) entries kept per row
+    int *ell_col;      // (n x ell_w)
+    double *ell_val;   // (n x ell_w)
+    int ell_w;
+};
+
+// out[r, c] = B[r, c] - sum_{interior cols} A[r0 + r, col] X[col, c], r < m, c < ncol
+struct EllProduct {
+    const int *ell_cnt, *ell_col;
+    const double *ell_val;
+    int ell_w;
+    int r0, m, ncol;
+    const double *X;
+    int ldx;
+    const double *B;   // may be null (= 0)
+    int ldb;
+    double *out;
+    int ldo;
+};
+
+// X[r, c] += d[r] sum_k K[r, k] float(d[k] R[k, c]),  r, k < n, c < ncol
+struct MixedUpdate {
+    const float *K;
+    int ldk;
+    const double *d;
+    const double *R;
+    int ldr;
+    double *X;
+    int ldx;
+    int n, ncol;
+};
+
+// S[i, j] -= sum_k X[k, i] R[k, j], i, j < m, k < n
+struct GramCorrect {
+    const double *X;
+    int ldx;
+    const double *R;
+    int ldr;
+    double *S;
+    int lds;
+    int n, m;
+};
+
+void launch_equilibrate(const MixedSub *subs, int nsub, cudaStream_t s);
+// items: (sub, row), one warp each
+void launch_ell_build(const MixedSub *subs, const int2 *items, int nitems, DevStatus *st, cudaStream_t s);
+// items: (product, block of 256 (r, c) pairs)
+void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cudaStream_t s);
+// items: (update, 64-row tile, 64-column tile)
+void launch_mixed_update(const MixedUpdate *us, const int4 *items, int nitems, cudaStream_t s);
+// items: (correction, 64-row tile, 64-column tile)
+void launch_gram_correct(const GramCorrect *gs, const int4 *items, int nitems, cudaStream_t s);
+void launch_residual_norms(const EllProduct *ps, int np, double *out, cudaStream_t s);
+void launch_symmetrize(double *const *S, const int *n, const int *ld, int ns, cudaStream_t s);
+
+}  // namespace bddc
