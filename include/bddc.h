@@ -86,6 +86,8 @@ typedef struct {
     double kappa;          /* Lanczos estimate lambda_max / lambda_min */
     double setup_ms;       /* last bddc_setup + bddc_adapt, device time */
     double solve_ms;       /* this solve, device time */
+    int interior_fp32;     /* 1: S_i came from the FP32 factorization + FP64 refinement */
+    int coarse_fp32;       /* 1: the local saddle operators came from the FP32 factorization */
 } bddc_solve_info;
 
 /* Fills *opt with the defaults above. */
@@ -170,6 +172,13 @@ BDDC_API bddc_status bddc_get_interface_dofs(const bddc_handle *h, int s, int64_
 /* S_s after bddc_setup, n x n column-major into S (ld >= n), ordered as
  * bddc_get_interface_dofs; mem = where S lives. */
 BDDC_API bddc_status bddc_get_schur(const bddc_handle *h, int s, double *S, int ld, int mem);
+
+/* The assembled local stiffness matrix A_s (n x n, column-major into A, ld >= n),
+ * ordered [interior dofs ascending; interface dofs ascending], as assembled by
+ * the last bddc_setup.  In BDDC_FP64 mode the factorization overwrites the
+ * lower triangle in place, so the call returns BDDC_ESTATE after a setup in
+ * that mode; in BDDC_MIXED mode the assembled matrix is kept. */
+BDDC_API bddc_status bddc_get_local_matrix(const bddc_handle *h, int s, double *A, int ld, int mem);
 
 /* One application of the preconditioner (z = M r) or of the assembled Schur
  * operator (y = S x) to an interface vector (length n_interface). */

@@ -25,7 +25,7 @@ EXPORTS = ["bddc_default_options", "bddc_create", "bddc_destroy", "bddc_set_mesh
            "bddc_setup", "bddc_adapt", "bddc_solve", "bddc_condition_estimate", "bddc_get_sizes",
            "bddc_get_corners", "bddc_get_face_eigs", "bddc_get_interface_dofs", "bddc_get_schur",
            "bddc_apply_preconditioner", "bddc_apply_schur", "bddc_launch_count", "bddc_status_str",
-           "bddc_last_error", "bddc_get_phase_times"]
+           "bddc_last_error", "bddc_get_phase_times", "bddc_get_local_matrix"]
 PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
           "analysis_host", "condensed_rhs", "pcg", "recovery"]
 
@@ -41,7 +41,8 @@ class AdaptInfo(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("relres", C.c_double), ("kappa", C.c_double),
-                ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("interior_fp32", C.c_int),
+                ("coarse_fp32", C.c_int)]
 
 
 class BddcError(RuntimeError):
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
         "bddc_status_str": (C.c_char_p, [i32]),
         "bddc_last_error": (C.c_char_p, [vp]),
         "bddc_get_phase_times": (i32, [vp, vp, vp, i32, vp]),
+        "bddc_get_local_matrix": (i32, [vp, i32, vp, i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -182,7 +184,8 @@ class Solver:
         assert mem == mem2
         info = SolveInfo()
         st = self.lib.bddc_solve(self.h, pf, pu, mem, C.byref(info))
-        out = {"iters": info.iters, "converged": bool(info.converged), "relres": info.relres, "kappa": info.kappa}
+        out = {"iters": info.iters, "converged": bool(info.converged), "relres": info.relres, "kappa": info.kappa,
+               "interior_fp32": bool(info.interior_fp32), "coarse_fp32": bool(info.coarse_fp32)}
         if check or st not in (0, 5):
             self._check(st)
         out["status"] = STATUS.get(st, st)
@@ -229,6 +232,12 @@ class Solver:
         S = np.zeros((n, n))
         self._check(self.lib.bddc_get_schur(self.h, s, S.ctypes.data, n, MEM_HOST))
         return S.T.copy()   # column-major -> row-major (symmetric anyway)
+
+    def local_matrix(self, s, n):
+        """Assembled A_s (n x n, [interior; interface]); mixed mode, after setup."""
+        A = np.zeros((n, n))
+        self._check(self.lib.bddc_get_local_matrix(self.h, s, A.ctypes.data, n, MEM_HOST))
+        return A.T.copy()
 
     def apply_preconditioner(self, r):
         r = np.ascontiguousarray(r, dtype=np.float64)

@@ -132,6 +132,13 @@ struct bddc_handle {
     std::vector<double *> face_rows_dev;
     int face_row_ld = 0;
     bool coarse_dirty = true;   // coarse operators are (re)built before the next solve
+    bool assembled = false;     // dense local matrices hold the assembled A_i
+    bool coarse_fp32 = false;   // the current coarse operators used the FP32 local saddle
+    bool interior_fp32 = false; // the current S_i came from the mixed interior elimination
+    int interior_fallbacks = 0; // mixed mode: FP32 interior elimination rejected, redone in FP64
+    int coarse_fallbacks = 0;   // mixed mode: FP32 local saddle rejected, rebuilt in FP64
+    float m1_min_pivot = 0.f;
+    bool factored = false;      // FP64 mode: A_i factored in place
     int mixed_iters = 0;        // refinement steps the interior elimination needed (mixed mode)
     double mixed_relres = 0.0;  // largest relative residual of the refined A_II X = A_IG
     // phase timing: events [2k, 2k+1] bracket phase k
@@ -148,9 +155,14 @@ void fail_check(bddc_handle *h, const char *where) {
     DevStatus hs;
     BDDC_CUDA(cudaMemcpyAsync(&hs, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
     BDDC_CUDA(cudaStreamSynchronize(h->stream));
-    if (hs.code == BDDC_DEV_ERR_NOTSPD)
-        throw Error{BDDC_ENOTSPD, std::string(where) + ": non-positive pivot in matrix " + std::to_string(hs.item) +
-                                      " near column " + std::to_string(hs.pos)};
+    if (hs.code == BDDC_DEV_ERR_NOTSPD) {
+        static const char *names[] = {"?", "interior A_II", "local saddle", "local saddle (FP32)", "local saddle stage 2",
+                                      "coarse matrix", "face condensation", "pair corner elimination",
+                                      "pair deflated jump system", "interior A_II (FP32)"};
+        const int tag = hs.item / 100000, m = hs.item % 100000;
+        throw Error{BDDC_ENOTSPD, std::string(where) + ": non-positive pivot in " + names[tag >= 0 && tag < 10 ? tag : 0] +
+                                      " matrix " + std::to_string(m) + " near column " + std::to_string(hs.pos)};
+    }
     if (hs.code == BDDC_DEV_ERR_TIMEOUT) throw Error{BDDC_ETIMEOUT, std::string(where) + ": device wait timed out"};
     if (hs.code != 0) throw Error{BDDC_ECUDA, std::string(where) + ": device error " + std::to_string(hs.code)};
 }
@@ -179,9 +191,23 @@ void check_launch(bddc_handle *h) {
 }
 
 // ---- batched partial Cholesky ------------------------------------------------
+// batch tags reported with a failed pivot
+int pchol_tag(const std::string &name) {
+    static const char *names[] = {"", "AII", "M1", "M1f", "M2", "MC", "E1", "E2", "E3", "F"};
+    for (int k = 1; k < 10; ++k)
+        if (name == names[k]) return k;
+    return 0;
+}
+
 template <typename T>
-void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs, const std::string &tag) {
-    if (descs.empty()) return;
+void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const std::string &tag) {
+    if (descs_in.empty()) return;
+    std::vector<PcholDesc<T>> descs(descs_in);
+    T *scratch = static_cast<T *>(h->ar.get("pc_diag_" + tag, descs.size() * kPanelNB * kPanelNB * sizeof(T)));
+    for (size_t k = 0; k < descs.size(); ++k) {
+        descs[k].tag = pchol_tag(tag);
+        descs[k].diag = scratch + k * kPanelNB * kPanelNB;
+    }
     int nsteps = 0;
     for (auto &d : descs) nsteps = std::max(nsteps, (d.nstop + kPanelNB - 1) / kPanelNB);
     std::vector<int2> pitems;
@@ -198,6 +224,7 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs, const std
             int below = d.n - kb - nb;
             int np = std::max(1, (below + kPanelRows - 1) / kPanelRows);
             for (int r = 0; r < np; ++r) pitems.push_back(make_int2(m, r));
+            uitems.push_back(make_int4(m, -1, -1, 0));  // copy of the factored diagonal block
             int tn = d.n - kb - nb;
             int nt = (tn + kTile - 1) / kTile;
             for (int ti = 0; ti < nt; ++ti)
@@ -213,10 +240,8 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs, const std
         int kb = s * kPanelNB;
         launch_pchol_panel<T>(dd, dp + poff[s], poff[s + 1] - poff[s], kb, h->dst, h->stream);
         check_launch(h);
-        if (uoff[s + 1] > uoff[s]) {
-            launch_pchol_update<T>(dd, du + uoff[s], uoff[s + 1] - uoff[s], kb, h->stream);
-            check_launch(h);
-        }
+        launch_pchol_update<T>(dd, du + uoff[s], uoff[s + 1] - uoff[s], kb, h->stream);
+        check_launch(h);
     }
 }
 
@@ -820,9 +845,12 @@ void layout_constraints(bddc_handle *h) {
 //   M2 = [G . . .; Z_a K . .; H^T Z_c^T J .; I 0 0 0], stop n_a:
 //        trailing = [[P_rr, -Phi_rc, -Phi_ra]; [., J - H^T G^-1 H, -H^T G^-1]; [., ., -G^-1]]
 // with K = S_rr^-1, Z = K [S_rc, C_r^T], G = C_r K C_r^T, H = C_r K S_rc, J = S_cr K S_rc.
-void coarse_setup(bddc_handle *h) {
+// Thrown by the mixed local saddle factorization when FP32 is not accurate enough.
+struct Fp32Breakdown {};
+
+void coarse_setup(bddc_handle *h, bool allow_fp32) {
     const int ns = h->nsub;
-    const bool mixed = h->opt.precision == BDDC_MIXED;
+    const bool mixed = h->opt.precision == BDDC_MIXED && allow_fp32;
     layout_constraints(h);
     // mixed: M1 in FP32 with the symmetric equilibration d = diag(S)^-1/2 of the remaining dofs
     double *eqS = nullptr, *dr = nullptr, *s2 = nullptr;
@@ -915,10 +943,22 @@ void coarse_setup(bddc_handle *h) {
     zero_all(h, zl, "M12");
     run_gathers(h, g1, "M1");
     run_diag(h, id1, "M1");
-    if (mixed)
+    if (mixed) {
+        // the equilibrated S_rr has a unit diagonal: a pivot below 1e-5 means a condition
+        // number FP32 cannot carry; the coarse operators are then rebuilt in FP64
+        static const unsigned inf_bits = 0x7f800000u;
+        BDDC_CUDA(cudaMemcpyAsync(&h->dst->minpiv, &inf_bits, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream));
         run_pchol<float>(h, d1f, "M1f");
-    else
+        DevStatus hs;
+        BDDC_CUDA(cudaMemcpyAsync(&hs, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        float minpiv;
+        memcpy(&minpiv, &hs.minpiv, sizeof(float));
+        h->m1_min_pivot = minpiv;
+        if (hs.code == BDDC_DEV_ERR_NOTSPD || !(minpiv >= 1e-5f)) throw Fp32Breakdown{};
+    } else {
         run_pchol<double>(h, d1, "M1");
+    }
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
         const int nr = (int)sd.rpos.size(), nc = (int)sd.cpos.size(), na = sd.na;
@@ -949,6 +989,12 @@ void coarse_setup(bddc_handle *h) {
     run_gathers(h, g2, "M2");
     run_diag(h, id2, "M2");
     run_pchol<double>(h, d2, "M2");
+    if (mixed) {  // G = C_r S_rr^-1 C_r^T from the FP32 stage must factor
+        DevStatus hs;
+        BDDC_CUDA(cudaMemcpyAsync(&hs, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        if (hs.code == BDDC_DEV_ERR_NOTSPD) throw Fp32Breakdown{};
+    }
     // extraction of P~, Phi~, S_C,i
     std::vector<CoarseAsmDesc> cad;
     std::vector<int> Rc_all;
@@ -1211,6 +1257,7 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     std::vector<EllProduct> ps;
     std::vector<MixedUpdate> us, us0;
     std::vector<int4> uitems;
+    std::vector<int2> vitems;
     ZeroList zx;
     for (int k = 0; k < (int)jobs.size(); ++k) {
         const auto &j = jobs[k];
@@ -1232,25 +1279,38 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
         const double *eq = h->ar.get_t<double>("eq_" + t, sd.n);
         us.push_back(MixedUpdate{K, ldk, eq, j.R, j.ldr, j.X, j.ldx, sd.nI, j.ncol});
         us0.push_back(MixedUpdate{K, ldk, eq, j.B, j.ldb, j.X, j.ldx, sd.nI, j.ncol});
-        for (int a = 0; a < (sd.nI + 63) / 64; ++a)
-            for (int b = 0; b < (j.ncol + 63) / 64; ++b) uitems.push_back(make_int4(k, a, b, 0));
+        if (j.ncol == 1) {
+            for (int a = 0; a < (sd.nI + 7) / 8; ++a) vitems.push_back(make_int2(k, a));
+        } else {
+            for (int a = 0; a < (sd.nI + 63) / 64; ++a)
+                for (int b = 0; b < (j.ncol + 63) / 64; ++b) uitems.push_back(make_int4(k, a, b, 0));
+        }
         zx.add(j.X, (size_t)j.ldx * j.ncol);
     }
     zero_all(h, zx, "X_" + tag);
     auto *dus = h->ar.upload("mu_" + tag, us, h->stream);
     auto *dus0 = h->ar.upload("mu0_" + tag, us0, h->stream);
     auto *dui = h->ar.upload("mui_" + tag, uitems, h->stream);
+    auto *dvi = h->ar.upload("mvi_" + tag, vitems, h->stream);
+    auto update = [&](const MixedUpdate *d) {
+        launch_mixed_update(d, dui, (int)uitems.size(), h->stream);
+        launch_mixed_update_vec(d, dvi, (int)vitems.size(), h->stream);
+        check_launch(h);
+    };
     auto *dps = h->ar.upload("mps_" + tag, ps, h->stream);
     double *norms = h->ar.get_t<double>("rnorm_" + tag, 2 * jobs.size());
     std::vector<double> hn(2 * jobs.size());
-    launch_mixed_update(dus0, dui, (int)uitems.size(), h->stream);
-    check_launch(h);
+    std::vector<int> col_off(jobs.size() + 1, 0);
+    for (size_t k = 0; k < jobs.size(); ++k) col_off[k + 1] = col_off[k] + jobs[k].ncol;
+    int *dcol_off = h->ar.upload("rn_off_" + tag, col_off, h->stream);
+    double *colsums = h->ar.get_t<double>("rn_cols_" + tag, 2 * (size_t)std::max(col_off.back(), 1));
+    update(dus0);
     int done = 1;
     for (;;) {
         if (!check && done >= corrections) break;
         run_ell(h, ps, tag);
         if (check) {
-            launch_residual_norms(dps, (int)ps.size(), norms, h->stream);
+            launch_residual_norms(dps, (int)ps.size(), colsums, dcol_off, norms, h->stream);
             check_launch(h);
             BDDC_CUDA(cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             BDDC_CUDA(cudaStreamSynchronize(h->stream));
@@ -1263,8 +1323,7 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
                          "mixed-precision refinement of the interior solves did not converge (relative residual " +
                              std::to_string(worst) + "); use BDDC_FP64");
         }
-        launch_mixed_update(dus, dui, (int)uitems.size(), h->stream);
-        check_launch(h);
+        update(dus);
         ++done;
     }
     return done;
@@ -1376,7 +1435,19 @@ void count_coarse(bddc_handle *h) {
 void ensure_coarse(bddc_handle *h) {
     if (!h->coarse_dirty) return;
     phase_begin(h, 2);
-    coarse_setup(h);
+    h->coarse_fp32 = false;
+    if (h->opt.precision == BDDC_MIXED) {
+        try {
+            coarse_setup(h, true);
+            h->coarse_fp32 = true;
+        } catch (const Fp32Breakdown &) {
+            reset_status(h);
+            h->coarse_fallbacks++;
+            coarse_setup(h, false);
+        }
+    } else {
+        coarse_setup(h, false);
+    }
     phase_end(h, 2);
     phase_collect(h, 2, 2);
     h->coarse_dirty = false;
@@ -1433,15 +1504,29 @@ void do_setup(bddc_handle *h) {
     launch_weights(h->ops, diag, total, delta, h->stream);
     check_launch(h);
     phase_end(h, 0);
+    h->assembled = true;
     phase_begin(h, 1);
     // interior elimination: partial Cholesky of every A_i with nstop = n_I
     double fl = 0.0;
     for (auto &sd : h->subs)
         fl += (double)sd.nI * sd.nI * sd.nI / 3.0 + (double)sd.nI * sd.nI * sd.nG + (double)sd.nI * sd.nG * sd.nG;
     h->phase_flop[1] = fl;
-    if (h->opt.precision == BDDC_MIXED) {
-        interior_mixed(h);
-    } else {
+    h->interior_fp32 = false;
+    bool fp64_interior = h->opt.precision != BDDC_MIXED;
+    if (!fp64_interior) {
+        try {
+            interior_mixed(h);
+            h->interior_fp32 = true;
+        } catch (const Error &e) {
+            // FP32 factorization or refinement failed: the interior elimination is redone in FP64
+            if (e.status != BDDC_ENOCONV && e.status != BDDC_ENOTSPD) throw;
+            reset_status(h);
+            h->interior_fallbacks++;
+            fp64_interior = true;
+        }
+    }
+    h->factored = fp64_interior;
+    if (fp64_interior) {
         std::vector<PcholDesc<double>> d;
         for (int s = 0; s < ns; ++s)
             d.push_back(PcholDesc<double>{h->subs[s].A, h->subs[s].n, h->subs[s].ld, h->subs[s].nI, 0});
@@ -1853,7 +1938,7 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
     launch_gatherv(yI, gIall, df, h->sumI, h->stream);
     check_launch(h);
     (void)gGall;
-    const bool mixed = h->opt.precision == BDDC_MIXED;
+    const bool mixed = h->interior_fp32;
     // mixed: y = A_II^{-1} f_I by refinement (yI keeps f_I), g_i = -A_GI y (sparse)
     double *yx = h->ar.get_t<double>("yIx", std::max<int64_t>(h->sumI, 1));
     double *yr = h->ar.get_t<double>("yIr", std::max<int64_t>(h->sumI, 1));
@@ -1966,6 +2051,8 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
         info->setup_ms = h->phase_ms[0] + h->phase_ms[1] + h->phase_ms[2] + h->phase_ms[3] + h->phase_ms[4] +
                          h->phase_ms[5];
         info->solve_ms = h->phase_ms[6] + h->phase_ms[7] + h->phase_ms[8];
+        info->interior_fp32 = h->interior_fp32 ? 1 : 0;
+        info->coarse_fp32 = h->coarse_fp32 ? 1 : 0;
     }
     if (!it[1]) throw Error{BDDC_ENOCONV, "PCG did not reach the tolerance within maxit"};
 }
@@ -2065,6 +2152,7 @@ bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double
         BDDC_REQUIRE(xyz && elems && coef && elem_sub && dirichlet, BDDC_EINVAL, "null array");
         const auto t_host0 = std::chrono::steady_clock::now();
         h->have_mesh = h->have_setup = false;
+        h->assembled = h->factored = false;
         h->ncomp = ncomp;
         h->nn = nn;
         h->ne = ne;
@@ -2250,6 +2338,17 @@ bddc_status bddc_get_interface_dofs(const bddc_handle *h, int s, int64_t *gdofs,
     if (n) *n = sd.nG;
     for (int k = 0; k < sd.nG && k < cap; ++k) gdofs[k] = sd.gG[k];
     return BDDC_OK;
+}
+
+bddc_status bddc_get_local_matrix(const bddc_handle *h, int s, double *A, int ld, int mem) {
+    if (!h || !h->assembled) return BDDC_ESTATE;
+    if (h->opt.precision != BDDC_MIXED && h->factored) return BDDC_ESTATE;
+    if (s < 0 || s >= h->nsub || ld < h->subs[s].n) return BDDC_EINVAL;
+    const auto &sd = h->subs[s];
+    cudaError_t e = cudaMemcpy2D(A, (size_t)ld * sizeof(double), sd.A, (size_t)sd.ld * sizeof(double),
+                                 (size_t)sd.n * sizeof(double), sd.n,
+                                 mem == BDDC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? BDDC_OK : BDDC_ECUDA;
 }
 
 bddc_status bddc_get_schur(const bddc_handle *h, int s, double *S, int ld, int mem) {

@@ -15,7 +15,8 @@ struct DevStatus {
     int pos;
     unsigned arrive;
     unsigned gen;
-    unsigned pad[3];
+    unsigned minpiv;   // FP32 factorizations: bits of the smallest positive pivot seen
+    unsigned pad[2];
 };
 
 __device__ __forceinline__ void dev_fail(DevStatus *st, int code, int item, int pos) {

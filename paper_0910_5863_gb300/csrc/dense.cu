@@ -52,6 +52,8 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
                 bad = 1;
                 dj = T(1);
                 Ld[j][j] = dj;
+            } else if (sizeof(T) == 4 && w.y == 0) {
+                atomicMin(&st->minpiv, __float_as_uint((float)dj));  // positive floats order as unsigned
             }
             inv_d[j] = rsqrt(dj);
         }
@@ -71,11 +73,14 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
         else if (i == j) Ld[j][j] *= inv_d[j];  // a_jj / sqrt(a_jj)
     }
     __syncthreads();
-    if (bad && tid == 0 && w.y == 0) dev_fail(st, BDDC_DEV_ERR_NOTSPD, w.x, kb);
+    if (bad && tid == 0 && w.y == 0) dev_fail(st, BDDC_DEV_ERR_NOTSPD, d.tag * 100000 + w.x, kb);
+    // Every CTA of this matrix factors the diagonal block from A, so the factor
+    // must not be written into A during this launch: CTA 0 leaves it in the
+    // scratch and the update launch of the same step copies it into A.
     if (w.y == 0) {
         for (int e = tid; e < nb * nb; e += blockDim.x) {
             int i = e % nb, j = e / nb;
-            if (i >= j) A[(size_t)(kb + j) * ld + kb + i] = Ld[i][j];
+            if (i >= j) d.diag[j * NB + i] = Ld[i][j];
         }
     }
     int r = kb + nb + w.y * PANEL_ROWS + tid;
@@ -113,6 +118,13 @@ __global__ void __launch_bounds__(256) pchol_update_kernel(const PcholDesc<T> *d
     const PcholDesc<T> d = descs[w.x];
     const int n = d.n, ld = d.ld;
     const int nb = min(NB, d.nstop - kb);
+    if (w.y < 0) {  // the factored diagonal block of this step, from the panel's scratch
+        for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+            int i = e % nb, j = e / nb;
+            if (i >= j) d.A[(size_t)(kb + j) * ld + kb + i] = d.diag[j * NB + i];
+        }
+        return;
+    }
     const int t0 = kb + nb;
     const int i0 = t0 + w.y * TILE, j0 = t0 + w.z * TILE;
     T *A = d.A;

@@ -13,7 +13,8 @@ struct PcholDesc {
     int n;
     int ld;
     int nstop;
-    int pad;
+    int tag;    // batch tag reported with a failed pivot (item = tag * 100000 + matrix)
+    T *diag;    // NB x NB scratch: the factored diagonal block of the current step
 };
 
 // dst[p + dst_row_off, q + dst_col_off] (+)= scale * rscale[p] * cscale[q] * src(rmap[p], cmap[q])
@@ -65,6 +66,8 @@ struct TrsvDesc {
 template <typename T>
 void launch_pchol_panel(const PcholDesc<T> *descs, const int2 *items, int nitems, int kb, DevStatus *st,
                         cudaStream_t s);
+// update items: (matrix, tile row, tile col); an item with tile row -1 copies the
+// factored diagonal block of the step from the scratch into A
 template <typename T>
 void launch_pchol_update(const PcholDesc<T> *descs, const int4 *items, int nitems, int kb, cudaStream_t s);
 void launch_gather(const GatherOp *ops, const int2 *items, int nitems, cudaStream_t s);

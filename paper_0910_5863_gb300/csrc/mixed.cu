@@ -57,9 +57,9 @@ __global__ void ell_residual_kernel(const EllProduct *ps, const int2 *items, int
     if (it >= nitems) return;
     const int2 w = items[it];
     const EllProduct p = ps[w.x];
-    const int64_t e = (int64_t)w.y * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)p.m * p.ncol) return;
-    const int i = (int)(e % p.m), c = (int)(e / p.m);
+    const int e = w.y * blockDim.x + threadIdx.x;   // m * ncol < 2^31
+    if (e >= p.m * p.ncol) return;
+    const int c = e / p.m, i = e - c * p.m;
     const int r = p.r0 + i;
     const int cnt = p.ell_cnt[r];
     const int *cols = p.ell_col + (size_t)r * p.ell_w;
@@ -124,6 +124,22 @@ __global__ void __launch_bounds__(256) mixed_update_kernel(const MixedUpdate *us
     }
 }
 
+// single right-hand side: x[r] += d[r] sum_k K[r, k] float(d[k] r[k]); one warp per row
+// (K is symmetric, so row r is read as column r).  items: (update, block of 8 rows)
+__global__ void mixed_update_vec_kernel(const MixedUpdate *us, const int2 *items, int nitems) {
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const int2 w = items[it];
+    const MixedUpdate u = us[w.x];
+    const int lane = threadIdx.x & 31, r = w.y * 8 + (threadIdx.x >> 5);
+    if (r >= u.n) return;
+    const float *kr = u.K + (size_t)r * u.ldk;
+    float acc = 0.f;
+    for (int k = lane; k < u.n; k += 32) acc += kr[k] * (float)(u.d[k] * u.R[k]);
+    acc = warp_sum(acc);
+    if (lane == 0) u.X[r] += u.d[r] * (double)acc;
+}
+
 // S[i, j] -= sum_k X[k, i] R[k, j]  (i, j < m, k < n): the energy correction of the
 // Schur complement, S(X) = A_GG - A_GI X - X^T (A_IG - A_II X) = S + E^T A_II E for
 // X = A_II^-1 A_IG + E.  The term is small, so FP32 products suffice.
@@ -175,24 +191,41 @@ __global__ void __launch_bounds__(256) gram_correct_kernel(const GramCorrect *gs
     }
 }
 
-// per substructure: sums of R^2 and B^2 (for the refinement check)
-__global__ void residual_norms_kernel(const EllProduct *ps, int np, double *out) {
+// per product: sums of R^2 and B^2 (for the refinement check).  Blocks =
+// (product, column); the per-column sums are reduced in column order by
+// residual_norms_finish_kernel, so the result is deterministic.
+__global__ void residual_norms_kernel(const EllProduct *ps, int np, double *colsums, const int *col_off) {
     __shared__ double scratch[32];
-    const EllProduct p = ps[blockIdx.x];
+    const int k = blockIdx.y;
+    if (k >= np) return;
+    const EllProduct p = ps[k];
+    for (int c = blockIdx.x; c < p.ncol; c += gridDim.x) {
+        double rr = 0.0, bb = 0.0;
+        const double *o = p.out + (size_t)c * p.ldo;
+        const double *b = p.B ? p.B + (size_t)c * p.ldb : nullptr;
+        for (int i = threadIdx.x; i < p.m; i += blockDim.x) {
+            rr += o[i] * o[i];
+            if (b) bb += b[i] * b[i];
+        }
+        rr = block_sum(rr, scratch);
+        bb = block_sum(bb, scratch);
+        if (threadIdx.x == 0) {
+            colsums[2 * (col_off[k] + c)] = rr;
+            colsums[2 * (col_off[k] + c) + 1] = bb;
+        }
+    }
+}
+
+__global__ void residual_norms_finish_kernel(const double *colsums, const int *col_off, int np, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
     double rr = 0.0, bb = 0.0;
-    for (int64_t e = threadIdx.x; e < (int64_t)p.m * p.ncol; e += blockDim.x) {
-        const int i = (int)(e % p.m), c = (int)(e / p.m);
-        const double r = p.out[(size_t)c * p.ldo + i];
-        const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
-        rr += r * r;
-        bb += b * b;
+    for (int c = col_off[k]; c < col_off[k + 1]; ++c) {
+        rr += colsums[2 * c];
+        bb += colsums[2 * c + 1];
     }
-    rr = block_sum(rr, scratch);
-    bb = block_sum(bb, scratch);
-    if (threadIdx.x == 0) {
-        out[2 * blockIdx.x] = rr;
-        out[2 * blockIdx.x + 1] = bb;
-    }
+    out[2 * k] = rr;
+    out[2 * k + 1] = bb;
 }
 
 // S <- (S + S^T) / 2 for n x n column-major blocks
@@ -223,11 +256,17 @@ void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cu
 void launch_mixed_update(const MixedUpdate *us, const int4 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) mixed_update_kernel<<<nitems, 256, 0, s>>>(us, items, nitems);
 }
+void launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) mixed_update_vec_kernel<<<nitems, 256, 0, s>>>(us, items, nitems);
+}
 void launch_gram_correct(const GramCorrect *gs, const int4 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) gram_correct_kernel<<<nitems, 256, 0, s>>>(gs, items, nitems);
 }
-void launch_residual_norms(const EllProduct *ps, int np, double *out, cudaStream_t s) {
-    if (np > 0) residual_norms_kernel<<<np, 256, 0, s>>>(ps, np, out);
+void launch_residual_norms(const EllProduct *ps, int np, double *colsums, const int *col_off, double *out,
+                           cudaStream_t s) {
+    if (np <= 0) return;
+    residual_norms_kernel<<<dim3(64, np), 256, 0, s>>>(ps, np, colsums, col_off);
+    residual_norms_finish_kernel<<<(np + 127) / 128, 128, 0, s>>>(colsums, col_off, np, out);
 }
 void launch_symmetrize(double *const *S, const int *n, const int *ld, int ns, cudaStream_t s) {
     if (ns > 0) symmetrize_kernel<<<dim3(64, ns), 256, 0, s>>>(S, n, ld, ns);

@@ -42,6 +42,9 @@ struct MixedUpdate {
     int n, ncol;
 };
 
+// ncol == 1 variant; items: (update, block of 8 rows)
+void launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, cudaStream_t s);
+
 // S[i, j] -= sum_k X[k, i] R[k, j], i, j < m, k < n
 struct GramCorrect {
     const double *X;
@@ -62,7 +65,10 @@ void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cu
 void launch_mixed_update(const MixedUpdate *us, const int4 *items, int nitems, cudaStream_t s);
 // items: (correction, 64-row tile, 64-column tile)
 void launch_gram_correct(const GramCorrect *gs, const int4 *items, int nitems, cudaStream_t s);
-void launch_residual_norms(const EllProduct *ps, int np, double *out, cudaStream_t s);
+// out[2k] = |R_k|^2, out[2k+1] = |B_k|^2; colsums holds 2 doubles per column of all products,
+// col_off (np + 1) the first column of each product
+void launch_residual_norms(const EllProduct *ps, int np, double *colsums, const int *col_off, double *out,
+                           cudaStream_t s);
 void launch_symmetrize(double *const *S, const int *n, const int *ld, int ns, cudaStream_t s);
 
 }  // namespace bddc

@@ -69,14 +69,14 @@ __device__ __host__ inline int update_count(int n, int n_int, int k) {
     int kb = k * bddc::kPanelNB, nb = n_int - kb < bddc::kPanelNB ? n_int - kb : bddc::kPanelNB;
     int below = n - kb - nb;
     int nt = (below + bddc::kTile - 1) / bddc::kTile;
-    return nt * (nt + 1) / 2;
+    return nt * (nt + 1) / 2 + 1;  // + the copy of the factored diagonal block
 }
 
 __global__ void static_init_kernel(double *W, int n, int ld, int n_int, int steps, bddc::PcholDesc<double> *desc,
-                                   DevStatus *st, int2 *pit, int4 *uit) {
+                                   DevStatus *st, int2 *pit, int4 *uit, double *diag) {
     const int k = blockIdx.x;
     if (k == 0 && threadIdx.x == 0) {
-        *desc = bddc::PcholDesc<double>{W, n, ld, n_int, 0};
+        *desc = bddc::PcholDesc<double>{W, n, ld, n_int, 0, diag};
         st->code = st->item = st->pos = 0;
         st->arrive = st->gen = 0;
     }
@@ -97,6 +97,7 @@ __global__ void static_init_kernel(double *W, int n, int ld, int n_int, int step
         int tj = e - ti * (ti + 1) / 2;
         uit[uo + e] = make_int4(0, ti, tj, 0);
     }
+    if (threadIdx.x == 0) uit[uo + nt * (nt + 1) / 2] = make_int4(0, -1, -1, 0);
 }
 
 // S[p, q] = W[m + max(p, q), m + min(p, q)] (lower triangle of the trailing block)
@@ -139,6 +140,7 @@ extern "C" bddc_status bddc_schur_dense_static(int n, int n_int, const double *A
     unsigned char *lists = p + kMatBytes;
     DevStatus *st = reinterpret_cast<DevStatus *>(lists);
     PcholDesc<double> *desc = reinterpret_cast<PcholDesc<double> *>(lists + 256);
+    double *diag = reinterpret_cast<double *>(lists + kListBytes - kPanelNB * kPanelNB * sizeof(double));
     // work lists of the batched partial Cholesky (a batch of one matrix), built on the device
     const int steps = (n_int + kPanelNB - 1) / kPanelNB;
     size_t npit = 0, nuit = 0;
@@ -147,13 +149,13 @@ extern "C" bddc_status bddc_schur_dense_static(int n, int n_int, const double *A
         nuit += update_count(n, n_int, k);
     }
     const size_t pit_off = 512, uit_off = pit_off + (npit * sizeof(int2) + 255) / 256 * 256;
-    if (uit_off + nuit * sizeof(int4) > kListBytes) {
+    if (uit_off + nuit * sizeof(int4) > kListBytes - kPanelNB * kPanelNB * sizeof(double)) {
         set_msg(msg, msg_cap, "bddc_schur_dense_static: work lists exceed the static scratch");
         return BDDC_EINVAL;
     }
     int2 *d_pit = reinterpret_cast<int2 *>(lists + pit_off);
     int4 *d_uit = reinterpret_cast<int4 *>(lists + uit_off);
-    static_init_kernel<<<steps > 0 ? steps : 1, 256, 0, s>>>(W, n, ld, n_int, steps, desc, st, d_pit, d_uit);
+    static_init_kernel<<<steps > 0 ? steps : 1, 256, 0, s>>>(W, n, ld, n_int, steps, desc, st, d_pit, d_uit, diag);
     e = cudaMemcpy2DAsync(W, (size_t)ld * sizeof(double), A, (size_t)lda * sizeof(double), (size_t)n * sizeof(double),
                           n, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) {

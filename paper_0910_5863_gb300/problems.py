@@ -247,3 +247,25 @@ def config_adaptive_poisson(seed: int = 1) -> Problem:
 def config_elasticity_channels(seed: int = 1) -> Problem:
     """32^3 elasticity, 4x4x4 substructures of 8^3, 8 stiff channels E = 1e6."""
     return elasticity_cube(32, 4, seed, channels=8, name="elast32_4x4x4_channels")
+
+
+def planar_cubes(k: int, m: int = 8, nu: float = 0.3, name=None) -> Problem:
+    """k x k x 1 cubic substructures of m^3 Q1 elasticity elements (h = 1/m per cube,
+    the paper's weak-scaling problem, Section 7 and its last table): fixed on the side
+    x = 0, loaded on the opposite side x = k by a uniform traction (0, 0, -1)
+    distributed to the face nodes by their tributary areas.  E = 1."""
+    nx, ny, nz = k * m, k * m, m
+    h = 1.0 / m
+    xyz, elems = box_mesh(nx, ny, nz, h)
+    ne = elems.shape[0]
+    dirichlet = np.isclose(xyz[:, 0], 0.0)
+    load = np.zeros((xyz.shape[0], 3))
+    face = np.isclose(xyz[:, 0], nx * h)
+    # tributary area of a node of the loaded face: h^2 / 4 per adjacent face quad
+    j = np.rint(xyz[:, 1] / h).astype(int)
+    kk = np.rint(xyz[:, 2] / h).astype(int)
+    wy = np.where((j == 0) | (j == ny), 0.5, 1.0)
+    wz = np.where((kk == 0) | (kk == nz), 0.5, 1.0)
+    load[face, 2] = -(h * h) * wy[face] * wz[face]
+    return Problem(name or f"planar_cubes_{k}x{k}x1_m{m}", 3, (nx, ny, nz), h, xyz, elems, np.ones(ne), nu,
+                   cubic_partition(nx, ny, nz, k, k, 1), k * k, dirichlet, load, {"k": k, "m": m})
