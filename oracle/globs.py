@@ -90,9 +90,64 @@ class Globs:
                 self.edges[s] = keep
         self.interface_nodes = sorted(n for n, s in enumerate(self.sets) if len(s) >= 2 and not dirich[n])
         self.corner_set = set(self.corners)
+        self.augmented = self._augment(prob)
+
+    def _augment(self, prob):
+        """Corner augmentation (reading of Assumptions 1 and 2): for every face pair (i, j),
+        in increasing order, one of whose substructures has no Dirichlet node, the
+        shared corners must fix the rigid modes -- 1 corner for a scalar problem, 3
+        non-collinear corners for elasticity.  While they do not, the face node that
+        maximises the smallest squared distance to the current shared corners becomes a
+        corner (the lowest node id when there are none yet; ties within 1e-12 relative
+        go to the lowest id).  A node promoted for (i, j) lies on that face only, so the
+        faces do not interact."""
+        need = 1 if prob.ncomp == 1 else 3
+        dirich = prob.dirichlet
+        anchored = np.zeros(prob.nsub, dtype=bool)
+        for e in range(prob.ne):
+            if dirich[prob.elems[e]].any():
+                anchored[prob.elem_sub[e]] = True
+        added = []
+        for (i, j) in sorted(self.faces):
+            if anchored[i] and anchored[j]:
+                continue
+            face = list(self.faces[(i, j)])
+            pair = {i, j}
+            shared = [n for n in self.corners if pair <= self.sets[n]]
+            while _corner_rank(prob.xyz, shared, need) < need and face:
+                if not shared:
+                    pick = face[0]
+                else:
+                    X = prob.xyz[face][:, None, :] - prob.xyz[shared][None, :, :]
+                    dmin = (X ** 2).sum(axis=2).min(axis=1)
+                    best = dmin.max()
+                    pick = min(n for n, d in zip(face, dmin) if d >= best * (1 - 1e-12))
+                face.remove(pick)
+                shared.append(pick)
+                added.append(pick)
+                self.corners.append(pick)
+            self.faces[(i, j)] = face
+        self.corners = sorted(self.corners)
+        self.corner_set = set(self.corners)
+        self.faces = {k: v for k, v in self.faces.items() if v}
+        return sorted(added)
 
     def counts(self):
         return len(self.corners), len(self.edges), len(self.faces)
+
+
+def _corner_rank(xyz, nodes, need):
+    """1 if any node (scalar case); for need = 3, 3 if three of the nodes are not collinear."""
+    if not nodes:
+        return 0
+    if need == 1:
+        return 1
+    P = xyz[nodes]
+    D = P[1:] - P[0]
+    if D.shape[0] == 0 or np.abs(D).max() == 0:
+        return 1
+    r = np.linalg.matrix_rank(D, tol=1e-8 * np.abs(D).max())
+    return 3 if r >= 2 else 2
 
 
 def weights(subs, ndof):

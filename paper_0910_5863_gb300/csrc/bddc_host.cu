@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <iterator>
 #include <map>
 #include <numeric>
 #include <set>
@@ -107,6 +108,7 @@ struct bddc_handle {
     std::vector<std::vector<int>> sets;     // set id -> sorted substructures
     std::vector<int64_t> corners;
     std::vector<char> is_corner;
+    int n_augmented = 0;  // face nodes promoted to corners (Assumptions 1 and 2)
     int n_edges = 0;
     std::vector<std::pair<std::vector<int>, std::vector<int64_t>>> edge_globs;  // (subs, nodes)
     std::vector<FacePair> faces;
@@ -334,6 +336,88 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 const int HEX_EDGES[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
                               {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
 
+// Corner augmentation (Assumptions 1 and 2: the corners shared by a face pair with a
+// floating member must fix its rigid modes).  Face pairs are visited in increasing
+// (i, j); while the shared corners fix fewer than 1 (scalar) or 3 (elasticity: three
+// non-collinear points) modes, the face node farthest from the shared corners (the
+// largest smallest squared distance; ties within 1e-12 relative go to the lowest node
+// id; the lowest node id when there are no shared corners) becomes a corner.  A node
+// promoted for (i, j) belongs to that face only, so the faces do not interact.
+using FaceList = std::vector<std::pair<std::pair<int, int>, std::vector<int64_t>>>;
+
+int corner_fixed_modes(const bddc_handle *h, const std::vector<int64_t> &cn, int need) {
+    if (cn.empty()) return 0;
+    if (need == 1) return 1;
+    const double *x0 = &h->xyz[cn[0] * 3];
+    int best = 1;
+    for (size_t a = 1; a < cn.size(); ++a) {
+        const double *xa = &h->xyz[cn[a] * 3];
+        double d1[3] = {xa[0] - x0[0], xa[1] - x0[1], xa[2] - x0[2]};
+        double n1 = std::sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+        if (n1 > 0) best = 2;
+        for (size_t b = a + 1; b < cn.size(); ++b) {
+            const double *xb = &h->xyz[cn[b] * 3];
+            double d2[3] = {xb[0] - x0[0], xb[1] - x0[1], xb[2] - x0[2]};
+            double cr[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2],
+                            d1[0] * d2[1] - d1[1] * d2[0]};
+            double n2 = std::sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+            if (std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) > 1e-8 * n1 * n2) return 3;
+        }
+    }
+    return best;
+}
+
+void augment_corners(bddc_handle *h, FaceList &face_list) {
+    const int ns = h->nsub, need = (h->ncomp == 1) ? 1 : 3;
+    std::vector<char> anchored(ns, 0);
+    for (int64_t e = 0; e < h->ne; ++e)
+        for (int a = 0; a < 8; ++a)
+            if (h->dirich[h->elems[e * 8 + a]]) anchored[h->esub[e]] = 1;
+    std::vector<std::vector<int64_t>> sub_corners(ns);
+    for (int64_t v : h->corners)
+        for (int sb : h->sets[h->node_set[v]]) sub_corners[sb].push_back(v);
+    h->n_augmented = 0;
+    for (auto &fl : face_list) {
+        const int i = fl.first.first, j = fl.first.second;
+        if (anchored[i] && anchored[j]) continue;
+        std::vector<int64_t> shared;
+        std::set_intersection(sub_corners[i].begin(), sub_corners[i].end(), sub_corners[j].begin(),
+                              sub_corners[j].end(), std::back_inserter(shared));
+        auto &face = fl.second;
+        while (!face.empty() && corner_fixed_modes(h, shared, need) < need) {
+            size_t pick = 0;
+            if (!shared.empty()) {
+                std::vector<double> dmin(face.size());
+                double best = -1.0;
+                for (size_t q = 0; q < face.size(); ++q) {
+                    const double *x = &h->xyz[face[q] * 3];
+                    double m = INFINITY;
+                    for (int64_t v : shared) {
+                        const double *y = &h->xyz[v * 3];
+                        double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+                        m = std::min(m, dx * dx + dy * dy + dz * dz);
+                    }
+                    dmin[q] = m;
+                    best = std::max(best, m);
+                }
+                while (dmin[pick] < best * (1 - 1e-12)) ++pick;
+            }
+            const int64_t v = face[pick];
+            face.erase(face.begin() + pick);
+            shared.push_back(v);
+            h->is_corner[v] = 1;
+            h->corners.push_back(v);
+            h->n_augmented++;
+        }
+    }
+    if (h->n_augmented) {
+        std::sort(h->corners.begin(), h->corners.end());
+        face_list.erase(std::remove_if(face_list.begin(), face_list.end(),
+                                       [](const FaceList::value_type &f) { return f.second.empty(); }),
+                        face_list.end());
+    }
+}
+
 void classify(bddc_handle *h) {
     const auto tc0 = std::chrono::steady_clock::now();
     const int64_t nn = h->nn, ne = h->ne;
@@ -462,7 +546,7 @@ void classify(bddc_handle *h) {
     }
     // globs: interface nodes grouped by set (the key sort keeps each set contiguous, ascending node ids)
     h->edge_globs.clear();
-    std::vector<std::pair<std::pair<int, int>, std::vector<int64_t>>> face_list;
+    FaceList face_list;
     for (size_t q = 0; q < keys.size();) {
         const int sid = h->node_set[keys[q].node];
         size_t q1 = q;
@@ -481,6 +565,7 @@ void classify(bddc_handle *h) {
     }
     std::sort(face_list.begin(), face_list.end());
     h->n_edges = (int)h->edge_globs.size();
+    augment_corners(h, face_list);
 
     // substructures
     const int ns = h->nsub;
@@ -647,13 +732,16 @@ void classify(bddc_handle *h) {
         }
         fp.floating = si.floating && sj.floating;
         const int nsd = (int)fp.s_g.size();
-        if (fp.floating) {
+        if (si.floating || sj.floating) {
+            // with one floating member the pair matrix is singular unless the shared corners fix its rigid modes
             int need = (c == 1) ? 1 : 3;
             std::vector<int64_t> cnu;
             for (size_t k = 0; k < fp.ci_pos.size(); k += c) cnu.push_back(dof_node[si.gG[fp.ci_pos[k]]]);
             if (rank_corners(cnu) < need)
                 throw Error{BDDC_EASSUMPTION, "Assumption 2: corners shared by substructures " + std::to_string(fp.i) +
                                                   " and " + std::to_string(fp.j) + " do not fix relative rigid motions"};
+        }
+        if (fp.floating) {
             // null space of S^ on s: rigid modes, identical on both sides; N0 orthonormal with N = [N0; N0]
             int nr = (c == 1) ? 1 : 6;
             std::vector<double> R((size_t)nsd * nr, 0.0);

@@ -1,0 +1,46 @@
+"""k x k x 1 elastic cubes clamped on one side (the paper's weak-scaling geometry,
+Section 7): the substructures away from the clamped side float, so the corner
+augmentation of Assumptions 1 and 2 must promote face nodes to corners.  The GPU
+library and the oracle must promote the same nodes and then agree on the face
+eigenvalues, the constraint counts, the iteration count and the solution."""
+import numpy as np
+import pytest
+
+from paper_0910_5863_gb300 import problems as P
+from paper_0910_5863_gb300 import bddc as B
+import oracle
+from oracle.adaptive import orthonormal_rows
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
+@pytest.mark.parametrize("k", [2, 3])
+def test_planar_cubes_adaptive(k, prec):
+    prob = P.planar_cubes(k, m=4)
+    m, ad, ref = oracle.run(prob, tau=10.0, tol=1e-10, maxit=800)
+    s = B.Solver(precision=prec, tol=1e-10)
+    s.set_problem(prob)
+    assert list(s.corners()) == m.globs.corners
+    sz = s.sizes()
+    assert (sz["n_corners"], sz["n_edges"], sz["n_faces"]) == m.globs.counts()
+    s.setup()
+    info = s.adapt(10.0)
+    keys = sorted(m.globs.faces)
+    for f, key in enumerate(keys):
+        g = s.face_eigs(f)
+        r = ad.pairs[key]
+        assert g["pair"] == key
+        assert g["selected"] == r.selected
+        kept = orthonormal_rows(r.face_rows).shape[0] if r.selected else 0
+        assert g["kept"] == kept
+        n = min(len(g["lam"]), r.selected + 1)
+        assert np.allclose(g["lam"][:n], r.lam[:n], rtol=1e-6)
+    assert info["n_added"] == ad.n_added
+    u, sinfo = s.solve(B.free_load_vector(prob))
+    assert sinfo["converged"]
+    assert abs(sinfo["iters"] - ref.iters) <= 1
+    F = m.F
+    assert np.linalg.norm(m.K @ u - F) <= 1e-8 * np.linalg.norm(F)
+    # both sides at PCG tolerance 1e-10 with kappa ~ 10: solutions agree to ~1e-9
+    assert np.linalg.norm(u - ref.u) <= 1e-8 * np.linalg.norm(ref.u)

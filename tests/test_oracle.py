@@ -210,12 +210,8 @@ def test_all_interface_primal_is_exact():
 def _two_substructures():
     prob = P.poisson_cube(6, 2, coef="lognormal", s_xyz=(2, 1, 1), seed=3)
     m = oracle.Model(prob)
-    assert len(m.globs.faces) == 1 and not m.globs.corners
-    # one corner so that Assumptions 1 and 2 hold (the floating substructure)
-    face = m.globs.faces[(0, 1)]
-    m.globs.corners = [face[len(face) // 2]]
-    m.globs.corner_set = set(m.globs.corners)
-    m.globs.faces[(0, 1)] = [n for n in face if n != m.globs.corners[0]]
+    # substructure 1 floats: augmentation promotes one face node to a corner (Assumptions 1, 2)
+    assert len(m.globs.faces) == 1 and m.globs.corners == m.globs.augmented and len(m.globs.corners) == 1
     m.schur()
     return m
 
@@ -325,3 +321,53 @@ def test_adaptive_indicator_bounds_condition():
     assert k1 < 10.0 * 1.01
     assert 0.3 * ad.omega < k0 < 3 * ad.omega
     assert r1.iters < r0.iters
+
+
+# --- corner augmentation (Assumptions 1 and 2) ------------------------------------
+
+def _min_rel_eig(A):
+    w = np.linalg.eigvalsh(A)
+    return w[0] / w[-1]
+
+
+def test_corner_augmentation_planar_elasticity():
+    """k x k x 1 cubes fixed on x = 0: the substructures away from x = 0 float and
+    share only the two ends of the vertical centre edge (collinear) with their
+    neighbours, so each face pair with a floating member needs one more corner.
+    Closed form for k = 2: the farthest face node from the centre edge is the
+    mid-height node of the face's outer edge (distance^2 = 1 + 1/4 in cube units)."""
+    prob = P.planar_cubes(2, m=2)
+    m = oracle.Model(prob)
+    g = m.globs
+    assert len(g.augmented) == 3
+    for n in g.augmented:
+        x, y, z = prob.xyz[n]
+        assert abs(z - 0.5) < 1e-12
+        assert abs((x - 1.0) ** 2 + (y - 1.0) ** 2 - 1.0) < 1e-12
+    floating = [s for s in range(prob.nsub)
+                if not prob.dirichlet[prob.elems[prob.elem_sub == s]].any()]
+    assert len(floating) == 2
+    before = set(g.corners) - set(g.augmented)
+    for s, sub in enumerate(m.subs):
+        nodes = sub.free_nodes.repeat(3)
+        A = sub.A.toarray()
+        keep_after = np.array([int(n) not in g.corner_set for n in nodes])
+        keep_before = np.array([int(n) not in before for n in nodes])
+        # Assumption 1: with the corners fixed every local problem is nonsingular
+        assert _min_rel_eig(A[np.ix_(keep_after, keep_after)]) > 1e-10
+        if s in floating:
+            # the rotation about the centre edge is left free by the corners before augmentation
+            assert _min_rel_eig(A[np.ix_(keep_before, keep_before)]) < 1e-12
+    # Assumption 2: the pair problems are well posed; rigid modes only when both float
+    m.schur()
+    for (i, j) in g.faces:
+        r = pair_problem(m, i, j, tau=10.0)
+        both = i in floating and j in floating
+        assert r.n_null == (6 if both else 0)
+        assert np.isfinite(r.lam).all() and r.lam.max() < 1e6
+
+
+def test_corner_augmentation_is_not_needed_when_anchored():
+    """Every substructure touching the Dirichlet boundary: no face node is promoted."""
+    for prob in (P.config_small(), P.poisson_cube(6, 2, coef="lognormal")):
+        assert oracle.Model(prob).globs.augmented == []
