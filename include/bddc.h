@@ -22,12 +22,13 @@
  *    non-Dirichlet nodes in increasing node id, ncomp consecutive dofs per
  *    node.  Interface dofs (dofs of nodes in more than one substructure)
  *    are numbered by increasing global dof.
- *  - Device memory is allocated with cudaMalloc by the handle and released by
- *    bddc_destroy.
+ *  - Device memory is allocated by the handle (cudaMalloc, or the caller's
+ *    allocator of bddc_options) and released by bddc_destroy.
  */
 #ifndef BDDC_H
 #define BDDC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -68,7 +69,30 @@ typedef struct {
     double drop_rel;       /* per-face rank drop of adaptive rows, default 1e-10 */
     double timeout_s;      /* limit of every bounded device wait, default 10 s */
     void *stream;          /* cudaStream_t; NULL = default stream */
+    /* Device memory of the handle.  NULL (default) = cudaMalloc / cudaFree.
+     * Otherwise every device buffer the handle owns comes from dev_alloc(bytes,
+     * alloc_ctx) (it must return device memory usable on ``stream``, 256-byte
+     * aligned, or NULL on failure -> BDDC_ENOMEM) and goes back through
+     * dev_free(ptr, bytes, alloc_ctx).  Buffers are freed only after the
+     * handle's stream is synchronized, so a stream-ordered allocator
+     * (cudaMallocAsync on the same stream, a caching allocator keyed on the
+     * stream) is safe.  Both callbacks or neither must be given. */
+    void *(*dev_alloc)(size_t bytes, void *alloc_ctx);
+    void (*dev_free)(void *ptr, size_t bytes, void *alloc_ctx);
+    void *alloc_ctx;
 } bddc_options;
+
+/* One substructure of an algebraic problem (bddc_set_problem): its local matrix
+ * A_i (Section 2: A_i is the subassembly of the substructure's part of the
+ * bilinear form, so A = sum_i R_i^T A_i R_i) in CSR over local dofs. */
+typedef struct {
+    int32_t n_local;       /* local dofs (rows of A_i) */
+    const int64_t *l2g;    /* (n_local) local dof -> global dof, 0 <= g < n_global */
+    const int64_t *rowptr; /* (n_local + 1) CSR row pointers, rowptr[0] = 0 */
+    const int32_t *col;    /* (rowptr[n_local]) local column indices */
+    const double *val;     /* (rowptr[n_local]) values; both triangles of the symmetric A_i,
+                              duplicate (row, col) entries are summed */
+} bddc_subdomain;
 
 typedef struct bddc_handle bddc_handle;
 
@@ -121,9 +145,49 @@ BDDC_API bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, con
                              const int64_t *elems, const double *coef, double nu, const int32_t *elem_sub,
                              int32_t nsub, const uint8_t *dirichlet, int mem);
 
+/* Defines the problem algebraically from the substructure matrices A_i
+ * (Section 2: A = sum_i R_i^T A_i R_i).  Dirichlet dofs are already
+ * eliminated by the caller, so every global dof is free and the global dof
+ * numbering is the caller's, 0 <= g < n_global.  Node of dof g = g / ncomp:
+ * the ncomp dofs of a node are consecutive, and a substructure holds either
+ * all or none of them.
+ *   ncomp      1 = scalar, 3 = elasticity (rigid modes from node_xyz)
+ *   subs       (n_sub) CSR matrices; arrays in memory ``mem``
+ *   node_xyz   (n_global / ncomp) x 3 row-major coordinates; required for
+ *              ncomp = 3 (rigid body modes, corner augmentation), may be NULL
+ *              for ncomp = 1
+ * Globs follow Section 2 (faces: nodes of exactly two substructures; edges:
+ * nodes of one set of three or more).  Corners are chosen by the rule of
+ * bddc_set_mesh_q1 with "neighbour" read as a node coupled to it in some A_i
+ * (the element-edge graph is not known here), on the free nodes only; then
+ * face pairs with a floating member receive augmented corners (Assumptions 1
+ * and 2).  A substructure floats when A_i annihilates the rigid modes (the
+ * constant, or the six rigid body motions of node_xyz) to 1e-8 relative.
+ * bddc_set_corners replaces the corner choice.  Resets constraints to corners
+ * only.  Inputs are copied.  Errors: BDDC_EINVAL (sizes, indices, a dof in no
+ * substructure, a node split between substructures, missing node_xyz for
+ * ncomp = 3), BDDC_EASSUMPTION, BDDC_ENOMEM. */
+BDDC_API bddc_status bddc_set_problem(bddc_handle *h, int64_t n_global, int ncomp, int32_t n_sub,
+                                      const bddc_subdomain *subs, const double *node_xyz, int mem);
+
+/* Replaces the corners (Section 2: the coarse point constraints, W^c of the
+ * paper's Fig. 3) by the n given node ids (host memory, any order, duplicates
+ * ignored); no rule and no augmentation is applied.  Every node must be an
+ * interface node.  Edges and faces are re-derived without those nodes.
+ * Resets constraints to corners only.  Must follow bddc_set_problem or
+ * bddc_set_mesh_q1 and precede bddc_setup.  Errors: BDDC_ESTATE, BDDC_EINVAL
+ * (node out of range or not on the interface), BDDC_EASSUMPTION (the corners
+ * do not fix the rigid modes of a floating substructure or face pair). */
+BDDC_API bddc_status bddc_set_corners(bddc_handle *h, int64_t n, const int64_t *nodes);
+
+/* Re-applies the default corner rule and augmentation (undoing
+ * bddc_set_corners); *n_out (may be NULL) receives the number of corners.
+ * Resets constraints to corners only.  Errors: BDDC_ESTATE, BDDC_EASSUMPTION. */
+BDDC_API bddc_status bddc_select_corners(bddc_handle *h, int64_t *n_out);
+
 /* Adds arithmetic averages as initial constraints (Section 2, eq. (Wtilde);
  * one coarse dof per glob and component): flags = BDDC_AVG_EDGE | BDDC_AVG_FACE.
- * Must follow bddc_set_mesh_q1 and precede bddc_setup. */
+ * Must follow bddc_set_mesh_q1 or bddc_set_problem and precede bddc_setup. */
 BDDC_API bddc_status bddc_set_averages(bddc_handle *h, int flags);
 
 /* Numeric setup: assembles A_i on the device, factors A_II and forms
@@ -152,7 +216,7 @@ BDDC_API bddc_status bddc_solve(bddc_handle *h, const double *f, double *u, int 
  * coefficients alpha_k, beta_k (caption of Table 1 of the paper). */
 BDDC_API bddc_status bddc_condition_estimate(const bddc_handle *h, double *lmin, double *lmax);
 
-/* Sizes after bddc_set_mesh_q1 (any pointer may be NULL). */
+/* Sizes after bddc_set_mesh_q1 or bddc_set_problem (any pointer may be NULL). */
 BDDC_API bddc_status bddc_get_sizes(const bddc_handle *h, int64_t *n_free, int64_t *n_interface, int *n_corners,
                            int *n_edges, int *n_faces, int *n_coarse);
 

@@ -25,14 +25,25 @@ EXPORTS = ["bddc_default_options", "bddc_create", "bddc_destroy", "bddc_set_mesh
            "bddc_setup", "bddc_adapt", "bddc_solve", "bddc_condition_estimate", "bddc_get_sizes",
            "bddc_get_corners", "bddc_get_face_eigs", "bddc_get_interface_dofs", "bddc_get_schur",
            "bddc_apply_preconditioner", "bddc_apply_schur", "bddc_launch_count", "bddc_status_str",
-           "bddc_last_error", "bddc_get_phase_times", "bddc_get_local_matrix"]
+           "bddc_last_error", "bddc_get_phase_times", "bddc_get_local_matrix", "bddc_set_problem",
+           "bddc_set_corners", "bddc_select_corners"]
 PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
           "analysis_host", "condensed_rhs", "pcg", "recovery"]
 
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int), ("drop_rel", C.c_double),
-                ("timeout_s", C.c_double), ("stream", C.c_void_p)]
+                ("timeout_s", C.c_double), ("stream", C.c_void_p), ("dev_alloc", C.c_void_p),
+                ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p)]
+
+
+class Subdomain(C.Structure):
+    _fields_ = [("n_local", C.c_int32), ("l2g", C.c_void_p), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 
 class AdaptInfo(C.Structure):
@@ -85,6 +96,9 @@ def load(path: str = LIB_PATH):
         "bddc_last_error": (C.c_char_p, [vp]),
         "bddc_get_phase_times": (i32, [vp, vp, vp, i32, vp]),
         "bddc_get_local_matrix": (i32, [vp, i32, vp, i32, i32]),
+        "bddc_set_problem": (i32, [vp, i64, i32, C.c_int32, vp, vp, i32]),
+        "bddc_set_corners": (i32, [vp, i64, vp]),
+        "bddc_select_corners": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -92,6 +106,24 @@ def load(path: str = LIB_PATH):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def _torch_allocator(stream):
+    """ctypes callbacks that take device memory from PyTorch's caching allocator."""
+    import torch
+    dev = torch.cuda.current_device()
+    sid = int(stream) if stream else torch.cuda.current_stream(dev).cuda_stream
+
+    def alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, sid)
+        except Exception:
+            return None
+
+    def free(ptr, nbytes, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return _ALLOC_FN(alloc), _FREE_FN(free)
 
 
 def _ptr(a):
@@ -107,7 +139,10 @@ def _ptr(a):
 class Solver:
     """One handle of the library (one GPU, one stream)."""
 
-    def __init__(self, precision=FP64, tol=1e-8, maxit=1000, drop_rel=1e-10, timeout_s=10.0, stream=None):
+    def __init__(self, precision=FP64, tol=1e-8, maxit=1000, drop_rel=1e-10, timeout_s=10.0, stream=None,
+                 allocator=None):
+        """allocator: None (the library's cudaMalloc) or "torch" (device memory from
+        PyTorch's caching allocator on the handle's stream)."""
         self.lib = load()
         opt = Options()
         self.lib.bddc_default_options(C.byref(opt))
@@ -117,6 +152,13 @@ class Solver:
         opt.drop_rel = drop_rel
         opt.timeout_s = timeout_s
         opt.stream = stream
+        self._callbacks = None
+        if allocator == "torch":
+            self._callbacks = _torch_allocator(stream)
+            opt.dev_alloc = C.cast(self._callbacks[0], C.c_void_p)
+            opt.dev_free = C.cast(self._callbacks[1], C.c_void_p)
+        elif allocator is not None:
+            raise ValueError("allocator must be None or 'torch'")
         h = C.c_void_p()
         st = self.lib.bddc_create(C.byref(opt), C.byref(h))
         if st != 0:
@@ -152,7 +194,37 @@ class Solver:
                                               ptrs[3][0], int(nsub), ptrs[4][0], mem))
         self.nfree = self.sizes()["n_free"]
 
-    def set_problem(self, prob):
+    def set_problem(self, n_global, ncomp, subs, node_xyz=None):
+        """Algebraic problem: subs = [(l2g, A_i)] with l2g (n_local,) global dof ids
+        and A_i a scipy.sparse matrix (any format) or a (rowptr, col, val) triple over
+        local dofs; node_xyz (n_global // ncomp, 3) or None.  Host memory."""
+        keep, desc = [], (Subdomain * len(subs))()
+        for k, (l2g, A) in enumerate(subs):
+            if isinstance(A, tuple):
+                rowptr, col, val = A
+            else:
+                A = A.tocsr()
+                rowptr, col, val = A.indptr, A.indices, A.data
+            arrs = (np.ascontiguousarray(l2g, dtype=np.int64), np.ascontiguousarray(rowptr, dtype=np.int64),
+                    np.ascontiguousarray(col, dtype=np.int32), np.ascontiguousarray(val, dtype=np.float64))
+            keep.append(arrs)
+            desc[k] = Subdomain(arrs[0].size, arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
+                                arrs[3].ctypes.data)
+        xyz = None if node_xyz is None else np.ascontiguousarray(node_xyz, dtype=np.float64)
+        self._check(self.lib.bddc_set_problem(self.h, int(n_global), int(ncomp), len(subs), desc,
+                                              None if xyz is None else xyz.ctypes.data, MEM_HOST))
+        self.nfree = self.sizes()["n_free"]
+
+    def set_corners(self, nodes):
+        a = np.ascontiguousarray(nodes, dtype=np.int64)
+        self._check(self.lib.bddc_set_corners(self.h, a.size, a.ctypes.data))
+
+    def select_corners(self):
+        n = C.c_int64()
+        self._check(self.lib.bddc_select_corners(self.h, C.byref(n)))
+        return n.value
+
+    def set_mesh_problem(self, prob):
         """Host arrays of a paper_0910_5863_gb300.problems.Problem."""
         self.set_mesh(prob.ncomp, np.ascontiguousarray(prob.xyz, dtype=np.float64),
                       np.ascontiguousarray(prob.elems, dtype=np.int64),

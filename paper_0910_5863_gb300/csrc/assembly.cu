@@ -105,6 +105,31 @@ __global__ void element_scatter_kernel(const AssemblyArgs args, const int32_t *c
     }
 }
 
+// Algebraic input: one thread per (merged) CSR entry of every substructure
+// writes its value at the precomputed dense offset (column-major, the local
+// ordering [interior; interface]).  sub_start (ns + 1) splits the entries by
+// substructure; entries are unique per destination, so plain stores suffice.
+__global__ void csr_scatter_kernel(double *const *A, const int64_t *sub_start, int ns, const int64_t *off,
+                                   const double *val, int64_t nnz) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnz) return;
+    int lo = 0, hi = ns - 1;  // largest s with sub_start[s] <= t
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sub_start[mid] <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    A[lo][off[t]] = val[t];
+}
+
+void launch_csr_scatter(double *const *A, const int64_t *sub_start, int ns, const int64_t *off, const double *val,
+                        int64_t nnz, cudaStream_t s) {
+    if (nnz > 0 && ns > 0)
+        csr_scatter_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(A, sub_start, ns, off, val, nnz);
+}
+
 void launch_element_geometry(const double *xyz, const int64_t *elems, int64_t ne, double *grads, double *wdet,
                              cudaStream_t s) {
     if (ne > 0) element_geometry_kernel<<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(xyz, elems, ne, grads, wdet);

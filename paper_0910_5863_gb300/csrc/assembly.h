@@ -20,5 +20,7 @@ struct AssemblyArgs {
 void launch_element_geometry(const double *xyz, const int64_t *elems, int64_t ne, double *grads, double *wdet,
                              cudaStream_t s);
 void launch_element_scatter(const AssemblyArgs &args, const int32_t *color_elems, int n, cudaStream_t s);
+void launch_csr_scatter(double *const *A, const int64_t *sub_start, int ns, const int64_t *off, const double *val,
+                        int64_t nnz, cudaStream_t s);
 
 }  // namespace bddc

@@ -101,6 +101,16 @@ struct bddc_handle {
     std::vector<int32_t> esub;
     std::vector<uint8_t> dirich;
     bool have_mesh = false, have_setup = false;
+    // algebraic input (bddc_set_problem): per-substructure CSR, host copies
+    bool csr_mode = false;
+    std::vector<std::vector<int64_t>> csr_l2g, csr_rowptr;
+    std::vector<std::vector<int32_t>> csr_col;
+    std::vector<std::vector<double>> csr_val;
+    // corners given by bddc_set_corners (used instead of the rule when set)
+    bool user_corners = false;
+    std::vector<int64_t> corner_list;
+    std::vector<char> sub_floating;  // substructure without Dirichlet support
+    int64_t csr_nnz = 0;             // merged CSR entries uploaded for the dense fill
     // numbering / classification
     std::vector<int64_t> node_first;
     int64_t nfree = 0;
@@ -369,17 +379,13 @@ int corner_fixed_modes(const bddc_handle *h, const std::vector<int64_t> &cn, int
 
 void augment_corners(bddc_handle *h, FaceList &face_list) {
     const int ns = h->nsub, need = (h->ncomp == 1) ? 1 : 3;
-    std::vector<char> anchored(ns, 0);
-    for (int64_t e = 0; e < h->ne; ++e)
-        for (int a = 0; a < 8; ++a)
-            if (h->dirich[h->elems[e * 8 + a]]) anchored[h->esub[e]] = 1;
     std::vector<std::vector<int64_t>> sub_corners(ns);
     for (int64_t v : h->corners)
         for (int sb : h->sets[h->node_set[v]]) sub_corners[sb].push_back(v);
     h->n_augmented = 0;
     for (auto &fl : face_list) {
         const int i = fl.first.first, j = fl.first.second;
-        if (anchored[i] && anchored[j]) continue;
+        if (!h->sub_floating[i] && !h->sub_floating[j]) continue;
         std::vector<int64_t> shared;
         std::set_intersection(sub_corners[i].begin(), sub_corners[i].end(), sub_corners[j].begin(),
                               sub_corners[j].end(), std::back_inserter(shared));
@@ -418,6 +424,56 @@ void augment_corners(bddc_handle *h, FaceList &face_list) {
     }
 }
 
+// Floating substructures (no Dirichlet support).  Mesh input: no element of the
+// substructure touches a Dirichlet node.  Algebraic input: A_i annihilates every
+// rigid mode r (the constant for ncomp = 1; three translations and three
+// rotations e_a x x for ncomp = 3) to 1e-8 relative: max |A_i r| <= 1e-8 max_k
+// sum_l |A_i,kl| |r_l|.
+void mark_floating(bddc_handle *h) {
+    const int ns = h->nsub, c = h->ncomp;
+    h->sub_floating.assign(ns, 1);
+    if (!h->csr_mode) {
+        for (int64_t e = 0; e < h->ne; ++e)
+            for (int a = 0; a < 8; ++a)
+                if (h->dirich[h->elems[e * 8 + a]]) h->sub_floating[h->esub[e]] = 0;
+        return;
+    }
+    const int nmodes = (c == 1) ? 1 : 6;
+    for (int s = 0; s < ns; ++s) {
+        const auto &l2g = h->csr_l2g[s];
+        const auto &rp = h->csr_rowptr[s];
+        const auto &cl = h->csr_col[s];
+        const auto &vl = h->csr_val[s];
+        const size_t n = l2g.size();
+        std::vector<double> r(n);
+        for (int m = 0; m < nmodes && h->sub_floating[s]; ++m) {
+            for (size_t k = 0; k < n; ++k) {
+                const int64_t g = l2g[k];
+                const int comp = (int)(g % c);
+                if (m < 3 || c == 1) {
+                    r[k] = (c == 1 || comp == m) ? 1.0 : 0.0;
+                } else {
+                    // (e_a x x)_comp for a = m - 3
+                    const double *x = &h->xyz[(g / c) * 3];
+                    const int a = m - 3, b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+                    r[k] = comp == b1 ? -x[b2] : (comp == b2 ? x[b1] : 0.0);
+                }
+            }
+            double worst = 0.0, scale = 0.0;
+            for (size_t k = 0; k < n; ++k) {
+                double y = 0.0, a = 0.0;
+                for (int64_t q = rp[k]; q < rp[k + 1]; ++q) {
+                    y += vl[q] * r[cl[q]];
+                    a += std::fabs(vl[q]) * std::fabs(r[cl[q]]);
+                }
+                worst = std::max(worst, std::fabs(y));
+                scale = std::max(scale, a);
+            }
+            if (worst > 1e-8 * scale) h->sub_floating[s] = 0;
+        }
+    }
+}
+
 void classify(bddc_handle *h) {
     const auto tc0 = std::chrono::steady_clock::now();
     const int64_t nn = h->nn, ne = h->ne;
@@ -439,21 +495,19 @@ void classify(bddc_handle *h) {
     };
     std::vector<NodeSubs> nsv(nn);
     for (auto &x : nsv) x.cnt = 0;
-    for (int64_t e = 0; e < ne; ++e) {
-        const int sb = h->esub[e];
-        for (int a = 0; a < 8; ++a) {
-            NodeSubs &x = nsv[h->elems[e * 8 + a]];
-            bool found = false;
-            for (int k = 0; k < x.cnt; ++k)
-                if (x.s[k] == sb) {
-                    found = true;
-                    break;
-                }
-            if (!found) {
-                BDDC_REQUIRE(x.cnt < kMaxSet, BDDC_EINVAL, "a node lies in more than 16 substructures");
-                x.s[x.cnt++] = sb;
-            }
-        }
+    auto add_sub = [&](int64_t v, int sb) {
+        NodeSubs &x = nsv[v];
+        for (int k = 0; k < x.cnt; ++k)
+            if (x.s[k] == sb) return;
+        BDDC_REQUIRE(x.cnt < kMaxSet, BDDC_EINVAL, "a node lies in more than 16 substructures");
+        x.s[x.cnt++] = sb;
+    };
+    if (h->csr_mode) {
+        for (int sb = 0; sb < h->nsub; ++sb)
+            for (int64_t g : h->csr_l2g[sb]) add_sub(g / c, sb);
+    } else {
+        for (int64_t e = 0; e < ne; ++e)
+            for (int a = 0; a < 8; ++a) add_sub(h->elems[e * 8 + a], h->esub[e]);
     }
     for (auto &x : nsv) std::sort(x.s, x.s + x.cnt);
     // set ids: {s} -> s for the one-substructure sets; interface sets are sorted by key
@@ -469,7 +523,7 @@ void classify(bddc_handle *h) {
     std::vector<Key> keys;
     for (int64_t v = 0; v < nn; ++v) {
         const NodeSubs &x = nsv[v];
-        BDDC_REQUIRE(x.cnt >= 1, BDDC_EINVAL, "a node belongs to no element");
+        BDDC_REQUIRE(x.cnt >= 1, BDDC_EINVAL, "a node belongs to no substructure");
         if (x.cnt == 1) {
             h->node_set[v] = x.s[0];
             set_count[x.s[0]]++;
@@ -508,19 +562,44 @@ void classify(bddc_handle *h) {
     for (int64_t v = 0; v < nn; ++v)
         if (nsv[v].cnt >= 3) eidx[v] = n_edge_nodes++;
     std::vector<std::vector<int64_t>> nb(n_edge_nodes);
-    for (int64_t e = 0; e < ne; ++e)
-        for (auto &ed : HEX_EDGES) {
-            int64_t a = h->elems[e * 8 + ed[0]], b = h->elems[e * 8 + ed[1]];
-            if (eidx[a] >= 0) nb[eidx[a]].push_back(b);
-            if (eidx[b] >= 0) nb[eidx[b]].push_back(a);
+    if (h->csr_mode) {
+        // neighbours = nodes coupled to the node in some A_i
+        for (int sb = 0; sb < h->nsub; ++sb) {
+            const auto &l2g = h->csr_l2g[sb];
+            const auto &rp = h->csr_rowptr[sb];
+            const auto &cl = h->csr_col[sb];
+            for (size_t r = 0; r < l2g.size(); ++r) {
+                const int64_t u = l2g[r] / c;
+                if (eidx[u] < 0) continue;
+                for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+                    const int64_t v = l2g[cl[q]] / c;
+                    if (v != u) nb[eidx[u]].push_back(v);
+                }
+            }
         }
+    } else {
+        for (int64_t e = 0; e < ne; ++e)
+            for (auto &ed : HEX_EDGES) {
+                int64_t a = h->elems[e * 8 + ed[0]], b = h->elems[e * 8 + ed[1]];
+                if (eidx[a] >= 0) nb[eidx[a]].push_back(b);
+                if (eidx[b] >= 0) nb[eidx[b]].push_back(a);
+            }
+    }
     auto is_superset = [&](int big, int small) {
         const auto &B = h->sets[big], &S = h->sets[small];
         if (B.size() <= S.size()) return false;
         return std::includes(B.begin(), B.end(), S.begin(), S.end());
     };
     h->is_corner.assign(nn, 0);
-    for (int64_t v = 0; v < nn; ++v) {
+    if (h->user_corners) {
+        for (int64_t v : h->corner_list) {
+            BDDC_REQUIRE(v >= 0 && v < nn, BDDC_EINVAL, "corner node id out of range");
+            BDDC_REQUIRE(h->sets[h->node_set[v]].size() >= 2 && !h->dirich[v], BDDC_EINVAL,
+                         "corner node " + std::to_string(v) + " is not an interface node");
+            h->is_corner[v] = 1;
+        }
+    }
+    for (int64_t v = 0; v < nn && !h->user_corners; ++v) {
         int sid = h->node_set[v];
         if (h->sets[sid].size() < 3) continue;
         if (set_count[sid] == 1) {
@@ -565,7 +644,9 @@ void classify(bddc_handle *h) {
     }
     std::sort(face_list.begin(), face_list.end());
     h->n_edges = (int)h->edge_globs.size();
-    augment_corners(h, face_list);
+    mark_floating(h);
+    h->n_augmented = 0;
+    if (!h->user_corners) augment_corners(h, face_list);
 
     // substructures
     const int ns = h->nsub;
@@ -595,7 +676,8 @@ void classify(bddc_handle *h) {
             }
             for (int k = 0; k < c; ++k) (is_iface_node[v] ? sd.gG : sd.gI).push_back(h->node_first[v] + k);
         }
-        sd.floating = !touches_dirichlet;
+        (void)touches_dirichlet;
+        sd.floating = h->sub_floating[s] != 0;
         sd.nI = (int)sd.gI.size();
         sd.nG = (int)sd.gG.size();
         sd.n = sd.nI + sd.nG;
@@ -1545,13 +1627,6 @@ void do_setup(bddc_handle *h) {
     const int ns = h->nsub;
     reset_status(h);
     phase_begin(h, 0);
-    // element geometry and assembly
-    double *grads = h->ar.get_t<double>("grads", (size_t)h->ne * 8 * 8 * 3);
-    double *wdet = h->ar.get_t<double>("wdet", (size_t)h->ne * 8);
-    const double *dxyz = h->ar.get_t<double>("xyz", h->nn * 3);
-    const int64_t *delems = h->ar.get_t<int64_t>("elems", h->ne * 8);
-    launch_element_geometry(dxyz, delems, h->ne, grads, wdet, h->stream);
-    check_launch(h);
     std::vector<double *> Aptr(ns);
     std::vector<int> lds(ns);
     ZeroList zl;
@@ -1562,20 +1637,35 @@ void do_setup(bddc_handle *h) {
         lds[s] = sd.ld;
     }
     zero_all(h, zl, "A");
-    AssemblyArgs aa;
-    aa.grads = grads;
-    aa.wdet = wdet;
-    aa.coef = h->ar.get_t<double>("coef", h->ne);
-    aa.elem_sub = h->ar.get_t<int32_t>("esub", h->ne);
-    aa.elem_pos = h->ar.get_t<int32_t>("epos", h->ne * 8);
-    aa.A = h->ar.upload("Aptr", Aptr, h->stream);
-    aa.ld = h->ar.upload("Ald", lds, h->stream);
-    aa.nu = h->nu;
-    aa.ncomp = h->ncomp;
-    for (size_t col = 0; col < h->colors.size(); ++col) {
-        const int32_t *ce = h->ar.get_t<int32_t>("color_" + std::to_string(col), h->colors[col].size());
-        launch_element_scatter(aa, ce, (int)h->colors[col].size(), h->stream);
+    if (h->csr_mode) {
+        // algebraic input: the CSR entries of every A_i into the dense local matrices
+        launch_csr_scatter(h->ar.upload("Aptr", Aptr, h->stream), h->ar.get_t<int64_t>("csr_start", ns + 1), ns,
+                           h->ar.get_t<int64_t>("csr_off", std::max<int64_t>(h->csr_nnz, 1)),
+                           h->ar.get_t<double>("csr_val", std::max<int64_t>(h->csr_nnz, 1)), h->csr_nnz, h->stream);
         check_launch(h);
+    } else {
+        // element geometry and assembly
+        double *grads = h->ar.get_t<double>("grads", (size_t)h->ne * 8 * 8 * 3);
+        double *wdet = h->ar.get_t<double>("wdet", (size_t)h->ne * 8);
+        const double *dxyz = h->ar.get_t<double>("xyz", h->nn * 3);
+        const int64_t *delems = h->ar.get_t<int64_t>("elems", h->ne * 8);
+        launch_element_geometry(dxyz, delems, h->ne, grads, wdet, h->stream);
+        check_launch(h);
+        AssemblyArgs aa;
+        aa.grads = grads;
+        aa.wdet = wdet;
+        aa.coef = h->ar.get_t<double>("coef", h->ne);
+        aa.elem_sub = h->ar.get_t<int32_t>("esub", h->ne);
+        aa.elem_pos = h->ar.get_t<int32_t>("epos", h->ne * 8);
+        aa.A = h->ar.upload("Aptr", Aptr, h->stream);
+        aa.ld = h->ar.upload("Ald", lds, h->stream);
+        aa.nu = h->nu;
+        aa.ncomp = h->ncomp;
+        for (size_t col = 0; col < h->colors.size(); ++col) {
+            const int32_t *ce = h->ar.get_t<int32_t>("color_" + std::to_string(col), h->colors[col].size());
+            launch_element_scatter(aa, ce, (int)h->colors[col].size(), h->stream);
+            check_launch(h);
+        }
     }
     // weights: diag of the interface block (before elimination of interiors)
     double *diag = h->ar.get_t<double>("diag", std::max<int64_t>(h->sumG, 1));
@@ -1666,6 +1756,10 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         if (info) *info = bddc_adapt_info{0, 0, 0, 0.0};
         return;
     }
+    for (auto &fp : h->faces) {
+        fp.lam.clear();
+        fp.nsel = fp.nkept = fp.ties = 0;
+    }
     phase_begin(h, 3);
     // E1: per (sub, face) Schur complement of S_i onto t = [s (s order); shared corners]
     std::vector<PcholDesc<double>> dE1, dE2, dE3;
@@ -1680,6 +1774,10 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         int ldM3;
         double *Q, *W1, *C;
         int ns, nc;
+        // initial constraints on s (averages): the problem in u with z = G u
+        int nsp = 0, pi = -1;   // order of the reduced problem; index into pis (-1: none)
+        double *M3c = nullptr, *Xg = nullptr;
+        int ldM3c = 0, ldXg = 0;
     };
     std::vector<PairBufs> pbufs(nf);
     int nmax = 0;
@@ -1770,6 +1868,9 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
     run_pchol<double>(h, dE2, "E2");
     for (auto &dd : dE2) cflop += pchol_flop(dd.n, dd.nstop);
     // E3: M3 = [[Mww, ., .], [Mbw, Mbb, .], [0, I, 0]] from S^ blocks, + deflation, eliminate 2 ns
+    // (pairs with initial constraints: compressed to the jumps that satisfy them first)
+    std::vector<PiDesc> pis;
+    int pi_nmax = 0;
     std::vector<DeflateDesc> defl;
     std::vector<PairWeightDesc> pw;
     ZeroList zm;
@@ -1807,7 +1908,76 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
             double *N0 = h->ar.upload("N0_" + std::to_string(f), fp.N0, h->stream);
             defl.push_back(DeflateDesc{B.Y + (size_t)nc * B.ldY + nc, B.ldY, B.M3, B.ldM3, N0, ns, fp.nnull});
         }
-        dE3.push_back(PcholDesc<double>{B.M3, n3, B.ldM3, 2 * ns, 0});
+        // initial constraints (averages over globs inside s shared by i and j): groups of s positions
+        std::vector<std::vector<int>> groups;
+        for (auto &g : h->globs) {
+            if (g.face >= 0) continue;
+            if (std::find(g.subs.begin(), g.subs.end(), fp.i) == g.subs.end() ||
+                std::find(g.subs.begin(), g.subs.end(), fp.j) == g.subs.end())
+                continue;
+            std::vector<int> pos(g.gdofs.size());
+            bool inside = true;
+            for (size_t k = 0; k < g.gdofs.size() && inside; ++k) {
+                auto it = std::lower_bound(fp.s_g.begin(), fp.s_g.end(), g.gdofs[k]);
+                inside = it != fp.s_g.end() && *it == g.gdofs[k];
+                if (inside) pos[k] = (int)(it - fp.s_g.begin());
+            }
+            if (!inside) continue;
+            for (int comp = 0; comp < h->ncomp; ++comp) {
+                std::vector<int> mem;
+                for (size_t k = comp; k < pos.size(); k += h->ncomp) mem.push_back(pos[k]);
+                if (!mem.empty()) groups.push_back(mem);
+            }
+        }
+        if (groups.empty()) {
+            dE3.push_back(PcholDesc<double>{B.M3, n3, B.ldM3, 2 * ns, 0});
+        } else {
+            std::vector<int> newidx(ns, 0), lead(ns, -1), grp(ns, -1), keep, gptr{0}, gidx;
+            for (size_t g = 0; g < groups.size(); ++g) {
+                for (size_t q = 0; q < groups[g].size(); ++q) {
+                    const int a = groups[g][q];
+                    grp[a] = (int)g;
+                    if (q == 0)
+                        newidx[a] = -1;
+                    else
+                        lead[a] = groups[g][0];
+                    gidx.push_back(a);
+                }
+                gptr.push_back((int)gidx.size());
+            }
+            for (int a = 0; a < ns; ++a)
+                if (newidx[a] >= 0) {
+                    newidx[a] = (int)keep.size();
+                    keep.push_back(a);
+                }
+            const std::string fs = std::to_string(f);
+            B.nsp = (int)keep.size();
+            const int nc3 = ns + 2 * B.nsp;
+            B.ldM3c = round_up(std::max(nc3, 1), 8);
+            B.M3c = h->ar.get_t<double>("M3c_" + fs, (size_t)B.ldM3c * std::max(nc3, 1));
+            B.ldXg = round_up(ns, 8);
+            B.Xg = h->ar.get_t<double>("Xg_" + fs, (size_t)B.ldXg * std::max(B.nsp, 1));
+            PiDesc pd{};
+            pd.M3 = B.M3;
+            pd.ld3 = B.ldM3;
+            pd.M3c = B.M3c;
+            pd.ldc = B.ldM3c;
+            pd.Xg = B.Xg;
+            pd.ldg = B.ldXg;
+            pd.newidx = h->ar.upload("pin_" + fs, newidx, h->stream);
+            pd.lead = h->ar.upload("pil_" + fs, lead, h->stream);
+            pd.grp = h->ar.upload("pig_" + fs, grp, h->stream);
+            pd.keep = h->ar.upload("pik_" + fs, keep, h->stream);
+            pd.gptr = h->ar.upload("pip_" + fs, gptr, h->stream);
+            pd.gidx = h->ar.upload("pii_" + fs, gidx, h->stream);
+            pd.ns = ns;
+            pd.nsp = B.nsp;
+            pd.ngroups = (int)groups.size();
+            B.pi = (int)pis.size();
+            pis.push_back(pd);
+            pi_nmax = std::max(pi_nmax, ns);
+            if (B.nsp > 0) dE3.push_back(PcholDesc<double>{B.M3c, nc3, B.ldM3c, ns + B.nsp, 0});
+        }
         // pair weights for Q
         double *di = h->ar.get_t<double>("pwi_" + std::to_string(f), ns);
         double *dj = h->ar.get_t<double>("pwj_" + std::to_string(f), ns);
@@ -1856,6 +2026,13 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         launch_deflate(dd, (int)defl.size(), h->stream);
         check_launch(h);
     }
+    PiDesc *dpis = nullptr;
+    if (!pis.empty()) {
+        // every PiDesc needs its W1 pointer, set below; upload after that, compress needs only M3/M3c
+        dpis = h->ar.upload("pidesc", pis, h->stream);
+        launch_pi_compress(dpis, (int)pis.size(), pi_nmax, h->stream);
+        check_launch(h);
+    }
     run_pchol<double>(h, dE3, "E3");
     for (auto &dd : dE3) cflop += pchol_flop(dd.n, dd.nstop);
     h->phase_flop[3] = cflop;
@@ -1876,6 +2053,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         auto &B = pbufs[f];
         const int ns = B.ns;
         if (ns == 0) continue;
+        if (B.pi >= 0 && B.nsp == 0) continue;  // the initial constraints fix every jump on s
         int ldq = round_up(ns, 8);
         B.Q = h->ar.get_t<double>("Q_" + std::to_string(f), (size_t)ldq * ns);
         B.W1 = h->ar.get_t<double>("W1_" + std::to_string(f), (size_t)ldq * ns);
@@ -1897,16 +2075,23 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         o.cscale = di;
         o.accumulate = 1;
         gq2.push_back(o);
-        const double *X = B.M3 + (size_t)ns * B.ldM3 + 2 * ns;
-        GemmDesc g1{B.Q, X, B.W1, ldq, B.ldM3, ldq, ns, ns, ns, 0, 0, 1.0, 0.0};
-        GemmDesc g2{X, B.W1, B.C, B.ldM3, ldq, ldq, ns, ns, ns, 1, 0, 1.0, 0.0};
+        // order of the eigenproblem: ns, or nsp with initial constraints (X -> Xg = G X')
+        const int ne = B.pi >= 0 ? B.nsp : ns;
+        const double *X = B.pi >= 0 ? B.Xg : B.M3 + (size_t)ns * B.ldM3 + 2 * ns;
+        const int ldx = B.pi >= 0 ? B.ldXg : B.ldM3;
+        if (B.pi >= 0) {
+            pis[B.pi].W1 = B.W1;
+            pis[B.pi].ldw = ldq;
+        }
+        GemmDesc g1{B.Q, X, B.W1, ldq, ldx, ldq, ns, ne, ns, 0, 0, 1.0, 0.0};
+        GemmDesc g2{X, B.W1, B.C, ldx, ldq, ldq, ne, ne, ns, 1, 0, 1.0, 0.0};
         gm1.push_back(g1);
         gm2.push_back(g2);
         int nface = (int)fp.face_idx.size();
         int *fpos = h->ar.upload("fpos_" + std::to_string(f), fp.face_idx, h->stream);
         EigDesc e;
         e.C = B.C;
-        e.n = ns;
+        e.n = ne;
         e.ld = ldq;
         e.W1 = B.W1;
         e.ldw = ldq;
@@ -1922,7 +2107,18 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
     }
     run_gathers(h, gq1, "Q1");
     run_gathers(h, gq2, "Q2");
+    if (!pis.empty()) {
+        // Xg = G X' for the constrained pairs (W1 pointers now set)
+        dpis = h->ar.upload("pidesc", pis, h->stream);
+        launch_pi_expand(dpis, (int)pis.size(), pi_nmax, h->stream);
+        check_launch(h);
+    }
     run_gemm(h, gm1, "W1");
+    if (!pis.empty()) {
+        // W1 <- P W1 (the face rows become P L P w); C = Xg^T W1 is unchanged by P
+        launch_pi_project(dpis, (int)pis.size(), h->stream);
+        check_launch(h);
+    }
     run_gemm(h, gm2, "C");
     auto *ded = h->ar.upload("eigdesc", eds, h->stream);
     launch_face_eig_n(ded, (int)eds.size(), nmax, tau, h->opt.drop_rel, h->dst, h->stream);
@@ -2159,6 +2355,9 @@ void bddc_default_options(bddc_options *opt) {
     opt->drop_rel = 1e-10;
     opt->timeout_s = 10.0;
     opt->stream = nullptr;
+    opt->dev_alloc = nullptr;
+    opt->dev_free = nullptr;
+    opt->alloc_ctx = nullptr;
 }
 
 const char *bddc_status_str(bddc_status s) {
@@ -2203,14 +2402,24 @@ bddc_status bddc_create(const bddc_options *opt, bddc_handle **out) {
     else
         bddc_default_options(&h->opt);
     h->stream = (cudaStream_t)h->opt.stream;
-    if (cudaMalloc(&h->dst, sizeof(DevStatus)) != cudaSuccess) {
+    if ((h->opt.dev_alloc == nullptr) != (h->opt.dev_free == nullptr)) {
+        delete h;
+        return BDDC_EINVAL;
+    }
+    h->ar.set_allocator(h->opt.dev_alloc, h->opt.dev_free, h->opt.alloc_ctx, h->stream);
+    try {
+        h->dst = h->ar.get_t<DevStatus>("status", 1);
+    } catch (const Error &) {
         delete h;
         return BDDC_ENOMEM;
     }
-    cudaMemset(h->dst, 0, sizeof(DevStatus));
+    if (cudaMemsetAsync(h->dst, 0, sizeof(DevStatus), h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        delete h;
+        return BDDC_ECUDA;
+    }
     for (auto &e : h->ev) {
         if (cudaEventCreate(&e) != cudaSuccess) {
-            cudaFree(h->dst);
             delete h;
             return BDDC_ECUDA;
         }
@@ -2224,10 +2433,97 @@ void bddc_destroy(bddc_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     h->ar.release();
-    cudaFree(h->dst);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
     delete h;
+}
+
+// Classification, index maps, device copies of the input and solver buffers;
+// shared by bddc_set_mesh_q1, bddc_set_problem, bddc_set_corners and
+// bddc_select_corners.  Constraints are reset to corners only.
+void analyze(bddc_handle *h, std::chrono::steady_clock::time_point t_host0) {
+    h->have_mesh = h->have_setup = false;
+    h->assembled = h->factored = false;
+    h->coarse_dirty = true;
+    if (h->xyz.size() < (size_t)h->nn * 3) h->xyz.assign((size_t)h->nn * 3, 0.0);
+    classify(h);
+    const auto t_class = std::chrono::steady_clock::now();
+    for (auto &sd : h->subs) BDDC_REQUIRE(sd.n > 0, BDDC_EINVAL, "substructure without free dofs");
+    h->avg_flags = 0;
+    if (h->csr_mode) {
+        // merged CSR entries with their dense offsets (column-major, [interior; interface])
+        const int ns = h->nsub;
+        std::vector<int64_t> start(ns + 1, 0), off;
+        std::vector<double> val;
+        std::vector<int32_t> lp(h->nfree, -1);
+        std::vector<std::pair<int64_t, double>> ent;
+        for (int s = 0; s < ns; ++s) {
+            const auto &sd = h->subs[s];
+            for (int k = 0; k < sd.nI; ++k) lp[sd.gI[k]] = k;
+            for (int k = 0; k < sd.nG; ++k) lp[sd.gG[k]] = sd.nI + k;
+            const auto &l2g = h->csr_l2g[s];
+            const auto &rp = h->csr_rowptr[s];
+            const auto &cl = h->csr_col[s];
+            const auto &vl = h->csr_val[s];
+            ent.clear();
+            ent.reserve(vl.size());
+            for (size_t r = 0; r < l2g.size(); ++r) {
+                const int64_t pr = lp[l2g[r]];
+                BDDC_REQUIRE(pr >= 0, BDDC_EINVAL, "internal: CSR row outside the substructure's dofs");
+                for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+                    const int64_t pc = lp[l2g[cl[q]]];
+                    BDDC_REQUIRE(pc >= 0, BDDC_EINVAL, "internal: CSR column outside the substructure's dofs");
+                    ent.push_back({pc * sd.ld + pr, vl[q]});
+                }
+            }
+            std::sort(ent.begin(), ent.end(),
+                      [](const std::pair<int64_t, double> &x, const std::pair<int64_t, double> &y) { return x.first < y.first; });
+            for (size_t q = 0; q < ent.size(); ++q) {
+                if (q > 0 && ent[q].first == ent[q - 1].first)
+                    val.back() += ent[q].second;
+                else {
+                    off.push_back(ent[q].first);
+                    val.push_back(ent[q].second);
+                }
+            }
+            start[s + 1] = (int64_t)off.size();
+            for (int k = 0; k < sd.nI; ++k) lp[sd.gI[k]] = -1;
+            for (int k = 0; k < sd.nG; ++k) lp[sd.gG[k]] = -1;
+        }
+        h->csr_nnz = (int64_t)off.size();
+        h->ar.upload("csr_start", start, h->stream);
+        h->ar.upload("csr_off", off, h->stream);
+        h->ar.upload("csr_val", val, h->stream);
+    } else {
+        h->ar.upload("xyz", h->xyz, h->stream);
+        h->ar.upload("elems", h->elems, h->stream);
+        h->ar.upload("coef", h->coef, h->stream);
+        h->ar.upload("esub", h->esub, h->stream);
+        h->ar.upload("epos", element_positions(h), h->stream);
+        for (size_t col = 0; col < h->colors.size(); ++col)
+            h->ar.upload("color_" + std::to_string(col), h->colors[col], h->stream);
+    }
+    std::vector<int64_t> gIall, gGall, RG64;
+    for (auto &sd : h->subs) {
+        gIall.insert(gIall.end(), sd.gI.begin(), sd.gI.end());
+        gGall.insert(gGall.end(), sd.gG.begin(), sd.gG.end());
+        for (int x : sd.RG) RG64.push_back(x);
+    }
+    h->ar.upload("gIall", gIall, h->stream);
+    h->ar.upload("gGall", gGall, h->stream);
+    h->ar.upload("RG64", RG64, h->stream);
+    h->ar.upload("ifgdof", h->iface_gdof, h->stream);
+    const auto t_up = std::chrono::steady_clock::now();
+    alloc_solver_buffers(h);
+    BDDC_CUDA(cudaStreamSynchronize(h->stream));
+    const auto t_end = std::chrono::steady_clock::now();
+    h->phase_ms[5] = std::chrono::duration<double, std::milli>(t_end - t_host0).count();
+    if (getenv("BDDC_DEBUG_TIMING")) {
+        auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
+        fprintf(stderr, "analysis: input+classify %.3f uploads %.3f buffers %.3f ms\n", ms(t_host0, t_class),
+                ms(t_class, t_up), ms(t_up, t_end));
+    }
+    h->have_mesh = true;
 }
 
 bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double *xyz, int64_t ne,
@@ -2259,44 +2555,116 @@ bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double
         cp(h->coef.data(), coef, ne * sizeof(double));
         cp(h->esub.data(), elem_sub, ne * sizeof(int32_t));
         cp(h->dirich.data(), dirichlet, nn);
-        const auto t_copy = std::chrono::steady_clock::now();
         for (int64_t k = 0; k < ne * 8; ++k)
             BDDC_REQUIRE(h->elems[k] >= 0 && h->elems[k] < nn, BDDC_EINVAL, "element node id out of range");
         for (int64_t e = 0; e < ne; ++e)
             BDDC_REQUIRE(h->esub[e] >= 0 && h->esub[e] < nsub, BDDC_EINVAL, "substructure id out of range");
-        classify(h);
-        const auto t_class = std::chrono::steady_clock::now();
-        for (auto &sd : h->subs) BDDC_REQUIRE(sd.n > 0, BDDC_EINVAL, "substructure without free dofs");
-        h->avg_flags = 0;
-        // device copies of the mesh and index maps
-        h->ar.upload("xyz", h->xyz, h->stream);
-        h->ar.upload("elems", h->elems, h->stream);
-        h->ar.upload("coef", h->coef, h->stream);
-        h->ar.upload("esub", h->esub, h->stream);
-        h->ar.upload("epos", element_positions(h), h->stream);
-        for (size_t col = 0; col < h->colors.size(); ++col)
-            h->ar.upload("color_" + std::to_string(col), h->colors[col], h->stream);
-        std::vector<int64_t> gIall, gGall, RG64;
-        for (auto &sd : h->subs) {
-            gIall.insert(gIall.end(), sd.gI.begin(), sd.gI.end());
-            gGall.insert(gGall.end(), sd.gG.begin(), sd.gG.end());
-            for (int x : sd.RG) RG64.push_back(x);
+        h->csr_mode = false;
+        h->user_corners = false;
+        h->corner_list.clear();
+        h->csr_l2g.clear();
+        h->csr_rowptr.clear();
+        h->csr_col.clear();
+        h->csr_val.clear();
+        analyze(h, t_host0);
+    });
+}
+
+bddc_status bddc_set_problem(bddc_handle *h, int64_t n_global, int ncomp, int32_t n_sub, const bddc_subdomain *subs,
+                             const double *node_xyz, int mem) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(ncomp == 1 || ncomp == 3, BDDC_EINVAL, "ncomp must be 1 or 3");
+        BDDC_REQUIRE(n_global > 0 && n_sub > 0 && subs, BDDC_EINVAL, "empty problem");
+        BDDC_REQUIRE(n_global % ncomp == 0, BDDC_EINVAL, "n_global must be a multiple of ncomp");
+        BDDC_REQUIRE(ncomp == 1 || node_xyz, BDDC_EINVAL, "node_xyz is required for ncomp = 3 (rigid body modes)");
+        const auto t_host0 = std::chrono::steady_clock::now();
+        const int64_t nn = n_global / ncomp;
+        auto cp = [&](void *dst, const void *src, size_t bytes) {
+            if (bytes == 0) return;
+            BDDC_REQUIRE(src, BDDC_EINVAL, "null array");
+            BDDC_CUDA(cudaMemcpy(dst, src, bytes, mem == BDDC_MEM_DEVICE ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+        };
+        std::vector<std::vector<int64_t>> l2g(n_sub), rowptr(n_sub);
+        std::vector<std::vector<int32_t>> col(n_sub);
+        std::vector<std::vector<double>> val(n_sub);
+        std::vector<int32_t> owner(nn, -1);
+        for (int s = 0; s < n_sub; ++s) {
+            const bddc_subdomain &d = subs[s];
+            BDDC_REQUIRE(d.n_local > 0, BDDC_EINVAL, "substructure " + std::to_string(s) + " has no dofs");
+            const int n = d.n_local;
+            l2g[s].resize(n);
+            rowptr[s].resize(n + 1);
+            cp(l2g[s].data(), d.l2g, n * sizeof(int64_t));
+            cp(rowptr[s].data(), d.rowptr, (n + 1) * sizeof(int64_t));
+            const int64_t nnz = rowptr[s][n];
+            BDDC_REQUIRE(rowptr[s][0] == 0 && nnz >= 0, BDDC_EINVAL, "bad rowptr of substructure " + std::to_string(s));
+            for (int r = 0; r < n; ++r)
+                BDDC_REQUIRE(rowptr[s][r + 1] >= rowptr[s][r], BDDC_EINVAL, "rowptr not monotone");
+            col[s].resize(nnz);
+            val[s].resize(nnz);
+            cp(col[s].data(), d.col, nnz * sizeof(int32_t));
+            cp(val[s].data(), d.val, nnz * sizeof(double));
+            for (int32_t q : col[s]) BDDC_REQUIRE(q >= 0 && q < n, BDDC_EINVAL, "column index out of range");
+            // every node of the substructure complete, each global dof once
+            std::vector<int64_t> sorted = l2g[s];
+            std::sort(sorted.begin(), sorted.end());
+            for (size_t k = 0; k < sorted.size(); ++k) {
+                BDDC_REQUIRE(sorted[k] >= 0 && sorted[k] < n_global, BDDC_EINVAL, "l2g entry out of range");
+                BDDC_REQUIRE(k == 0 || sorted[k] != sorted[k - 1], BDDC_EINVAL, "l2g repeats a global dof");
+            }
+            BDDC_REQUIRE(sorted.size() % ncomp == 0, BDDC_EINVAL, "a node is split between substructures");
+            for (size_t k = 0; k < sorted.size(); k += ncomp)
+                BDDC_REQUIRE(sorted[k] % ncomp == 0 && sorted[k + ncomp - 1] == sorted[k] + ncomp - 1, BDDC_EINVAL,
+                             "substructure " + std::to_string(s) + " holds only some dofs of a node");
         }
-        h->ar.upload("gIall", gIall, h->stream);
-        h->ar.upload("gGall", gGall, h->stream);
-        h->ar.upload("RG64", RG64, h->stream);
-        h->ar.upload("ifgdof", h->iface_gdof, h->stream);
-        const auto t_up = std::chrono::steady_clock::now();
-        alloc_solver_buffers(h);
-        BDDC_CUDA(cudaStreamSynchronize(h->stream));
-        const auto t_end = std::chrono::steady_clock::now();
-        h->phase_ms[5] = std::chrono::duration<double, std::milli>(t_end - t_host0).count();
-        if (getenv("BDDC_DEBUG_TIMING")) {
-            auto ms = [](auto a, auto b) { return std::chrono::duration<double, std::milli>(b - a).count(); };
-            fprintf(stderr, "set_mesh: copy %.3f classify %.3f uploads %.3f buffers %.3f ms\n", ms(t_host0, t_copy),
-                    ms(t_copy, t_class), ms(t_class, t_up), ms(t_up, t_end));
-        }
-        h->have_mesh = true;
+        h->csr_mode = true;
+        h->user_corners = false;
+        h->corner_list.clear();
+        h->ncomp = ncomp;
+        h->nn = nn;
+        h->ne = 0;
+        h->nsub = n_sub;
+        h->nu = 0.0;
+        h->elems.clear();
+        h->coef.clear();
+        h->esub.clear();
+        h->dirich.assign(nn, 0);
+        h->xyz.assign((size_t)nn * 3, 0.0);
+        if (node_xyz) cp(h->xyz.data(), node_xyz, (size_t)nn * 3 * sizeof(double));
+        h->csr_l2g = std::move(l2g);
+        h->csr_rowptr = std::move(rowptr);
+        h->csr_col = std::move(col);
+        h->csr_val = std::move(val);
+        analyze(h, t_host0);
+    });
+}
+
+bddc_status bddc_set_corners(bddc_handle *h, int64_t n, const int64_t *nodes) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(h->have_mesh, BDDC_ESTATE, "set_corners before set_problem / set_mesh_q1");
+        BDDC_REQUIRE(n >= 0 && (n == 0 || nodes), BDDC_EINVAL, "null corner list");
+        const auto t_host0 = std::chrono::steady_clock::now();
+        std::vector<int64_t> list(nodes, nodes + n);
+        std::sort(list.begin(), list.end());
+        list.erase(std::unique(list.begin(), list.end()), list.end());
+        for (int64_t v : list) BDDC_REQUIRE(v >= 0 && v < h->nn, BDDC_EINVAL, "corner node id out of range");
+        h->user_corners = true;
+        h->corner_list = list;
+        analyze(h, t_host0);
+    });
+}
+
+bddc_status bddc_select_corners(bddc_handle *h, int64_t *n_out) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(h->have_mesh, BDDC_ESTATE, "select_corners before set_problem / set_mesh_q1");
+        const auto t_host0 = std::chrono::steady_clock::now();
+        h->user_corners = false;
+        h->corner_list.clear();
+        analyze(h, t_host0);
+        if (n_out) *n_out = (int64_t)h->corners.size();
     });
 }
 

@@ -14,6 +14,7 @@
 //      are dropped as in the paper's Remark), normalised and orthogonalised
 //      with row pivoting; rows whose pivot is below drop_rel are dropped.
 #include "common.cuh"
+#include <algorithm>
 #include "eig.h"
 
 namespace bddc {
@@ -382,6 +383,97 @@ __global__ void deflate_kernel(const DeflateDesc *dd, int np) {
 
 void launch_deflate(const DeflateDesc *d, int npairs, cudaStream_t s) {
     if (npairs > 0) deflate_kernel<<<npairs, 256, 0, s>>>(d, npairs);
+}
+
+// ---- pair problems with initial constraints (the projection of Section 3 onto
+// the jumps that satisfy the initial glob constraints) ----
+__device__ __forceinline__ double sym_lower(const double *M, int ld, int i, int j) {
+    return i >= j ? M[(size_t)j * ld + i] : M[(size_t)i * ld + j];
+}
+
+// grid (pairs, row blocks): one thread per lower entry of a column strip
+__global__ void pi_compress_kernel(const PiDesc *dd, int np) {
+    const PiDesc d = dd[blockIdx.x];
+    const int ns = d.ns, nsp = d.nsp, n = ns + 2 * nsp;
+    if (nsp == 0) return;
+    const int64_t total = (int64_t)n * n;
+    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.y * blockDim.x) {
+        const int r = (int)(e % n), c = (int)(e / n);
+        if (r < c) continue;
+        double v = 0.0;
+        if (r < ns) {                       // (w2, w2)
+            v = sym_lower(d.M3, d.ld3, r, c);
+        } else if (r < ns + nsp) {          // (u, w2) or (u, u)
+            const int a = d.keep[r - ns], la = d.lead[a];
+            if (c < ns) {
+                v = d.M3[(size_t)c * d.ld3 + ns + a];
+                if (la >= 0) v -= d.M3[(size_t)c * d.ld3 + ns + la];
+            } else {
+                const int b = d.keep[c - ns], lb = d.lead[b];
+                v = sym_lower(d.M3, d.ld3, ns + a, ns + b);
+                if (lb >= 0) v -= sym_lower(d.M3, d.ld3, ns + a, ns + lb);
+                if (la >= 0) v -= sym_lower(d.M3, d.ld3, ns + la, ns + b);
+                if (la >= 0 && lb >= 0) v += sym_lower(d.M3, d.ld3, ns + la, ns + lb);
+            }
+        } else {                            // identity row block
+            v = (c >= ns && c < ns + nsp && r - ns - nsp == c - ns) ? 1.0 : 0.0;
+        }
+        d.M3c[(size_t)c * d.ldc + r] = v;
+    }
+}
+
+void launch_pi_compress(const PiDesc *d, int npairs, int nmax, cudaStream_t s) {
+    if (npairs <= 0) return;
+    const int64_t n = 3 * (int64_t)nmax;
+    const int ny = (int)std::min<int64_t>(64, (n * n + 255) / 256);
+    pi_compress_kernel<<<dim3(npairs, std::max(ny, 1)), 256, 0, s>>>(d, npairs);
+}
+
+__global__ void pi_expand_kernel(const PiDesc *dd, int np) {
+    const PiDesc d = dd[blockIdx.x];
+    const int ns = d.ns, nsp = d.nsp;
+    if (nsp == 0) return;
+    const double *Xc = d.M3c + (size_t)ns * d.ldc + ns + nsp;   // X'(i, j) = Xc[j * ldc + i]
+    const int64_t total = (int64_t)ns * nsp;
+    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.y * blockDim.x) {
+        const int a = (int)(e % ns), j = (int)(e / ns);
+        double v;
+        if (d.newidx[a] >= 0) {
+            v = Xc[(size_t)j * d.ldc + d.newidx[a]];
+        } else {
+            // a leads its group: minus the sum of the other members' rows
+            v = 0.0;
+            const int g = d.grp[a];
+            for (int q = d.gptr[g] + 1; q < d.gptr[g + 1]; ++q) v -= Xc[(size_t)j * d.ldc + d.newidx[d.gidx[q]]];
+        }
+        d.Xg[(size_t)j * d.ldg + a] = v;
+    }
+}
+
+void launch_pi_expand(const PiDesc *d, int npairs, int nmax, cudaStream_t s) {
+    if (npairs <= 0) return;
+    const int64_t n = nmax;
+    const int ny = (int)std::min<int64_t>(64, (n * n + 255) / 256);
+    pi_expand_kernel<<<dim3(npairs, std::max(ny, 1)), 256, 0, s>>>(d, npairs);
+}
+
+// one thread per (group, column)
+__global__ void pi_project_kernel(const PiDesc *dd, int np) {
+    const PiDesc d = dd[blockIdx.x];
+    const int64_t total = (int64_t)d.ngroups * d.nsp;
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+        const int g = (int)(e % d.ngroups), j = (int)(e / d.ngroups);
+        const int q0 = d.gptr[g], q1 = d.gptr[g + 1];
+        double *col = d.W1 + (size_t)j * d.ldw;
+        double m = 0.0;
+        for (int q = q0; q < q1; ++q) m += col[d.gidx[q]];
+        m /= (double)(q1 - q0);
+        for (int q = q0; q < q1; ++q) col[d.gidx[q]] -= m;
+    }
+}
+
+void launch_pi_project(const PiDesc *d, int npairs, cudaStream_t s) {
+    if (npairs > 0) pi_project_kernel<<<npairs, 256, 0, s>>>(d, npairs);
 }
 
 __global__ void pair_weights_kernel(const PairWeightDesc *dd, int np) {

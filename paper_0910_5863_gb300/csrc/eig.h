@@ -39,6 +39,38 @@ struct DeflateDesc {
 };
 void launch_deflate(const DeflateDesc *d, int npairs, cudaStream_t s);
 
+// Initial constraints of a pair (averages over globs inside s): the pair problem
+// is restricted to jumps z with R z = 0, R the indicator rows of the groups
+// (one glob and one component each).  z = G u with G's columns e_a (a in no
+// group) and e_q - e_lead (q a non-leading member of a group); the leader
+// (first member) of every group is dropped, so u has nsp = ns - ngroups entries.
+//   compress: M3c = [[Mww, ., .], [G^T Mbw, G^T Mbb G, .], [0, I_nsp, 0]] from the
+//             full M3 (lower blocks as built by the adapt phase)
+//   expand:   Xg = G X' with X' = M3c[ns+nsp : ns+2nsp, ns : ns+nsp] after the
+//             partial Cholesky of M3c (ns + nsp columns)
+//   project:  W1 <- P W1, P the orthogonal projector onto null(R): the group
+//             mean is removed from every column of W1 within each group
+struct PiDesc {
+    const double *M3;     // 3ns x 3ns, ld3
+    int ld3;
+    double *M3c;          // (ns + 2nsp)^2, ldc
+    int ldc;
+    double *Xg;           // ns x nsp, ldg
+    int ldg;
+    double *W1;           // ns x nsp, ldw
+    int ldw;
+    const int *newidx;    // (ns) index in u, -1 for a leader
+    const int *lead;      // (ns) leader of the member's group, -1 for leaders and non-members
+    const int *grp;       // (ns) group of the position, -1 if none
+    const int *keep;      // (nsp) position of every u entry
+    const int *gptr;      // (ngroups + 1)
+    const int *gidx;      // members, leader first
+    int ns, nsp, ngroups;
+};
+void launch_pi_compress(const PiDesc *d, int npairs, int nmax, cudaStream_t s);
+void launch_pi_expand(const PiDesc *d, int npairs, int nmax, cudaStream_t s);
+void launch_pi_project(const PiDesc *d, int npairs, cudaStream_t s);
+
 // Pair weights d_i = a_i / (a_i + a_j), d_j = a_j / (a_i + a_j) over s.
 struct PairWeightDesc {
     const double *diag_i, *diag_j;   // packed diag(A) of the two substructures' interface dofs

@@ -40,6 +40,10 @@ def test_host_only_calls(lib):
     opt = B.Options()
     B._lib.bddc_default_options(ctypes.byref(opt))
     assert opt.tol == 1e-8 and opt.maxit == 1000 and opt.precision == B.FP64
+    assert opt.dev_alloc is None and opt.dev_free is None and opt.alloc_ctx is None
     assert B._lib.bddc_status_str(3) == b"matrix not positive definite"
     assert B._lib.bddc_launch_count(None) == 0
     assert B._lib.bddc_setup(None) == 1
+    assert B._lib.bddc_set_corners(None, 0, None) == 1
+    assert B._lib.bddc_select_corners(None, None) == 1
+    assert B._lib.bddc_set_problem(None, 1, 1, 1, None, None, 0) == 1

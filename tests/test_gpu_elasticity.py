@@ -22,7 +22,7 @@ def elast():
     runs = {}
     for prec in (B.FP64, B.MIXED):
         s = B.Solver(precision=prec, tol=1e-10)
-        s.set_problem(prob)
+        s.set_mesh_problem(prob)
         s.setup()
         info = s.adapt(10.0)
         u, sinfo = s.solve(B.free_load_vector(prob))

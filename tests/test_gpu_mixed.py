@@ -21,7 +21,7 @@ def _rel(a, b):
 
 def _solver(prob, averages=(), tol=1e-8):
     s = B.Solver(precision=B.MIXED, tol=tol)
-    s.set_problem(prob)
+    s.set_mesh_problem(prob)
     s.set_averages(edge="edge" in averages, face="face" in averages)
     s.setup()
     return s

@@ -15,7 +15,7 @@ TOL_LAM = 1e-6       # adaptive eigenvalues, relative
 
 def _solver(prob, averages=(), tol=1e-8):
     s = B.Solver(tol=tol)
-    s.set_problem(prob)
+    s.set_mesh_problem(prob)
     s.set_averages(edge="edge" in averages, face="face" in averages)
     s.setup()
     return s
@@ -132,8 +132,10 @@ def test_errors_are_statuses():
     prob = P.poisson_cube(4, 2, s_xyz=(2, 1, 1))
     prob.dirichlet[:] = False
     s = B.Solver()
+    s.set_mesh_problem(prob)           # the augmentation gives the floating pair a corner
+    assert s.sizes()["n_corners"] == 1
     with pytest.raises(B.BddcError) as e:
-        s.set_problem(prob)       # floating substructures without corners
+        s.set_corners([])              # floating substructures without corners
     assert e.value.status == 4
     s2 = B.Solver()
     with pytest.raises(B.BddcError) as e:

@@ -371,3 +371,64 @@ def test_corner_augmentation_is_not_needed_when_anchored():
     """Every substructure touching the Dirichlet boundary: no face node is promoted."""
     for prob in (P.config_small(), P.poisson_cube(6, 2, coef="lognormal")):
         assert oracle.Model(prob).globs.augmented == []
+
+
+def _planar_table():
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "planar_cubes_weak_scaling.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            n, dofs, kappa, iters = line.split()
+            rows.append((int(n), int(dofs), float(kappa), int(iters)))
+    return rows
+
+
+def test_planar_cubes_condition_number_matches_the_paper():
+    """The weak-scaling table of Section 7 (corners only, H/h = 8): the dof counts
+    are exact, and the Lanczos condition estimate of the corner-only BDDC with the
+    augmented corners lands within 5% of the printed value for 4 and 9 cubes.  The
+    iteration counts depend on the load, which the paper does not fix, so they are
+    not compared."""
+    for n, dofs, kappa, _ in _planar_table()[:2]:
+        k = int(round(n ** 0.5))
+        prob = P.planar_cubes(k, m=8)
+        assert prob.xyz.shape[0] * 3 == dofs
+        m, _, res = oracle.run(prob, tol=1e-8, maxit=500)
+        lo, hi = res.condition()
+        assert abs(hi / lo - kappa) <= 0.05 * kappa, (n, hi / lo, kappa)
+
+
+def test_two_substructure_pair_problem_with_initial_face_average():
+    """Corollary 3.1 with an initial constraint (Pi != I): corners plus the face
+    arithmetic average as the initial coarse space.  The pair problem restricted to
+    the jumps with zero face average gives lambda_max(M S) exactly, and adding its
+    k top eigen-constraints leaves lambda_max(M S) = lambda_{12,k+1}."""
+    prob = P.poisson_cube(6, 2, coef="lognormal", s_xyz=(2, 1, 1), seed=3)
+
+    def model():
+        m = oracle.Model(prob, averages=("face",))
+        m.schur()
+        return m
+
+    m = model()
+    res = pair_problem(m, 0, 1, tau=1.0)
+    lam = res.lam
+    S = _dense_op(m.apply_S, m.nG)
+    M = _dense_op(m.apply_M, m.nG)
+    lmax = np.linalg.eigvals(M @ S).real.max()
+    assert abs(lmax - lam[0]) < 1e-8 * lam[0]
+    # the average is a real constraint: without it the top eigenvalue is larger
+    m0 = oracle.Model(prob)
+    m0.schur()
+    assert pair_problem(m0, 0, 1, tau=1.0).lam[0] > lam[0] * (1 + 1e-6)
+    for k in (1, 2):
+        m2 = model()
+        r2 = pair_problem(m2, 0, 1, tau=lam[k] * (1 + 1e-9))
+        assert r2.selected == k
+        rows = orthonormal_rows(r2.face_rows)
+        # the rows are orthogonal to the face average (d = w^T Pi L Pi)
+        assert np.abs(rows.sum(axis=1)).max() < 1e-10
+        m2.add_constraint("adaptive", m2.globs.faces[(0, 1)], (0, 1), rows)
+        M2 = _dense_op(m2.apply_M, m2.nG)
+        lmax2 = np.linalg.eigvals(M2 @ S).real.max()
+        assert abs(lmax2 - lam[k]) < 1e-7 * lam[k]

@@ -43,7 +43,7 @@ def test_static_scratch_schur_matches_setup_path():
     fn = _fn()
     prob = P.config_small()
     s = B.Solver()
-    s.set_problem(prob)
+    s.set_mesh_problem(prob)
     s.setup()
     m = oracle.Model(prob)
     msg = C.create_string_buffer(256)
