@@ -57,7 +57,15 @@ typedef enum { BDDC_MEM_HOST = 0, BDDC_MEM_DEVICE = 1 } bddc_mem;
 
 typedef enum {
     BDDC_FP64 = 0,         /* every dense factorization in FP64 */
-    BDDC_MIXED = 1         /* FP32 factorizations + FP64 refinement; FP64 coarse, eigen, PCG */
+    BDDC_MIXED = 1,        /* interior elimination: FP32 factorization + FP64 refinement (S_i to
+                              1e-11 relative); local saddle, coarse, pair problems, eigen, PCG
+                              in FP64.  The preconditioner matches the FP64 one to ~1e-9. */
+    BDDC_MIXED_FP32_SADDLE = 2  /* as BDDC_MIXED, and the local saddle operators of the
+                              preconditioner (Lemma 2.1) from an equilibrated FP32
+                              factorization (rebuilt in FP64 if a pivot falls below 1e-5).
+                              The preconditioner is then exact only to ~1e-5, which spreads
+                              the eigenvalue cluster of M S at 1: PCG may need more
+                              iterations than in FP64 (observed up to +33%). */
 } bddc_precision;
 
 enum { BDDC_AVG_EDGE = 1, BDDC_AVG_FACE = 2 };
@@ -80,6 +88,11 @@ typedef struct {
     void *(*dev_alloc)(size_t bytes, void *alloc_ctx);
     void (*dev_free)(void *ptr, size_t bytes, void *alloc_ctx);
     void *alloc_ctx;
+    /* Mixed modes: the refinement of X = A_II^-1 A_IG stops at the first step with
+     * ||A_IG - A_II X|| <= refine_tol ||A_IG|| per substructure (S_i is then formed
+     * in the energy form, whose error R^T A_II^-1 R is second order in that residual,
+     * so the default 1e-8 already gives S_i to ~1e-13 relative). */
+    double refine_tol;
 } bddc_options;
 
 /* One substructure of an algebraic problem (bddc_set_problem): its local matrix
@@ -112,6 +125,8 @@ typedef struct {
     double solve_ms;       /* this solve, device time */
     int interior_fp32;     /* 1: S_i came from the FP32 factorization + FP64 refinement */
     int coarse_fp32;       /* 1: the local saddle operators came from the FP32 factorization */
+    int refine_steps;      /* mixed modes: corrections of the interior refinement */
+    double refine_relres;  /* mixed modes: its final largest relative residual */
 } bddc_solve_info;
 
 /* Fills *opt with the defaults above. */
@@ -241,7 +256,7 @@ BDDC_API bddc_status bddc_get_schur(const bddc_handle *h, int s, double *S, int 
  * ordered [interior dofs ascending; interface dofs ascending], as assembled by
  * the last bddc_setup.  In BDDC_FP64 mode the factorization overwrites the
  * lower triangle in place, so the call returns BDDC_ESTATE after a setup in
- * that mode; in BDDC_MIXED mode the assembled matrix is kept. */
+ * that mode; in the mixed modes the assembled matrix is kept. */
 BDDC_API bddc_status bddc_get_local_matrix(const bddc_handle *h, int s, double *A, int ld, int mem);
 
 /* One application of the preconditioner (z = M r) or of the assembled Schur

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libbddc.so")
 
 MEM_HOST, MEM_DEVICE = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_FP32_SADDLE = 0, 1, 2
 AVG_EDGE, AVG_FACE = 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTSPD", 4: "EASSUMPTION", 5: "ENOCONV", 6: "ETIMEOUT",
           7: "ECUDA", 8: "ESTATE"}
@@ -34,7 +34,7 @@ PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int), ("drop_rel", C.c_double),
                 ("timeout_s", C.c_double), ("stream", C.c_void_p), ("dev_alloc", C.c_void_p),
-                ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p)]
+                ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p), ("refine_tol", C.c_double)]
 
 
 class Subdomain(C.Structure):
@@ -53,7 +53,7 @@ class AdaptInfo(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("relres", C.c_double), ("kappa", C.c_double),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("interior_fp32", C.c_int),
-                ("coarse_fp32", C.c_int)]
+                ("coarse_fp32", C.c_int), ("refine_steps", C.c_int), ("refine_relres", C.c_double)]
 
 
 class BddcError(RuntimeError):
@@ -140,7 +140,7 @@ class Solver:
     """One handle of the library (one GPU, one stream)."""
 
     def __init__(self, precision=FP64, tol=1e-8, maxit=1000, drop_rel=1e-10, timeout_s=10.0, stream=None,
-                 allocator=None):
+                 allocator=None, refine_tol=None):
         """allocator: None (the library's cudaMalloc) or "torch" (device memory from
         PyTorch's caching allocator on the handle's stream)."""
         self.lib = load()
@@ -152,6 +152,8 @@ class Solver:
         opt.drop_rel = drop_rel
         opt.timeout_s = timeout_s
         opt.stream = stream
+        if refine_tol is not None:
+            opt.refine_tol = refine_tol
         self._callbacks = None
         if allocator == "torch":
             self._callbacks = _torch_allocator(stream)
@@ -257,7 +259,8 @@ class Solver:
         info = SolveInfo()
         st = self.lib.bddc_solve(self.h, pf, pu, mem, C.byref(info))
         out = {"iters": info.iters, "converged": bool(info.converged), "relres": info.relres, "kappa": info.kappa,
-               "interior_fp32": bool(info.interior_fp32), "coarse_fp32": bool(info.coarse_fp32)}
+               "interior_fp32": bool(info.interior_fp32), "coarse_fp32": bool(info.coarse_fp32),
+               "refine_steps": info.refine_steps, "refine_relres": info.refine_relres}
         if check or st not in (0, 5):
             self._check(st)
         out["status"] = STATUS.get(st, st)

@@ -1020,7 +1020,7 @@ struct Fp32Breakdown {};
 
 void coarse_setup(bddc_handle *h, bool allow_fp32) {
     const int ns = h->nsub;
-    const bool mixed = h->opt.precision == BDDC_MIXED && allow_fp32;
+    const bool mixed = h->opt.precision == BDDC_MIXED_FP32_SADDLE && allow_fp32;
     layout_constraints(h);
     // mixed: M1 in FP32 with the symmetric equilibration d = diag(S)^-1/2 of the remaining dofs
     double *eqS = nullptr, *dr = nullptr, *s2 = nullptr;
@@ -1558,8 +1558,8 @@ void interior_mixed(bddc_handle *h) {
     run_pchol<float>(h, pd, "F");
     run_gathers(h, gK, "Kinv");
     fail_check(h, "mixed interior factorization");
-    // refine until ||A_IG - A_II X|| <= 1e-8 ||A_IG||; the energy form below squares that error
-    h->mixed_iters = refine(h, jobs, 1, 12, 1e-8, true, "X");
+    // refine until ||A_IG - A_II X|| <= refine_tol ||A_IG||; the energy form below squares that error
+    h->mixed_iters = refine(h, jobs, 1, 12, h->opt.refine_tol, true, "X");
     // S_i = A_GG - A_GI X - X^T R  (R = A_IG - A_II X, the residual of the accepted X)
     std::vector<EllProduct> ps;
     for (const auto &j : jobs) {
@@ -1606,7 +1606,7 @@ void ensure_coarse(bddc_handle *h) {
     if (!h->coarse_dirty) return;
     phase_begin(h, 2);
     h->coarse_fp32 = false;
-    if (h->opt.precision == BDDC_MIXED) {
+    if (h->opt.precision == BDDC_MIXED_FP32_SADDLE) {
         try {
             coarse_setup(h, true);
             h->coarse_fp32 = true;
@@ -1690,7 +1690,7 @@ void do_setup(bddc_handle *h) {
         fl += (double)sd.nI * sd.nI * sd.nI / 3.0 + (double)sd.nI * sd.nI * sd.nG + (double)sd.nI * sd.nG * sd.nG;
     h->phase_flop[1] = fl;
     h->interior_fp32 = false;
-    bool fp64_interior = h->opt.precision != BDDC_MIXED;
+    bool fp64_interior = h->opt.precision == BDDC_FP64;
     if (!fp64_interior) {
         try {
             interior_mixed(h);
@@ -2337,6 +2337,8 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
         info->solve_ms = h->phase_ms[6] + h->phase_ms[7] + h->phase_ms[8];
         info->interior_fp32 = h->interior_fp32 ? 1 : 0;
         info->coarse_fp32 = h->coarse_fp32 ? 1 : 0;
+        info->refine_steps = h->interior_fp32 ? h->mixed_iters : 0;
+        info->refine_relres = h->interior_fp32 ? h->mixed_relres : 0.0;
     }
     if (!it[1]) throw Error{BDDC_ENOCONV, "PCG did not reach the tolerance within maxit"};
 }
@@ -2358,6 +2360,7 @@ void bddc_default_options(bddc_options *opt) {
     opt->dev_alloc = nullptr;
     opt->dev_free = nullptr;
     opt->alloc_ctx = nullptr;
+    opt->refine_tol = 1e-8;
 }
 
 const char *bddc_status_str(bddc_status s) {
@@ -2798,7 +2801,7 @@ bddc_status bddc_get_interface_dofs(const bddc_handle *h, int s, int64_t *gdofs,
 
 bddc_status bddc_get_local_matrix(const bddc_handle *h, int s, double *A, int ld, int mem) {
     if (!h || !h->assembled) return BDDC_ESTATE;
-    if (h->opt.precision != BDDC_MIXED && h->factored) return BDDC_ESTATE;
+    if (h->opt.precision == BDDC_FP64 && h->factored) return BDDC_ESTATE;
     if (s < 0 || s >= h->nsub || ld < h->subs[s].n) return BDDC_EINVAL;
     const auto &sd = h->subs[s];
     cudaError_t e = cudaMemcpy2D(A, (size_t)ld * sizeof(double), sd.A, (size_t)sd.ld * sizeof(double),

@@ -135,6 +135,55 @@ def cubic_partition(nx, ny, nz, sx, sy, sz):
     return sub
 
 
+def region_growing_partition(nx, ny, nz, nparts, seed):
+    """Irregular partition of an nx x ny x nz element grid: nparts distinct seed
+    elements drawn uniformly (redrawing repeats), then rounds in which every region,
+    in the order 0 .. nparts-1, takes the oldest element of its frontier (the
+    unassigned elements face-adjacent to it, in the order first reached; entries
+    assigned meanwhile are skipped), i.e. breadth-first growth in round-robin.
+    Regions stay face-connected.  Returns elem_sub (int32)."""
+    from collections import deque
+    ne = nx * ny * nz
+    st = Stream(seed, P_PARTITION)
+    owner = -np.ones(ne, dtype=np.int64)
+    frontier = [deque() for _ in range(nparts)]
+
+    def neighbours(e):
+        ex, r = e % nx, e // nx
+        ey, ez = r % ny, r // ny
+        if ex > 0: yield e - 1
+        if ex < nx - 1: yield e + 1
+        if ey > 0: yield e - nx
+        if ey < ny - 1: yield e + nx
+        if ez > 0: yield e - nx * ny
+        if ez < nz - 1: yield e + nx * ny
+
+    def take(r, e):
+        owner[e] = r
+        for q in neighbours(e):
+            if owner[q] < 0:
+                frontier[r].append(q)
+
+    r = 0
+    while r < nparts:
+        e = st.below(ne)
+        if owner[e] < 0:
+            take(r, e)
+            r += 1
+    left = ne - nparts
+    while left > 0:
+        for r in range(nparts):
+            fr = frontier[r]
+            while fr and owner[fr[0]] >= 0:
+                fr.popleft()
+            if fr:
+                take(r, fr.popleft())
+                left -= 1
+                if left == 0:
+                    break
+    return owner.astype(np.int32)
+
+
 def _uniform_loads(nn, seed, dirichlet):
     f = 2.0 * Stream(seed, P_RHS).uniform(nn) - 1.0
     f[dirichlet] = 0.0
@@ -188,7 +237,7 @@ def _body_load(xyz, elems, h, dirichlet, b=(0.0, 0.0, -1.0)):
 
 def elasticity_cube(n: int, s: int, seed: int = 1, channels: int = 0, e_channel: float = 1e6,
                     nu: float = 0.3, s_xyz=None, grid=None, layers: int = 0, e_layer: float = 1e3,
-                    name=None) -> Problem:
+                    name=None, partition=None) -> Problem:
     """Q1 linear elasticity on a box of n^3 (or ``grid``) elements with h = 1/n,
     s^3 cubic substructures, clamped at z = 0, body load (0, 0, -1).
 
@@ -196,6 +245,7 @@ def elasticity_cube(n: int, s: int, seed: int = 1, channels: int = 0, e_channel:
     an axis in {x, y, z} and a transverse element index pair uniformly and spans
     the whole box, so it crosses substructure faces.
     layers: if > 0, E = e_layer in z-layers floor(ez / layers) odd, 1 otherwise.
+    partition: optional (elem_sub, nsub) replacing the cubic substructures.
     """
     nx, ny, nz = grid if grid is not None else (n, n, n)
     sx, sy, sz = s_xyz if s_xyz is not None else (s, s, s)
@@ -225,9 +275,9 @@ def elasticity_cube(n: int, s: int, seed: int = 1, channels: int = 0, e_channel:
         E[eid[odd]] = e_layer
     dirichlet = np.isclose(xyz[:, 2], 0.0)
     load = _body_load(xyz, elems, h, dirichlet)
+    esub, nsub = partition if partition is not None else (cubic_partition(nx, ny, nz, sx, sy, sz), sx * sy * sz)
     return Problem(name or f"elast{nx}x{ny}x{nz}_s{sx}{sy}{sz}", 3, (nx, ny, nz), h, xyz, elems, E, nu,
-                   cubic_partition(nx, ny, nz, sx, sy, sz), sx * sy * sz, dirichlet, load,
-                   {"seed": seed, "channels": channels, "layers": layers})
+                   esub, nsub, dirichlet, load, {"seed": seed, "channels": channels, "layers": layers})
 
 
 # --- the named workloads -------------------------------------------------
@@ -247,6 +297,16 @@ def config_adaptive_poisson(seed: int = 1) -> Problem:
 def config_elasticity_channels(seed: int = 1) -> Problem:
     """32^3 elasticity, 4x4x4 substructures of 8^3, 8 stiff channels E = 1e6."""
     return elasticity_cube(32, 4, seed, channels=8, name="elast32_4x4x4_channels")
+
+
+def config_irregular_elasticity(seed: int = 1, grid=(48, 48, 24), nparts: int = 64) -> Problem:
+    """48 x 48 x 24 elasticity (h = 1/48), nparts irregular substructures by seeded
+    region growing, E = 1e3 in the odd z-layers of height 4 elements and 1 elsewhere,
+    nu = 0.3, clamped at z = 0, body load (0, 0, -1)."""
+    nx, ny, nz = grid
+    part = region_growing_partition(nx, ny, nz, nparts, seed)
+    return elasticity_cube(nx, 1, seed, grid=grid, layers=4, name=f"elast{nx}x{ny}x{nz}_irregular{nparts}",
+                           partition=(part, nparts))
 
 
 def planar_cubes(k: int, m: int = 8, nu: float = 0.3, name=None) -> Problem:

@@ -46,9 +46,11 @@ def test_global_residual_and_agreement(elast):
     u64, u32 = runs[B.FP64][2], runs[B.MIXED][2]
     assert np.linalg.norm(u64 - u32) <= 1e-8 * np.linalg.norm(u64)
     # kappa ~ 7.5e3 after adaptivity here (the face-only constraints do not bound the
-    # channels crossing edges): counts agree to the rounding sensitivity of PCG
+    # channels crossing edges).  At that conditioning rounding-level (1e-13) changes of
+    # the S_i move the oracle's own count by up to 3 (tests/pcg_spread.py); the oracle
+    # cannot run PCG at this size, so FP64 and mixed are held to that spread.
     it64, it32 = runs[B.FP64][3]["iters"], runs[B.MIXED][3]["iters"]
-    assert abs(it64 - it32) <= max(1, 0.03 * it64)
+    assert abs(it64 - it32) <= 3
     assert runs[B.MIXED][3]["interior_fp32"]
     assert runs[B.FP64][1]["n_added"] == runs[B.MIXED][1]["n_added"]
 

@@ -7,6 +7,7 @@ import pytest
 from paper_0910_5863_gb300 import problems as P
 from paper_0910_5863_gb300 import bddc as B
 import oracle
+from pcg_spread import iterations_agree
 
 pytestmark = pytest.mark.gpu
 
@@ -19,8 +20,8 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def _solver(prob, averages=(), tol=1e-8):
-    s = B.Solver(precision=B.MIXED, tol=tol)
+def _solver(prob, averages=(), tol=1e-8, precision=B.MIXED):
+    s = B.Solver(precision=precision, tol=tol)
     s.set_mesh_problem(prob)
     s.set_averages(edge="edge" in averages, face="face" in averages)
     s.setup()
@@ -44,9 +45,8 @@ def test_mixed_schur_and_solve(case):
     m8, _, ref8 = oracle.run(prob, averages=av, tol=1e-8)
     s8 = _solver(prob, av)
     u8, info8 = s8.solve(B.free_load_vector(prob))
-    # the mixed local saddle factorization is FP32: on corner-only runs with kappa ~ 1e4 the
-    # iteration count may move by a few percent (the FP64 path already differs by one there)
-    assert abs(info8["iters"] - ref8.iters) <= max(1, 0.03 * ref8.iters)
+    # +-1, or within the oracle's own spread under rounding-level perturbations at kappa > 1e3
+    assert iterations_agree(info8["iters"], m8, info8["kappa"]), (info8["iters"], ref8.iters)
     if not av:  # the adaptive run of the same problem (kappa <= tau): within one iteration
         ma, ada, refa = oracle.run(prob, tau=10.0, tol=1e-8)
         sa = _solver(prob)
@@ -74,3 +74,20 @@ def test_mixed_adaptive_poisson24_full_size():
     u, sinfo = s.solve(B.free_load_vector(prob))
     assert abs(sinfo["iters"] - res.iters) <= 1
     assert _rel(u, res.u) < 1e-7
+
+
+@pytest.mark.parametrize("case", ["jump_corner", "planar2"])
+def test_fp32_saddle_mode(case):
+    """BDDC_MIXED_FP32_SADDLE: the local saddle operators from an FP32 factorization.
+    The solution still meets the mixed tolerance; the preconditioner is exact only
+    to ~1e-5, so the iteration count may grow (bounded here by a third)."""
+    prob = P.poisson_cube(12, 2, coef="random_high", seed=2) if case == "jump_corner" else P.planar_cubes(2, m=8)
+    m, _, ref = oracle.run(prob, tol=1e-13)
+    s = _solver(prob, tol=1e-13, precision=B.MIXED_FP32_SADDLE)
+    u, info = s.solve(B.free_load_vector(prob))
+    assert _rel(u, ref.u) < TOL_U_MIXED
+    m8, _, ref8 = oracle.run(prob, tol=1e-8)
+    s8 = _solver(prob, precision=B.MIXED_FP32_SADDLE)
+    u8, info8 = s8.solve(B.free_load_vector(prob))
+    assert info8["converged"] and info8["iters"] <= 1.34 * ref8.iters + 1
+    assert abs(info8["kappa"] - ref8.condition()[1] / ref8.condition()[0]) <= 0.01 * info8["kappa"]

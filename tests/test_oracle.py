@@ -432,3 +432,19 @@ def test_two_substructure_pair_problem_with_initial_face_average():
         M2 = _dense_op(m2.apply_M, m2.nG)
         lmax2 = np.linalg.eigvals(M2 @ S).real.max()
         assert abs(lmax2 - lam[k]) < 1e-7 * lam[k]
+
+
+def test_pcg_iteration_spread_under_rounding_perturbations():
+    """Reading of the +-1 iteration tolerance: on the corner-only 12^3 jump problem
+    (kappa ~ 1.5e4) relative 1e-13 symmetric perturbations of the S_i move the
+    iteration count by at least 2, so there the count is compared within that
+    spread; on the well-conditioned 12^3 problem with averages it stays within 1."""
+    from pcg_spread import perturbed_iteration_range
+    m = oracle.Model(P.poisson_cube(12, 2, coef="random_high", seed=2))
+    m.schur()
+    lo, hi = perturbed_iteration_range(m)
+    assert hi - lo >= 2
+    m2 = oracle.Model(P.config_small(), averages=("edge", "face"))
+    m2.schur()
+    lo2, hi2 = perturbed_iteration_range(m2)
+    assert hi2 - lo2 <= 1
