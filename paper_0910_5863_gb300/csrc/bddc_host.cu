@@ -30,6 +30,7 @@
 #include "common.cuh"
 #include "dense.h"
 #include "eig.h"
+#include "ff.cuh"
 #include "host_util.h"
 #include "mixed.h"
 #include "pcg.h"
@@ -255,6 +256,30 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const 
         launch_pchol_update<T>(dd, du + uoff[s], uoff[s + 1] - uoff[s], kb, h->stream);
         check_launch(h);
     }
+}
+
+// Partial Cholesky of FP64 matrices in the FP64-class arithmetic of the precision
+// mode: FP64 in BDDC_FP64; in the mixed modes double-float on the FP32 pipe (the
+// lower triangles are converted in place before and after, the upper triangles
+// are not touched).
+void run_pchol_fp64class(bddc_handle *h, const std::vector<PcholDesc<double>> &descs, const std::string &tag) {
+    if (descs.empty()) return;
+    if (h->opt.precision == BDDC_FP64) {
+        run_pchol<double>(h, descs, tag);
+        return;
+    }
+    std::vector<int2> items;
+    for (int m = 0; m < (int)descs.size(); ++m)
+        for (int j = 0; j < descs[m].n; ++j) items.push_back(make_int2(m, j));
+    auto *dd = h->ar.upload("ffc_desc_" + tag, descs, h->stream);
+    auto *di = h->ar.upload("ffc_it_" + tag, items, h->stream);
+    launch_ff_convert(dd, di, (int)items.size(), 1, h->stream);
+    check_launch(h);
+    std::vector<PcholDesc<ff>> fd;
+    for (const auto &d : descs) fd.push_back(PcholDesc<ff>{reinterpret_cast<ff *>(d.A), d.n, d.ld, d.nstop, d.tag, nullptr});
+    run_pchol<ff>(h, fd, tag);
+    launch_ff_convert(dd, di, (int)items.size(), 0, h->stream);
+    check_launch(h);
 }
 
 void run_gathers(bddc_handle *h, const std::vector<GatherOp> &ops, const std::string &tag) {
@@ -1127,7 +1152,7 @@ void coarse_setup(bddc_handle *h, bool allow_fp32) {
         h->m1_min_pivot = minpiv;
         if (hs.code == BDDC_DEV_ERR_NOTSPD || !(minpiv >= 1e-5f)) throw Fp32Breakdown{};
     } else {
-        run_pchol<double>(h, d1, "M1");
+        run_pchol_fp64class(h, d1, "M1");
     }
     for (int s = 0; s < ns; ++s) {
         auto &sd = h->subs[s];
@@ -1158,7 +1183,7 @@ void coarse_setup(bddc_handle *h, bool allow_fp32) {
     }
     run_gathers(h, g2, "M2");
     run_diag(h, id2, "M2");
-    run_pchol<double>(h, d2, "M2");
+    run_pchol_fp64class(h, d2, "M2");
     if (mixed) {  // G = C_r S_rr^-1 C_r^T from the FP32 stage must factor
         DevStatus hs;
         BDDC_CUDA(cudaMemcpyAsync(&hs, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
@@ -1414,6 +1439,7 @@ EllProduct ell_of(bddc_handle *h, int s) {
     p.ell_col = h->ar.get_t<int>("ellj_" + t, (size_t)sd.n * W);
     p.ell_val = h->ar.get_t<double>("ellv_" + t, (size_t)sd.n * W);
     p.ell_w = W;
+    p.ell_n = sd.n;
     return p;
 }
 
@@ -1817,7 +1843,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         }
     }
     run_gathers(h, gE1, "E1");
-    run_pchol<double>(h, dE1, "E1");
+    run_pchol_fp64class(h, dE1, "E1");
     // algorithmic FP64 flops of the condensations: partial Cholesky of n with nstop = m
     // (m^3/3 + m^2 (n - m) + m (n - m)^2), for the E1 matrices here and E2, E3 below
     auto pchol_flop = [](double n, double m) { return m * m * m / 3.0 + m * m * (n - m) + m * (n - m) * (n - m); };
@@ -1865,7 +1891,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
     run_gathers(h, gE2, "E2a");
     run_gathers(h, gE3, "E2b");
     gE3.clear();
-    run_pchol<double>(h, dE2, "E2");
+    run_pchol_fp64class(h, dE2, "E2");
     for (auto &dd : dE2) cflop += pchol_flop(dd.n, dd.nstop);
     // E3: M3 = [[Mww, ., .], [Mbw, Mbb, .], [0, I, 0]] from S^ blocks, + deflation, eliminate 2 ns
     // (pairs with initial constraints: compressed to the jumps that satisfy them first)
@@ -2033,7 +2059,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         launch_pi_compress(dpis, (int)pis.size(), pi_nmax, h->stream);
         check_launch(h);
     }
-    run_pchol<double>(h, dE3, "E3");
+    run_pchol_fp64class(h, dE3, "E3");
     for (auto &dd : dE3) cflop += pchol_flop(dd.n, dd.nstop);
     h->phase_flop[3] = cflop;
     {

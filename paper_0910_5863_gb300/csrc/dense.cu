@@ -12,7 +12,9 @@
 // and with augmented matrices it also yields inverses and coarse operators.
 #include "common.cuh"
 #include "dense.h"
+#include "ff.cuh"
 #include <algorithm>
+#include <type_traits>
 
 namespace bddc {
 
@@ -52,10 +54,13 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
                 bad = 1;
                 dj = T(1);
                 Ld[j][j] = dj;
-            } else if (sizeof(T) == 4 && w.y == 0) {
-                atomicMin(&st->minpiv, __float_as_uint((float)dj));  // positive floats order as unsigned
+            } else if constexpr (std::is_same<T, float>::value) {
+                if (w.y == 0) atomicMin(&st->minpiv, __float_as_uint(dj));  // positive floats order as unsigned
             }
-            inv_d[j] = rsqrt(dj);
+            if constexpr (std::is_same<T, ff>::value)
+                inv_d[j] = ff_rsqrt(dj);
+            else
+                inv_d[j] = ::rsqrt(dj);
         }
         __syncthreads();
         // trailing update with the unscaled column: a_ik -= a_ij a_kj / a_jj
@@ -157,7 +162,12 @@ __global__ void __launch_bounds__(256) pchol_update_kernel(const PcholDesc<T> *d
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += pa[a] * pb[b];
+            for (int b = 0; b < 4; ++b) {
+                if constexpr (std::is_same<T, ff>::value)
+                    ff_fma_acc(acc[a][b], pa[a], pb[b]);
+                else
+                    acc[a][b] += pa[a] * pb[b];
+            }
     }
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
@@ -166,7 +176,12 @@ __global__ void __launch_bounds__(256) pchol_update_kernel(const PcholDesc<T> *d
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             int r = i0 + tx + 16 * a;
-            if (r < n && r >= c) A[(size_t)c * ld + r] -= acc[a][b];
+            if (r < n && r >= c) {
+                if constexpr (std::is_same<T, ff>::value)
+                    A[(size_t)c * ld + r] -= ff_norm(acc[a][b]);
+                else
+                    A[(size_t)c * ld + r] -= acc[a][b];
+            }
         }
     }
 }
@@ -460,6 +475,32 @@ template <typename T>
 void launch_pchol_update(const PcholDesc<T> *descs, const int4 *items, int nitems, int kb, cudaStream_t s) {
     if (nitems > 0) pchol_update_kernel<T><<<nitems, 256, 0, s>>>(descs, items, nitems, kb);
 }
+template void launch_pchol_panel<ff>(const PcholDesc<ff> *, const int2 *, int, int, DevStatus *, cudaStream_t);
+template void launch_pchol_update<ff>(const PcholDesc<ff> *, const int4 *, int, int, cudaStream_t);
+
+// In-place conversion of the lower triangle of every matrix between FP64 and
+// double-float (both 8 bytes per entry); items = (matrix, column).
+__global__ void ff_convert_kernel(const PcholDesc<double> *descs, const int2 *items, int nitems, int to_ff) {
+    int it = blockIdx.x;
+    if (it >= nitems) return;
+    const int2 w = items[it];
+    const PcholDesc<double> d = descs[w.x];
+    const int j = w.y;
+    double *col = d.A + (size_t)j * d.ld;
+    for (int i = j + threadIdx.x; i < d.n; i += blockDim.x) {
+        if (to_ff) {
+            const ff v = ff_from_double(col[i]);
+            reinterpret_cast<ff *>(col)[i] = v;
+        } else {
+            const ff v = reinterpret_cast<const ff *>(col)[i];
+            col[i] = ff_to_double(v);
+        }
+    }
+}
+void launch_ff_convert(const PcholDesc<double> *descs, const int2 *items, int nitems, int to_ff, cudaStream_t s) {
+    if (nitems > 0) ff_convert_kernel<<<nitems, 128, 0, s>>>(descs, items, nitems, to_ff);
+}
+
 template void launch_pchol_panel<double>(const PcholDesc<double> *, const int2 *, int, int, DevStatus *, cudaStream_t);
 template void launch_pchol_panel<float>(const PcholDesc<float> *, const int2 *, int, int, DevStatus *, cudaStream_t);
 template void launch_pchol_update<double>(const PcholDesc<double> *, const int4 *, int, int, cudaStream_t);

@@ -37,9 +37,9 @@ __global__ void ell_build_kernel(const MixedSub *subs, const int2 *items, int ni
         const double v = c < s.nI ? col[c] : 0.0;
         const unsigned m = __ballot_sync(0xffffffffu, v != 0.0);
         const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-        if (v != 0.0 && pos < s.ell_w) {
-            s.ell_col[(size_t)r * s.ell_w + pos] = c;
-            s.ell_val[(size_t)r * s.ell_w + pos] = v;
+        if (v != 0.0 && pos < s.ell_w) {  // entry-major: entry q of row r at q * n + r
+            s.ell_col[(size_t)pos * s.n + r] = c;
+            s.ell_val[(size_t)pos * s.n + r] = v;
         }
         cnt += __popc(m);
     }
@@ -62,11 +62,11 @@ __global__ void ell_residual_kernel(const EllProduct *ps, const int2 *items, int
     const int c = e / p.m, i = e - c * p.m;
     const int r = p.r0 + i;
     const int cnt = p.ell_cnt[r];
-    const int *cols = p.ell_col + (size_t)r * p.ell_w;
-    const double *vals = p.ell_val + (size_t)r * p.ell_w;
+    const int *cols = p.ell_col + r;       // entry-major: consecutive rows are consecutive
+    const double *vals = p.ell_val + r;
     const double *x = p.X + (size_t)c * p.ldx;
     double acc = 0.0;
-    for (int q = 0; q < cnt; ++q) acc += vals[q] * x[cols[q]];
+    for (int q = 0; q < cnt; ++q) acc += vals[(size_t)q * p.ell_n] * x[cols[(size_t)q * p.ell_n]];
     const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
     p.out[(size_t)c * p.ldo + i] = b - acc;
 }

@@ -11,16 +11,16 @@ struct MixedSub {
     int n, nI, ld;
     double *eq;        // (n) equilibration 1/sqrt(A_kk)
     int *ell_cnt;      // (n) entries kept per row
-    int *ell_col;      // (n x ell_w)
-    double *ell_val;   // (n x ell_w)
+    int *ell_col;      // (ell_w x n): entry q of row r at q * n + r
+    double *ell_val;   // (ell_w x n)
     int ell_w;
 };
 
 // out[r, c] = B[r, c] - sum_{interior cols} A[r0 + r, col] X[col, c], r < m, c < ncol
 struct EllProduct {
-    const int *ell_cnt, *ell_col;
+    const int *ell_cnt, *ell_col;   // entry-major: entry q of row r at q * ell_n + r
     const double *ell_val;
-    int ell_w;
+    int ell_w, ell_n;
     int r0, m, ncol;
     const double *X;
     int ldx;
