@@ -238,6 +238,16 @@ BDDC_API bddc_status bddc_get_sizes(const bddc_handle *h, int64_t *n_free, int64
 /* Corner node ids (ascending) into nodes[cap]; *n = count. */
 BDDC_API bddc_status bddc_get_corners(const bddc_handle *h, int64_t *nodes, int cap, int *n);
 
+/* The adaptive constraint rows of face f kept by the last bddc_adapt
+ * (eq. (d-def) restricted to the face dofs, normalised and orthogonalised
+ * with row pivoting; the Remark at the end of Section 3 drops the edge
+ * parts).  gdofs[n_dofs]: the face's global free dofs (ascending); rows:
+ * row-major n_rows x n_dofs, host memory.  With cap_rows * cap_dofs too small
+ * (or NULL buffers) only *n_rows and *n_dofs are set.  Errors: BDDC_ESTATE
+ * (no mesh), BDDC_EINVAL (f out of range). */
+BDDC_API bddc_status bddc_get_face_rows(const bddc_handle *h, int f, int64_t *gdofs, double *rows, int cap_rows,
+                                        int cap_dofs, int *n_rows, int *n_dofs);
+
 /* Face f (0 <= f < n_faces, faces ordered by (i, j), i < j): the pair, the
  * eigenvalues computed by the last bddc_adapt in descending order (the
  * selected ones plus the largest rejected one; at most cap) and the number

@@ -32,6 +32,7 @@
 #include "eig.h"
 #include "ff.cuh"
 #include "host_util.h"
+#include "tc_gemm.h"
 #include "mixed.h"
 #include "pcg.h"
 
@@ -149,7 +150,8 @@ struct bddc_handle {
     bool coarse_fp32 = false;   // the current coarse operators used the FP32 local saddle
     bool interior_fp32 = false; // the current S_i came from the mixed interior elimination
     int interior_fallbacks = 0; // mixed mode: FP32 interior elimination rejected, redone in FP64
-    int coarse_fallbacks = 0;   // mixed mode: FP32 local saddle rejected, rebuilt in FP64
+    int coarse_fallbacks = 0;   // mixed modes: local saddle rejected, rebuilt in FP64
+    bool fp64_class_forced = false;  // mixed mode fallback: FP64-class factorizations in FP64
     float m1_min_pivot = 0.f;
     bool factored = false;      // FP64 mode: A_i factored in place
     int mixed_iters = 0;        // refinement steps the interior elimination needed (mixed mode)
@@ -240,8 +242,13 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const 
             uitems.push_back(make_int4(m, -1, -1, 0));  // copy of the factored diagonal block
             int tn = d.n - kb - nb;
             int nt = (tn + kTile - 1) / kTile;
+            int ct = nt;   // column tiles: all, or those left of d.ncol
+            if (d.ncol > 0) {
+                const int cw = std::min(d.ncol, d.n) - kb - nb;
+                ct = cw > 0 ? (cw + kTile - 1) / kTile : 0;
+            }
             for (int ti = 0; ti < nt; ++ti)
-                for (int tj = 0; tj <= ti; ++tj) uitems.push_back(make_int4(m, ti, tj, 0));
+                for (int tj = 0; tj <= ti && tj < ct; ++tj) uitems.push_back(make_int4(m, ti, tj, 0));
         }
     }
     poff[nsteps] = (int)pitems.size();
@@ -264,7 +271,7 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const 
 // are not touched).
 void run_pchol_fp64class(bddc_handle *h, const std::vector<PcholDesc<double>> &descs, const std::string &tag) {
     if (descs.empty()) return;
-    if (h->opt.precision == BDDC_FP64) {
+    if (h->opt.precision == BDDC_FP64 || h->fp64_class_forced) {
         run_pchol<double>(h, descs, tag);
         return;
     }
@@ -323,6 +330,92 @@ void run_gemv(bddc_handle *h, const std::vector<GemmDesc> &descs, const std::str
     auto *di = h->ar.upload("gv_it_" + tag, items, h->stream);
     launch_gemv(dd, di, (int)items.size(), h->stream);
     check_launch(h);
+}
+
+// Batched 3xTF32 tensor-core GEMMs (tc_gemm.cu): items are the 128 x 128 output tiles
+// (with lower_only, the tiles on or below the diagonal of a square C).
+std::vector<int4> tc_items(const std::vector<TcGemm> &jobs, bool lower_only = false) {
+    std::vector<int4> items;
+    for (int k = 0; k < (int)jobs.size(); ++k) {
+        const auto &g = jobs[k];
+        if (g.M <= 0 || g.N <= 0 || g.K <= 0) continue;
+        const auto aligned = [](const void *p, int ld, int f64) {
+            return ((uintptr_t)p % 16 == 0) && ((size_t)ld * (f64 ? 8 : 4)) % 16 == 0;
+        };
+        BDDC_REQUIRE(aligned(g.A, g.lda, g.a_f64) && aligned(g.B, g.ldb, g.b_f64), BDDC_EINVAL,
+                     "tensor-core GEMM operand rows must be 16-byte aligned");
+        for (int a = 0; a < (g.M + kTcM - 1) / kTcM; ++a)
+            for (int b = 0; b < (g.N + kTcN - 1) / kTcN; ++b)
+                if (!lower_only || b * kTcN <= a * kTcM + kTcM - 1) items.push_back(make_int4(k, a, b, 0));
+    }
+    return items;
+}
+
+void run_tc_gemm(bddc_handle *h, const std::vector<TcGemm> &jobs, const std::string &tag, bool lower_only = false) {
+    std::vector<int4> items = tc_items(jobs, lower_only);
+    if (items.empty()) return;
+    auto *dj = h->ar.upload("tcj_" + tag, jobs, h->stream);
+    auto *di = h->ar.upload("tci_" + tag, items, h->stream);
+    launch_tc_gemm(dj, di, (int)items.size(), h->dst, h->opt.timeout_s, h->stream);
+    check_launch(h);
+}
+
+// FP32 partial Cholesky, left-looking in block columns of 128 with the long
+// updates on the tensor cores (3xTF32, tc_gemm.cu).  For every block column J:
+//   1. A[J:n, J:J+w] -= L[J:n, 0:J] L[J:J+w, 0:J]^T   (tensor cores, K = J),
+//   2. the block column is factored by the right-looking panel kernels with
+//      their updates confined to its w columns,
+//   3. its L is copied, transposed, into the strict upper triangle, so that
+//      row r of L is contiguous there (the K-major operand layout of step 1).
+// After the last block column the trailing block is updated once,
+// A[nstop:n, nstop:n] -= L21 L21^T (lower tiles only).  The strict upper
+// triangle is overwritten: it must not hold anything the caller needs.
+void run_pchol_tc(bddc_handle *h, const std::vector<PcholDesc<float>> &descs, const std::string &tag) {
+    constexpr int W = 128;
+    int nJ = 0;
+    for (const auto &d : descs) nJ = std::max(nJ, (d.nstop + W - 1) / W);
+    for (int jb = 0; jb < nJ; ++jb) {
+        const int J = jb * W;
+        const std::string t = tag + "_" + std::to_string(jb);
+        std::vector<TcGemm> upd;
+        std::vector<PcholDesc<float>> pv;
+        std::vector<TransposeOp> tr;
+        std::vector<int4> titems;
+        for (const auto &d : descs) {
+            if (J >= d.nstop) continue;
+            const int w = std::min(W, d.nstop - J);
+            float *F = d.A;
+            const size_t ld = (size_t)d.ld;
+            if (J > 0)
+                upd.push_back(TcGemm{F + J * ld, F + J * ld, F + J * ld + J, nullptr, nullptr, d.ld, d.ld, d.ld,
+                                     d.n - J, w, J, 0, 0, -1.0, 1});
+            PcholDesc<float> v{F + J * ld + J, d.n - J, d.ld, w, 0, nullptr, w};
+            pv.push_back(v);
+            if (J + w < d.n) {   // upper (J + p, J + w + q) <- lower (J + w + q, J + p)
+                const int k = (int)tr.size(), nc = d.n - J - w;
+                tr.push_back(TransposeOp{F, d.ld, J, J + w, w, nc});
+                for (int a = 0; a < (w + 31) / 32; ++a)
+                    for (int b = 0; b < (nc + 31) / 32; ++b) titems.push_back(make_int4(k, a, b, 0));
+            }
+        }
+        run_tc_gemm(h, upd, t);
+        run_pchol<float>(h, pv, tag);
+        if (!titems.empty()) {
+            auto *dto = h->ar.upload("tr_o_" + t, tr, h->stream);
+            auto *dti = h->ar.upload("tr_i_" + t, titems, h->stream);
+            launch_transpose_block(dto, dti, (int)titems.size(), h->stream);
+            check_launch(h);
+        }
+    }
+    std::vector<TcGemm> trail;
+    for (const auto &d : descs) {
+        if (d.nstop <= 0 || d.nstop >= d.n) continue;
+        float *F = d.A;
+        const size_t ld = (size_t)d.ld, k = (size_t)d.nstop;
+        trail.push_back(TcGemm{F + k * ld, F + k * ld, F + k * ld + k, nullptr, nullptr, d.ld, d.ld, d.ld,
+                               d.n - d.nstop, d.n - d.nstop, d.nstop, 0, 0, -1.0, 1});
+    }
+    run_tc_gemm(h, trail, tag + "_trail", true);
 }
 
 void zero(bddc_handle *h, double *p, size_t n) {
@@ -1359,7 +1452,12 @@ void alloc_solver_buffers(bddc_handle *h) {
         nGi[s] = h->subs[s].nG;
         ldS[s] = h->subs[s].ldS;
         RG.insert(RG.end(), h->subs[s].RG.begin(), h->subs[s].RG.end());
-        for (int r = 0; r < nGi[s]; r += 32) rb.push_back(make_int2(s, r));
+        for (int r = 0; r < nGi[s]; r += 64) rb.push_back(make_int2(s, r));
+    }
+    {   // S_i and P~_i together larger than about 3/4 of L2 (126 MB): stream them
+        size_t bytes = 0;
+        for (int s = 0; s < ns; ++s) bytes += 2 * sizeof(double) * (size_t)ldS[s] * nGi[s];
+        h->ops.stream_mats = bytes > ((size_t)96 << 20) ? 1 : 0;
     }
     h->ops.nGi = h->ar.upload("nGi", nGi, h->stream);
     h->ops.ldS = h->ar.upload("ldS", ldS, h->stream);
@@ -1452,7 +1550,7 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     if (jobs.empty()) return 0;
     std::vector<EllProduct> ps;
     std::vector<MixedUpdate> us, us0;
-    std::vector<int4> uitems;
+    std::vector<TcGemm> tg, tg0;
     std::vector<int2> vitems;
     ZeroList zx;
     for (int k = 0; k < (int)jobs.size(); ++k) {
@@ -1478,20 +1576,29 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
         if (j.ncol == 1) {
             for (int a = 0; a < (sd.nI + 7) / 8; ++a) vitems.push_back(make_int2(k, a));
         } else {
-            for (int a = 0; a < (sd.nI + 63) / 64; ++a)
-                for (int b = 0; b < (j.ncol + 63) / 64; ++b) uitems.push_back(make_int4(k, a, b, 0));
+            // X[r, c] += d[r] sum_k K_s[r, k] d[k] R[k, c]: rows of the symmetric K_s are its columns
+            tg.push_back(TcGemm{K, j.R, j.X, eq, eq, ldk, j.ldr, j.ldx, sd.nI, j.ncol, sd.nI, 0, 1, 1.0});
+            tg0.push_back(TcGemm{K, j.B, j.X, eq, eq, ldk, j.ldb, j.ldx, sd.nI, j.ncol, sd.nI, 0, 1, 1.0});
         }
         zx.add(j.X, (size_t)j.ldx * j.ncol);
     }
     zero_all(h, zx, "X_" + tag);
     auto *dus = h->ar.upload("mu_" + tag, us, h->stream);
     auto *dus0 = h->ar.upload("mu0_" + tag, us0, h->stream);
-    auto *dui = h->ar.upload("mui_" + tag, uitems, h->stream);
     auto *dvi = h->ar.upload("mvi_" + tag, vitems, h->stream);
-    auto update = [&](const MixedUpdate *d) {
-        launch_mixed_update(d, dui, (int)uitems.size(), h->stream);
-        launch_mixed_update_vec(d, dvi, (int)vitems.size(), h->stream);
-        check_launch(h);
+    const std::vector<int4> titems = tc_items(tg);
+    auto *dtg = h->ar.upload("mtg_" + tag, tg, h->stream);
+    auto *dtg0 = h->ar.upload("mtg0_" + tag, tg0, h->stream);
+    auto *dti = h->ar.upload("mti_" + tag, titems, h->stream);
+    auto update = [&](const MixedUpdate *d, const TcGemm *t) {
+        if (!titems.empty()) {
+            launch_tc_gemm(t, dti, (int)titems.size(), h->dst, h->opt.timeout_s, h->stream);
+            check_launch(h);
+        }
+        if (!vitems.empty()) {
+            launch_mixed_update_vec(d, dvi, (int)vitems.size(), h->stream);
+            check_launch(h);
+        }
     };
     auto *dps = h->ar.upload("mps_" + tag, ps, h->stream);
     double *norms = h->ar.get_t<double>("rnorm_" + tag, 2 * jobs.size());
@@ -1500,7 +1607,7 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     for (size_t k = 0; k < jobs.size(); ++k) col_off[k + 1] = col_off[k] + jobs[k].ncol;
     int *dcol_off = h->ar.upload("rn_off_" + tag, col_off, h->stream);
     double *colsums = h->ar.get_t<double>("rn_cols_" + tag, 2 * (size_t)std::max(col_off.back(), 1));
-    update(dus0);
+    update(dus0, dtg0);
     int done = 1;
     for (;;) {
         if (!check && done >= corrections) break;
@@ -1519,7 +1626,7 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
                          "mixed-precision refinement of the interior solves did not converge (relative residual " +
                              std::to_string(worst) + "); use BDDC_FP64");
         }
-        update(dus);
+        update(dus, dtg);
         ++done;
     }
     return done;
@@ -1603,19 +1710,13 @@ void interior_mixed(bddc_handle *h) {
         ps.push_back(p);
     }
     run_ell(h, ps, "S");
-    std::vector<GramCorrect> gc;
-    std::vector<int4> gitems;
+    // S[a, b] -= sum_k X[k, a] R[k, b]  (3xTF32 tensor-core products; the term is second order)
+    std::vector<TcGemm> gc;
     for (const auto &j : jobs) {
         auto &sd = h->subs[j.s];
-        const int k = (int)gc.size();
-        gc.push_back(GramCorrect{j.X, j.ldx, j.R, j.ldr, sd.S, sd.ldS, sd.nI, sd.nG});
-        for (int a = 0; a < (sd.nG + 63) / 64; ++a)
-            for (int b = 0; b < (sd.nG + 63) / 64; ++b) gitems.push_back(make_int4(k, a, b, 0));
+        gc.push_back(TcGemm{j.X, j.R, sd.S, nullptr, nullptr, j.ldx, j.ldr, sd.ldS, sd.nG, sd.nG, sd.nI, 1, 1, -1.0});
     }
-    auto *dgc = h->ar.upload("gc", gc, h->stream);
-    auto *dgi = h->ar.upload("gci", gitems, h->stream);
-    launch_gram_correct(dgc, dgi, (int)gitems.size(), h->stream);
-    check_launch(h);
+    run_tc_gemm(h, gc, "gc");
     launch_symmetrize(h->ops.S, h->ops.nGi, h->ops.ldS, ns, h->stream);
     check_launch(h);
 }
@@ -1640,6 +1741,24 @@ void ensure_coarse(bddc_handle *h) {
             reset_status(h);
             h->coarse_fallbacks++;
             coarse_setup(h, false);
+        }
+    } else if (h->opt.precision == BDDC_MIXED) {
+        // the local saddle runs in double-float; a coarse matrix that does not factor
+        // in that precision is rebuilt with FP64 local saddles
+        try {
+            coarse_setup(h, false);
+        } catch (const Error &e) {
+            if (e.status != BDDC_ENOTSPD) throw;
+            reset_status(h);
+            h->coarse_fallbacks++;
+            h->fp64_class_forced = true;
+            try {
+                coarse_setup(h, false);
+            } catch (const Error &e2) {
+                h->fp64_class_forced = false;
+                throw Error{e2.status, e2.msg + " (after an FP64 rebuild of the local saddle operators)"};
+            }
+            h->fp64_class_forced = false;
         }
     } else {
         coarse_setup(h, false);
@@ -2813,6 +2932,32 @@ bddc_status bddc_get_face_eigs(const bddc_handle *h, int f, int32_t *i, int32_t 
     if (n_selected) *n_selected = fp.nsel;
     if (n_kept) *n_kept = fp.nkept;
     for (int k = 0; k < (int)fp.lam.size() && k < cap; ++k) lam[k] = fp.lam[k];
+    return BDDC_OK;
+}
+
+bddc_status bddc_get_face_rows(const bddc_handle *h, int f, int64_t *gdofs, double *rows, int cap_rows,
+                               int cap_dofs, int *n_rows, int *n_dofs) {
+    if (!h || !h->have_mesh) return BDDC_ESTATE;
+    if (f < 0 || f >= (int)h->faces.size()) return BDDC_EINVAL;
+    const auto &fp = h->faces[f];
+    const int nd = (int)fp.face_idx.size();
+    const int nr = (f < (int)h->face_rows_dev.size() && h->face_rows_dev[f]) ? fp.nkept : 0;
+    if (n_rows) *n_rows = nr;
+    if (n_dofs) *n_dofs = nd;
+    if (!gdofs || !rows || cap_rows < nr || cap_dofs < nd) return BDDC_OK;
+    try {
+        for (int k = 0; k < nd; ++k) gdofs[k] = fp.s_g[fp.face_idx[k]];
+        if (nr == 0) return BDDC_OK;
+        std::vector<double> T((size_t)nr * nd);   // column-major nr x nd on the device
+        BDDC_CUDA(cudaMemcpyAsync(T.data(), h->face_rows_dev[f], T.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                  h->stream));
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        for (int l = 0; l < nr; ++l)
+            for (int k = 0; k < nd; ++k) rows[(size_t)l * nd + k] = T[(size_t)k * nr + l];
+    } catch (const Error &e) {
+        const_cast<bddc_handle *>(h)->err = e.msg;
+        return (bddc_status)e.status;
+    }
     return BDDC_OK;
 }
 

@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(256) pchol_update_kernel(const PcholDesc<T> *d
     }
     const int t0 = kb + nb;
     const int i0 = t0 + w.y * TILE, j0 = t0 + w.z * TILE;
+    const int cend = d.ncol > 0 ? min(d.ncol, n) : n;
     T *A = d.A;
     __shared__ T Pa[NB][TILE + 1];
     __shared__ T Pb[NB][TILE + 1];
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(256) pchol_update_kernel(const PcholDesc<T> *d
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         int c = j0 + ty + 16 * b;
-        if (c >= n) continue;
+        if (c >= cend) continue;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             int r = i0 + tx + 16 * a;
@@ -183,6 +184,28 @@ __global__ void __launch_bounds__(256) pchol_update_kernel(const PcholDesc<T> *d
                     A[(size_t)c * ld + r] -= acc[a][b];
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// mirrored block copy through a 32 x 33 shared tile: reads along the source
+// columns and writes along the destination columns, both coalesced.
+__global__ void transpose_block_kernel(const TransposeOp *ops, const int4 *items, int nitems) {
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const int4 w = items[it];
+    const TransposeOp o = ops[w.x];
+    const int p0 = w.y * 32, q0 = w.z * 32;
+    __shared__ float t[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 8 rows of 32
+    for (int j = ty; j < 32; j += 8) {
+        const int p = p0 + j, q = q0 + tx;
+        if (p < o.nr && q < o.nc) t[j][tx] = o.A[(size_t)(o.r0 + p) * o.ld + o.c0 + q];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int q = q0 + j, p = p0 + tx;
+        if (p < o.nr && q < o.nc) o.A[(size_t)(o.c0 + q) * o.ld + o.r0 + p] = t[tx][j];
     }
 }
 
@@ -508,6 +531,9 @@ template void launch_pchol_update<float>(const PcholDesc<float> *, const int4 *,
 
 void launch_gather(const GatherOp *ops, const int2 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) gather_kernel<<<nitems, 256, 0, s>>>(ops, items, nitems);
+}
+void launch_transpose_block(const TransposeOp *ops, const int4 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) transpose_block_kernel<<<nitems, 256, 0, s>>>(ops, items, nitems);
 }
 void launch_diag_set(const DiagOp *ops, int nops, cudaStream_t s) {
     if (nops > 0) diag_set_kernel<<<nops, 256, 0, s>>>(ops, nops);

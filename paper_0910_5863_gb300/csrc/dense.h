@@ -15,6 +15,7 @@ struct PcholDesc {
     int nstop;
     int tag;    // batch tag reported with a failed pivot (item = tag * 100000 + matrix)
     T *diag;    // NB x NB scratch: the factored diagonal block of the current step
+    int ncol;   // > 0: the trailing updates stop at column ncol (a block-column panel)
 };
 
 // dst[p + dst_row_off, q + dst_col_off] (+)= scale * rscale[p] * cscale[q] * src(rmap[p], cmap[q])
@@ -36,6 +37,15 @@ struct GatherOp {
     int src_f32;          // src points to float
     int dst_f32;          // dst points to float
     int pad;
+};
+
+// A[r0 + p, c0 + q] = A[c0 + q, r0 + p] for p < nr, q < nc (FP32, column-major):
+// copies a block of one triangle into the mirrored block of the other
+struct TransposeOp {
+    float *A;
+    int ld;
+    int r0, c0;
+    int nr, nc;
 };
 
 struct DiagOp {
@@ -75,6 +85,8 @@ void launch_pchol_update(const PcholDesc<T> *descs, const int4 *items, int nitem
 void launch_ff_convert(const PcholDesc<double> *descs, const int2 *items, int nitems, int to_ff, cudaStream_t s);
 void launch_gather(const GatherOp *ops, const int2 *items, int nitems, cudaStream_t s);
 void launch_diag_set(const DiagOp *ops, int nops, cudaStream_t s);
+// items: (op, 32-row tile, 32-column tile)
+void launch_transpose_block(const TransposeOp *ops, const int4 *items, int nitems, cudaStream_t s);
 void launch_zero(double *p, size_t n, cudaStream_t s);
 // zero many buffers in one launch; items = (segment, 8192-element chunk)
 void launch_zero_many(double *const *ptrs, const int64_t *sizes, const int2 *items, int nitems, cudaStream_t s);

@@ -317,11 +317,12 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
         const double pn = sh_val[0];
         if (first < 0) first = pn;
         if (!(pn > drop_rel * first) || pn == 0.0) break;
-        // swap rows best <-> step, normalise
+        // swap rows best <-> step and normalise (the normalised row is written last, so
+        // best == step also leaves a unit row)
         for (int f = tid; f < nf; f += nt) {
             double a = R[(size_t)best * nf + f], b = R[(size_t)step * nf + f];
-            R[(size_t)step * nf + f] = a / pn;
             R[(size_t)best * nf + f] = b;
+            R[(size_t)step * nf + f] = a / pn;
         }
         __syncthreads();
         for (int l = step + 1 + wid; l < nsel; l += nw) {

@@ -4,8 +4,8 @@
 //   1. an FP32 partial Cholesky of [[D A_II D, .], [I, 0]] leaves -(D A_II D)^-1
 //      in its trailing block (the explicit FP32 inverse K_s);
 //   2. X = A_II^-1 A_IG is refined in FP64:  R = A_IG - A_II X  (FP64, the
-//      sparse interior columns of A_i in ELL form),  X += D K_s D R  (FP32
-//      product, FP64 accumulation of X);
+//      sparse interior columns of A_i in ELL form),  X += D K_s D R  (3xTF32
+//      tensor-core product, tc_gemm.cu; FP64 accumulation of X);
 //   3. S_i = A_GG - A_GI X  in FP64 (the same sparse product over the
 //      interface rows) -- the Schur complement of Section 2 of the paper.
 // The same refinement solves A_II y = f_I for the condensed right-hand side
@@ -71,59 +71,6 @@ __global__ void ell_residual_kernel(const EllProduct *ps, const int2 *items, int
     p.out[(size_t)c * p.ldo + i] = b - acc;
 }
 
-// X[r, c] += d[r] * sum_k K[r, k] * float(d[k] R[k, c])   (64 x 64 tiles, k-step 32, FP32 products)
-__global__ void __launch_bounds__(256) mixed_update_kernel(const MixedUpdate *us, const int4 *items, int nitems) {
-    const int it = blockIdx.x;
-    if (it >= nitems) return;
-    const int4 w = items[it];
-    const MixedUpdate u = us[w.x];
-    const int m0 = w.y * 64, n0 = w.z * 64;
-    __shared__ float Ks[32][65];
-    __shared__ float Rs[32][65];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < u.n; k0 += 32) {
-        for (int e = tid; e < 32 * 64; e += 256) {
-            const int rr = e % 64, kk = e / 64;
-            // K[m0 + rr, k0 + kk], column-major (contiguous in rr)
-            float kv = 0.f;
-            if (m0 + rr < u.n && k0 + kk < u.n) kv = u.K[(size_t)(k0 + kk) * u.ldk + m0 + rr];
-            Ks[kk][rr] = kv;
-        }
-        for (int e = tid; e < 32 * 64; e += 256) {
-            const int kk = e % 32, cc = e / 32;
-            float rv = 0.f;
-            if (k0 + kk < u.n && n0 + cc < u.ncol)
-                rv = (float)(u.d[k0 + kk] * u.R[(size_t)(n0 + cc) * u.ldr + k0 + kk]);
-            Rs[kk][cc] = rv;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < 32; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = Ks[kk][tx + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Rs[kk][ty + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int c = n0 + ty + 16 * j;
-        if (c >= u.ncol) continue;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = m0 + tx + 16 * i;
-            if (r < u.n) u.X[(size_t)c * u.ldx + r] += u.d[r] * (double)acc[i][j];
-        }
-    }
-}
-
 // single right-hand side: x[r] += d[r] sum_k K[r, k] float(d[k] r[k]); one warp per row
 // (K is symmetric, so row r is read as column r).  items: (update, block of 8 rows)
 __global__ void mixed_update_vec_kernel(const MixedUpdate *us, const int2 *items, int nitems) {
@@ -138,57 +85,6 @@ __global__ void mixed_update_vec_kernel(const MixedUpdate *us, const int2 *items
     for (int k = lane; k < u.n; k += 32) acc += kr[k] * (float)(u.d[k] * u.R[k]);
     acc = warp_sum(acc);
     if (lane == 0) u.X[r] += u.d[r] * (double)acc;
-}
-
-// S[i, j] -= sum_k X[k, i] R[k, j]  (i, j < m, k < n): the energy correction of the
-// Schur complement, S(X) = A_GG - A_GI X - X^T (A_IG - A_II X) = S + E^T A_II E for
-// X = A_II^-1 A_IG + E.  The term is small, so FP32 products suffice.
-__global__ void __launch_bounds__(256) gram_correct_kernel(const GramCorrect *gs, const int4 *items, int nitems) {
-    const int it = blockIdx.x;
-    if (it >= nitems) return;
-    const int4 w = items[it];
-    const GramCorrect g = gs[w.x];
-    const int i0 = w.y * 64, j0 = w.z * 64;
-    __shared__ float Xs[32][65];
-    __shared__ float Rs[32][65];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < g.n; k0 += 32) {
-        for (int e = tid; e < 32 * 64; e += 256) {
-            const int kk = e % 32, cc = e / 32;
-            float xv = 0.f, rv = 0.f;
-            if (k0 + kk < g.n) {
-                if (i0 + cc < g.m) xv = (float)g.X[(size_t)(i0 + cc) * g.ldx + k0 + kk];
-                if (j0 + cc < g.m) rv = (float)g.R[(size_t)(j0 + cc) * g.ldr + k0 + kk];
-            }
-            Xs[kk][cc] = xv;
-            Rs[kk][cc] = rv;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < 32; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = Xs[kk][tx + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Rs[kk][ty + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int c = j0 + ty + 16 * j;
-        if (c >= g.m) continue;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = i0 + tx + 16 * i;
-            if (r < g.m) g.S[(size_t)c * g.lds + r] -= (double)acc[i][j];
-        }
-    }
 }
 
 // per product: sums of R^2 and B^2 (for the refinement check).  Blocks =
@@ -253,14 +149,8 @@ void launch_ell_build(const MixedSub *subs, const int2 *items, int nitems, DevSt
 void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) ell_residual_kernel<<<nitems, 256, 0, s>>>(ps, items, nitems);
 }
-void launch_mixed_update(const MixedUpdate *us, const int4 *items, int nitems, cudaStream_t s) {
-    if (nitems > 0) mixed_update_kernel<<<nitems, 256, 0, s>>>(us, items, nitems);
-}
 void launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) mixed_update_vec_kernel<<<nitems, 256, 0, s>>>(us, items, nitems);
-}
-void launch_gram_correct(const GramCorrect *gs, const int4 *items, int nitems, cudaStream_t s) {
-    if (nitems > 0) gram_correct_kernel<<<nitems, 256, 0, s>>>(gs, items, nitems);
 }
 void launch_residual_norms(const EllProduct *ps, int np, double *colsums, const int *col_off, double *out,
                            cudaStream_t s) {

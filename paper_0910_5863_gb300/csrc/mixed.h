@@ -45,26 +45,11 @@ struct MixedUpdate {
 // ncol == 1 variant; items: (update, block of 8 rows)
 void launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, cudaStream_t s);
 
-// S[i, j] -= sum_k X[k, i] R[k, j], i, j < m, k < n
-struct GramCorrect {
-    const double *X;
-    int ldx;
-    const double *R;
-    int ldr;
-    double *S;
-    int lds;
-    int n, m;
-};
-
 void launch_equilibrate(const MixedSub *subs, int nsub, cudaStream_t s);
 // items: (sub, row), one warp each
 void launch_ell_build(const MixedSub *subs, const int2 *items, int nitems, DevStatus *st, cudaStream_t s);
 // items: (product, block of 256 (r, c) pairs)
 void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cudaStream_t s);
-// items: (update, 64-row tile, 64-column tile)
-void launch_mixed_update(const MixedUpdate *us, const int4 *items, int nitems, cudaStream_t s);
-// items: (correction, 64-row tile, 64-column tile)
-void launch_gram_correct(const GramCorrect *gs, const int4 *items, int nitems, cudaStream_t s);
 // out[2k] = |R_k|^2, out[2k+1] = |B_k|^2; colsums holds 2 doubles per column of all products,
 // col_off (np + 1) the first column of each product
 void launch_residual_norms(const EllProduct *ps, int np, double *colsums, const int *col_off, double *out,

@@ -36,14 +36,24 @@ struct PcgParams {
     uint64_t timeout_ns;
 };
 
-// y_i = Mats_i * v_i for every (substructure, 32-row block); v_i = R_i v is
+// y_i = Mats_i * v_i for every (substructure, 64-row block); v_i = R_i v is
 // staged in shared memory once per substructure, then the warps split the
-// columns and the lanes the rows (coalesced column reads).
+// columns and every lane reads two consecutive rows of a column with one
+// 16-byte load (512 coalesced bytes per warp and column).  Eight columns per
+// warp are loaded before they are used, so 64 KB per SM are in flight: the
+// matrices are streamed from HBM once per application.  When they do not fit
+// in L2 they are read with the evict-first policy, which keeps the vectors and
+// the coarse data resident.
 // If pold != nullptr, v[g] = z[g] + beta * pold[g] (the new search direction).
+__device__ __forceinline__ double2 ld_mat2(const double *p, bool stream) {
+    return stream ? __ldcs(reinterpret_cast<const double2 *>(p)) : __ldg(reinterpret_cast<const double2 *>(p));
+}
+
 __device__ void local_gemv(const PcgParams &P, double *const *Mats, const double *vin, const double *pold,
                            double beta, double *yout, double *red, double *vs) {
     const IfaceOps &o = P.o;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool stream = o.stream_mats != 0;
     int cur = -1;
     for (int it = blockIdx.x; it < o.nrowblk; it += gridDim.x) {
         int2 w = o.rowblk[it];
@@ -60,18 +70,35 @@ __device__ void local_gemv(const PcgParams &P, double *const *Mats, const double
             cur = s;
         }
         const double *A = Mats[s];
-        const int r = r0 + lane;
-        double acc = 0.0;
-        if (r < n) {
-#pragma unroll 4
-            for (int c = wid; c < n; c += PCG_WARPS) acc += A[(size_t)c * ld + r] * vs[c];
+        const int r = r0 + 2 * lane;   // ld is even, so A + c * ld + r is 16-byte aligned
+        double a0 = 0.0, a1 = 0.0;
+        if (r < n) {   // rows r + 1 < ld stay inside the allocation; a row r + 1 >= n is ignored
+            int c = wid;
+            for (; c + 7 * PCG_WARPS < n; c += 8 * PCG_WARPS) {
+                double2 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = ld_mat2(A + (size_t)(c + u * PCG_WARPS) * ld + r, stream);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const double x = vs[c + u * PCG_WARPS];
+                    a0 += v[u].x * x;
+                    a1 += v[u].y * x;
+                }
+            }
+            for (; c < n; c += PCG_WARPS) {
+                const double2 v = ld_mat2(A + (size_t)c * ld + r, stream);
+                const double x = vs[c];
+                a0 += v.x * x;
+                a1 += v.y * x;
+            }
         }
-        red[wid * 32 + lane] = acc;
+        red[wid * 64 + 2 * lane] = a0;
+        red[wid * 64 + 2 * lane + 1] = a1;
         __syncthreads();
-        if (threadIdx.x < 32) {
+        if (threadIdx.x < 64) {
             double sum = 0.0;
 #pragma unroll
-            for (int k = 0; k < PCG_WARPS; ++k) sum += red[k * 32 + threadIdx.x];
+            for (int k = 0; k < PCG_WARPS; ++k) sum += red[k * 64 + threadIdx.x];
             if (r0 + threadIdx.x < n) yout[o.off[s] + r0 + threadIdx.x] = sum;
         }
         __syncthreads();
@@ -149,8 +176,8 @@ __device__ double reduce_partials(const double *partial, int nb) {
 
 __global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(PcgParams P) {
     extern __shared__ double smem[];
-    double *red = smem;                    // PCG_WARPS * 32
-    double *rc = smem + PCG_WARPS * 32;    // nC (coarse phase) ...
+    double *red = smem;                    // PCG_WARPS * 64
+    double *rc = smem + PCG_WARPS * 64;    // nC (coarse phase) ...
     double *vs = rc;                       // ... or max nGi (local products)
     __shared__ double scratch[32];
     const IfaceOps &o = P.o;
@@ -266,7 +293,7 @@ cudaError_t launch_pcg(const IfaceOps &ops, const PcgBuffers &buf, int mode, dou
     P.maxit = maxit;
     P.st = st;
     P.timeout_ns = (uint64_t)(timeout_s * 1e9);
-    size_t smem = sizeof(double) * (PCG_WARPS * 32 + (size_t)std::max(std::max(ops.nC, ops.maxGi), 1));
+    size_t smem = sizeof(double) * (PCG_WARPS * 64 + (size_t)std::max(std::max(ops.nC, ops.maxGi), 1));
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

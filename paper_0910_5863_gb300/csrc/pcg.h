@@ -29,8 +29,9 @@ struct IfaceOps {
     const int *gsub;         // substructure of each entry
     const int *cptr;         // (nC+1)
     const int64_t *cent;     // packed local coarse index of each entry
-    const int2 *rowblk;      // (sub, first row) GEMV work items, 32 rows each
+    const int2 *rowblk;      // (sub, first row) GEMV work items, 64 rows each
     int nrowblk;
+    int stream_mats;         // S_i and P~_i exceed L2: read them with the evict-first policy
     const int2 *cdot;        // (sub, first coarse column) items, 16 columns each
     int ncdot;
 };

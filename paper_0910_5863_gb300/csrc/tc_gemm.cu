@@ -1,0 +1,320 @@
+// Batched GEMM on the fifth-generation tensor cores (tcgen05, kind::tf32) with
+// the three-term TF32 split ("3xTF32"):
+//     x = x_hi + x_lo,  x_hi = tf32(x),  x_lo = tf32(x - x_hi),
+//     a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi          (relative error ~ 2^-21),
+// accumulated in FP32 in tensor memory.  It carries the FP32-class products of
+// the mixed-precision interior elimination (the refinement corrections
+// X += D K_s D R and the energy correction S -= X^T R of the Schur complement
+// of Section 2 of the paper), where FP32 accuracy is what the FP64 refinement
+// needs and TF32 alone (2^-11) would stall it.
+//
+// One CTA per 128 x 128 output tile of one batch item:
+//   * 256 threads load 128 x 32 slabs of A and B from global memory (FP32 or
+//     FP64, K contiguous), split them and store hi / lo parts into shared
+//     memory in the K-major 128-byte-swizzled layout (rows of 32 TF32 values =
+//     128 bytes, 8-row atoms of 1024 bytes, 16-byte chunk c of row r stored at
+//     chunk c ^ (r mod 8));
+//   * one thread issues tcgen05.mma (M = 128, N = 128, K = 8 per instruction,
+//     4 x 3 instructions per slab) into a 128-column TMEM accumulator and
+//     commits them to the slab's mbarrier; two slab buffers alternate, so the
+//     loads of slab k+1 overlap the MMAs of slab k;
+//   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+//     lanes 32 (w mod 4) .. + 31, i.e. those output rows) and adds
+//     alpha * cscale[m] * acc into the FP64 (or FP32) output with coalesced
+//     stores.
+// Every mbarrier wait is bounded; on a timeout the CTA records
+// BDDC_DEV_ERR_TIMEOUT, waits (bounded) for its issued MMAs, frees its TMEM and
+// returns.
+#include "common.cuh"
+#include "tc_gemm.h"
+
+namespace bddc {
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int TC_KB = 32;                     // K per slab: 32 x 4 bytes = one 128-byte swizzle row
+constexpr int TC_TILE_BYTES = 128 * 128;      // 128 rows x 128 bytes
+constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;   // A_hi, A_lo, B_hi, B_lo
+constexpr int TC_STAGES = 2;
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;   // + alignment slack
+constexpr uint32_t TC_TMEM_COLS = 128;
+
+// instruction descriptor of tcgen05.mma kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9 = bits 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// shared-memory matrix descriptor, K-major with 128-byte swizzling: start address >> 4
+// (bits 0-13), leading byte offset (unused by swizzled K-major layouts; 16 bytes) at
+// bits 16-29, stride byte offset 1024 >> 4 (8-row atoms) at bits 32-45, descriptor
+// version 1 at bits 46-47, swizzle mode 2 (128 bytes) at bits 61-63
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the completion of the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t deadline) {
+    unsigned spins = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if ((++spins & 1023u) == 0 && globaltimer_ns() > deadline) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 32 consecutive TMEM columns of this thread's lane
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// round to the nearest TF32 value (10 stored mantissa bits; ties away from zero)
+__device__ __forceinline__ float tf32_round(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// four consecutive k values of row `row` (zero outside [0, nrows) x [0, K))
+__device__ __forceinline__ void load4(const void *base, int ld, int f64, int row, int nrows, int k, int K,
+                                      const double *kscale, float (&out)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = 0.f;
+    if (row >= nrows || k >= K) return;
+    if (f64) {
+        const double *p = static_cast<const double *>(base) + (size_t)row * ld + k;
+        double d[4];
+        if (k + 4 <= K) {
+            const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+            const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+            d[0] = a.x, d[1] = a.y, d[2] = b.x, d[3] = b.y;
+            if (kscale) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) d[i] *= __ldg(kscale + k + i);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d[i] = (k + i < K) ? __ldg(p + i) * (kscale ? __ldg(kscale + k + i) : 1.0) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[i] = (float)d[i];
+    } else {
+        const float *p = static_cast<const float *>(base) + (size_t)row * ld + k;
+        if (k + 4 <= K) {
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+            out[0] = a.x, out[1] = a.y, out[2] = a.z, out[3] = a.w;
+            if (kscale) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) out[i] = (float)((double)out[i] * __ldg(kscale + k + i));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                out[i] = (k + i < K) ? (float)((double)__ldg(p + i) * (kscale ? __ldg(kscale + k + i) : 1.0)) : 0.f;
+        }
+    }
+}
+
+// split four values into TF32 hi / lo parts and store them at the swizzled chunk
+__device__ __forceinline__ void store_split(uint8_t *hi_tile, uint8_t *lo_tile, int r, int c, const float (&v)[4]) {
+    float4 h, l;
+    float hv[4], lv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        hv[i] = tf32_round(v[i]);
+        lv[i] = tf32_round(v[i] - hv[i]);
+    }
+    h = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    l = make_float4(lv[0], lv[1], lv[2], lv[3]);
+    const int off = r * 128 + ((c ^ (r & 7)) << 4);
+    *reinterpret_cast<float4 *>(hi_tile + off) = h;
+    *reinterpret_cast<float4 *>(lo_tile + off) = l;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const TcGemm *jobs, const int4 *items, int nitems, DevStatus *st, uint64_t timeout_ns) {
+    extern __shared__ uint8_t tc_smem_raw[];
+    __shared__ uint64_t bars[TC_STAGES];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const int4 w = items[it];
+    const TcGemm g = jobs[w.x];
+    const int m0 = w.y * kTcM, n0 = w.z * kTcN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const uint32_t raw = smem_u32(tc_smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t *tiles = tc_smem_raw + (sbase - raw);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        failed = 0;
+        for (int s = 0; s < TC_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint64_t deadline = globaltimer_ns() + timeout_ns;
+    const uint32_t idesc = tc_idesc(kTcM, kTcN);
+
+    const int nkb = (g.K + TC_KB - 1) / TC_KB;
+    // this thread's chunks: chunk c = tid % 8 (4 k values) of rows tid / 8 + 32 j
+    const int c = tid & 7, rbase = tid >> 3;
+    bool ok = true;
+    int issued = -1;   // last slab whose MMAs were committed (uniform over the block)
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb & 1;
+        const int k = kb * TC_KB + 4 * c;
+        float va[4][4], vb[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            load4(g.A, g.lda, g.a_f64, m0 + rbase + 32 * j, g.M, k, g.K, nullptr, va[j]);
+            load4(g.B, g.ldb, g.b_f64, n0 + rbase + 32 * j, g.N, k, g.K, g.bscale, vb[j]);
+        }
+        // the slab buffer is free once the MMAs of slab kb - 2 have completed
+        if (kb >= TC_STAGES && !mbar_wait(smem_u32(&bars[s]), (uint32_t)(((kb - TC_STAGES) / TC_STAGES) & 1),
+                                          deadline)) {
+            ok = false;
+        }
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            break;
+        }
+        uint8_t *stage = tiles + s * TC_STAGE_BYTES;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = rbase + 32 * j;
+            store_split(stage, stage + TC_TILE_BYTES, r, c, va[j]);
+            store_split(stage + 2 * TC_TILE_BYTES, stage + 3 * TC_TILE_BYTES, r, c, vb[j]);
+        }
+        // make the generic-proxy stores visible to the tensor cores (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a_hi = smem_u32(stage), a_lo = a_hi + TC_TILE_BYTES;
+            const uint32_t b_hi = a_hi + 2 * TC_TILE_BYTES, b_lo = a_hi + 3 * TC_TILE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_KB / 8; ++kk) {
+                const uint32_t koff = kk * 32;   // 8 TF32 values = 32 bytes along the swizzled row
+                tc_mma(tmem, tc_sdesc(a_lo + koff), tc_sdesc(b_hi + koff), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                tc_mma(tmem, tc_sdesc(a_hi + koff), tc_sdesc(b_lo + koff), idesc, 1u);
+                tc_mma(tmem, tc_sdesc(a_hi + koff), tc_sdesc(b_hi + koff), idesc, 1u);
+            }
+            tc_commit(smem_u32(&bars[s]));
+        }
+        issued = kb;
+    }
+    // the last commit covers every MMA issued before it (after a timeout: wait again, bounded)
+    if (issued >= 0) {
+        const uint64_t dl = ok ? deadline : globaltimer_ns() + timeout_ns;
+        if (!mbar_wait(smem_u32(&bars[issued & 1]), (uint32_t)((issued / TC_STAGES) & 1), dl)) ok = false;
+    }
+    if (!ok && lane == 0) atomicExch(&failed, 1);
+    __syncthreads();
+    tc_fence_after();
+    if (!failed && nkb > 0) {
+        const int q = warp & 3, half = warp >> 2;
+        const int m = m0 + 32 * q + lane;
+        const double cs = (m < g.M && g.cscale) ? g.cscale[m] : 1.0;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            const int col0 = half * 64 + part * 32;
+            uint32_t v[32];
+            tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0, v);
+            if (m < g.M) {
+                if (g.c_f32) {
+                    float *C = static_cast<float *>(g.C);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int n = n0 + col0 + j;
+                        if (n < g.N) C[(size_t)n * g.ldc + m] += (float)(g.alpha * cs * (double)__uint_as_float(v[j]));
+                    }
+                } else {
+                    double *C = static_cast<double *>(g.C);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int n = n0 + col0 + j;
+                        if (n < g.N) C[(size_t)n * g.ldc + m] += g.alpha * cs * (double)__uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    if (failed && tid == 0) dev_fail(st, BDDC_DEV_ERR_TIMEOUT, w.x, -2);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+void launch_tc_gemm(const TcGemm *jobs, const int4 *items, int nitems, DevStatus *st, double timeout_s,
+                    cudaStream_t s) {
+    if (nitems <= 0) return;
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    const uint64_t tns = (uint64_t)(timeout_s * 1e9);
+    tc_gemm_kernel<<<nitems, TC_THREADS, TC_SMEM, s>>>(jobs, items, nitems, st, tns);
+}
+
+}  // namespace bddc

@@ -1,0 +1,34 @@
+// Batched 3xTF32 GEMM on the fifth-generation tensor cores (tc_gemm.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+
+namespace bddc {
+
+// C[m, n] += alpha * cscale[m] * sum_k A[m, k] * bscale[k] * B[n, k]
+//   A: row m at A + m * lda, contiguous in k (float, or double when a_f64)
+//   B: row n at B + n * ldb, contiguous in k (float, or double when b_f64)
+//   C: column-major, C[m, n] at C[n * ldc + m], FP64 (or FP32 when c_f32)
+// lda / ldb must keep every row 16-byte aligned (multiples of 4 floats or 2 doubles).
+struct TcGemm {
+    const void *A;
+    const void *B;
+    void *C;
+    const double *cscale;   // null = 1
+    const double *bscale;   // null = 1
+    int lda, ldb, ldc;
+    int M, N, K;
+    int a_f64, b_f64;
+    double alpha;
+    int c_f32;
+};
+
+constexpr int kTcM = 128;   // rows of an output tile (one TMEM lane per row)
+constexpr int kTcN = 128;   // columns of an output tile (TMEM columns)
+
+// items: (job, 128-row tile, 128-column tile, unused)
+void launch_tc_gemm(const TcGemm *jobs, const int4 *items, int nitems, DevStatus *st, double timeout_s,
+                    cudaStream_t s);
+
+}  // namespace bddc

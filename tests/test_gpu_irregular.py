@@ -12,10 +12,18 @@ from paper_0910_5863_gb300 import problems as P
 from paper_0910_5863_gb300 import bddc as B
 import oracle
 from oracle.adaptive import pair_problem, orthonormal_rows
+from test_gpu_parity import check_face_rows
 
 pytestmark = pytest.mark.gpu
 
 TAU = 10.0
+# Eigenvalues against the oracle: the FP64 path meets 1e-6 on every face.  The mixed
+# path condenses the pairs in double-float (unit roundoff 2^-48, 32 times FP64's);
+# on this problem the worst faces amplify rounding by ~1e9 (the FP64 path's own
+# deviation from the oracle reaches 1.3e-7 there), so the mixed path is held to
+# 32 x 1.3e-7 ~ 4e-6, rounded up to 1e-5.
+TOL_LAM = {B.FP64: 1e-6, B.MIXED: 1e-5}
+TOL_SPAN = {B.FP64: 1e-6, B.MIXED: 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -53,11 +61,31 @@ def test_solution_and_agreement(irregular):
     assert abs(runs[B.FP64][3]["iters"] - runs[B.MIXED][3]["iters"]) <= 3
 
 
+def test_face_rows_orthonormal_and_counts(irregular):
+    """Every face's kept rows are orthonormal in both precisions, and both paths
+    select and keep the same number of rows on every face."""
+    prob, m, runs = irregular
+    nf = runs[B.FP64][1]["n_faces"]
+    for f in range(nf):
+        counts = []
+        for prec, (s, info, u, sinfo) in runs.items():
+            g = s.face_eigs(f)
+            gd, rows = s.face_rows(f)
+            assert rows.shape[0] == g["kept"] <= gd.size
+            if g["kept"]:
+                assert np.abs(rows @ rows.T - np.eye(g["kept"])).max() < 1e-10, (prec, f)
+            counts.append((g["selected"], g["kept"]))
+        assert counts[0] == counts[1], (f, counts)
+
+
 def _sampled_faces(m):
+    """Faces at the 5/8, 1/2 and 1/8 quantiles of the face size: the oracle's dense
+    Jacobi on the condensed 2 n_s pencil takes seconds there (the largest faces,
+    2 n_s ~ 1700, take many minutes)."""
     keys = sorted(m.globs.faces)
     sizes = [len(m.globs.faces[k]) for k in keys]
     order = np.argsort(sizes, kind="stable")
-    return [int(order[-1]), int(order[len(order) // 2]), int(order[len(order) // 8])]
+    return [int(order[5 * len(order) // 8]), int(order[len(order) // 2]), int(order[len(order) // 8])]
 
 
 def test_sampled_face_eigs(irregular):
@@ -78,4 +106,5 @@ def test_sampled_face_eigs(irregular):
             assert g["pair"] == (i, j)
             assert g["selected"] == ref.selected and g["kept"] == kept, (prec, f, g["lam"][:4], ref.lam[:4])
             n = min(len(g["lam"]), ref.selected + 1)
-            assert np.allclose(g["lam"][:n], ref.lam[:n], rtol=1e-6), (prec, f)
+            assert np.allclose(g["lam"][:n], ref.lam[:n], rtol=TOL_LAM[prec]), (prec, f)
+            check_face_rows(s, f, ref, m, tol_span=TOL_SPAN[prec])

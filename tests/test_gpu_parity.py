@@ -5,6 +5,7 @@ import pytest
 from paper_0910_5863_gb300 import problems as P
 from paper_0910_5863_gb300 import bddc as B
 import oracle
+from oracle.adaptive import orthonormal_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -112,6 +113,7 @@ def _check_adaptive(m, ad, res, s, info, prob):
         assert g["kept"] == ad.per_face[key]
         n = min(len(g["lam"]), r.selected + 1)
         assert np.allclose(g["lam"][:n], r.lam[:n], rtol=TOL_LAM), (key, g["lam"][:n], r.lam[:n])
+        check_face_rows(s, f, r, m)
     assert info["n_added"] == ad.n_added
     assert abs(info["omega"] - ad.omega) <= TOL_LAM * ad.omega
     u, sinfo = s.solve(B.free_load_vector(prob))
@@ -119,6 +121,27 @@ def _check_adaptive(m, ad, res, s, info, prob):
     kr = res.condition()[1] / res.condition()[0]
     assert abs(sinfo["kappa"] - kr) <= 0.01 * kr
     assert _rel(u, res.u) < 1e-7
+
+
+def check_face_rows(s, f, r, m, tol_span=1e-6):
+    """The kept rows of face f are orthonormal, live on the oracle's face dofs and
+    span the oracle's row space.  The span is as well determined as the normalised
+    face rows are independent, so its tolerance is divided by their smallest
+    singular value."""
+    gd, rows = s.face_rows(f)
+    if r.selected == 0:
+        assert rows.shape[0] == 0
+        return
+    face_g = np.sort(m.dofs.of_nodes(np.asarray(r.face_nodes)).ravel())
+    assert np.array_equal(gd, face_g)
+    assert np.abs(rows @ rows.T - np.eye(rows.shape[0])).max() < 1e-10
+    ref = orthonormal_rows(r.face_rows)
+    assert rows.shape[0] == ref.shape[0]
+    nrm = r.face_rows / np.linalg.norm(r.face_rows, axis=1, keepdims=True)
+    sv = np.linalg.svd(nrm, compute_uv=False)
+    smin = sv[ref.shape[0] - 1]
+    gap = np.linalg.norm(rows.T @ rows - ref.T @ ref, 2)
+    assert gap <= tol_span / smin, (f, gap, smin)
 
 
 def test_adaptive_poisson24_full_size():
