@@ -1550,7 +1550,8 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     if (jobs.empty()) return 0;
     std::vector<EllProduct> ps;
     std::vector<MixedUpdate> us, us0;
-    std::vector<TcGemm> tg, tg0;
+    std::vector<TcGemm> tg;
+    std::vector<GatherOp> gB;   // float(B) into the FP32 residual copy before the first correction
     std::vector<int2> vitems;
     ZeroList zx;
     for (int k = 0; k < (int)jobs.size(); ++k) {
@@ -1567,18 +1568,24 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
         p.ldb = j.ldb;
         p.out = j.R;
         p.ldo = j.ldr;
+        float *Rf = j.ncol > 1 ? h->ar.get_t<float>("Rf_" + tag + t, (size_t)j.ldr * j.ncol) : nullptr;
+        p.outf = Rf;
         ps.push_back(p);
         const int ldk = round_up(std::max(sd.nI, 1), 8);
         const float *K = reinterpret_cast<const float *>(h->ar.get("Kinv_" + t, (size_t)ldk * sd.nI * 4 + 16));
         const double *eq = h->ar.get_t<double>("eq_" + t, sd.n);
+        const float *eqf = h->ar.get_t<float>("eqf_" + t, sd.n);
         us.push_back(MixedUpdate{K, ldk, eq, j.R, j.ldr, j.X, j.ldx, sd.nI, j.ncol});
         us0.push_back(MixedUpdate{K, ldk, eq, j.B, j.ldb, j.X, j.ldx, sd.nI, j.ncol});
         if (j.ncol == 1) {
             for (int a = 0; a < (sd.nI + 7) / 8; ++a) vitems.push_back(make_int2(k, a));
         } else {
-            // X[r, c] += d[r] sum_k K_s[r, k] d[k] R[k, c]: rows of the symmetric K_s are its columns
-            tg.push_back(TcGemm{K, j.R, j.X, eq, eq, ldk, j.ldr, j.ldx, sd.nI, j.ncol, sd.nI, 0, 1, 1.0});
-            tg0.push_back(TcGemm{K, j.B, j.X, eq, eq, ldk, j.ldb, j.ldx, sd.nI, j.ncol, sd.nI, 0, 1, 1.0});
+            // X[r, c] += d[r] sum_k K_s[r, k] d[k] R[k, c]: rows of the symmetric K_s are its columns;
+            // R is read from its FP32 copy (written by the residual kernel, or float(B) at first)
+            tg.push_back(TcGemm{K, Rf, j.X, eq, eqf, ldk, j.ldr, j.ldx, sd.nI, j.ncol, sd.nI, 0, 0, 1.0});
+            GatherOp o = gop(j.B, j.ldb, reinterpret_cast<double *>(Rf), j.ldr, sd.nI, j.ncol);
+            o.dst_f32 = 1;
+            gB.push_back(o);
         }
         zx.add(j.X, (size_t)j.ldx * j.ncol);
     }
@@ -1588,8 +1595,8 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     auto *dvi = h->ar.upload("mvi_" + tag, vitems, h->stream);
     const std::vector<int4> titems = tc_items(tg);
     auto *dtg = h->ar.upload("mtg_" + tag, tg, h->stream);
-    auto *dtg0 = h->ar.upload("mtg0_" + tag, tg0, h->stream);
     auto *dti = h->ar.upload("mti_" + tag, titems, h->stream);
+    run_gathers(h, gB, "Bf_" + tag);
     auto update = [&](const MixedUpdate *d, const TcGemm *t) {
         if (!titems.empty()) {
             launch_tc_gemm(t, dti, (int)titems.size(), h->dst, h->opt.timeout_s, h->stream);
@@ -1607,7 +1614,7 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     for (size_t k = 0; k < jobs.size(); ++k) col_off[k + 1] = col_off[k] + jobs[k].ncol;
     int *dcol_off = h->ar.upload("rn_off_" + tag, col_off, h->stream);
     double *colsums = h->ar.get_t<double>("rn_cols_" + tag, 2 * (size_t)std::max(col_off.back(), 1));
-    update(dus0, dtg0);
+    update(dus0, dtg);
     int done = 1;
     for (;;) {
         if (!check && done >= corrections) break;
@@ -1648,9 +1655,10 @@ void interior_mixed(bddc_handle *h) {
         const int n = sd.n, nI = sd.nI, nG = sd.nG;
         const std::string t = std::to_string(s);
         double *eq = h->ar.get_t<double>("eq_" + t, n);
+        float *eqf = h->ar.get_t<float>("eqf_" + t, n);
         EllProduct e = ell_of(h, s);
         ms[s] = MixedSub{sd.A, n, nI, sd.ld, eq, const_cast<int *>(e.ell_cnt), const_cast<int *>(e.ell_col),
-                         const_cast<double *>(e.ell_val), W};
+                         const_cast<double *>(e.ell_val), W, eqf};
         for (int r = 0; r < n; ++r) eitems.push_back(make_int2(s, r));
         if (nI == 0) continue;
         const int ldF = round_up(2 * nI, 8);
@@ -1688,7 +1696,7 @@ void interior_mixed(bddc_handle *h) {
     zero_all(h, zl, "F");
     run_gathers(h, gF, "F");
     run_diag(h, dI, "F");
-    run_pchol<float>(h, pd, "F");
+    run_pchol_tc(h, pd, "F");
     run_gathers(h, gK, "Kinv");
     fail_check(h, "mixed interior factorization");
     // refine until ||A_IG - A_II X|| <= refine_tol ||A_IG||; the energy form below squares that error
@@ -1711,11 +1719,19 @@ void interior_mixed(bddc_handle *h) {
     }
     run_ell(h, ps, "S");
     // S[a, b] -= sum_k X[k, a] R[k, b]  (3xTF32 tensor-core products; the term is second order)
+    // (FP32 copies of X and of R, the residual of the accepted X written by the refinement)
     std::vector<TcGemm> gc;
+    std::vector<GatherOp> gx;
     for (const auto &j : jobs) {
         auto &sd = h->subs[j.s];
-        gc.push_back(TcGemm{j.X, j.R, sd.S, nullptr, nullptr, j.ldx, j.ldr, sd.ldS, sd.nG, sd.nG, sd.nI, 1, 1, -1.0});
+        float *Xf = h->ar.get_t<float>("Xf_" + std::to_string(j.s), (size_t)j.ldx * j.ncol);
+        const float *Rf = h->ar.get_t<float>("Rf_X" + std::to_string(j.s), (size_t)j.ldr * j.ncol);
+        GatherOp o = gop(j.X, j.ldx, reinterpret_cast<double *>(Xf), j.ldx, sd.nI, j.ncol);
+        o.dst_f32 = 1;
+        gx.push_back(o);
+        gc.push_back(TcGemm{Xf, Rf, sd.S, nullptr, nullptr, j.ldx, j.ldr, sd.ldS, sd.nG, sd.nG, sd.nI, 0, 0, -1.0});
     }
+    run_gathers(h, gx, "Xf");
     run_tc_gemm(h, gc, "gc");
     launch_symmetrize(h->ops.S, h->ops.nGi, h->ops.ldS, ns, h->stream);
     check_launch(h);

@@ -4,8 +4,9 @@
 //   1. an FP32 partial Cholesky of [[D A_II D, .], [I, 0]] leaves -(D A_II D)^-1
 //      in its trailing block (the explicit FP32 inverse K_s);
 //   2. X = A_II^-1 A_IG is refined in FP64:  R = A_IG - A_II X  (FP64, the
-//      sparse interior columns of A_i in ELL form),  X += D K_s D R  (3xTF32
-//      tensor-core product, tc_gemm.cu; FP64 accumulation of X);
+//      sparse interior columns of A_i in ELL form; an FP32 copy of R feeds the
+//      correction),  X += D K_s D R  (3xTF32 tensor-core product, tc_gemm.cu;
+//      FP64 accumulation of X);
 //   3. S_i = A_GG - A_GI X  in FP64 (the same sparse product over the
 //      interface rows) -- the Schur complement of Section 2 of the paper.
 // The same refinement solves A_II y = f_I for the condensed right-hand side
@@ -18,7 +19,11 @@ namespace bddc {
 // eq[k] = 1 / sqrt(A_kk) for every local dof of every substructure
 __global__ void equilibrate_kernel(const MixedSub *subs, int nsub) {
     const MixedSub s = subs[blockIdx.x];
-    for (int k = threadIdx.x; k < s.n; k += blockDim.x) s.eq[k] = rsqrt(s.A[(size_t)k * s.ld + k]);
+    for (int k = threadIdx.x; k < s.n; k += blockDim.x) {
+        const double e = rsqrt(s.A[(size_t)k * s.ld + k]);
+        s.eq[k] = e;
+        if (s.eqf) s.eqf[k] = (float)e;
+    }
 }
 
 // ELL copy of the interior columns of A: row r keeps (c, a_rc) for c < nI and a_rc != 0.
@@ -69,6 +74,7 @@ __global__ void ell_residual_kernel(const EllProduct *ps, const int2 *items, int
     for (int q = 0; q < cnt; ++q) acc += vals[(size_t)q * p.ell_n] * x[cols[(size_t)q * p.ell_n]];
     const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
     p.out[(size_t)c * p.ldo + i] = b - acc;
+    if (p.outf) p.outf[(size_t)c * p.ldo + i] = (float)(b - acc);
 }
 
 // single right-hand side: x[r] += d[r] sum_k K[r, k] float(d[k] r[k]); one warp per row

@@ -14,6 +14,7 @@ struct MixedSub {
     int *ell_col;      // (ell_w x n): entry q of row r at q * n + r
     double *ell_val;   // (ell_w x n)
     int ell_w;
+    float *eqf;        // (n) eq in FP32, or null
 };
 
 // out[r, c] = B[r, c] - sum_{interior cols} A[r0 + r, col] X[col, c], r < m, c < ncol
@@ -28,6 +29,7 @@ struct EllProduct {
     int ldb;
     double *out;
     int ldo;
+    float *outf;       // optional FP32 copy of out (ldo), the operand of the tensor-core corrections
 };
 
 // X[r, c] += d[r] sum_k K[r, k] float(d[k] R[k, c]),  r, k < n, c < ncol

@@ -117,7 +117,21 @@ __device__ void coarse_dots(const PcgParams &P, const double *rin) {
             const double *col = o.Phi[s] + (size_t)m * ld;
             const int *RG = o.RG + o.off[s];
             double acc = 0.0;
-            for (int k = lane; k < n; k += 32) acc += col[k] * ldx(rin + RG[k]);
+            int k = lane;
+            for (; k + 96 < n; k += 128) {   // four independent gathers in flight
+                int g[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) g[u] = RG[k + 32 * u];
+                double rv[4], cv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    rv[u] = ldx(rin + g[u]);
+                    cv[u] = col[k + 32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc += cv[u] * rv[u];
+            }
+            for (; k < n; k += 32) acc += col[k] * ldx(rin + RG[k]);
             acc = warp_sum(acc);
             if (lane == 0) P.b.cl[o.offc[s] + m] = acc;
         }
@@ -157,7 +171,21 @@ __device__ double assemble_z(const PcgParams &P, const double *rin, double *zout
             int nc = o.nci[s], ld = o.ldS[s];
             const double *Ph = o.Phi[s];
             const int *Rc = o.Rc + o.offc[s];
-            for (int m = 0; m < nc; ++m) w += Ph[(size_t)m * ld + k] * ldx(P.b.uc + Rc[m]);
+            int m = 0;
+            for (; m + 7 < nc; m += 8) {   // eight independent coarse gathers in flight
+                int c[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) c[u] = Rc[m + u];
+                double uv[8], pv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    uv[u] = ldx(P.b.uc + c[u]);
+                    pv[u] = Ph[(size_t)(m + u) * ld + k];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) w += pv[u] * uv[u];
+            }
+            for (; m < nc; ++m) w += Ph[(size_t)m * ld + k] * ldx(P.b.uc + Rc[m]);
             v += w;
         }
         zout[x] = v;
@@ -174,7 +202,7 @@ __device__ double reduce_partials(const double *partial, int nb) {
     return warp_sum(s);
 }
 
-__global__ void __launch_bounds__(PCG_THREADS) pcg_kernel(PcgParams P) {
+__global__ void __launch_bounds__(PCG_THREADS, 1) pcg_kernel(PcgParams P) {
     extern __shared__ double smem[];
     double *red = smem;                    // PCG_WARPS * 64
     double *rc = smem + PCG_WARPS * 64;    // nC (coarse phase) ...

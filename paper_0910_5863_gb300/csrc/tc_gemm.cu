@@ -122,43 +122,38 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// four consecutive k values of row `row` (zero outside [0, nrows) x [0, K))
+// four consecutive k values of row `row` as FP32 (zero outside [0, nrows) x [0, K)),
+// times kscale[k] (in FP32) when kscale is given.  FP32 sources use the FP32 pipe
+// only; FP64 sources need one conversion per value (FP64 pipe).
 __device__ __forceinline__ void load4(const void *base, int ld, int f64, int row, int nrows, int k, int K,
-                                      const double *kscale, float (&out)[4]) {
+                                      const float *kscale, float (&out)[4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) out[i] = 0.f;
     if (row >= nrows || k >= K) return;
     if (f64) {
         const double *p = static_cast<const double *>(base) + (size_t)row * ld + k;
-        double d[4];
         if (k + 4 <= K) {
             const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
             const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
-            d[0] = a.x, d[1] = a.y, d[2] = b.x, d[3] = b.y;
-            if (kscale) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) d[i] *= __ldg(kscale + k + i);
-            }
+            out[0] = __double2float_rn(a.x), out[1] = __double2float_rn(a.y);
+            out[2] = __double2float_rn(b.x), out[3] = __double2float_rn(b.y);
         } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) d[i] = (k + i < K) ? __ldg(p + i) * (kscale ? __ldg(kscale + k + i) : 1.0) : 0.0;
+            for (int i = 0; i < 4; ++i) out[i] = (k + i < K) ? __double2float_rn(__ldg(p + i)) : 0.f;
         }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) out[i] = (float)d[i];
     } else {
         const float *p = static_cast<const float *>(base) + (size_t)row * ld + k;
         if (k + 4 <= K) {
             const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
             out[0] = a.x, out[1] = a.y, out[2] = a.z, out[3] = a.w;
-            if (kscale) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) out[i] = (float)((double)out[i] * __ldg(kscale + k + i));
-            }
         } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                out[i] = (k + i < K) ? (float)((double)__ldg(p + i) * (kscale ? __ldg(kscale + k + i) : 1.0)) : 0.f;
+            for (int i = 0; i < 4; ++i) out[i] = (k + i < K) ? __ldg(p + i) : 0.f;
         }
+    }
+    if (kscale) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[i] *= (k + i < K) ? __ldg(kscale + k + i) : 0.f;
     }
 }
 
@@ -274,7 +269,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (!failed && nkb > 0) {
         const int q = warp & 3, half = warp >> 2;
         const int m = m0 + 32 * q + lane;
-        const double cs = (m < g.M && g.cscale) ? g.cscale[m] : 1.0;
+        const double csa = g.alpha * ((m < g.M && g.cscale) ? g.cscale[m] : 1.0);
+        const float csa_f = (float)csa;   // the FP32 output path stays on the FP32 pipe
 #pragma unroll
         for (int part = 0; part < 2; ++part) {
             const int col0 = half * 64 + part * 32;
@@ -286,14 +282,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int n = n0 + col0 + j;
-                        if (n < g.N) C[(size_t)n * g.ldc + m] += (float)(g.alpha * cs * (double)__uint_as_float(v[j]));
+                        if (n < g.N) C[(size_t)n * g.ldc + m] += csa_f * __uint_as_float(v[j]);
                     }
                 } else {
                     double *C = static_cast<double *>(g.C);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int n = n0 + col0 + j;
-                        if (n < g.N) C[(size_t)n * g.ldc + m] += g.alpha * cs * (double)__uint_as_float(v[j]);
+                        if (n < g.N) C[(size_t)n * g.ldc + m] = fma(csa, (double)__uint_as_float(v[j]), C[(size_t)n * g.ldc + m]);
                     }
                 }
             }

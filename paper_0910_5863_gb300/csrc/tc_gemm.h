@@ -7,6 +7,8 @@
 namespace bddc {
 
 // C[m, n] += alpha * cscale[m] * sum_k A[m, k] * bscale[k] * B[n, k]
+// (bscale is applied in FP32 to the FP32 value of B, cscale and alpha in the
+// output precision)
 //   A: row m at A + m * lda, contiguous in k (float, or double when a_f64)
 //   B: row n at B + n * ldb, contiguous in k (float, or double when b_f64)
 //   C: column-major, C[m, n] at C[n * ldc + m], FP64 (or FP32 when c_f32)
@@ -16,7 +18,7 @@ struct TcGemm {
     const void *B;
     void *C;
     const double *cscale;   // null = 1
-    const double *bscale;   // null = 1
+    const float *bscale;    // null = 1
     int lda, ldb, ldc;
     int M, N, K;
     int a_f64, b_f64;
