@@ -179,6 +179,28 @@ FF_INSTR_PER_FMA = 12
 FP32_LANE_RATE = 152 * 128 * 2.07e9
 
 
+# DRAM bytes (read + write) of one pcg_kernel launch on the 24^3 Poisson workload, from
+# the ncu capture summarised in profiles/pcg_kernel_poisson24.md; None when unknown.
+PCG_TRAFFIC_POISSON24 = 34915072 + 8192
+
+
+def _pcg_roofline(solver, phases, iters, hbm, src, workload):
+    """The persistent PCG kernel: algorithmic bytes = per iteration one pass over every
+    S_i and P~_i (the two local GEMVs, 2 x 8 sum_i n_Gamma,i^2 bytes); coarse and vector
+    traffic are not counted."""
+    ph = phases["pcg"]
+    ms = sum(m for m, _ in ph) / len(ph)
+    nsub = solver.nsub
+    gemv = sum(2 * 8 * solver.interface_dofs(i).size ** 2 for i in range(nsub))
+    bytes_ = gemv * iters
+    achieved = bytes_ / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": "pcg_kernel (one launch = the whole PCG solve)", "achieved": achieved,
+            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": PCG_TRAFFIC_POISSON24 if workload == "poisson24" else None,
+            "peak_source": f"{src} HBM copy bandwidth (of {src})", "bytes_per_launch": bytes_,
+            "iterations": iters, "ms_per_launch": ms}
+
+
 def _roofline(phases, phase, kernel, peak, bound, peak_source):
     ph = phases[phase]
     ms = sum(m for m, _ in ph) / len(ph)
@@ -237,11 +259,13 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": t_mixed, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_mixed * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": _config(prob, args.seed, args.workload),
-        "roofline": _roofline(ph_mixed, "pair_condensation",
-                              "pchol_panel+pchol_update <ff> (pair condensations in double-float on the FP32 pipe)",
-                              ff_peak, "alu",
-                              "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 12 instructions per double-float "
-                              "multiply-add x 2 flop (FP64-equivalent flop)"),
+        "roofline": _pcg_roofline(solver, ph_mixed, info["iters"], hbm, src, args.workload),
+        "phase_rooflines": {
+            "pair_condensation": _roofline(
+                ph_mixed, "pair_condensation",
+                "pchol_panel+pchol_update <ff> (pair condensations in double-float on the FP32 pipe)", ff_peak, "alu",
+                "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 12 instructions per double-float "
+                "multiply-add x 2 flop (FP64-equivalent flop)")},
         "e2e": {"value": statistics.median(e2e_times), "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

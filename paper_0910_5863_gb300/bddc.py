@@ -196,6 +196,7 @@ class Solver:
         self._check(self.lib.bddc_set_mesh_q1(self.h, ncomp, nn, ptrs[0][0], ne, ptrs[1][0], ptrs[2][0], float(nu),
                                               ptrs[3][0], int(nsub), ptrs[4][0], mem))
         self.nfree = self.sizes()["n_free"]
+        self.nsub = int(nsub)
 
     def set_problem(self, n_global, ncomp, subs, node_xyz=None):
         """Algebraic problem: subs = [(l2g, A_i)] with l2g (n_local,) global dof ids
@@ -217,6 +218,7 @@ class Solver:
         self._check(self.lib.bddc_set_problem(self.h, int(n_global), int(ncomp), len(subs), desc,
                                               None if xyz is None else xyz.ctypes.data, MEM_HOST))
         self.nfree = self.sizes()["n_free"]
+        self.nsub = len(subs)
 
     def set_corners(self, nodes):
         a = np.ascontiguousarray(nodes, dtype=np.int64)

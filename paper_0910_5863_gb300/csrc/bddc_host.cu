@@ -1538,6 +1538,7 @@ EllProduct ell_of(bddc_handle *h, int s) {
     p.ell_val = h->ar.get_t<double>("ellv_" + t, (size_t)sd.n * W);
     p.ell_w = W;
     p.ell_n = sd.n;
+    p.ell_valf = h->ar.get_t<double>("ellvf_" + t, (size_t)sd.n * W);
     return p;
 }
 
@@ -1545,13 +1546,23 @@ EllProduct ell_of(bddc_handle *h, int s) {
 // R = B - A_II X (FP64) and X += D K_s D R.  With check, stops at the first residual
 // whose relative norm is below tol for every job (R then holds that residual);
 // without, stops after exactly `corrections` corrections.  Returns the corrections made.
+//
+// Jobs with several columns (the interior elimination, X = A_II^-1 A_IG) use the
+// tensor cores for the correction dX = D K_s D R (FP32 copy of R in, FP32 dX out).
+// The first residual R = B - A_II X is formed in FP64; the later ones are updated,
+// R <- R - A_II dX, with the product in double-float: its error is relative to the
+// small correction, so the updated R tracks B - A_II X to FP64 accuracy while the
+// FP64 pipe (~2 multiply-adds per clock and SM on this GPU) only adds dX into X.
+// Single-column jobs (right-hand sides) form every residual in FP64.
 int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, int max_corr, double tol, bool check,
            const std::string &tag) {
     if (jobs.empty()) return 0;
-    std::vector<EllProduct> ps;
+    const bool multi = jobs[0].ncol > 1;
+    for (const auto &j : jobs) BDDC_REQUIRE((j.ncol > 1) == multi, BDDC_EINVAL, "refine: mixed job kinds");
+    std::vector<EllProduct> ps, pu;
     std::vector<MixedUpdate> us, us0;
     std::vector<TcGemm> tg;
-    std::vector<GatherOp> gB;   // float(B) into the FP32 residual copy before the first correction
+    std::vector<GatherOp> gB, gX;   // float(B) into the FP32 residual copy; X += dX after the first correction
     std::vector<int2> vitems;
     ZeroList zx;
     for (int k = 0; k < (int)jobs.size(); ++k) {
@@ -1568,24 +1579,37 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
         p.ldb = j.ldb;
         p.out = j.R;
         p.ldo = j.ldr;
-        float *Rf = j.ncol > 1 ? h->ar.get_t<float>("Rf_" + tag + t, (size_t)j.ldr * j.ncol) : nullptr;
+        float *Rf = multi ? h->ar.get_t<float>("Rf_" + tag + t, (size_t)j.ldr * j.ncol) : nullptr;
         p.outf = Rf;
         ps.push_back(p);
         const int ldk = round_up(std::max(sd.nI, 1), 8);
         const float *K = reinterpret_cast<const float *>(h->ar.get("Kinv_" + t, (size_t)ldk * sd.nI * 4 + 16));
         const double *eq = h->ar.get_t<double>("eq_" + t, sd.n);
         const float *eqf = h->ar.get_t<float>("eqf_" + t, sd.n);
-        us.push_back(MixedUpdate{K, ldk, eq, j.R, j.ldr, j.X, j.ldx, sd.nI, j.ncol});
-        us0.push_back(MixedUpdate{K, ldk, eq, j.B, j.ldb, j.X, j.ldx, sd.nI, j.ncol});
-        if (j.ncol == 1) {
+        if (!multi) {
+            us.push_back(MixedUpdate{K, ldk, eq, j.R, j.ldr, j.X, j.ldx, sd.nI, j.ncol});
+            us0.push_back(MixedUpdate{K, ldk, eq, j.B, j.ldb, j.X, j.ldx, sd.nI, j.ncol});
             for (int a = 0; a < (sd.nI + 7) / 8; ++a) vitems.push_back(make_int2(k, a));
         } else {
-            // X[r, c] += d[r] sum_k K_s[r, k] d[k] R[k, c]: rows of the symmetric K_s are its columns;
-            // R is read from its FP32 copy (written by the residual kernel, or float(B) at first)
-            tg.push_back(TcGemm{K, Rf, j.X, eq, eqf, ldk, j.ldr, j.ldx, sd.nI, j.ncol, sd.nI, 0, 0, 1.0});
+            // dX[r, c] = d[r] sum_k K_s[r, k] d[k] R[k, c]: rows of the symmetric K_s are its columns
+            float *dX = h->ar.get_t<float>("dX_" + tag + t, (size_t)j.ldx * j.ncol);
+            TcGemm g{K, Rf, dX, eq, eqf, ldk, j.ldr, j.ldx, sd.nI, j.ncol, sd.nI, 0, 0, 1.0};
+            g.c_f32 = 1;
+            g.store = 1;
+            tg.push_back(g);
             GatherOp o = gop(j.B, j.ldb, reinterpret_cast<double *>(Rf), j.ldr, sd.nI, j.ncol);
             o.dst_f32 = 1;
             gB.push_back(o);
+            o = gop(reinterpret_cast<const double *>(dX), j.ldx, j.X, j.ldx, sd.nI, j.ncol);
+            o.src_f32 = 1;
+            gX.push_back(o);   // X = dX (X starts at zero)
+            EllProduct q = p;
+            q.B = j.R;         // R <- R - A dX in place
+            q.ldb = j.ldr;
+            q.update = 1;
+            q.dXf = dX;
+            q.Xu = j.X;
+            pu.push_back(q);
         }
         zx.add(j.X, (size_t)j.ldx * j.ncol);
     }
@@ -1597,15 +1621,13 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     auto *dtg = h->ar.upload("mtg_" + tag, tg, h->stream);
     auto *dti = h->ar.upload("mti_" + tag, titems, h->stream);
     run_gathers(h, gB, "Bf_" + tag);
-    auto update = [&](const MixedUpdate *d, const TcGemm *t) {
-        if (!titems.empty()) {
-            launch_tc_gemm(t, dti, (int)titems.size(), h->dst, h->opt.timeout_s, h->stream);
-            check_launch(h);
-        }
-        if (!vitems.empty()) {
+    auto correction = [&](const MixedUpdate *d) {
+        if (multi) {
+            launch_tc_gemm(dtg, dti, (int)titems.size(), h->dst, h->opt.timeout_s, h->stream);
+        } else {
             launch_mixed_update_vec(d, dvi, (int)vitems.size(), h->stream);
-            check_launch(h);
         }
+        check_launch(h);
     };
     auto *dps = h->ar.upload("mps_" + tag, ps, h->stream);
     double *norms = h->ar.get_t<double>("rnorm_" + tag, 2 * jobs.size());
@@ -1614,11 +1636,15 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     for (size_t k = 0; k < jobs.size(); ++k) col_off[k + 1] = col_off[k] + jobs[k].ncol;
     int *dcol_off = h->ar.upload("rn_off_" + tag, col_off, h->stream);
     double *colsums = h->ar.get_t<double>("rn_cols_" + tag, 2 * (size_t)std::max(col_off.back(), 1));
-    update(dus0, dtg);
+    correction(dus0);
+    if (multi) run_gathers(h, gX, "dX0_" + tag);
     int done = 1;
     for (;;) {
         if (!check && done >= corrections) break;
-        run_ell(h, ps, tag);
+        if (multi && done > 1)
+            run_ell(h, pu, tag + "u");   // R -= A dX, X += dX
+        else
+            run_ell(h, ps, tag);         // R = B - A X (FP64)
         if (check) {
             launch_residual_norms(dps, (int)ps.size(), colsums, dcol_off, norms, h->stream);
             check_launch(h);
@@ -1633,9 +1659,10 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
                          "mixed-precision refinement of the interior solves did not converge (relative residual " +
                              std::to_string(worst) + "); use BDDC_FP64");
         }
-        update(dus, dtg);
+        correction(dus);
         ++done;
     }
+    if (multi && done > 1 && !check) run_ell(h, pu, tag + "u");   // fold the last correction into X
     return done;
 }
 
@@ -1658,7 +1685,7 @@ void interior_mixed(bddc_handle *h) {
         float *eqf = h->ar.get_t<float>("eqf_" + t, n);
         EllProduct e = ell_of(h, s);
         ms[s] = MixedSub{sd.A, n, nI, sd.ld, eq, const_cast<int *>(e.ell_cnt), const_cast<int *>(e.ell_col),
-                         const_cast<double *>(e.ell_val), W, eqf};
+                         const_cast<double *>(e.ell_val), W, eqf, const_cast<double *>(e.ell_valf)};
         for (int r = 0; r < n; ++r) eitems.push_back(make_int2(s, r));
         if (nI == 0) continue;
         const int ldF = round_up(2 * nI, 8);
@@ -2282,7 +2309,8 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
     }
     run_gemm(h, gm2, "C");
     auto *ded = h->ar.upload("eigdesc", eds, h->stream);
-    launch_face_eig_n(ded, (int)eds.size(), nmax, tau, h->opt.drop_rel, h->dst, h->stream);
+    launch_face_eig_n(ded, (int)eds.size(), nmax, tau, h->opt.drop_rel, h->opt.precision != BDDC_FP64 ? 1 : 0, h->dst,
+                      h->stream);
     check_launch(h);
     phase_end(h, 4);
     fail_check(h, "adapt");

@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include <algorithm>
 #include "eig.h"
+#include "ff.cuh"
 
 namespace bddc {
 
@@ -34,8 +35,91 @@ __device__ int sturm_less(const double *d, const double *e, int n, double x, dou
     return cnt;
 }
 
+// Householder tridiagonalisation in double-float (the mixed modes): the same
+// steps as the FP64 loop of face_eig_kernel, with the O(n^3) work (B x and the
+// rank-2 update) on the FP32 pipe.  On entry A holds the matrix as doubles; it
+// is converted to double-float in place, reduced, and the reflectors (below the
+// subdiagonal) are converted back to doubles, so that everything after the
+// reduction reads the same layout as in FP64 mode.  bet and ee are written as
+// in the FP64 loop; the diagonal is returned in dd.
+__device__ void householder_ff(double *A, int lda, int n, double *dd, double *ee, double *bet, double *Pw, double *Ww,
+                               double *scratch) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    ff *F = reinterpret_cast<ff *>(A);
+    ff *P = reinterpret_cast<ff *>(Pw);
+    ff *W = reinterpret_cast<ff *>(Ww);
+    for (int e = tid; e < n * n; e += nt) {
+        const size_t o = (size_t)(e / n) * lda + e % n;
+        F[o] = ff_from_double(A[o]);
+    }
+    __syncthreads();
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        ff *x = F + (size_t)k * lda + k + 1;
+        ff acc(0.f, 0.f);
+        for (int i = tid; i < m; i += nt) ff_fma_acc(acc, x[i], x[i]);
+        const double s = block_sum(ff_to_double(ff_norm(acc)), scratch);
+        const double x0 = ff_to_double(x[0]);
+        const double rest = s - x0 * x0;
+        if (rest <= 1e-300 * (s + 1e-300)) {
+            if (tid == 0) {
+                bet[k] = 0.0;
+                ee[k] = x0;
+            }
+            __syncthreads();
+            continue;
+        }
+        const double nrm = sqrt(s);
+        const double alpha = x0 > 0 ? -nrm : nrm;
+        const double v0 = x0 - alpha;
+        const double beta = 2.0 / (rest + v0 * v0);
+        __syncthreads();
+        if (tid == 0) {
+            x[0] = ff_from_double(v0);
+            bet[k] = beta;
+            ee[k] = alpha;
+        }
+        __syncthreads();
+        ff *B = F + (size_t)(k + 1) * lda + k + 1;
+        const ff fbeta = ff_from_double(beta);
+        for (int i = tid; i < m; i += nt) {
+            ff a(0.f, 0.f);
+            for (int j = 0; j < m; ++j) {
+                ff_fma_acc(a, B[(size_t)j * lda + i], x[j]);
+                if ((j & 15) == 15) a = ff_norm(a);
+            }
+            P[i] = fbeta * ff_norm(a);
+        }
+        __syncthreads();
+        ff pa(0.f, 0.f);
+        for (int i = tid; i < m; i += nt) ff_fma_acc(pa, P[i], x[i]);
+        const double pv = block_sum(ff_to_double(ff_norm(pa)), scratch);
+        const ff K = ff_from_double(0.5 * beta * pv);
+        for (int i = tid; i < m; i += nt) W[i] = P[i] - K * x[i];
+        __syncthreads();
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = e % m, j = e / m;
+            B[(size_t)j * lda + i] -= x[i] * W[j] + W[i] * x[j];
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += nt) dd[i] = ff_to_double(F[(size_t)i * lda + i]);
+    if (tid == 0 && n >= 2) ee[n - 2] = ff_to_double(F[(size_t)(n - 2) * lda + n - 1]);
+    __syncthreads();
+    // reflectors back to doubles (column k, rows k + 1 .. n - 1)
+    for (int e = tid; e < n * n; e += nt) {
+        const int i = e % n, j = e / n;
+        if (i > j) {
+            const size_t o = (size_t)j * lda + i;
+            A[o] = ff_to_double(F[o]);
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *descs, int np, double tau,
-                                                               double drop_rel, DevStatus *st, int use_smem) {
+                                                               double drop_rel, DevStatus *st, int use_smem,
+                                                               int use_ff) {
     extern __shared__ double sm[];
     __shared__ double scratch[32];
     __shared__ double sh_val[4];
@@ -64,7 +148,8 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     double *dd = work, *ee = work + n, *bet = work + 2 * n, *P = work + 3 * n, *Wv = work + 4 * n;
     __syncthreads();
     // ---- 1. Householder tridiagonalisation: A = Q T Q^T ----
-    for (int k = 0; k + 2 < n; ++k) {
+    if (use_ff) householder_ff(A, lda, n, dd, ee, bet, P, Wv, scratch);
+    for (int k = 0; !use_ff && k + 2 < n; ++k) {
         const int m = n - k - 1;
         double *x = A + (size_t)k * lda + k + 1;   // column k below the diagonal
         double s = 0.0;
@@ -110,10 +195,11 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
         }
         __syncthreads();
     }
-    for (int i = tid; i < n; i += nt) dd[i] = A[(size_t)i * lda + i];
+    if (!use_ff)
+        for (int i = tid; i < n; i += nt) dd[i] = A[(size_t)i * lda + i];
     if (tid == 0) {
         if (n >= 2) {
-            ee[n - 2] = A[(size_t)(n - 2) * lda + n - 1];
+            if (!use_ff) ee[n - 2] = A[(size_t)(n - 2) * lda + n - 1];
             bet[n - 2] = 0.0;
         }
         bet[n - 1] = 0.0;
@@ -343,14 +429,14 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     }
 }
 
-void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, DevStatus *st,
-                       cudaStream_t s) {
+void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, int use_ff,
+                       DevStatus *st, cudaStream_t s) {
     if (npairs <= 0) return;
     size_t need = sizeof(double) * ((size_t)nmax * nmax + (10 + 6 * (EIG_THREADS / 32)) * (size_t)nmax + 16);
     int use_smem = need <= 200 * 1024;
     size_t smem = use_smem ? need : 0;
     if (smem > 48 * 1024) cudaFuncSetAttribute(face_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    face_eig_kernel<<<npairs, EIG_THREADS, smem, s>>>(descs, npairs, tau, drop_rel, st, use_smem);
+    face_eig_kernel<<<npairs, EIG_THREADS, smem, s>>>(descs, npairs, tau, drop_rel, st, use_smem, use_ff);
 }
 
 // ---------------------------------------------------------------------------

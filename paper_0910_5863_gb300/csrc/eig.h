@@ -24,8 +24,9 @@ struct EigDesc {
 // nmax: largest n of the batch; when the matrix and work arrays do not fit in
 // 200 KB of shared memory the matrix is reduced in place and work (64 n + 16
 // doubles) is used from global memory.
-void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, DevStatus *st,
-                       cudaStream_t s);
+// use_ff: the Householder reduction runs in double-float on the FP32 pipe (mixed modes)
+void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, int use_ff,
+                       DevStatus *st, cudaStream_t s);
 
 // Deflated pair matrix M3 (see adapt phase): adds sigma*c_blk*N0 N0^T to the
 // (w2,w2), (b,w2) and (b,b) blocks with c = 4, 2, 1; sigma = max diag(S^).

@@ -13,6 +13,7 @@
 // and the interior recovery.
 #include "common.cuh"
 #include "mixed.h"
+#include "ff.cuh"
 
 namespace bddc {
 
@@ -45,6 +46,7 @@ __global__ void ell_build_kernel(const MixedSub *subs, const int2 *items, int ni
         if (v != 0.0 && pos < s.ell_w) {  // entry-major: entry q of row r at q * n + r
             s.ell_col[(size_t)pos * s.n + r] = c;
             s.ell_val[(size_t)pos * s.n + r] = v;
+            if (s.ell_valf) reinterpret_cast<ff *>(s.ell_valf)[(size_t)pos * s.n + r] = ff_from_double(v);
         }
         cnt += __popc(m);
     }
@@ -68,6 +70,21 @@ __global__ void ell_residual_kernel(const EllProduct *ps, const int2 *items, int
     const int r = p.r0 + i;
     const int cnt = p.ell_cnt[r];
     const int *cols = p.ell_col + r;       // entry-major: consecutive rows are consecutive
+    if (p.update) {
+        // the correction is small, so its product is carried in double-float on the FP32
+        // pipe (FP64 accuracy relative to the correction); only the update of out and of
+        // X uses the FP64 pipe
+        const ff *vf = reinterpret_cast<const ff *>(p.ell_valf) + r;
+        const float *dx = p.dXf + (size_t)c * p.ldx;
+        ff acc(0.f, 0.f);
+        for (int q = 0; q < cnt; ++q) ff_fma_acc(acc, vf[(size_t)q * p.ell_n], ff(dx[cols[(size_t)q * p.ell_n]], 0.f));
+        const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
+        const double res = b - ff_to_double(ff_norm(acc));
+        p.out[(size_t)c * p.ldo + i] = res;
+        if (p.outf) p.outf[(size_t)c * p.ldo + i] = (float)res;
+        if (p.Xu) p.Xu[(size_t)c * p.ldx + r] += (double)dx[r];
+        return;
+    }
     const double *vals = p.ell_val + r;
     const double *x = p.X + (size_t)c * p.ldx;
     double acc = 0.0;

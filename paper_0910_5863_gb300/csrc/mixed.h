@@ -15,6 +15,7 @@ struct MixedSub {
     double *ell_val;   // (ell_w x n)
     int ell_w;
     float *eqf;        // (n) eq in FP32, or null
+    double *ell_valf;  // (ell_w x n) the ELL values as double-float pairs (struct ff), or null
 };
 
 // out[r, c] = B[r, c] - sum_{interior cols} A[r0 + r, col] X[col, c], r < m, c < ncol
@@ -30,6 +31,13 @@ struct EllProduct {
     double *out;
     int ldo;
     float *outf;       // optional FP32 copy of out (ldo), the operand of the tensor-core corrections
+    // update form (update != 0): out = B - sum A dX accumulated in double-float from the
+    // double-float ELL values and the FP32 correction dX (ldx), and Xu += dX (ldx) on the
+    // same index space (r0 = 0, m = rows of X); B may alias out
+    int update;
+    const double *ell_valf;
+    const float *dXf;
+    double *Xu;
 };
 
 // X[r, c] += d[r] sum_k K[r, k] float(d[k] R[k, c]),  r, k < n, c < ncol

@@ -16,8 +16,10 @@
 //     chunk c ^ (r mod 8));
 //   * one thread issues tcgen05.mma (M = 128, N = 128, K = 8 per instruction,
 //     4 x 3 instructions per slab) into a 128-column TMEM accumulator and
-//     commits them to the slab's mbarrier; two slab buffers alternate, so the
-//     loads of slab k+1 overlap the MMAs of slab k;
+//     commits them to the slab's mbarrier; the global loads of slab k+1 are
+//     issued before the wait for the MMAs of slab k, and two CTAs share an SM
+//     (66 KB of shared memory and 128 TMEM columns each), so one CTA's MMAs
+//     overlap the other's loads;
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 //     lanes 32 (w mod 4) .. + 31, i.e. those output rows) and adds
 //     alpha * cscale[m] * acc into the FP64 (or FP32) output with coalesced
@@ -36,7 +38,7 @@ constexpr int TC_THREADS = 256;
 constexpr int TC_KB = 32;                     // K per slab: 32 x 4 bytes = one 128-byte swizzle row
 constexpr int TC_TILE_BYTES = 128 * 128;      // 128 rows x 128 bytes
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;   // A_hi, A_lo, B_hi, B_lo
-constexpr int TC_STAGES = 2;
+constexpr int TC_STAGES = 1;   // with two CTAs per SM the other CTA's MMAs cover this one's loads
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;   // + alignment slack
 constexpr uint32_t TC_TMEM_COLS = 128;
 
@@ -175,7 +177,7 @@ __device__ __forceinline__ void store_split(uint8_t *hi_tile, uint8_t *lo_tile, 
 
 }  // namespace
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
     tc_gemm_kernel(const TcGemm *jobs, const int4 *items, int nitems, DevStatus *st, uint64_t timeout_ns) {
     extern __shared__ uint8_t tc_smem_raw[];
     __shared__ uint64_t bars[TC_STAGES];
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool ok = true;
     int issued = -1;   // last slab whose MMAs were committed (uniform over the block)
     for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb & 1;
+        const int s = kb % TC_STAGES;
         const int k = kb * TC_KB + 4 * c;
         float va[4][4], vb[4][4];
 #pragma unroll
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // the last commit covers every MMA issued before it (after a timeout: wait again, bounded)
     if (issued >= 0) {
         const uint64_t dl = ok ? deadline : globaltimer_ns() + timeout_ns;
-        if (!mbar_wait(smem_u32(&bars[issued & 1]), (uint32_t)((issued / TC_STAGES) & 1), dl)) ok = false;
+        if (!mbar_wait(smem_u32(&bars[issued % TC_STAGES]), (uint32_t)((issued / TC_STAGES) & 1), dl)) ok = false;
     }
     if (!ok && lane == 0) atomicExch(&failed, 1);
     __syncthreads();
@@ -282,14 +284,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int n = n0 + col0 + j;
-                        if (n < g.N) C[(size_t)n * g.ldc + m] += csa_f * __uint_as_float(v[j]);
+                        if (n < g.N) {
+                            const float t = csa_f * __uint_as_float(v[j]);
+                            C[(size_t)n * g.ldc + m] = g.store ? t : C[(size_t)n * g.ldc + m] + t;
+                        }
                     }
                 } else {
                     double *C = static_cast<double *>(g.C);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int n = n0 + col0 + j;
-                        if (n < g.N) C[(size_t)n * g.ldc + m] = fma(csa, (double)__uint_as_float(v[j]), C[(size_t)n * g.ldc + m]);
+                        if (n < g.N) {
+                            const double t = (double)__uint_as_float(v[j]);
+                            C[(size_t)n * g.ldc + m] = g.store ? csa * t : fma(csa, t, C[(size_t)n * g.ldc + m]);
+                        }
                     }
                 }
             }

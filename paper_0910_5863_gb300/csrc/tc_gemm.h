@@ -24,6 +24,7 @@ struct TcGemm {
     int a_f64, b_f64;
     double alpha;
     int c_f32;
+    int store;              // 1: C[m, n] = (instead of +=) the product term
 };
 
 constexpr int kTcM = 128;   // rows of an output tile (one TMEM lane per row)
