@@ -22,15 +22,47 @@ namespace bddc {
 
 constexpr int EIG_THREADS = 256;
 
-__device__ int sturm_less(const double *d, const double *e, int n, double x, double pivmin) {
-    int cnt = 0;
-    double q = d[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0) ++cnt;
+__device__ __forceinline__ int lane_of(int tid) { return tid & 31; }
+// threads per row for a matrix-vector product of order m on nt threads: the largest
+// power of two (at most 8) with m * tpr <= nt, so the rows still fit in one pass
+__device__ __forceinline__ int rows_per_pass_split(int m, int nt) {
+    int t = 1;
+    while (t < 8 && m * t * 2 <= nt) t <<= 1;
+    return t;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Number of eigenvalues of the symmetric tridiagonal T (diagonal d, squared
+// off-diagonal e2) below x: the sign changes of the leading principal minors
+// p_0 = 1, p_1 = d_0 - x, p_{i+1} = (d_i - x) p_i - e2_{i-1} p_{i-1}.  The product
+// form needs three FP64 operations per step where the quotient form
+// q_i = p_i / p_{i-1} needs a division (the FP64 pipe of this GPU retires ~2
+// operations per clock and SM).  (p_{i-1}, p_i) is rescaled by a power of two
+// when p_i leaves [2^-512, 2^512]; a zero minor counts as negative, like the
+// quotient form's -pivmin.  Signs, zero tests and exponents use integer ops.
+__device__ __forceinline__ bool dneg(double v) { return __double2hiint(v) < 0; }
+__device__ __forceinline__ bool dzero(double v) { return ((__double2hiint(v) & 0x7fffffff) | __double2loint(v)) == 0; }
+
+__device__ int sturm_less(const double *d, const double *e2, int n, double x) {
+    double pm = 1.0, p = d[0] - x;
+    if (dzero(p)) p = -0x1p-100;
+    int cnt = dneg(p) ? 1 : 0;
     for (int i = 1; i < n; ++i) {
-        q = d[i] - x - e[i - 1] * e[i - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        if (q < 0) ++cnt;
+        double pn = fma(d[i] - x, p, -e2[i - 1] * pm);
+        if (dzero(pn)) pn = -p * 0x1p-100;
+        if ((__double2hiint(pn) ^ __double2hiint(p)) < 0) ++cnt;
+        const int ex = (__double2hiint(pn) >> 20) & 0x7ff;
+        if (ex > 1023 + 512 || ex < 1023 - 512) {
+            const double sc = __hiloint2double((2046 - ex) << 20, 0);   // 2^(1023 - ex)
+            pn *= sc;
+            p *= sc;
+        }
+        pm = p;
+        p = pn;
     }
     return cnt;
 }
@@ -82,13 +114,25 @@ __device__ void householder_ff(double *A, int lda, int n, double *dd, double *ee
         __syncthreads();
         ff *B = F + (size_t)(k + 1) * lda + k + 1;
         const ff fbeta = ff_from_double(beta);
-        for (int i = tid; i < m; i += nt) {
-            ff a(0.f, 0.f);
-            for (int j = 0; j < m; ++j) {
-                ff_fma_acc(a, B[(size_t)j * lda + i], x[j]);
-                if ((j & 15) == 15) a = ff_norm(a);
+        {   // tpr consecutive threads share a row (shorter dependency chains)
+            const int tpr = rows_per_pass_split(m, nt), part = tid & (tpr - 1);
+            for (int i0 = 0; i0 < m; i0 += nt / tpr) {
+                const int i = i0 + tid / tpr;
+                ff a(0.f, 0.f);
+                if (i < m) {
+                    int c = 0;
+                    for (int j = part; j < m; j += tpr) {
+                        ff_fma_acc(a, B[(size_t)j * lda + i], x[j]);
+                        if ((++c & 15) == 0) a = ff_norm(a);
+                    }
+                }
+                a = ff_norm(a);
+                for (int o = tpr >> 1; o > 0; o >>= 1) {
+                    const ff b(__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o));
+                    a = a + b;
+                }
+                if (i < m && part == 0) P[i] = fbeta * a;
             }
-            P[i] = fbeta * ff_norm(a);
         }
         __syncthreads();
         ff pa(0.f, 0.f);
@@ -177,10 +221,16 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
         }
         __syncthreads();
         double *B = A + (size_t)(k + 1) * lda + k + 1;
-        for (int i = tid; i < m; i += nt) {
-            double acc = 0.0;
-            for (int j = 0; j < m; ++j) acc += B[(size_t)j * lda + i] * x[j];
-            P[i] = beta * acc;
+        {   // P = beta B x: tpr consecutive threads share a row (shorter dependency chains)
+            const int tpr = rows_per_pass_split(m, nt), part = tid & (tpr - 1);
+            for (int i0 = 0; i0 < m; i0 += nt / tpr) {
+                const int i = i0 + tid / tpr;
+                double acc = 0.0;
+                if (i < m)
+                    for (int j = part; j < m; j += tpr) acc += B[(size_t)j * lda + i] * x[j];
+                for (int o = tpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (i < m && part == 0) P[i] = beta * acc;
+            }
         }
         __syncthreads();
         double pv = 0.0;
@@ -207,17 +257,23 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     }
     __syncthreads();
     // ---- 2. counts and bisection ----
-    double tnorm = 0.0, emax2 = 0.0;
-    for (int i = 0; i < n; ++i) {
-        double r = fabs(dd[i]) + (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i + 1 < n ? fabs(ee[i]) : 0.0);
-        tnorm = fmax(tnorm, r);
-        if (i + 1 < n) emax2 = fmax(emax2, ee[i] * ee[i]);
+    double *e2 = work + 5 * n;
+    double tn = 0.0;   // infinity norm of T (block max)
+    for (int i = tid; i < n; i += nt) {
+        const double a = i > 0 ? fabs(ee[i - 1]) : 0.0, b = i + 1 < n ? fabs(ee[i]) : 0.0;
+        tn = fmax(tn, fabs(dd[i]) + a + b);
+        if (i + 1 < n) e2[i] = ee[i] * ee[i];
     }
-    const double pivmin = fmax(1e-300, 1e-290 * fmax(emax2, 1.0));
+    tn = warp_max(tn);
+    if (lane_of(tid) == 0) scratch[tid >> 5] = tn;
+    __syncthreads();
+    double tnorm = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) tnorm = fmax(tnorm, scratch[w]);
+    __syncthreads();
     if (tid == 0) {
-        int less = sturm_less(dd, ee, n, tau, pivmin);
+        int less = sturm_less(dd, e2, n, tau);
         int nsel = n - less;
-        int ties = sturm_less(dd, ee, n, tau * (1 + 1e-6), pivmin) - sturm_less(dd, ee, n, tau * (1 - 1e-6), pivmin);
+        int ties = sturm_less(dd, e2, n, tau * (1 + 1e-6)) - sturm_less(dd, e2, n, tau * (1 - 1e-6));
         int over = 0;
         if (nsel > kEigCap) {
             nsel = kEigCap;
@@ -240,7 +296,7 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
             const double w = hi - lo;
             if (w <= 1e-15 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
             const double x = lo + w * (double)(lane + 1) * (1.0 / 32.0);
-            const bool above = lane < 31 && sturm_less(dd, ee, n, x, pivmin) > j;
+            const bool above = lane < 31 && sturm_less(dd, e2, n, x) > j;
             const unsigned mask = __ballot_sync(0xffffffffu, above);
             const int first = mask ? __ffs(mask) - 1 : 31;
             const double nlo = first == 0 ? lo : lo + w * (double)first * (1.0 / 32.0);
