@@ -1427,6 +1427,16 @@ void coarse_setup(bddc_handle *h, bool allow_fp32) {
     h->ops.cent = h->ar.upload("cent", cent, h->stream);
     h->ops.cdot = h->ar.upload("cdot", cdot, h->stream);
     h->ops.ncdot = (int)cdot.size();
+    {   // assembly records of the interface entries
+        std::vector<ZEntry> ze(h->gent.size());
+        for (size_t e = 0; e < h->gent.size(); ++e) {
+            const int s = h->gsub[e];
+            const auto &sd = h->subs[s];
+            const int k = (int)(h->gent[e] - h->offG[s]);
+            ze[e] = ZEntry{h->gent[e], sd.Phi + k, dRc + offc[s], sd.ldS, nci_v[s]};
+        }
+        h->ops.zent = h->ar.upload("zent", ze, h->stream);
+    }
     h->pb.cl = h->ar.get_t<double>("cl", std::max<int64_t>(oc, 1));
     h->pb.uc = h->ar.get_t<double>("uc", nC);
 }

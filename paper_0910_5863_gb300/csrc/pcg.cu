@@ -21,6 +21,7 @@ namespace bddc {
 
 constexpr int PCG_THREADS = 512;
 constexpr int PCG_WARPS = PCG_THREADS / 32;
+constexpr int PCG_PARTIALS = 2048;   // the partials buffer holds two sets of this many blocks
 
 // Data written by other blocks of this launch is read through L2 only
 // (ld.global.cg), so no block can see a stale L1 line after a grid barrier.
@@ -49,8 +50,11 @@ __device__ __forceinline__ double2 ld_mat2(const double *p, bool stream) {
     return stream ? __ldcs(reinterpret_cast<const double2 *>(p)) : __ldg(reinterpret_cast<const double2 *>(p));
 }
 
-__device__ void local_gemv(const PcgParams &P, double *const *Mats, const double *vin, const double *pold,
-                           double beta, double *yout, double *red, double *vs) {
+// Returns this thread's share of sum_i v_i . y_i (the rows it stored), which for
+// Mats = S gives p^T S p without assembling S p.
+__device__ double local_gemv(const PcgParams &P, double *const *Mats, const double *vin, const double *pold,
+                             double beta, double *yout, double *red, double *vs) {
+    double vy = 0.0;
     const IfaceOps &o = P.o;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const bool stream = o.stream_mats != 0;
@@ -99,10 +103,14 @@ __device__ void local_gemv(const PcgParams &P, double *const *Mats, const double
             double sum = 0.0;
 #pragma unroll
             for (int k = 0; k < PCG_WARPS; ++k) sum += red[k * 64 + threadIdx.x];
-            if (r0 + threadIdx.x < n) yout[o.off[s] + r0 + threadIdx.x] = sum;
+            if (r0 + threadIdx.x < n) {
+                yout[o.off[s] + r0 + threadIdx.x] = sum;
+                vy += vs[r0 + threadIdx.x] * sum;
+            }
         }
         __syncthreads();
     }
+    return vy;
 }
 
 // c_i[m] = Phi~_i[:, m] . r_i
@@ -164,13 +172,11 @@ __device__ double assemble_z(const PcgParams &P, const double *rin, double *zout
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < o.nG; x += gridDim.x * blockDim.x) {
         double v = 0.0;
         for (int e = o.gptr[x]; e < o.gptr[x + 1]; ++e) {
-            int64_t pe = o.gent[e];
-            int s = o.gsub[e];
-            int k = (int)(pe - o.off[s]);
-            double w = ldx(P.b.zl + pe);
-            int nc = o.nci[s], ld = o.ldS[s];
-            const double *Ph = o.Phi[s];
-            const int *Rc = o.Rc + o.offc[s];
+            const ZEntry ze = o.zent[e];   // one record instead of a chain of dependent lookups
+            double w = ldx(P.b.zl + ze.pe);
+            const int nc = ze.nc, ld = ze.ld, k = 0;
+            const double *Ph = ze.phi;
+            const int *Rc = ze.rc;
             int m = 0;
             for (; m + 7 < nc; m += 8) {   // eight independent coarse gathers in flight
                 int c[8];
@@ -263,21 +269,14 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) pcg_kernel(PcgParams P) {
         // beta, p = z + beta p, y_i = S_i p_i
         const double rz = reduce_partials(b.partial, nb);
         const double beta = (k == 1) ? 0.0 : rz / rz_old;
+        // p . S p = sum_i p_i . S_i p_i comes out of the local products (second partials
+        // buffer: other blocks may still be reading r . z from the first)
         for (int x = gtid; x < o.nG; x += gstride) pnew[x] = b.z[x] + beta * pold[x];
-        local_gemv(P, o.S, b.z, pold, beta, b.yl, red, vs);
-        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
-        // q = sum R_i^T y_i, p . q
-        part = 0.0;
-        for (int x = gtid; x < o.nG; x += gstride) {
-            double v = 0.0;
-            for (int e = o.gptr[x]; e < o.gptr[x + 1]; ++e) v += ldx(b.yl + o.gent[e]);
-            b.q[x] = v;
-            part += pnew[x] * v;
-        }
+        part = local_gemv(P, o.S, b.z, pold, beta, b.yl, red, vs);
         part = block_sum(part, scratch);
-        if (threadIdx.x == 0) b.partial[blockIdx.x] = part;
+        if (threadIdx.x == 0) b.partial[PCG_PARTIALS + blockIdx.x] = part;
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
-        const double pq = reduce_partials(b.partial, nb);
+        const double pq = reduce_partials(b.partial + PCG_PARTIALS, nb);
         if (!(pq > 0.0)) {
             --k;
             break;
@@ -287,10 +286,13 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) pcg_kernel(PcgParams P) {
             b.alpha[k - 1] = alpha;
             if (k > 1) b.beta[k - 2] = beta;
         }
+        // q = sum R_i^T y_i assembled on the fly; x += alpha p, r -= alpha q
         part = 0.0;
         for (int x = gtid; x < o.nG; x += gstride) {
+            double q = 0.0;
+            for (int e = o.gptr[x]; e < o.gptr[x + 1]; ++e) q += ldx(b.yl + o.gent[e]);
             b.x[x] += alpha * pnew[x];
-            double rv = b.r[x] - alpha * b.q[x];
+            double rv = b.r[x] - alpha * q;
             b.r[x] = rv;
             part += rv * rv;
         }
@@ -334,6 +336,7 @@ cudaError_t launch_pcg(const IfaceOps &ops, const PcgBuffers &buf, int mode, dou
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (per_sm > 1) per_sm = 1;
     int nblocks = nsm * per_sm;
+    if (nblocks > PCG_PARTIALS) nblocks = PCG_PARTIALS;   // the two partials sets of the buffer
     if (nblocks_out) *nblocks_out = nblocks;
     void *args[] = {&P};
     return cudaLaunchCooperativeKernel((void *)pcg_kernel, dim3(nblocks), dim3(PCG_THREADS), args, smem, s);

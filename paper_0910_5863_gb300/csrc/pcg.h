@@ -10,6 +10,15 @@ namespace bddc {
 // M r = sum R_i^T D_i (P_i D_i R_i r + Phi_i R_ci u_c), S_C u_c = sum R_ci^T Phi_i^T D_i R_i r
 // need, packed per substructure.  P~ = D P D and Phi~ = D Phi are stored
 // with the weights folded in.
+// One entry (substructure s, local interface position k) of an interface dof, with
+// everything the assembly of z = sum (z_i + Phi~_i u_c,i) needs in one record.
+struct ZEntry {
+    int64_t pe;          // packed local index (offset of s + k)
+    const double *phi;   // Phi~_s + k: entry m at phi[m * ld]
+    const int *rc;       // R_c of s: global coarse index of local coarse dof m
+    int ld, nc;
+};
+
 struct IfaceOps {
     int nsub, nG, nC;
     int maxGi;               // largest nGi
@@ -27,6 +36,7 @@ struct IfaceOps {
     const int *gptr;         // (nG+1) local entries of each interface dof
     const int64_t *gent;     // packed local index of each entry
     const int *gsub;         // substructure of each entry
+    const ZEntry *zent;      // the entries again, as assembly records
     const int *cptr;         // (nC+1)
     const int64_t *cent;     // packed local coarse index of each entry
     const int2 *rowblk;      // (sub, first row) GEMV work items, 64 rows each
@@ -41,7 +51,7 @@ struct PcgBuffers {
     double *zl, *yl;                  // sum nGi
     double *cl;                       // sum nci
     double *uc;                       // nC
-    double *partial;                  // nblocks
+    double *partial;                  // 2 x 2048: two sets of per-block partial sums
     double *alpha, *beta;             // maxit
     int *iters, *converged;
     double *relres;
