@@ -35,7 +35,12 @@ WORKLOADS = {
     # 32^3 elasticity, 64 substructures, 8 stiff channels E = 1e6, clamped z = 0
     "elast32": ("elast32_4x4x4_channels1e6_adaptive_tau10", "32x32x32 Q1 hex, 3 dofs/node",
                 "config_elasticity_channels"),
+    # 256 independent Poisson problems (2^3 or 3^3 substructures of 6^3..10^3 elements,
+    # lognormal coefficients sigma = 2), solved by concurrent handles on separate streams
+    "batch256": ("batch256_poisson_lognormal_adaptive_tau10", "256 problems, 12^3..30^3 Q1 hex",
+                 "config_batch_poisson"),
 }
+BATCH_WORKERS = 8
 WORKLOAD = WORKLOADS["poisson24"][0]
 TAU = 10.0
 # FP64 dense peak: the measured bf16 burst peak times the nominal FP64/BF16 ratio (1.25 / 2250 TFLOP/s)
@@ -181,7 +186,7 @@ FP32_LANE_RATE = 152 * 128 * 2.07e9
 
 # DRAM bytes (read + write) of one pcg_kernel launch on the 24^3 Poisson workload, from
 # the ncu capture summarised in profiles/pcg_kernel_poisson24.md; None when unknown.
-PCG_TRAFFIC_POISSON24 = 34915072 + 8192
+PCG_TRAFFIC_POISSON24 = 35121664 + 13056
 
 
 def _pcg_roofline(solver, phases, iters, hbm, src, workload):
@@ -209,6 +214,73 @@ def _roofline(phases, phase, kernel, peak, bound, peak_source):
     return {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None, "peak_source": peak_source,
             "flop_per_launch": flop, "ms_per_launch": ms}
+
+
+def run_batch_gpu(args, world, local_rank):
+    """The 256-problem workload: every step solves all problems once (setup + adapt +
+    solve) with BATCH_WORKERS concurrent handles; value = seconds per problem."""
+    import torch
+    from paper_0910_5863_gb300 import problems as P
+    from paper_0910_5863_gb300 import bddc as B
+    from paper_0910_5863_gb300 import batch as BT
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    probs = P.config_batch_poisson(seed=args.seed)
+    arrays = BT.upload(probs, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    arms = {}
+    pools = {}
+    for prec in (B.MIXED, B.FP64):
+        pools[prec] = pool = BT.Pool(prec, workers=BATCH_WORKERS, device=dev)
+        for _ in range(args.warmup):
+            BT.run(probs, arrays, pool, tau=TAU)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        clocks = Clocks(local_rank)
+        clocks.start()
+        walls, recs = [], None
+        l0 = sum(sv.launch_count() for sv in pool.solvers)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize(dev)
+            wall, recs = BT.run(probs, arrays, pool, tau=TAU)
+            walls.append(wall)
+        clk = clocks.stop()
+        launches = sum(sv.launch_count() for sv in pool.solvers) - l0
+        wall = max_over_ranks(statistics.median(walls), world)
+        lat = sorted(r["latency_s"] for r in recs)
+        arms[prec] = {"s_per_problem": wall / len(probs), "problems_per_s": len(probs) / wall, "wall_s": wall,
+                      "latency_median_s": lat[len(lat) // 2], "latency_max_s": lat[-1],
+                      "iters_max": max(r["iters"] for r in recs), "n_added_total": sum(r["n_added"] for r in recs),
+                      "all_converged": all(r["converged"] for r in recs), "clocks": clk,
+                      "gpu_launches": int(launches)}
+    # end to end: host arrays in, solutions out, through the same runner (mixed arm)
+    h2d = sum(sum(t.numel() * t.element_size() for t in a) for a in arrays)
+    d2h = sum(a[5].numel() * 8 for a in arrays)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    arrays_e2e = BT.upload(probs, dev)
+    _, recs = BT.run(probs, arrays_e2e, pools[B.MIXED], tau=TAU, keep_solutions=True)
+    sols = [r["u"].cpu() for r in recs]
+    e2e = (time.perf_counter() - t0) / len(probs)
+    del sols
+    m, f = arms[B.MIXED], arms[B.FP64]
+    cfg = {"workload": WORKLOADS["batch256"][0], "mesh": WORKLOADS["batch256"][1], "problems": len(probs),
+           "free_dofs_total": int(sum(int((~p.dirichlet).sum()) for p in probs)), "tau": TAU, "tol": 1e-8,
+           "seed": args.seed, "workers": BATCH_WORKERS, "precision": "mixed",
+           "l2": "flushed before every step (256 MiB write)", "parallelism": "replicas"}
+    line = {"metric": METRIC, "value": m["s_per_problem"], "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["wall_s"] * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": cfg,
+            "roofline": None, "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                                      "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": m["gpu_launches"], "clocks": m["clocks"], "problems_per_s": m["problems_per_s"],
+            "latency_median_s": m["latency_median_s"], "latency_max_s": m["latency_max_s"],
+            "iters_max": m["iters_max"], "n_added_total": m["n_added_total"], "all_converged": m["all_converged"],
+            "fp64": f, "mixed_over_fp64_speedup": f["s_per_problem"] / m["s_per_problem"]}
+    return line
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -293,8 +365,19 @@ def run_oracle(args, sample_note):
     import oracle
     from oracle.adaptive import pair_problem
 
-    prob = getattr(P, WORKLOADS[args.workload][2])(seed=args.seed)
     cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count())))
+    if args.workload == "batch256":
+        # bounded sample: the first 4 of the 256 problems, whole runs, scaled per problem
+        probs = P.config_batch_poisson(seed=args.seed)[:4]
+        t0 = time.perf_counter()
+        for prob in probs:
+            m = oracle.Model(prob)
+            m.schur()
+            oracle.adapt(m, TAU)
+            m.solve(tol=1e-8)
+        t = (time.perf_counter() - t0) / len(probs)
+        return t, cores, None, None, "4 of the 256 problems, each a full run (setup + adapt + solve); value = s per problem"
+    prob = getattr(P, WORKLOADS[args.workload][2])(seed=args.seed)
     t0 = time.perf_counter()
     m = oracle.Model(prob)
     m.schur()
@@ -339,7 +422,11 @@ def main():
             times.append(t)
         v = statistics.median(times)
         P = __import__("paper_0910_5863_gb300.problems", fromlist=["x"])
-        cfg = _config(getattr(P, WORKLOADS[args.workload][2])(args.seed), args.seed, args.workload)
+        if args.workload == "batch256":
+            cfg = {"workload": WORKLOADS["batch256"][0], "mesh": WORKLOADS["batch256"][1], "problems": 256,
+                   "tau": TAU, "tol": 1e-8, "seed": args.seed, "precision": "fp64", "parallelism": "replicas"}
+        else:
+            cfg = _config(getattr(P, WORKLOADS[args.workload][2])(args.seed), args.seed, args.workload)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
                 "steps": len(times), "warmup": 0, "ms_per_step": v * 1e3, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
@@ -353,7 +440,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    line = run_gpu(args, rank, world, local_rank)
+    if args.workload == "batch256":
+        line = run_batch_gpu(args, world, local_rank)
+    else:
+        line = run_gpu(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu_baseline:
             t, cores, iters, added, sample = run_oracle(args, "")

@@ -309,6 +309,23 @@ def config_irregular_elasticity(seed: int = 1, grid=(48, 48, 24), nparts: int = 
                            partition=(part, nparts))
 
 
+def config_batch_poisson(seed: int = 1, count: int = 256) -> list:
+    """count independent Q1 Poisson problems: problem p has s^3 cubic substructures of
+    m^3 elements (s in {2, 3}, m in {6, ..., 10}, drawn from the (seed, per-problem)
+    stream), k_e = exp(2 z) with z ~ N(0, 1) (lognormal, sigma = 2), u = 0 on x = 0,
+    nodal loads U[-1, 1]; problem p uses seed 65536 * seed + p + 1 for its own
+    coefficient and load streams."""
+    st = Stream(seed, P_PROBLEM)
+    out = []
+    for p in range(count):
+        u = st.uniform(2)
+        s = 2 + int(u[0] * 2)
+        m = 6 + int(u[1] * 5)
+        out.append(poisson_cube(s * m, s, seed=65536 * seed + p + 1, coef="lognormal", sigma=2.0,
+                                name=f"batch{p}_poisson{s * m}_s{s}_m{m}"))
+    return out
+
+
 def planar_cubes(k: int, m: int = 8, nu: float = 0.3, name=None) -> Problem:
     """k x k x 1 cubic substructures of m^3 Q1 elasticity elements (h = 1/m per cube,
     the paper's weak-scaling problem, Section 7 and its last table): fixed on the side
