@@ -307,7 +307,7 @@ void run_diag(bddc_handle *h, const std::vector<DiagOp> &ops, const std::string 
     check_launch(h);
 }
 
-void run_gemm(bddc_handle *h, const std::vector<GemmDesc> &descs, const std::string &tag) {
+void run_gemm(bddc_handle *h, const std::vector<GemmDesc> &descs, const std::string &tag, bool use_ff = false) {
     if (descs.empty()) return;
     std::vector<int4> items;
     for (int k = 0; k < (int)descs.size(); ++k)
@@ -315,7 +315,7 @@ void run_gemm(bddc_handle *h, const std::vector<GemmDesc> &descs, const std::str
             for (int b = 0; b < (descs[k].n + kTile - 1) / kTile; ++b) items.push_back(make_int4(k, a, b, 0));
     auto *dd = h->ar.upload("gm_desc_" + tag, descs, h->stream);
     auto *di = h->ar.upload("gm_it_" + tag, items, h->stream);
-    launch_gemm(dd, di, (int)items.size(), h->stream);
+    launch_gemm(dd, di, (int)items.size(), use_ff ? 1 : 0, h->stream);
     check_launch(h);
 }
 
@@ -2311,13 +2311,14 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         launch_pi_expand(dpis, (int)pis.size(), pi_nmax, h->stream);
         check_launch(h);
     }
-    run_gemm(h, gm1, "W1");
+    const bool ff_mode = h->opt.precision != BDDC_FP64;   // FP64-class products in double-float
+    run_gemm(h, gm1, "W1", ff_mode);
     if (!pis.empty()) {
         // W1 <- P W1 (the face rows become P L P w); C = Xg^T W1 is unchanged by P
         launch_pi_project(dpis, (int)pis.size(), h->stream);
         check_launch(h);
     }
-    run_gemm(h, gm2, "C");
+    run_gemm(h, gm2, "C", ff_mode);
     auto *ded = h->ar.upload("eigdesc", eds, h->stream);
     launch_face_eig_n(ded, (int)eds.size(), nmax, tau, h->opt.drop_rel, h->opt.precision != BDDC_FP64 ? 1 : 0, h->dst,
                       h->stream);

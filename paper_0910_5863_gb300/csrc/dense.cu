@@ -356,17 +356,25 @@ __global__ void __launch_bounds__(256) gemv_kernel(const GemmDesc *descs, const 
 }
 
 // ---------------------------------------------------------------------------
-// batched GEMM, FP64: C = alpha op(A) op(B) + beta C, 64x64 tiles, k-step 16
+// batched GEMM: C = alpha op(A) op(B) + beta C, 64x64 tiles, k-step 16.  FP64, or
+// with FF the tiles are converted to double-float as they are staged and the
+// products accumulated in double-float on the FP32 pipe (C stays FP64).
+template <bool FF>
 __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const int4 *items, int nitems) {
+    using T = typename std::conditional<FF, ff, double>::type;
     int it = blockIdx.x;
     if (it >= nitems) return;
     int4 w = items[it];
     const GemmDesc d = descs[w.x];
     const int m0 = w.y * TILE, n0 = w.z * TILE;
-    __shared__ double As[16][TILE + 1];
-    __shared__ double Bs[16][TILE + 1];
+    __shared__ T As[16][TILE + 1];
+    __shared__ T Bs[16][TILE + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    double acc[4][4] = {};
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     for (int k0 = 0; k0 < d.k; k0 += 16) {
         for (int e = tid; e < 16 * TILE; e += 256) {
             int r, k;
@@ -381,7 +389,10 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const 
             double v = 0.0;
             if (m0 + r < d.m && k0 + k < d.k)
                 v = d.transA ? d.A[(size_t)(m0 + r) * d.lda + k0 + k] : d.A[(size_t)(k0 + k) * d.lda + m0 + r];
-            As[k][r] = v;
+            if constexpr (FF)
+                As[k][r] = ff_from_double(v);
+            else
+                As[k][r] = v;
             int c;
             if (d.transB) {
                 c = e % TILE;
@@ -393,12 +404,15 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const 
             v = 0.0;
             if (n0 + c < d.n && k0 + k < d.k)
                 v = d.transB ? d.B[(size_t)(k0 + k) * d.ldb + n0 + c] : d.B[(size_t)(n0 + c) * d.ldb + k0 + k];
-            Bs[k][c] = v;
+            if constexpr (FF)
+                Bs[k][c] = ff_from_double(v);
+            else
+                Bs[k][c] = v;
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            double a[4], b[4];
+            T a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[k][tx + 16 * i];
 #pragma unroll
@@ -406,7 +420,18 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const 
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+                for (int j = 0; j < 4; ++j) {
+                    if constexpr (FF)
+                        ff_fma_acc(acc[i][j], a[i], b[j]);
+                    else
+                        acc[i][j] += a[i] * b[j];
+                }
+        }
+        if constexpr (FF) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = ff_norm(acc[i][j]);
         }
         __syncthreads();
     }
@@ -419,7 +444,12 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const 
             int r = m0 + tx + 16 * i;
             if (r >= d.m) continue;
             double *cp = d.C + (size_t)c * d.ldc + r;
-            *cp = d.alpha * acc[i][j] + (d.beta == 0.0 ? 0.0 : d.beta * *cp);
+            double av;
+            if constexpr (FF)
+                av = ff_to_double(acc[i][j]);
+            else
+                av = acc[i][j];
+            *cp = d.alpha * av + (d.beta == 0.0 ? 0.0 : d.beta * *cp);
         }
     }
 }
@@ -562,8 +592,12 @@ void launch_coarse_assemble(const CoarseAsmDesc *d, int nsub, double *SC, int nC
 void launch_gemv(const GemmDesc *descs, const int2 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) gemv_kernel<<<nitems, 256, 0, s>>>(descs, items, nitems);
 }
-void launch_gemm(const GemmDesc *descs, const int4 *items, int nitems, cudaStream_t s) {
-    if (nitems > 0) gemm_kernel<<<nitems, 256, 0, s>>>(descs, items, nitems);
+void launch_gemm(const GemmDesc *descs, const int4 *items, int nitems, int use_ff, cudaStream_t s) {
+    if (nitems <= 0) return;
+    if (use_ff)
+        gemm_kernel<true><<<nitems, 256, 0, s>>>(descs, items, nitems);
+    else
+        gemm_kernel<false><<<nitems, 256, 0, s>>>(descs, items, nitems);
 }
 template <typename T>
 void launch_trsv(const TrsvDesc<T> *descs, int nd, int backward, cudaStream_t s) {

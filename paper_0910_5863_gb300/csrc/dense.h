@@ -102,7 +102,8 @@ struct CoarseAsmDesc {
     int nci, ld;
 };
 void launch_coarse_assemble(const CoarseAsmDesc *d, int nsub, double *SC, int nC, cudaStream_t s);
-void launch_gemm(const GemmDesc *descs, const int4 *items, int nitems, cudaStream_t s);
+// use_ff: products accumulated in double-float on the FP32 pipe (C stays FP64)
+void launch_gemm(const GemmDesc *descs, const int4 *items, int nitems, int use_ff, cudaStream_t s);
 // descriptors with n == 1 and one transA value for the whole batch
 void launch_gemv(const GemmDesc *descs, const int2 *items, int nitems, cudaStream_t s);
 template <typename T>
