@@ -342,6 +342,7 @@ std::vector<int4> tc_items(const std::vector<TcGemm> &jobs, bool lower_only = fa
         const auto aligned = [](const void *p, int ld, int f64) {
             return ((uintptr_t)p % 16 == 0) && ((size_t)ld * (f64 ? 8 : 4)) % 16 == 0;
         };
+        BDDC_REQUIRE(!g.a_f64 && !g.b_f64, BDDC_EINVAL, "tensor-core GEMM operands must be FP32");
         BDDC_REQUIRE(aligned(g.A, g.lda, g.a_f64) && aligned(g.B, g.ldb, g.b_f64), BDDC_EINVAL,
                      "tensor-core GEMM operand rows must be 16-byte aligned");
         for (int a = 0; a < (g.M + kTcM - 1) / kTcM; ++a)

@@ -8,18 +8,20 @@
 // of Section 2 of the paper), where FP32 accuracy is what the FP64 refinement
 // needs and TF32 alone (2^-11) would stall it.
 //
-// One CTA per 128 x 128 output tile of one batch item:
-//   * 256 threads load 128 x 32 slabs of A and B from global memory (FP32 or
-//     FP64, K contiguous), split them and store hi / lo parts into shared
-//     memory in the K-major 128-byte-swizzled layout (rows of 32 TF32 values =
-//     128 bytes, 8-row atoms of 1024 bytes, 16-byte chunk c of row r stored at
+// One CTA per 128 x 128 output tile of one batch item (two CTAs per SM):
+//   * the operand slabs (128 rows x 32 FP32 values of A and of B, K
+//     contiguous) are copied from global memory by cp.async into a raw shared
+//     buffer, one slab ahead of its use; each thread copies and later reads
+//     the same 16-byte chunks, so no block barrier separates the two;
+//   * each thread splits its chunks into TF32 hi / lo parts and stores them
+//     into the K-major 128-byte-swizzled layout (rows of 32 TF32 values = 128
+//     bytes, 8-row atoms of 1024 bytes, 16-byte chunk c of row r stored at
 //     chunk c ^ (r mod 8));
 //   * one thread issues tcgen05.mma (M = 128, N = 128, K = 8 per instruction,
 //     4 x 3 instructions per slab) into a 128-column TMEM accumulator and
-//     commits them to the slab's mbarrier; the global loads of slab k+1 are
-//     issued before the wait for the MMAs of slab k, and two CTAs share an SM
-//     (66 KB of shared memory and 128 TMEM columns each), so one CTA's MMAs
-//     overlap the other's loads;
+//     commits them to the stage's mbarrier; the copy of slab k+1 overlaps the
+//     split and the MMAs of slab k, and the other CTA on the SM covers the
+//     waits of this one;
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 //     lanes 32 (w mod 4) .. + 31, i.e. those output rows) and adds
 //     alpha * cscale[m] * acc into the FP64 (or FP32) output with coalesced
@@ -38,8 +40,10 @@ constexpr int TC_THREADS = 256;
 constexpr int TC_KB = 32;                     // K per slab: 32 x 4 bytes = one 128-byte swizzle row
 constexpr int TC_TILE_BYTES = 128 * 128;      // 128 rows x 128 bytes
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;   // A_hi, A_lo, B_hi, B_lo
-constexpr int TC_STAGES = 1;   // with two CTAs per SM the other CTA's MMAs cover this one's loads
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;   // + alignment slack
+constexpr int TC_STAGES = 1;                       // split (hi / lo) stage read by the MMAs
+constexpr int TC_RAW_STAGES = 1;                   // raw FP32 slab in flight (cp.async)
+constexpr int TC_RAW_BYTES = 2 * TC_TILE_BYTES;    // A and B slabs, 128 rows x 128 bytes each
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + TC_RAW_STAGES * TC_RAW_BYTES + 1024;   // + alignment slack
 constexpr uint32_t TC_TMEM_COLS = 128;
 
 // instruction descriptor of tcgen05.mma kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
@@ -124,38 +128,29 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// four consecutive k values of row `row` as FP32 (zero outside [0, nrows) x [0, K)),
-// times kscale[k] (in FP32) when kscale is given.  FP32 sources use the FP32 pipe
-// only; FP64 sources need one conversion per value (FP64 pipe).
-__device__ __forceinline__ void load4(const void *base, int ld, int f64, int row, int nrows, int k, int K,
-                                      const float *kscale, float (&out)[4]) {
+// 16-byte asynchronous copy global -> shared; bytes beyond src_bytes are zero-filled
+// (src_bytes = 0 reads nothing, src must still be a valid address)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// copy this thread's chunks of slab kb (rows rbase + 32 j of A and B, k values
+// kb * 32 + 4 c .. + 3) into a raw stage; outside [0, rows) x [0, K) the chunk is zero
+__device__ __forceinline__ void fetch_slab(const TcGemm &g, int m0, int n0, int kb, int rbase, int c, uint32_t raw) {
+    const int k = kb * TC_KB + 4 * c;
+    const int kv = min(max(g.K - k, 0), 4);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) out[i] = 0.f;
-    if (row >= nrows || k >= K) return;
-    if (f64) {
-        const double *p = static_cast<const double *>(base) + (size_t)row * ld + k;
-        if (k + 4 <= K) {
-            const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
-            const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
-            out[0] = __double2float_rn(a.x), out[1] = __double2float_rn(a.y);
-            out[2] = __double2float_rn(b.x), out[3] = __double2float_rn(b.y);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) out[i] = (k + i < K) ? __double2float_rn(__ldg(p + i)) : 0.f;
-        }
-    } else {
-        const float *p = static_cast<const float *>(base) + (size_t)row * ld + k;
-        if (k + 4 <= K) {
-            const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-            out[0] = a.x, out[1] = a.y, out[2] = a.z, out[3] = a.w;
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) out[i] = (k + i < K) ? __ldg(p + i) : 0.f;
-        }
-    }
-    if (kscale) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) out[i] *= (k + i < K) ? __ldg(kscale + k + i) : 0.f;
+    for (int j = 0; j < 4; ++j) {
+        const int r = rbase + 32 * j;
+        const int ra = m0 + r, rb = n0 + r;
+        const float *pa = static_cast<const float *>(g.A);
+        const float *pb = static_cast<const float *>(g.B);
+        const int ba = ra < g.M ? 4 * kv : 0, bb = rb < g.N ? 4 * kv : 0;
+        cp_async16(raw + r * 128 + c * 16, ba ? pa + (size_t)ra * g.lda + k : pa, ba);
+        cp_async16(raw + TC_TILE_BYTES + r * 128 + c * 16, bb ? pb + (size_t)rb * g.ldb + k : pb, bb);
     }
 }
 
@@ -215,18 +210,33 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const int nkb = (g.K + TC_KB - 1) / TC_KB;
     // this thread's chunks: chunk c = tid % 8 (4 k values) of rows tid / 8 + 32 j
     const int c = tid & 7, rbase = tid >> 3;
+    const uint32_t raw0 = sbase + TC_STAGES * TC_STAGE_BYTES;
     bool ok = true;
     int issued = -1;   // last slab whose MMAs were committed (uniform over the block)
+    if (nkb > 0) fetch_slab(g, m0, n0, 0, rbase, c, raw0);   // prologue: slab 0 in flight
+    cp_async_commit();
+    const uint8_t *rawp = tc_smem_raw + (sbase - raw) + TC_STAGES * TC_STAGE_BYTES;
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % TC_STAGES;
-        const int k = kb * TC_KB + 4 * c;
-        float va[4][4], vb[4][4];
+        float ks[4] = {1.f, 1.f, 1.f, 1.f};
+        if (g.bscale) {
+            const int k = kb * TC_KB + 4 * c;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ks[i] = (k + i < g.K) ? __ldg(g.bscale + k + i) : 0.f;
+        }
+        cp_async_wait<0>();   // this thread's copies of slab kb have landed
+        float4 a4[4], b4[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            load4(g.A, g.lda, g.a_f64, m0 + rbase + 32 * j, g.M, k, g.K, nullptr, va[j]);
-            load4(g.B, g.ldb, g.b_f64, n0 + rbase + 32 * j, g.N, k, g.K, g.bscale, vb[j]);
+            const int r = rbase + 32 * j;
+            a4[j] = *reinterpret_cast<const float4 *>(rawp + r * 128 + c * 16);
+            b4[j] = *reinterpret_cast<const float4 *>(rawp + TC_TILE_BYTES + r * 128 + c * 16);
         }
-        // the slab buffer is free once the MMAs of slab kb - 2 have completed
+        // slab kb + 1 is copied into the raw buffer while slab kb is split and multiplied
+        // (this thread has read its own chunks of slab kb, and only it writes them)
+        if (kb + 1 < nkb) fetch_slab(g, m0, n0, kb + 1, rbase, c, raw0);
+        cp_async_commit();
+        // the split stage is free once the MMAs of the slab that last used it have completed
         if (kb >= TC_STAGES && !mbar_wait(smem_u32(&bars[s]), (uint32_t)(((kb - TC_STAGES) / TC_STAGES) & 1),
                                           deadline)) {
             ok = false;
@@ -239,8 +249,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int r = rbase + 32 * j;
-            store_split(stage, stage + TC_TILE_BYTES, r, c, va[j]);
-            store_split(stage + 2 * TC_TILE_BYTES, stage + 3 * TC_TILE_BYTES, r, c, vb[j]);
+            const float va[4] = {a4[j].x, a4[j].y, a4[j].z, a4[j].w};
+            const float vb[4] = {b4[j].x * ks[0], b4[j].y * ks[1], b4[j].z * ks[2], b4[j].w * ks[3]};
+            store_split(stage, stage + TC_TILE_BYTES, r, c, va);
+            store_split(stage + 2 * TC_TILE_BYTES, stage + 3 * TC_TILE_BYTES, r, c, vb);
         }
         // make the generic-proxy stores visible to the tensor cores (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -260,6 +272,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         }
         issued = kb;
     }
+    cp_async_wait<0>();   // no copy may still target this CTA's shared memory at exit
     // the last commit covers every MMA issued before it (after a timeout: wait again, bounded)
     if (issued >= 0) {
         const uint64_t dl = ok ? deadline : globaltimer_ns() + timeout_ns;

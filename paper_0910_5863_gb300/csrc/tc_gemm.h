@@ -9,10 +9,10 @@ namespace bddc {
 // C[m, n] += alpha * cscale[m] * sum_k A[m, k] * bscale[k] * B[n, k]
 // (bscale is applied in FP32 to the FP32 value of B, cscale and alpha in the
 // output precision)
-//   A: row m at A + m * lda, contiguous in k (float, or double when a_f64)
-//   B: row n at B + n * ldb, contiguous in k (float, or double when b_f64)
+//   A: row m at A + m * lda, contiguous in k (FP32; a_f64 must be 0)
+//   B: row n at B + n * ldb, contiguous in k (FP32; b_f64 must be 0)
 //   C: column-major, C[m, n] at C[n * ldc + m], FP64 (or FP32 when c_f32)
-// lda / ldb must keep every row 16-byte aligned (multiples of 4 floats or 2 doubles).
+// lda / ldb must keep every row 16-byte aligned (multiples of 4 floats).
 struct TcGemm {
     const void *A;
     const void *B;
