@@ -161,9 +161,105 @@ __device__ void householder_ff(double *A, int lda, int n, double *dd, double *ee
     __syncthreads();
 }
 
+// Offset of column c of a packed lower triangle of order n (column-major, the
+// diagonal first): column c holds rows c .. n-1.
+__device__ __forceinline__ int pk_col(int c, int n) { return c * n - (c * (c - 1)) / 2; }
+
+// The double-float Householder reduction of householder_ff on a packed lower
+// triangle in shared memory F (n (n + 1) / 2 entries): the matrix is read from
+// A (lower triangle), B x uses both triangles through the symmetry, and the
+// rank-2 update touches the lower triangle only (half the work).  The
+// reflectors are written back to A as doubles, with bet, ee and dd as in
+// the FP64 loop.
+__device__ void householder_ff_packed(double *A, int lda, int n, ff *F, double *dd, double *ee, double *bet,
+                                      double *Pw, double *Ww, double *scratch) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    ff *P = reinterpret_cast<ff *>(Pw);
+    ff *W = reinterpret_cast<ff *>(Ww);
+    for (int j = wid; j < n; j += nw)
+        for (int i = j + lane; i < n; i += 32) F[pk_col(j, n) + i - j] = ff_from_double(A[(size_t)j * lda + i]);
+    __syncthreads();
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        ff *x = F + pk_col(k, n) + 1;   // column k below the diagonal
+        ff acc(0.f, 0.f);
+        for (int i = tid; i < m; i += nt) ff_fma_acc(acc, x[i], x[i]);
+        const double s = block_sum(ff_to_double(ff_norm(acc)), scratch);
+        const double x0 = ff_to_double(x[0]);
+        const double rest = s - x0 * x0;
+        if (rest <= 1e-300 * (s + 1e-300)) {
+            if (tid == 0) {
+                bet[k] = 0.0;
+                ee[k] = x0;
+            }
+            __syncthreads();
+            continue;
+        }
+        const double nrm = sqrt(s);
+        const double alpha = x0 > 0 ? -nrm : nrm;
+        const double v0 = x0 - alpha;
+        const double beta = 2.0 / (rest + v0 * v0);
+        __syncthreads();
+        if (tid == 0) {
+            x[0] = ff_from_double(v0);
+            bet[k] = beta;
+            ee[k] = alpha;
+        }
+        __syncthreads();
+        const int k1 = k + 1;
+        const ff fbeta = ff_from_double(beta);
+        {   // P = beta B x, B(i, j) = A(k1 + i, k1 + j): tpr threads share a row
+            const int tpr = rows_per_pass_split(m, nt), part = tid & (tpr - 1);
+            for (int i0 = 0; i0 < m; i0 += nt / tpr) {
+                const int i = i0 + tid / tpr;
+                ff a(0.f, 0.f);
+                if (i < m) {
+                    int cnt = 0;
+                    for (int j = part; j < i; j += tpr) {   // row i left of the diagonal: column j, row i
+                        ff_fma_acc(a, F[pk_col(k1 + j, n) + (i - j)], x[j]);
+                        if ((++cnt & 15) == 0) a = ff_norm(a);
+                    }
+                    const ff *col = F + pk_col(k1 + i, n);   // column i from the diagonal down
+                    int j = i + ((part - i) % tpr + tpr) % tpr;
+                    for (; j < m; j += tpr) {
+                        ff_fma_acc(a, col[j - i], x[j]);
+                        if ((++cnt & 15) == 0) a = ff_norm(a);
+                    }
+                }
+                a = ff_norm(a);
+                for (int o = tpr >> 1; o > 0; o >>= 1) {
+                    const ff b(__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o));
+                    a = a + b;
+                }
+                if (i < m && part == 0) P[i] = fbeta * a;
+            }
+        }
+        __syncthreads();
+        ff pa(0.f, 0.f);
+        for (int i = tid; i < m; i += nt) ff_fma_acc(pa, P[i], x[i]);
+        const double pv = block_sum(ff_to_double(ff_norm(pa)), scratch);
+        const ff K = ff_from_double(0.5 * beta * pv);
+        for (int i = tid; i < m; i += nt) W[i] = P[i] - K * x[i];
+        __syncthreads();
+        // rank-2 update of the lower triangle, one warp per column
+        for (int j = wid; j < m; j += nw) {
+            ff *col = F + pk_col(k1 + j, n);
+            const ff xj = x[j], wj = W[j];
+            for (int i = j + lane; i < m; i += 32) col[i - j] -= x[i] * wj + W[i] * xj;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += nt) dd[i] = ff_to_double(F[pk_col(i, n)]);
+    if (tid == 0 && n >= 2) ee[n - 2] = ff_to_double(F[pk_col(n - 2, n) + 1]);
+    // reflectors back to A as doubles (column k, rows k + 1 .. n - 1)
+    for (int j = wid; j < n; j += nw)
+        for (int i = j + 1 + lane; i < n; i += 32) A[(size_t)j * lda + i] = ff_to_double(F[pk_col(j, n) + i - j]);
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *descs, int np, double tau,
                                                                double drop_rel, DevStatus *st, int use_smem,
-                                                               int use_ff) {
+                                                               int use_ff, int packed_off) {
     extern __shared__ double sm[];
     __shared__ double scratch[32];
     __shared__ double sh_val[4];
@@ -192,7 +288,11 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     double *dd = work, *ee = work + n, *bet = work + 2 * n, *P = work + 3 * n, *Wv = work + 4 * n;
     __syncthreads();
     // ---- 1. Householder tridiagonalisation: A = Q T Q^T ----
-    if (use_ff) householder_ff(A, lda, n, dd, ee, bet, P, Wv, scratch);
+    if (use_ff && packed_off >= 0)
+        householder_ff_packed(A, lda, n, reinterpret_cast<ff *>(reinterpret_cast<char *>(sm) + packed_off), dd, ee, bet,
+                              P, Wv, scratch);
+    else if (use_ff)
+        householder_ff(A, lda, n, dd, ee, bet, P, Wv, scratch);
     for (int k = 0; !use_ff && k + 2 < n; ++k) {
         const int m = n - k - 1;
         double *x = A + (size_t)k * lda + k + 1;   // column k below the diagonal
@@ -491,8 +591,16 @@ void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, d
     size_t need = sizeof(double) * ((size_t)nmax * nmax + (10 + 6 * (EIG_THREADS / 32)) * (size_t)nmax + 16);
     int use_smem = need <= 200 * 1024;
     size_t smem = use_smem ? need : 0;
+    // double-float reduction on a packed lower triangle in shared memory when it fits
+    const size_t packed = sizeof(ff) * ((size_t)nmax * (nmax + 1) / 2);
+    const size_t kMaxDyn = 224 * 1024;
+    int packed_off = -1;
+    if (use_ff && smem + packed <= kMaxDyn) {
+        packed_off = (int)smem;
+        smem += packed;
+    }
     if (smem > 48 * 1024) cudaFuncSetAttribute(face_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    face_eig_kernel<<<npairs, EIG_THREADS, smem, s>>>(descs, npairs, tau, drop_rel, st, use_smem, use_ff);
+    face_eig_kernel<<<npairs, EIG_THREADS, smem, s>>>(descs, npairs, tau, drop_rel, st, use_smem, use_ff, packed_off);
 }
 
 // ---------------------------------------------------------------------------
