@@ -186,7 +186,7 @@ FP32_LANE_RATE = 152 * 128 * 2.07e9
 
 # DRAM bytes (read + write) of one pcg_kernel launch on the 24^3 Poisson workload, from
 # the ncu capture summarised in profiles/pcg_kernel_poisson24.md; None when unknown.
-PCG_TRAFFIC_POISSON24 = 35121664 + 13056
+PCG_TRAFFIC_POISSON24 = 35121152 + 13056
 
 
 def _pcg_roofline(solver, phases, iters, hbm, src, workload):
