@@ -238,6 +238,18 @@ BDDC_API bddc_status bddc_get_sizes(const bddc_handle *h, int64_t *n_free, int64
 /* Corner node ids (ascending) into nodes[cap]; *n = count. */
 BDDC_API bddc_status bddc_get_corners(const bddc_handle *h, int64_t *nodes, int cap, int *n);
 
+/* Self-test of the bounded device waits that the PCG kernel relies on (the
+ * paper has no counterpart: it is failure detection for this library).  One
+ * cooperative launch of a block per SM meets at the grid barrier of the PCG
+ * kernel, told to wait for `extra` blocks more than exist.  extra = 0: every
+ * block passes, *n_passed = the number of SMs, BDDC_OK.  extra > 0: nothing
+ * releases the barrier, the wait gives up after timeout_s seconds, every
+ * block returns, and the call reports BDDC_ETIMEOUT with *n_passed = 0; the
+ * CUDA context stays usable.  Uses the handle's stream and status word only.
+ * Errors: BDDC_ESTATE (null handle), BDDC_EINVAL (timeout_s <= 0 or > 60),
+ * BDDC_ECUDA. */
+BDDC_API bddc_status bddc_barrier_selftest(bddc_handle *h, int extra, double timeout_s, int *n_passed);
+
 /* The adaptive constraint rows of face f kept by the last bddc_adapt
  * (eq. (d-def) restricted to the face dofs, normalised and orthogonalised
  * with row pivoting; the Remark at the end of Section 3 drops the edge

@@ -26,7 +26,7 @@ EXPORTS = ["bddc_default_options", "bddc_create", "bddc_destroy", "bddc_set_mesh
            "bddc_get_corners", "bddc_get_face_eigs", "bddc_get_interface_dofs", "bddc_get_schur",
            "bddc_apply_preconditioner", "bddc_apply_schur", "bddc_launch_count", "bddc_status_str",
            "bddc_last_error", "bddc_get_phase_times", "bddc_get_local_matrix", "bddc_set_problem",
-           "bddc_set_corners", "bddc_select_corners", "bddc_get_face_rows"]
+           "bddc_set_corners", "bddc_select_corners", "bddc_get_face_rows", "bddc_barrier_selftest"]
 PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
           "analysis_host", "condensed_rhs", "pcg", "recovery"]
 
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         "bddc_set_corners": (i32, [vp, i64, vp]),
         "bddc_select_corners": (i32, [vp, vp]),
         "bddc_get_face_rows": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
+        "bddc_barrier_selftest": (i32, [vp, i32, dbl, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,6 +298,12 @@ class Solver:
         self._check(self.lib.bddc_get_face_eigs(self.h, f, C.byref(i), C.byref(j), buf.ctypes.data, 64, C.byref(nl),
                                                 C.byref(ns), C.byref(nk)))
         return {"pair": (i.value, j.value), "lam": buf[: nl.value].copy(), "selected": ns.value, "kept": nk.value}
+
+    def barrier_selftest(self, extra, timeout_s):
+        """(status, blocks that passed) of the bounded-barrier self-test (no exception)."""
+        n = C.c_int()
+        st = self.lib.bddc_barrier_selftest(self.h, int(extra), float(timeout_s), C.byref(n))
+        return STATUS.get(st, st), n.value
 
     def face_rows(self, f):
         """(global face dofs, kept adaptive rows n_rows x n_dofs) of face f."""

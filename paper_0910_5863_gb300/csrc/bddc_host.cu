@@ -2991,6 +2991,35 @@ bddc_status bddc_get_face_eigs(const bddc_handle *h, int f, int32_t *i, int32_t 
     return BDDC_OK;
 }
 
+bddc_status bddc_barrier_selftest(bddc_handle *h, int extra, double timeout_s, int *n_passed) {
+    if (!h) return BDDC_ESTATE;
+    if (!(timeout_s > 0.0 && timeout_s <= 60.0)) return BDDC_EINVAL;
+    try {
+        reset_status(h);
+        int *passed = h->ar.get_t<int>("selftest_passed", 1);
+        BDDC_CUDA(cudaMemsetAsync(passed, 0, sizeof(int), h->stream));
+        BDDC_CUDA(launch_barrier_selftest(h->dst, extra, timeout_s, passed, h->stream));
+        h->launches++;
+        int hp = 0;
+        DevStatus hs;
+        BDDC_CUDA(cudaMemcpyAsync(&hp, passed, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaMemcpyAsync(&hs, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        if (n_passed) *n_passed = hp;
+        reset_status(h);
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        if (hs.code == BDDC_DEV_ERR_TIMEOUT) {
+            h->err = "barrier self-test: the bounded wait gave up after " + std::to_string(timeout_s) + " s";
+            return BDDC_ETIMEOUT;
+        }
+        if (hs.code != 0) return BDDC_ECUDA;
+    } catch (const Error &e) {
+        h->err = e.msg;
+        return (bddc_status)e.status;
+    }
+    return BDDC_OK;
+}
+
 bddc_status bddc_get_face_rows(const bddc_handle *h, int f, int64_t *gdofs, double *rows, int cap_rows,
                                int cap_dofs, int *n_rows, int *n_dofs) {
     if (!h || !h->have_mesh) return BDDC_ESTATE;

@@ -342,6 +342,23 @@ cudaError_t launch_pcg(const IfaceOps &ops, const PcgBuffers &buf, int mode, dou
     return cudaLaunchCooperativeKernel((void *)pcg_kernel, dim3(nblocks), dim3(PCG_THREADS), args, smem, s);
 }
 
+// Self-test of the bounded grid barrier: every block waits for `expect` arrivals.
+// With expect > gridDim.x the barrier is never released, the wait runs out after
+// timeout_ns, BDDC_DEV_ERR_TIMEOUT is recorded and every block returns.
+__global__ void barrier_selftest_kernel(DevStatus *st, unsigned expect, uint64_t timeout_ns, int *passed) {
+    if (grid_barrier(st, expect, timeout_ns) && threadIdx.x == 0) atomicAdd(passed, 1);
+}
+
+cudaError_t launch_barrier_selftest(DevStatus *st, int extra, double timeout_s, int *passed, cudaStream_t s) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    unsigned expect = (unsigned)(nsm + (extra > 0 ? extra : 0));
+    uint64_t tns = (uint64_t)(timeout_s * 1e9);
+    void *args[] = {&st, &expect, &tns, &passed};
+    return cudaLaunchCooperativeKernel((void *)barrier_selftest_kernel, dim3(nsm), dim3(128), args, 0, s);
+}
+
 __global__ void iface_assemble_kernel(IfaceOps o, const double *packed, double *out) {
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < o.nG; x += gridDim.x * blockDim.x) {
         double v = 0.0;

@@ -63,6 +63,11 @@ enum PcgMode { PCG_SOLVE = 0, PCG_APPLY_M = 1, PCG_APPLY_S = 2 };
 cudaError_t launch_pcg(const IfaceOps &ops, const PcgBuffers &buf, int mode, double tol, int maxit,
                        DevStatus *st, double timeout_s, cudaStream_t s, int *nblocks_out);
 
+// One cooperative launch (a block per SM) through the bounded grid barrier of the PCG kernel,
+// told to wait for `extra` more blocks than exist (0: a normal barrier).  *passed counts the
+// blocks that got through; a timeout is recorded in st.
+cudaError_t launch_barrier_selftest(DevStatus *st, int extra, double timeout_s, int *passed, cudaStream_t s);
+
 // Weights: delta(k) = diag_i(k) / sum over the substructures sharing the dof.
 void launch_weights(const IfaceOps &ops, const double *diag_packed, double *total, double *delta_packed,
                     cudaStream_t s);
