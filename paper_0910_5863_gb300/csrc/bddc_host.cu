@@ -1527,6 +1527,19 @@ struct RefineJob {  // A_II X = B for one substructure, X starts at zero
 
 void run_ell(bddc_handle *h, const std::vector<EllProduct> &ps, const std::string &tag) {
     if (ps.empty()) return;
+    if (ps[0].update) {
+        std::vector<int4> items;
+        for (int k = 0; k < (int)ps.size(); ++k) {
+            BDDC_REQUIRE(ps[k].update && ps[k].r0 == 0, BDDC_EINVAL, "internal: mixed ELL product kinds");
+            for (int rb = 0; rb < (ps[k].m + 255) / 256; ++rb)
+                for (int c0 = 0; c0 < ps[k].ncol; c0 += 8) items.push_back(make_int4(k, rb, c0, 0));
+        }
+        auto *dp = h->ar.upload("ell_p_" + tag, ps, h->stream);
+        auto *di = h->ar.upload("ell_u_" + tag, items, h->stream);
+        launch_ell_update(dp, di, (int)items.size(), h->stream);
+        check_launch(h);
+        return;
+    }
     std::vector<int2> items;
     for (int k = 0; k < (int)ps.size(); ++k) {
         const int64_t cnt = (int64_t)ps[k].m * ps[k].ncol;

@@ -89,6 +89,17 @@ __device__ __forceinline__ void ff_fma_acc(ff &acc, ff a, ff b) {
     acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
 }
 
+// acc += a * b for an FP32 b (the same steps as ff_fma_acc with a zero low word of b)
+__device__ __forceinline__ void ff_fma_acc_f(ff &acc, ff a, float b) {
+    const float p = __fmul_rn(a.h, b);
+    float e = fmaf(a.h, b, -p);
+    e = fmaf(a.l, b, e);
+    float s, err;
+    two_sum(acc.h, p, s, err);
+    acc.h = s;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
+}
+
 __device__ __forceinline__ ff ff_norm(ff a) {
     float h, l;
     fast_two_sum(a.h, a.l, h, l);

@@ -70,21 +70,6 @@ __global__ void ell_residual_kernel(const EllProduct *ps, const int2 *items, int
     const int r = p.r0 + i;
     const int cnt = p.ell_cnt[r];
     const int *cols = p.ell_col + r;       // entry-major: consecutive rows are consecutive
-    if (p.update) {
-        // the correction is small, so its product is carried in double-float on the FP32
-        // pipe (FP64 accuracy relative to the correction); only the update of out and of
-        // X uses the FP64 pipe
-        const ff *vf = reinterpret_cast<const ff *>(p.ell_valf) + r;
-        const float *dx = p.dXf + (size_t)c * p.ldx;
-        ff acc(0.f, 0.f);
-        for (int q = 0; q < cnt; ++q) ff_fma_acc(acc, vf[(size_t)q * p.ell_n], ff(dx[cols[(size_t)q * p.ell_n]], 0.f));
-        const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
-        const double res = b - ff_to_double(ff_norm(acc));
-        p.out[(size_t)c * p.ldo + i] = res;
-        if (p.outf) p.outf[(size_t)c * p.ldo + i] = (float)res;
-        if (p.Xu) p.Xu[(size_t)c * p.ldx + r] += (double)dx[r];
-        return;
-    }
     const double *vals = p.ell_val + r;
     const double *x = p.X + (size_t)c * p.ldx;
     double acc = 0.0;
@@ -92,6 +77,49 @@ __global__ void ell_residual_kernel(const EllProduct *ps, const int2 *items, int
     const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
     p.out[(size_t)c * p.ldo + i] = b - acc;
     if (p.outf) p.outf[(size_t)c * p.ldo + i] = (float)(b - acc);
+}
+
+// Update form (p.update != 0): out[r, c] = B[r, c] - sum_q val[r, q] dX[col[r, q], c] and
+// Xu[r, c] += dX[r, c] for r < m (r0 = 0).  The correction is small, so its product
+// is carried in double-float on the FP32 pipe (FP64 accuracy relative to the
+// correction); only the update of out and of X uses the FP64 pipe.  Thread per
+// (row, 8 consecutive columns), rows fastest: a row's ELL entries are read once
+// for the 8 columns, and the gathers of the 8 dX columns, which neighbouring rows
+// share, stay in L1.  items: (product, 256-row block, first column, unused).
+constexpr int kEllCols = 8;
+__global__ void __launch_bounds__(256) ell_update_kernel(const EllProduct *ps, const int4 *items, int nitems) {
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const int4 w = items[it];
+    const EllProduct p = ps[w.x];
+    const int i = w.y * 256 + threadIdx.x;
+    if (i >= p.m) return;
+    const int r = p.r0 + i, c0 = w.z;
+    const int nc = min(kEllCols, p.ncol - c0);
+    const int cnt = p.ell_cnt[r];
+    const int *cols = p.ell_col + r;
+    const ff *vf = reinterpret_cast<const ff *>(p.ell_valf) + r;
+    const float *dx = p.dXf + (size_t)c0 * p.ldx;
+    ff acc[kEllCols];
+#pragma unroll
+    for (int u = 0; u < kEllCols; ++u) acc[u] = ff(0.f, 0.f);
+    for (int q = 0; q < cnt; ++q) {
+        const int k = cols[(size_t)q * p.ell_n];
+        const ff a = vf[(size_t)q * p.ell_n];
+#pragma unroll
+        for (int u = 0; u < kEllCols; ++u)
+            if (u < nc) ff_fma_acc_f(acc[u], a, __ldg(dx + (size_t)u * p.ldx + k));
+    }
+#pragma unroll
+    for (int u = 0; u < kEllCols; ++u) {
+        if (u >= nc) break;
+        const int c = c0 + u;
+        const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
+        const double res = b - ff_to_double(ff_norm(acc[u]));
+        p.out[(size_t)c * p.ldo + i] = res;
+        if (p.outf) p.outf[(size_t)c * p.ldo + i] = (float)res;
+        if (p.Xu) p.Xu[(size_t)c * p.ldx + r] += (double)dx[(size_t)u * p.ldx + r];
+    }
 }
 
 // single right-hand side: x[r] += d[r] sum_k K[r, k] float(d[k] r[k]); one warp per row
@@ -171,6 +199,9 @@ void launch_ell_build(const MixedSub *subs, const int2 *items, int nitems, DevSt
 }
 void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) ell_residual_kernel<<<nitems, 256, 0, s>>>(ps, items, nitems);
+}
+void launch_ell_update(const EllProduct *ps, const int4 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) ell_update_kernel<<<nitems, 256, 0, s>>>(ps, items, nitems);
 }
 void launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) mixed_update_vec_kernel<<<nitems, 256, 0, s>>>(us, items, nitems);
