@@ -1663,6 +1663,9 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     correction(dus0);
     if (multi) run_gathers(h, gX, "dX0_" + tag);
     int done = 1;
+    bool first_check = true;
+    int max_ncol = 0;
+    for (const auto &j : jobs) max_ncol = std::max(max_ncol, j.ncol);
     for (;;) {
         if (!check && done >= corrections) break;
         if (multi && done > 1)
@@ -1670,7 +1673,9 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
         else
             run_ell(h, ps, tag);         // R = B - A X (FP64)
         if (check) {
-            launch_residual_norms(dps, (int)ps.size(), colsums, dcol_off, norms, h->stream);
+            launch_residual_norms(dps, (int)ps.size(), max_ncol, colsums, dcol_off, norms, first_check ? 1 : 0,
+                                  h->stream);
+            first_check = false;
             check_launch(h);
             BDDC_CUDA(cudaMemcpyAsync(hn.data(), norms, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             BDDC_CUDA(cudaStreamSynchronize(h->stream));

@@ -138,28 +138,34 @@ __global__ void mixed_update_vec_kernel(const MixedUpdate *us, const int2 *items
     if (lane == 0) u.X[r] += u.d[r] * (double)acc;
 }
 
-// per product: sums of R^2 and B^2 (for the refinement check).  Blocks =
-// (product, column); the per-column sums are reduced in column order by
-// residual_norms_finish_kernel, so the result is deterministic.
-__global__ void residual_norms_kernel(const EllProduct *ps, int np, double *colsums, const int *col_off) {
-    __shared__ double scratch[32];
+// per product: sums of R^2 and B^2 (for the refinement check).  One warp per
+// column (eight loads in flight per lane), eight columns per block; the
+// per-column sums are reduced in column order by residual_norms_finish_kernel, so
+// the result is deterministic.  with_b = 0 keeps the B^2 sums of an earlier call
+// (B does not change during a refinement).
+__global__ void residual_norms_kernel(const EllProduct *ps, int np, double *colsums, const int *col_off, int with_b) {
     const int k = blockIdx.y;
     if (k >= np) return;
     const EllProduct p = ps[k];
-    for (int c = blockIdx.x; c < p.ncol; c += gridDim.x) {
-        double rr = 0.0, bb = 0.0;
-        const double *o = p.out + (size_t)c * p.ldo;
-        const double *b = p.B ? p.B + (size_t)c * p.ldb : nullptr;
-        for (int i = threadIdx.x; i < p.m; i += blockDim.x) {
-            rr += o[i] * o[i];
-            if (b) bb += b[i] * b[i];
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= p.ncol) return;
+    auto sumsq = [&](const double *col) {
+        double acc = 0.0;
+        for (int i0 = lane; i0 < p.m; i0 += 256) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (i0 + 32 * u < p.m) ? col[i0 + 32 * u] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += v[u] * v[u];
         }
-        rr = block_sum(rr, scratch);
-        bb = block_sum(bb, scratch);
-        if (threadIdx.x == 0) {
-            colsums[2 * (col_off[k] + c)] = rr;
-            colsums[2 * (col_off[k] + c) + 1] = bb;
-        }
+        return warp_sum(acc);
+    };
+    const double rr = sumsq(p.out + (size_t)c * p.ldo);
+    const double bb = (with_b && p.B) ? sumsq(p.B + (size_t)c * p.ldb) : 0.0;
+    if (lane == 0) {
+        colsums[2 * (col_off[k] + c)] = rr;
+        if (with_b) colsums[2 * (col_off[k] + c) + 1] = bb;
     }
 }
 
@@ -206,10 +212,10 @@ void launch_ell_update(const EllProduct *ps, const int4 *items, int nitems, cuda
 void launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, cudaStream_t s) {
     if (nitems > 0) mixed_update_vec_kernel<<<nitems, 256, 0, s>>>(us, items, nitems);
 }
-void launch_residual_norms(const EllProduct *ps, int np, double *colsums, const int *col_off, double *out,
-                           cudaStream_t s) {
-    if (np <= 0) return;
-    residual_norms_kernel<<<dim3(64, np), 256, 0, s>>>(ps, np, colsums, col_off);
+void launch_residual_norms(const EllProduct *ps, int np, int max_ncol, double *colsums, const int *col_off,
+                           double *out, int with_b, cudaStream_t s) {
+    if (np <= 0 || max_ncol <= 0) return;
+    residual_norms_kernel<<<dim3((max_ncol + 7) / 8, np), 256, 0, s>>>(ps, np, colsums, col_off, with_b);
     residual_norms_finish_kernel<<<(np + 127) / 128, 128, 0, s>>>(colsums, col_off, np, out);
 }
 void launch_symmetrize(double *const *S, const int *n, const int *ld, int ns, cudaStream_t s) {

@@ -64,8 +64,8 @@ void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cu
 void launch_ell_update(const EllProduct *ps, const int4 *items, int nitems, cudaStream_t s);
 // out[2k] = |R_k|^2, out[2k+1] = |B_k|^2; colsums holds 2 doubles per column of all products,
 // col_off (np + 1) the first column of each product
-void launch_residual_norms(const EllProduct *ps, int np, double *colsums, const int *col_off, double *out,
-                           cudaStream_t s);
+void launch_residual_norms(const EllProduct *ps, int np, int max_ncol, double *colsums, const int *col_off,
+                           double *out, int with_b, cudaStream_t s);
 void launch_symmetrize(double *const *S, const int *n, const int *ld, int ns, cudaStream_t s);
 
 }  // namespace bddc
