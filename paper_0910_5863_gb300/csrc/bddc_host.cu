@@ -1527,27 +1527,17 @@ struct RefineJob {  // A_II X = B for one substructure, X starts at zero
 
 void run_ell(bddc_handle *h, const std::vector<EllProduct> &ps, const std::string &tag) {
     if (ps.empty()) return;
-    if (ps[0].update) {
-        std::vector<int4> items;
-        for (int k = 0; k < (int)ps.size(); ++k) {
-            BDDC_REQUIRE(ps[k].update && ps[k].r0 == 0, BDDC_EINVAL, "internal: mixed ELL product kinds");
-            for (int rb = 0; rb < (ps[k].m + 255) / 256; ++rb)
-                for (int c0 = 0; c0 < ps[k].ncol; c0 += 8) items.push_back(make_int4(k, rb, c0, 0));
-        }
-        auto *dp = h->ar.upload("ell_p_" + tag, ps, h->stream);
-        auto *di = h->ar.upload("ell_u_" + tag, items, h->stream);
-        launch_ell_update(dp, di, (int)items.size(), h->stream);
-        check_launch(h);
-        return;
-    }
-    std::vector<int2> items;
+    const int update = ps[0].update ? 1 : 0;
+    std::vector<int4> items;
     for (int k = 0; k < (int)ps.size(); ++k) {
-        const int64_t cnt = (int64_t)ps[k].m * ps[k].ncol;
-        for (int64_t b = 0; b < (cnt + 255) / 256; ++b) items.push_back(make_int2(k, (int)b));
+        BDDC_REQUIRE((ps[k].update != 0) == (update != 0) && (!update || ps[k].r0 == 0), BDDC_EINVAL,
+                     "internal: mixed ELL product kinds");
+        for (int rb = 0; rb < (ps[k].m + 255) / 256; ++rb)
+            for (int c0 = 0; c0 < ps[k].ncol; c0 += 8) items.push_back(make_int4(k, rb, c0, 0));
     }
     auto *dp = h->ar.upload("ell_p_" + tag, ps, h->stream);
     auto *di = h->ar.upload("ell_i_" + tag, items, h->stream);
-    launch_ell_residual(dp, di, (int)items.size(), h->stream);
+    launch_ell_product(dp, di, (int)items.size(), update, h->stream);
     check_launch(h);
 }
 
@@ -1588,6 +1578,7 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
     std::vector<TcGemm> tg;
     std::vector<GatherOp> gB, gX;   // float(B) into the FP32 residual copy; X += dX after the first correction
     std::vector<int2> vitems;
+    int max_nI = 0;
     ZeroList zx;
     for (int k = 0; k < (int)jobs.size(); ++k) {
         const auto &j = jobs[k];
@@ -1613,7 +1604,8 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
         if (!multi) {
             us.push_back(MixedUpdate{K, ldk, eq, j.R, j.ldr, j.X, j.ldx, sd.nI, j.ncol});
             us0.push_back(MixedUpdate{K, ldk, eq, j.B, j.ldb, j.X, j.ldx, sd.nI, j.ncol});
-            for (int a = 0; a < (sd.nI + 7) / 8; ++a) vitems.push_back(make_int2(k, a));
+            for (int a = 0; a < (sd.nI + 31) / 32; ++a) vitems.push_back(make_int2(k, a));
+            max_nI = std::max(max_nI, sd.nI);
         } else {
             // dX[r, c] = d[r] sum_k K_s[r, k] d[k] R[k, c]: rows of the symmetric K_s are its columns
             float *dX = h->ar.get_t<float>("dX_" + tag + t, (size_t)j.ldx * j.ncol);
@@ -1649,7 +1641,7 @@ int refine(bddc_handle *h, const std::vector<RefineJob> &jobs, int corrections, 
         if (multi) {
             launch_tc_gemm(dtg, dti, (int)titems.size(), h->dst, h->opt.timeout_s, h->stream);
         } else {
-            launch_mixed_update_vec(d, dvi, (int)vitems.size(), h->stream);
+            BDDC_CUDA(launch_mixed_update_vec(d, dvi, (int)vitems.size(), max_nI, h->stream));
         }
         check_launch(h);
     };

@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "mixed.h"
 #include "ff.cuh"
+#include <algorithm>
 
 namespace bddc {
 
@@ -57,37 +58,22 @@ __global__ void ell_build_kernel(const MixedSub *subs, const int2 *items, int ni
     if (lane == 0) s.ell_cnt[r] = cnt;
 }
 
-// out[r, c] = B[r, c] - sum_q val[r, q] X[col[r, q], c]   for r in [r0, r0 + m), c < ncol
-// (B may be null = 0).  Thread per (r, c), r fastest.
-__global__ void ell_residual_kernel(const EllProduct *ps, const int2 *items, int nitems) {
-    const int it = blockIdx.x;
-    if (it >= nitems) return;
-    const int2 w = items[it];
-    const EllProduct p = ps[w.x];
-    const int e = w.y * blockDim.x + threadIdx.x;   // m * ncol < 2^31
-    if (e >= p.m * p.ncol) return;
-    const int c = e / p.m, i = e - c * p.m;
-    const int r = p.r0 + i;
-    const int cnt = p.ell_cnt[r];
-    const int *cols = p.ell_col + r;       // entry-major: consecutive rows are consecutive
-    const double *vals = p.ell_val + r;
-    const double *x = p.X + (size_t)c * p.ldx;
-    double acc = 0.0;
-    for (int q = 0; q < cnt; ++q) acc += vals[(size_t)q * p.ell_n] * x[cols[(size_t)q * p.ell_n]];
-    const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
-    p.out[(size_t)c * p.ldo + i] = b - acc;
-    if (p.outf) p.outf[(size_t)c * p.ldo + i] = (float)(b - acc);
-}
-
-// Update form (p.update != 0): out[r, c] = B[r, c] - sum_q val[r, q] dX[col[r, q], c] and
-// Xu[r, c] += dX[r, c] for r < m (r0 = 0).  The correction is small, so its product
-// is carried in double-float on the FP32 pipe (FP64 accuracy relative to the
-// correction); only the update of out and of X uses the FP64 pipe.  Thread per
-// (row, 8 consecutive columns), rows fastest: a row's ELL entries are read once
-// for the 8 columns, and the gathers of the 8 dX columns, which neighbouring rows
+// Sparse products with the interior columns of A_i (ELL form), thread per (row,
+// 8 consecutive columns), rows fastest: a row's ELL entries are read once for the
+// 8 columns, and the gathers of the 8 X (or dX) columns, which neighbouring rows
 // share, stay in L1.  items: (product, 256-row block, first column, unused).
+//   FP64 form:   out[r, c] = B[r, c] - sum_q val[r, q] X[col[r, q], c]
+//                for r in [r0, r0 + m), c < ncol (B may be null = 0).
+//   Update form (UPDATE, p.update != 0, r0 = 0): out[r, c] = B[r, c] -
+//                sum_q val[r, q] dX[col[r, q], c] and Xu[r, c] += dX[r, c].  The
+//                correction is small, so its product is carried in double-float on
+//                the FP32 pipe (FP64 accuracy relative to the correction); only the
+//                update of out and of X uses the FP64 pipe.
+// Each (r, c) sums its entries in row order, one accumulator, as a thread per
+// (r, c) would.
 constexpr int kEllCols = 8;
-__global__ void __launch_bounds__(256) ell_update_kernel(const EllProduct *ps, const int4 *items, int nitems) {
+template <bool UPDATE>
+__global__ void __launch_bounds__(256) ell_block_kernel(const EllProduct *ps, const int4 *items, int nitems) {
     const int it = blockIdx.x;
     if (it >= nitems) return;
     const int4 w = items[it];
@@ -97,45 +83,92 @@ __global__ void __launch_bounds__(256) ell_update_kernel(const EllProduct *ps, c
     const int r = p.r0 + i, c0 = w.z;
     const int nc = min(kEllCols, p.ncol - c0);
     const int cnt = p.ell_cnt[r];
-    const int *cols = p.ell_col + r;
-    const ff *vf = reinterpret_cast<const ff *>(p.ell_valf) + r;
-    const float *dx = p.dXf + (size_t)c0 * p.ldx;
-    ff acc[kEllCols];
+    const int *cols = p.ell_col + r;   // entry-major: consecutive rows are consecutive
+    if (UPDATE) {
+        const ff *vf = reinterpret_cast<const ff *>(p.ell_valf) + r;
+        const float *dx = p.dXf + (size_t)c0 * p.ldx;
+        ff acc[kEllCols];
 #pragma unroll
-    for (int u = 0; u < kEllCols; ++u) acc[u] = ff(0.f, 0.f);
-    for (int q = 0; q < cnt; ++q) {
-        const int k = cols[(size_t)q * p.ell_n];
-        const ff a = vf[(size_t)q * p.ell_n];
+        for (int u = 0; u < kEllCols; ++u) acc[u] = ff(0.f, 0.f);
+        for (int q = 0; q < cnt; ++q) {
+            const int k = cols[(size_t)q * p.ell_n];
+            const ff a = vf[(size_t)q * p.ell_n];
 #pragma unroll
-        for (int u = 0; u < kEllCols; ++u)
-            if (u < nc) ff_fma_acc_f(acc[u], a, __ldg(dx + (size_t)u * p.ldx + k));
-    }
+            for (int u = 0; u < kEllCols; ++u)
+                if (u < nc) ff_fma_acc_f(acc[u], a, __ldg(dx + (size_t)u * p.ldx + k));
+        }
 #pragma unroll
-    for (int u = 0; u < kEllCols; ++u) {
-        if (u >= nc) break;
-        const int c = c0 + u;
-        const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
-        const double res = b - ff_to_double(ff_norm(acc[u]));
-        p.out[(size_t)c * p.ldo + i] = res;
-        if (p.outf) p.outf[(size_t)c * p.ldo + i] = (float)res;
-        if (p.Xu) p.Xu[(size_t)c * p.ldx + r] += (double)dx[(size_t)u * p.ldx + r];
+        for (int u = 0; u < kEllCols; ++u) {
+            if (u >= nc) break;
+            const int c = c0 + u;
+            const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
+            const double res = b - ff_to_double(ff_norm(acc[u]));
+            p.out[(size_t)c * p.ldo + i] = res;
+            if (p.outf) p.outf[(size_t)c * p.ldo + i] = (float)res;
+            if (p.Xu) p.Xu[(size_t)c * p.ldx + r] += (double)dx[(size_t)u * p.ldx + r];
+        }
+    } else {
+        const double *vals = p.ell_val + r;
+        const double *x = p.X + (size_t)c0 * p.ldx;
+        double acc[kEllCols];
+#pragma unroll
+        for (int u = 0; u < kEllCols; ++u) acc[u] = 0.0;
+        for (int q = 0; q < cnt; ++q) {
+            const int k = cols[(size_t)q * p.ell_n];
+            const double a = vals[(size_t)q * p.ell_n];
+#pragma unroll
+            for (int u = 0; u < kEllCols; ++u)
+                if (u < nc) acc[u] += a * __ldg(x + (size_t)u * p.ldx + k);
+        }
+#pragma unroll
+        for (int u = 0; u < kEllCols; ++u) {
+            if (u >= nc) break;
+            const int c = c0 + u;
+            const double b = p.B ? p.B[(size_t)c * p.ldb + i] : 0.0;
+            p.out[(size_t)c * p.ldo + i] = b - acc[u];
+            if (p.outf) p.outf[(size_t)c * p.ldo + i] = (float)(b - acc[u]);
+        }
     }
 }
 
-// single right-hand side: x[r] += d[r] sum_k K[r, k] float(d[k] r[k]); one warp per row
-// (K is symmetric, so row r is read as column r).  items: (update, block of 8 rows)
-__global__ void mixed_update_vec_kernel(const MixedUpdate *us, const int2 *items, int nitems) {
+// single right-hand side: x[r] += d[r] sum_k K[r, k] w[k], w = float(d o R).  A block
+// takes 32 rows of one update: it forms w in shared memory (one FP64 product per
+// entry of the vector, not per matrix entry), then every warp sums 4 rows with
+// 16-byte loads of K, four in flight per lane (K is symmetric: row r is column r).
+// items: (update, block of 32 rows); dynamic shared memory: max n floats.
+__global__ void __launch_bounds__(256) mixed_update_vec_kernel(const MixedUpdate *us, const int2 *items, int nitems) {
+    extern __shared__ float wsh[];
     const int it = blockIdx.x;
     if (it >= nitems) return;
     const int2 w = items[it];
     const MixedUpdate u = us[w.x];
-    const int lane = threadIdx.x & 31, r = w.y * 8 + (threadIdx.x >> 5);
-    if (r >= u.n) return;
-    const float *kr = u.K + (size_t)r * u.ldk;
-    float acc = 0.f;
-    for (int k = lane; k < u.n; k += 32) acc += kr[k] * (float)(u.d[k] * u.R[k]);
-    acc = warp_sum(acc);
-    if (lane == 0) u.X[r] += u.d[r] * (double)acc;
+    for (int k = threadIdx.x; k < u.n; k += blockDim.x) wsh[k] = (float)(u.d[k] * u.R[k]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n4 = u.n >> 2;   // full float4 chunks; K rows are 16-byte aligned (ldk % 8 == 0)
+    const float4 *w4 = reinterpret_cast<const float4 *>(wsh);
+    for (int q = 0; q < 4; ++q) {
+        const int r = w.y * 32 + wid * 4 + q;
+        if (r >= u.n) break;
+        const float *kr = u.K + (size_t)r * u.ldk;
+        const float4 *k4 = reinterpret_cast<const float4 *>(kr);
+        float acc = 0.f;
+        for (int c0 = lane; c0 < n4; c0 += 128) {
+            float4 v[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) v[t] = (c0 + 32 * t < n4) ? __ldg(k4 + c0 + 32 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (c0 + 32 * t < n4) {
+                    const float4 x = w4[c0 + 32 * t];
+                    acc += v[t].x * x.x + v[t].y * x.y + v[t].z * x.z + v[t].w * x.w;
+                }
+            }
+        }
+        for (int k = 4 * n4 + lane; k < u.n; k += 32) acc += kr[k] * wsh[k];   // the last n % 4 entries
+        acc = warp_sum(acc);
+        if (lane == 0) u.X[r] += u.d[r] * (double)acc;
+    }
 }
 
 // per product: sums of R^2 and B^2 (for the refinement check).  One warp per
@@ -203,14 +236,22 @@ void launch_equilibrate(const MixedSub *subs, int nsub, cudaStream_t s) {
 void launch_ell_build(const MixedSub *subs, const int2 *items, int nitems, DevStatus *st, cudaStream_t s) {
     if (nitems > 0) ell_build_kernel<<<(nitems + 7) / 8, 256, 0, s>>>(subs, items, nitems, st);
 }
-void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cudaStream_t s) {
-    if (nitems > 0) ell_residual_kernel<<<nitems, 256, 0, s>>>(ps, items, nitems);
+void launch_ell_product(const EllProduct *ps, const int4 *items, int nitems, int update, cudaStream_t s) {
+    if (nitems <= 0) return;
+    if (update)
+        ell_block_kernel<true><<<nitems, 256, 0, s>>>(ps, items, nitems);
+    else
+        ell_block_kernel<false><<<nitems, 256, 0, s>>>(ps, items, nitems);
 }
-void launch_ell_update(const EllProduct *ps, const int4 *items, int nitems, cudaStream_t s) {
-    if (nitems > 0) ell_update_kernel<<<nitems, 256, 0, s>>>(ps, items, nitems);
-}
-void launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, cudaStream_t s) {
-    if (nitems > 0) mixed_update_vec_kernel<<<nitems, 256, 0, s>>>(us, items, nitems);
+cudaError_t launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, int max_n, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float) * (size_t)std::max(max_n, 4);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(mixed_update_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    mixed_update_vec_kernel<<<nitems, 256, smem, s>>>(us, items, nitems);
+    return cudaSuccess;
 }
 void launch_residual_norms(const EllProduct *ps, int np, int max_ncol, double *colsums, const int *col_off,
                            double *out, int with_b, cudaStream_t s) {

@@ -52,16 +52,15 @@ struct MixedUpdate {
     int n, ncol;
 };
 
-// ncol == 1 variant; items: (update, block of 8 rows)
-void launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, cudaStream_t s);
+// ncol == 1 variant; items: (update, block of 32 rows); max_n = largest n (shared memory)
+cudaError_t launch_mixed_update_vec(const MixedUpdate *us, const int2 *items, int nitems, int max_n, cudaStream_t s);
 
 void launch_equilibrate(const MixedSub *subs, int nsub, cudaStream_t s);
 // items: (sub, row), one warp each
 void launch_ell_build(const MixedSub *subs, const int2 *items, int nitems, DevStatus *st, cudaStream_t s);
-// items: (product, block of 256 (r, c) pairs)
-void launch_ell_residual(const EllProduct *ps, const int2 *items, int nitems, cudaStream_t s);
-// products with update != 0; items: (product, 256-row block, first of 8 columns, unused)
-void launch_ell_update(const EllProduct *ps, const int4 *items, int nitems, cudaStream_t s);
+// all products of one call have the same form (update = p.update);
+// items: (product, 256-row block, first of 8 columns, unused)
+void launch_ell_product(const EllProduct *ps, const int4 *items, int nitems, int update, cudaStream_t s);
 // out[2k] = |R_k|^2, out[2k+1] = |B_k|^2; colsums holds 2 doubles per column of all products,
 // col_off (np + 1) the first column of each product
 void launch_residual_norms(const EllProduct *ps, int np, int max_ncol, double *colsums, const int *col_off,
