@@ -20,6 +20,7 @@
 #include <cstring>
 #include <iterator>
 #include <map>
+#include <memory>
 #include <numeric>
 #include <set>
 #include <string>
@@ -612,8 +613,9 @@ void classify(bddc_handle *h) {
         int cnt;
         int s[kMaxSet];
     };
-    std::vector<NodeSubs> nsv(nn);
-    for (auto &x : nsv) x.cnt = 0;
+    std::unique_ptr<NodeSubs[]> nsv_buf(new NodeSubs[nn]);   // only the counts are initialised
+    NodeSubs *nsv = nsv_buf.get();
+    for (int64_t v = 0; v < nn; ++v) nsv[v].cnt = 0;
     auto add_sub = [&](int64_t v, int sb) {
         NodeSubs &x = nsv[v];
         for (int k = 0; k < x.cnt; ++k)
@@ -628,7 +630,7 @@ void classify(bddc_handle *h) {
         for (int64_t e = 0; e < ne; ++e)
             for (int a = 0; a < 8; ++a) add_sub(h->elems[e * 8 + a], h->esub[e]);
     }
-    for (auto &x : nsv) std::sort(x.s, x.s + x.cnt);
+    for (int64_t v = 0; v < nn; ++v) std::sort(nsv[v].s, nsv[v].s + nsv[v].cnt);
     // set ids: {s} -> s for the one-substructure sets; interface sets are sorted by key
     h->sets.clear();
     for (int sb = 0; sb < h->nsub; ++sb) h->sets.push_back({sb});
@@ -803,15 +805,17 @@ void classify(bddc_handle *h) {
         sd.ld = round_up(std::max(sd.n, 1), 8);
         sd.ldS = round_up(std::max(sd.nG, 1), 8);
     }
-    // interface numbering and gather maps
-    std::vector<int64_t> all;
-    for (auto &sd : h->subs) all.insert(all.end(), sd.gG.begin(), sd.gG.end());
-    std::sort(all.begin(), all.end());
-    all.erase(std::unique(all.begin(), all.end()), all.end());
-    h->iface_gdof = all;
-    h->nG = (int)all.size();
+    // interface numbering (ascending global dof) and gather maps
     std::vector<int> gidx(h->nfree, -1);
-    for (int x = 0; x < h->nG; ++x) gidx[all[x]] = x;
+    for (auto &sd : h->subs)
+        for (int64_t g : sd.gG) gidx[g] = 0;
+    h->iface_gdof.clear();
+    for (int64_t g = 0; g < h->nfree; ++g)
+        if (gidx[g] == 0) {
+            gidx[g] = (int)h->iface_gdof.size();
+            h->iface_gdof.push_back(g);
+        }
+    h->nG = (int)h->iface_gdof.size();
     h->offG.assign(ns, 0);
     int64_t off = 0, offI = 0;
     h->gptr.assign(h->nG + 1, 0);
@@ -900,21 +904,30 @@ void classify(bddc_handle *h) {
     const auto tc_faces = std::chrono::steady_clock::now();
     // face pairs
     h->faces.clear();
-    std::vector<int> pi(h->nfree, -1), pj(h->nfree, -1);
+    h->faces.reserve(face_list.size());
+    std::vector<int> pj(h->nfree, -1);   // position of a dof in sj's interface list
+    // per set: the face (index + 1) it was last tested for, and whether it holds both substructures
+    std::vector<int> set_stamp(h->sets.size(), 0);
+    std::vector<char> set_both(h->sets.size(), 0);
+    int face_no = 0;
     for (auto &fl : face_list) {
         FacePair fp;
         fp.i = fl.first.first;
         fp.j = fl.first.second;
+        ++face_no;
         auto &si = h->subs[fp.i], &sj = h->subs[fp.j];
-        for (int k = 0; k < si.nG; ++k) pi[si.gG[k]] = k;
         for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = k;
         std::vector<int64_t> cn;
         for (int k = 0; k < si.nG; ++k) {
             int64_t g = si.gG[k];
             int64_t v = dof_node[g];
-            const auto &S = h->sets[h->node_set[v]];
-            bool both = std::binary_search(S.begin(), S.end(), fp.i) && std::binary_search(S.begin(), S.end(), fp.j);
-            if (!both) continue;
+            const int sid = h->node_set[v];
+            if (set_stamp[sid] != face_no) {
+                const auto &S = h->sets[sid];
+                set_stamp[sid] = face_no;
+                set_both[sid] = std::binary_search(S.begin(), S.end(), fp.i) && std::binary_search(S.begin(), S.end(), fp.j);
+            }
+            if (!set_both[sid]) continue;
             if (h->is_corner[v]) {
                 fp.ci_pos.push_back(k);
                 fp.cj_pos.push_back(pj[g]);
@@ -922,11 +935,11 @@ void classify(bddc_handle *h) {
                 continue;
             }
             fp.s_g.push_back(g);
+            fp.pos_i.push_back(k);
         }
         // s sorted by global dof (si.gG is sorted so s_g is too)
         for (size_t k = 0; k < fp.s_g.size(); ++k) {
             int64_t g = fp.s_g[k];
-            fp.pos_i.push_back(pi[g]);
             fp.pos_j.push_back(pj[g]);
             const auto &S = h->sets[h->node_set[dof_node[g]]];
             if (S.size() == 2) fp.face_idx.push_back((int)k);
@@ -982,9 +995,8 @@ void classify(bddc_handle *h) {
             fp.N0 = Q;
             fp.nnull = kept;
         }
-        for (int k = 0; k < si.nG; ++k) pi[si.gG[k]] = -1;
         for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = -1;
-        h->faces.push_back(fp);
+        h->faces.push_back(std::move(fp));
     }
     const auto tc_color = std::chrono::steady_clock::now();
     // element colouring (greedy, nodes shared => different colours)
