@@ -89,6 +89,25 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
         }
     }
     int r = kb + nb + w.y * PANEL_ROWS + tid;
+    if constexpr (std::is_same<T, ff>::value) {
+        // Double-float: a fully unrolled solve would be ~10k instructions and thrash the
+        // instruction cache, so the row lives in shared memory (x_c of this thread at
+        // xs[c][tid], conflict-free) and the loops stay rolled; each x_c accumulates its
+        // products without renormalising and is normalised once, as the trailing update does.
+        __shared__ ff xs[NB][PANEL_ROWS];
+        if (r < n) {
+            for (int c = 0; c < nb; ++c) xs[c][tid] = A[(size_t)(kb + c) * ld + r];
+            for (int c = 0; c < nb; ++c) {
+                ff acc(0.f, 0.f);
+#pragma unroll 4
+                for (int k = 0; k < c; ++k) ff_fma_acc(acc, xs[k][tid], Ld[c][k]);
+                const ff v = (xs[c][tid] - ff_norm(acc)) * inv_d[c];
+                xs[c][tid] = v;
+                A[(size_t)(kb + c) * ld + r] = v;
+            }
+        }
+        return;
+    }
     if (r < n) {
         T x[NB];
 #pragma unroll

@@ -202,16 +202,21 @@ __global__ void residual_norms_kernel(const EllProduct *ps, int np, double *cols
     }
 }
 
+// one warp per product: lane-strided column sums, then the fixed warp reduction
 __global__ void residual_norms_finish_kernel(const double *colsums, const int *col_off, int np, double *out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (k >= np) return;
     double rr = 0.0, bb = 0.0;
-    for (int c = col_off[k]; c < col_off[k + 1]; ++c) {
+    for (int c = col_off[k] + lane; c < col_off[k + 1]; c += 32) {
         rr += colsums[2 * c];
         bb += colsums[2 * c + 1];
     }
-    out[2 * k] = rr;
-    out[2 * k + 1] = bb;
+    rr = warp_sum(rr);
+    bb = warp_sum(bb);
+    if (lane == 0) {
+        out[2 * k] = rr;
+        out[2 * k + 1] = bb;
+    }
 }
 
 // S <- (S + S^T) / 2 for n x n column-major blocks
@@ -257,7 +262,7 @@ void launch_residual_norms(const EllProduct *ps, int np, int max_ncol, double *c
                            double *out, int with_b, cudaStream_t s) {
     if (np <= 0 || max_ncol <= 0) return;
     residual_norms_kernel<<<dim3((max_ncol + 7) / 8, np), 256, 0, s>>>(ps, np, colsums, col_off, with_b);
-    residual_norms_finish_kernel<<<(np + 127) / 128, 128, 0, s>>>(colsums, col_off, np, out);
+    residual_norms_finish_kernel<<<(np + 3) / 4, 128, 0, s>>>(colsums, col_off, np, out);
 }
 void launch_symmetrize(double *const *S, const int *n, const int *ld, int ns, cudaStream_t s) {
     if (ns > 0) symmetrize_kernel<<<dim3(64, ns), 256, 0, s>>>(S, n, ld, ns);
