@@ -238,10 +238,13 @@ __global__ void gather_kernel(const GatherOp *ops, const int2 *items, int nitems
     int2 w = items[it];  // x = op, y = column block of 8
     const GatherOp o = ops[w.x];
     int q0 = w.y * 8;
+    // a scale of +-1 (every caller's) is applied as a sign: exact, and no FP64 multiply
+    const int sgn = o.scale == 1.0 ? 1 : (o.scale == -1.0 ? -1 : 0);
     for (int qq = 0; qq < 8; ++qq) {
         int q = q0 + qq;
         if (q >= o.nc) break;
         int cq = o.cmap ? o.cmap[q] : q;
+        const double cs = o.cscale ? o.cscale[q] : 1.0;
         for (int p = threadIdx.x; p < o.nr; p += blockDim.x) {
             if (o.dst_lower && p + o.dst_row_off < q + o.dst_col_off) continue;
             int rp = o.rmap ? o.rmap[p] : p;
@@ -260,21 +263,22 @@ __global__ void gather_kernel(const GatherOp *ops, const int2 *items, int nitems
                                   : o.src[(size_t)b * o.ld_src + a];
                 }
                 if (o.rscale) v *= o.rscale[p];
-                if (o.cscale) v *= o.cscale[q];
+                if (o.cscale) v *= cs;
             }
+            v = sgn == 1 ? v : (sgn == -1 ? -v : o.scale * v);
             const size_t di = (size_t)(q + o.dst_col_off) * o.ld_dst + p + o.dst_row_off;
             if (o.dst_f32) {
                 float *dp = reinterpret_cast<float *>(o.dst) + di;
                 if (o.accumulate)
-                    *dp += (float)(o.scale * v);
+                    *dp += (float)v;
                 else
-                    *dp = (float)(o.scale * v);
+                    *dp = (float)v;
             } else {
                 double *dp = o.dst + di;
                 if (o.accumulate)
-                    *dp += o.scale * v;
+                    *dp += v;
                 else
-                    *dp = o.scale * v;
+                    *dp = v;
             }
         }
     }
