@@ -185,6 +185,25 @@ BDDC_API bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, con
 BDDC_API bddc_status bddc_set_problem(bddc_handle *h, int64_t n_global, int ncomp, int32_t n_sub,
                                       const bddc_subdomain *subs, const double *node_xyz, int mem);
 
+/* Host-only mesh analysis: the classification that bddc_set_mesh_q1 performs
+ * (Section 2: faces, edges, corners by the same rule; Assumptions 1 and 2:
+ * floating substructures and face pairs, corner augmentation), run on the
+ * host without a handle, a GPU or any device memory.  Inputs as in
+ * bddc_set_mesh_q1 (host memory only; coef and nu are not needed).
+ * Outputs (each may be NULL):
+ *   n_free, n_interface   free dofs and interface dofs
+ *   n_corners, n_edges, n_faces   glob counts after Dirichlet nodes are dropped
+ *                         and corners augmented (faces that lost every node
+ *                         to augmentation are not counted)
+ *   n_augmented           face nodes promoted to corners
+ *   corners[corners_cap]  corner node ids, ascending (the first corners_cap)
+ * Errors: BDDC_EINVAL (sizes, ids out of range), BDDC_EASSUMPTION (a
+ * floating substructure whose corners cannot fix its rigid modes). */
+BDDC_API bddc_status bddc_classify_q1(int ncomp, int64_t nn, const double *xyz, int64_t ne, const int64_t *elems,
+                                      const int32_t *elem_sub, int32_t nsub, const uint8_t *dirichlet,
+                                      int64_t *n_free, int64_t *n_interface, int *n_corners, int *n_edges,
+                                      int *n_faces, int *n_augmented, int64_t *corners, int corners_cap);
+
 /* Replaces the corners (Section 2: the coarse point constraints, W^c of the
  * paper's Fig. 3) by the n given node ids (host memory, any order, duplicates
  * ignored); no rule and no augmentation is applied.  Every node must be an

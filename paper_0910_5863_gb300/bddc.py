@@ -26,7 +26,8 @@ EXPORTS = ["bddc_default_options", "bddc_create", "bddc_destroy", "bddc_set_mesh
            "bddc_get_corners", "bddc_get_face_eigs", "bddc_get_interface_dofs", "bddc_get_schur",
            "bddc_apply_preconditioner", "bddc_apply_schur", "bddc_launch_count", "bddc_status_str",
            "bddc_last_error", "bddc_get_phase_times", "bddc_get_local_matrix", "bddc_set_problem",
-           "bddc_set_corners", "bddc_select_corners", "bddc_get_face_rows", "bddc_barrier_selftest"]
+           "bddc_set_corners", "bddc_select_corners", "bddc_get_face_rows", "bddc_barrier_selftest",
+           "bddc_classify_q1"]
 PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
           "analysis_host", "condensed_rhs", "pcg", "recovery"]
 
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH):
         "bddc_select_corners": (i32, [vp, vp]),
         "bddc_get_face_rows": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
         "bddc_barrier_selftest": (i32, [vp, i32, dbl, vp]),
+        "bddc_classify_q1": (i32, [i32, i64, vp, i64, vp, vp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -356,6 +358,27 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.bddc_launch_count(self.h))
+
+
+def classify_mesh(prob):
+    """Host-only mesh analysis of a paper_0910_5863_gb300.problems.Problem (no GPU):
+    dict with n_free, n_interface, n_corners, n_edges, n_faces, n_augmented, corners."""
+    lib = load()
+    xyz = np.ascontiguousarray(prob.xyz, dtype=np.float64)
+    el = np.ascontiguousarray(prob.elems, dtype=np.int64)
+    sub = np.ascontiguousarray(prob.elem_sub, dtype=np.int32)
+    dr = np.ascontiguousarray(prob.dirichlet, dtype=np.uint8)
+    nf, ni = C.c_int64(), C.c_int64()
+    nc, ne, nfa, na = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    cap = xyz.shape[0]
+    corners = np.zeros(cap, dtype=np.int64)
+    st = lib.bddc_classify_q1(prob.ncomp, xyz.shape[0], xyz.ctypes.data, el.shape[0], el.ctypes.data,
+                              sub.ctypes.data, prob.nsub, dr.ctypes.data, C.byref(nf), C.byref(ni), C.byref(nc),
+                              C.byref(ne), C.byref(nfa), C.byref(na), corners.ctypes.data, cap)
+    if st != 0:
+        raise BddcError(st, lib.bddc_status_str(st).decode())
+    return {"n_free": nf.value, "n_interface": ni.value, "n_corners": nc.value, "n_edges": ne.value,
+            "n_faces": nfa.value, "n_augmented": na.value, "corners": corners[: nc.value].copy()}
 
 
 def free_load_vector(prob):

@@ -2796,6 +2796,49 @@ bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double
     });
 }
 
+bddc_status bddc_classify_q1(int ncomp, int64_t nn, const double *xyz, int64_t ne, const int64_t *elems,
+                             const int32_t *elem_sub, int32_t nsub, const uint8_t *dirichlet, int64_t *n_free,
+                             int64_t *n_interface, int *n_corners, int *n_edges, int *n_faces, int *n_augmented,
+                             int64_t *corners, int corners_cap) {
+    if (ncomp != 1 && ncomp != 3) return BDDC_EINVAL;
+    if (nn <= 0 || ne <= 0 || nsub <= 0 || !xyz || !elems || !elem_sub || !dirichlet) return BDDC_EINVAL;
+    if (corners_cap > 0 && !corners) return BDDC_EINVAL;
+    try {
+        // a handle that never touches the device: only the host mesh fields are set
+        std::unique_ptr<bddc_handle> hp(new bddc_handle());
+        bddc_handle *h = hp.get();
+        h->ncomp = ncomp;
+        h->nn = nn;
+        h->ne = ne;
+        h->nsub = nsub;
+        h->xyz.assign(xyz, xyz + nn * 3);
+        h->elems.assign(elems, elems + ne * 8);
+        h->esub.assign(elem_sub, elem_sub + ne);
+        h->dirich.assign(dirichlet, dirichlet + nn);
+        for (int64_t k = 0; k < ne * 8; ++k)
+            if (h->elems[k] < 0 || h->elems[k] >= nn) return BDDC_EINVAL;
+        for (int64_t e = 0; e < ne; ++e)
+            if (h->esub[e] < 0 || h->esub[e] >= nsub) return BDDC_EINVAL;
+        h->csr_mode = false;
+        h->user_corners = false;
+        classify(h);
+        for (auto &sd : h->subs)
+            if (sd.n <= 0) return BDDC_EINVAL;
+        if (n_free) *n_free = h->nfree;
+        if (n_interface) *n_interface = h->nG;
+        if (n_corners) *n_corners = (int)h->corners.size();
+        if (n_edges) *n_edges = h->n_edges;
+        if (n_faces) *n_faces = (int)h->faces.size();
+        if (n_augmented) *n_augmented = h->n_augmented;
+        for (int k = 0; k < corners_cap && k < (int)h->corners.size(); ++k) corners[k] = h->corners[k];
+    } catch (const Error &e) {
+        return (bddc_status)e.status;
+    } catch (const std::bad_alloc &) {
+        return BDDC_ENOMEM;
+    }
+    return BDDC_OK;
+}
+
 bddc_status bddc_set_problem(bddc_handle *h, int64_t n_global, int ncomp, int32_t n_sub, const bddc_subdomain *subs,
                              const double *node_xyz, int mem) {
     if (!h) return BDDC_EINVAL;
