@@ -20,7 +20,9 @@
 #include <cstring>
 #include <iterator>
 #include <map>
+#include <exception>
 #include <memory>
+#include <thread>
 #include <numeric>
 #include <set>
 #include <string>
@@ -122,6 +124,12 @@ struct bddc_handle {
     std::vector<int64_t> corners;
     std::vector<char> is_corner;
     int n_augmented = 0;  // face nodes promoted to corners (Assumptions 1 and 2)
+    std::vector<int32_t> epos;   // mesh input: local dof position of each element's 8 nodes (-1: Dirichlet)
+    bool mesh_uploaded = false;  // xyz, elems, coef, esub of this mesh are in the arena
+    // device-resident mesh arrays of the running bddc_set_mesh_q1 call (copied device to device)
+    const double *in_xyz = nullptr, *in_coef = nullptr;
+    const int64_t *in_elems = nullptr;
+    const int32_t *in_esub = nullptr;
     int n_edges = 0;
     std::vector<std::pair<std::vector<int>, std::vector<int64_t>>> edge_globs;  // (subs, nodes)
     std::vector<FacePair> faces;
@@ -594,10 +602,58 @@ void mark_floating(bddc_handle *h) {
     }
 }
 
+std::vector<int32_t> element_positions(bddc_handle *h);
+
+// Greedy element colouring for the race-free scatter of element matrices: an element
+// takes the lowest colour not used by an element sharing one of its nodes.
+void colour_elements(const bddc_handle *h, std::vector<std::vector<int32_t>> &colors) {
+    colors.clear();
+    std::vector<uint64_t> node_mask(h->nn, 0);
+    for (int64_t e = 0; e < h->ne; ++e) {
+        uint64_t used = 0;
+        for (int a = 0; a < 8; ++a) used |= node_mask[h->elems[e * 8 + a]];
+        int col = 0;
+        while (col < 64 && (used >> col) & 1ull) ++col;
+        BDDC_REQUIRE(col < 64, BDDC_EINVAL, "element colouring needs more than 64 colours");
+        for (int a = 0; a < 8; ++a) node_mask[h->elems[e * 8 + a]] |= (1ull << col);
+        if ((int)colors.size() <= col) colors.resize(col + 1);
+        colors[col].push_back((int32_t)e);
+    }
+}
+
+// A helper thread of the mesh analysis: joined when the scope ends (also on an
+// exception), its own exception kept for rethrow() on the calling thread.
+struct HostTask {
+    std::thread t;
+    std::exception_ptr err;
+    template <typename F>
+    void start(F f) {
+        t = std::thread([this, f]() {
+            try {
+                f();
+            } catch (...) {
+                err = std::current_exception();
+            }
+        });
+    }
+    void join() {
+        if (t.joinable()) t.join();
+    }
+    void rethrow() {
+        join();
+        if (err) std::rethrow_exception(err);
+    }
+    ~HostTask() { join(); }
+};
+
 void classify(bddc_handle *h) {
     const auto tc0 = std::chrono::steady_clock::now();
     const int64_t nn = h->nn, ne = h->ne;
     const int c = h->ncomp;
+    // mesh input: the element colouring needs only the elements; it runs beside the rest
+    std::vector<std::vector<int32_t>> colors;
+    HostTask colour_task, epos_task;
+    if (!h->csr_mode) colour_task.start([h, &colors]() { colour_elements(h, colors); });
     // free dofs
     h->node_first.assign(nn, -1);
     int64_t nf = 0;
@@ -902,6 +958,9 @@ void classify(bddc_handle *h) {
                                               " has too few corners to fix its rigid body modes"};
     }
     const auto tc_faces = std::chrono::steady_clock::now();
+    // element positions read the substructure dof lists, which are final now; the face
+    // pairs below only read them as well
+    if (!h->csr_mode) epos_task.start([h]() { h->epos = element_positions(h); });
     // face pairs
     h->faces.clear();
     h->faces.reserve(face_list.size());
@@ -999,22 +1058,9 @@ void classify(bddc_handle *h) {
         h->faces.push_back(std::move(fp));
     }
     const auto tc_color = std::chrono::steady_clock::now();
-    // element colouring (greedy, nodes shared => different colours)
-    h->colors.clear();
-    std::vector<int> ecol(ne, -1);
-    // greedy: an element takes the lowest colour not yet used by an element sharing one of its nodes
-    std::vector<uint64_t> node_mask(nn, 0);
-    for (int64_t e = 0; e < ne; ++e) {
-        uint64_t used = 0;
-        for (int a = 0; a < 8; ++a) used |= node_mask[h->elems[e * 8 + a]];
-        int col = 0;
-        while (col < 64 && (used >> col) & 1ull) ++col;
-        BDDC_REQUIRE(col < 64, BDDC_EINVAL, "element colouring needs more than 64 colours");
-        ecol[e] = col;
-        for (int a = 0; a < 8; ++a) node_mask[h->elems[e * 8 + a]] |= (1ull << col);
-        if ((int)h->colors.size() <= col) h->colors.resize(col + 1);
-        h->colors[col].push_back((int32_t)e);
-    }
+    colour_task.rethrow();
+    epos_task.rethrow();
+    if (!h->csr_mode) h->colors = std::move(colors);
     if (getenv("BDDC_DEBUG_TIMING")) {
         auto ms = [](auto x, auto y) { return std::chrono::duration<double, std::milli>(y - x).count(); };
         const auto tc_end = std::chrono::steady_clock::now();
@@ -2721,11 +2767,24 @@ void analyze(bddc_handle *h, std::chrono::steady_clock::time_point t_host0) {
         h->ar.upload("csr_off", off, h->stream);
         h->ar.upload("csr_val", val, h->stream);
     } else {
-        h->ar.upload("xyz", h->xyz, h->stream);
-        h->ar.upload("elems", h->elems, h->stream);
-        h->ar.upload("coef", h->coef, h->stream);
-        h->ar.upload("esub", h->esub, h->stream);
-        h->ar.upload("epos", element_positions(h), h->stream);
+        if (!h->mesh_uploaded) {
+            if (h->in_xyz) {   // device-resident input: device-to-device copies, no host round trip
+                auto d2d = [&](const std::string &name, const void *src, size_t bytes) {
+                    BDDC_CUDA(cudaMemcpyAsync(h->ar.get(name, bytes), src, bytes, cudaMemcpyDeviceToDevice, h->stream));
+                };
+                d2d("xyz", h->in_xyz, (size_t)h->nn * 3 * sizeof(double));
+                d2d("elems", h->in_elems, (size_t)h->ne * 8 * sizeof(int64_t));
+                d2d("coef", h->in_coef, (size_t)h->ne * sizeof(double));
+                d2d("esub", h->in_esub, (size_t)h->ne * sizeof(int32_t));
+            } else {
+                h->ar.upload("xyz", h->xyz, h->stream);
+                h->ar.upload("elems", h->elems, h->stream);
+                h->ar.upload("coef", h->coef, h->stream);
+                h->ar.upload("esub", h->esub, h->stream);
+            }
+            h->mesh_uploaded = true;
+        }
+        h->ar.upload("epos", h->epos, h->stream);
         for (size_t col = 0; col < h->colors.size(); ++col)
             h->ar.upload("color_" + std::to_string(col), h->colors[col], h->stream);
     }
@@ -2770,7 +2829,6 @@ bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double
         h->nu = nu;
         h->xyz.resize(nn * 3);
         h->elems.resize(ne * 8);
-        h->coef.resize(ne);
         h->esub.resize(ne);
         h->dirich.resize(nn);
         auto cp = [&](void *dst, const void *src, size_t bytes) {
@@ -2778,9 +2836,31 @@ bddc_status bddc_set_mesh_q1(bddc_handle *h, int ncomp, int64_t nn, const double
         };
         cp(h->xyz.data(), xyz, nn * 3 * sizeof(double));
         cp(h->elems.data(), elems, ne * 8 * sizeof(int64_t));
-        cp(h->coef.data(), coef, ne * sizeof(double));
         cp(h->esub.data(), elem_sub, ne * sizeof(int32_t));
         cp(h->dirich.data(), dirichlet, nn);
+        // the coefficients are only needed on the device; device-resident arrays are
+        // copied device to device by the analysis (the pointers are valid during this call)
+        h->mesh_uploaded = false;
+        if (mem == BDDC_MEM_DEVICE) {
+            h->coef.clear();
+            h->in_xyz = xyz;
+            h->in_elems = elems;
+            h->in_coef = coef;
+            h->in_esub = elem_sub;
+        } else {
+            h->coef.assign(coef, coef + ne);
+            h->in_xyz = h->in_coef = nullptr;
+            h->in_elems = nullptr;
+            h->in_esub = nullptr;
+        }
+        struct InputReset {
+            bddc_handle *h;
+            ~InputReset() {
+                h->in_xyz = h->in_coef = nullptr;
+                h->in_elems = nullptr;
+                h->in_esub = nullptr;
+            }
+        } input_reset{h};
         for (int64_t k = 0; k < ne * 8; ++k)
             BDDC_REQUIRE(h->elems[k] >= 0 && h->elems[k] < nn, BDDC_EINVAL, "element node id out of range");
         for (int64_t e = 0; e < ne; ++e)
