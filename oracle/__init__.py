@@ -13,10 +13,11 @@ from .bddc import Model, pcg, lanczos_condition, lanczos_tridiagonal
 from .adaptive import adapt, pair_problem, orthonormal_rows
 
 
-def run(prob, averages=(), tau=None, tol=1e-8, maxit=1000):
-    """Setup (+ adapt when tau is given) + solve.  Returns (model, adapt_result, pcg_result)."""
+def run(prob, averages=(), tau=None, tol=1e-8, maxit=1000, n_fixed=None):
+    """Setup (+ adapt when tau or n_fixed is given) + solve.  Returns (model, adapt_result,
+    pcg_result).  n_fixed: the n_fixed dominant eigenvectors per face (Section 7, "3eigv")."""
     m = Model(prob, averages=averages)
     m.schur()
-    ad = adapt(m, tau) if tau is not None else None
+    ad = adapt(m, tau, n_fixed=n_fixed) if (tau is not None or n_fixed is not None) else None
     res = m.solve(tol=tol, maxit=maxit)
     return m, ad, res

@@ -119,7 +119,11 @@ def initial_rows_on_s(model, i, j, s_g):
     return np.array(rows).reshape(-1, 2 * ns)
 
 
-def pair_problem(model, i, j, tau, keep_matrices=False):
+def pair_problem(model, i, j, tau, keep_matrices=False, n_fixed=None):
+    """tau: select lambda > tau (Algorithm 3.1).  n_fixed: instead select the n_fixed
+    largest eigenvalues (all when there are fewer) -- the paper's "3eigv" constraints
+    of Section 7, three dominant eigenvectors per face; ties then counts a boundary
+    lambda_k ~ lambda_{k+1} (within TIE_REL), where the selected subspace is not unique."""
     pd = pair_data(model, i, j)
     Sc, pos_i, pos_j = pd["Sc"], pd["pos_i"], pd["pos_j"]
     ns = pos_i.size
@@ -167,8 +171,12 @@ def pair_problem(model, i, j, tau, keep_matrices=False):
     lam, Y = lam[::-1], Y[:, ::-1]
     W = Q @ Vk @ Y
     PLP = Pi @ L @ Pi
-    sel = int((lam > tau).sum())
-    ties = int((np.abs(lam / tau - 1.0) < TIE_REL).sum())
+    if n_fixed is None:
+        sel = int((lam > tau).sum())
+        ties = int((np.abs(lam / tau - 1.0) < TIE_REL).sum())
+    else:
+        sel = min(int(n_fixed), lam.size)
+        ties = int(0 < sel < lam.size and abs(lam[sel] / lam[sel - 1] - 1.0) < TIE_REL)
     d = (PLP @ W[:, :sel]).T
     face_rows = d[:, :ns][:, pd["face_mask"]]
     res = PairResult((i, j), lam, n_null, sel, face_rows, np.unique(pd["s_nodes"][pd["face_mask"]]),
@@ -211,11 +219,13 @@ class AdaptResult:
     per_face: dict
 
 
-def adapt(model, tau):
-    """Algorithm 3.1 on every face pair; the new face rows are added to the model."""
+def adapt(model, tau, n_fixed=None):
+    """Algorithm 3.1 on every face pair; the new face rows are added to the model.
+    With n_fixed, the n_fixed dominant eigenvectors of every face are used instead of
+    those above tau (Section 7, "3eigv")."""
     pairs = {}
     for (i, j) in sorted(model.globs.faces):
-        pairs[(i, j)] = pair_problem(model, i, j, tau)
+        pairs[(i, j)] = pair_problem(model, i, j, tau, n_fixed=n_fixed)
     per_face = {}
     n_added = 0
     c = model.ncomp

@@ -10,7 +10,7 @@ import scipy.sparse.linalg as spla
 from paper_0910_5863_gb300 import problems as P
 import oracle
 from oracle import fe, globs as G, native
-from oracle.adaptive import pair_problem, pair_data, orthonormal_rows
+from oracle.adaptive import adapt, pair_problem, pair_data, orthonormal_rows
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -448,3 +448,41 @@ def test_pcg_iteration_spread_under_rounding_perturbations():
     m2.schur()
     lo2, hi2 = perturbed_iteration_range(m2)
     assert hi2 - lo2 <= 1
+
+
+def test_three_dominant_eigenvectors_per_face():
+    """Section 7's "c+e+f (3eigv)": corners, arithmetic edge averages and, on every
+    face, the constraints of the three dominant eigenvalues of the pair problem.
+    (1) With three components this gives exactly as many constraints as the
+    arithmetic face averages (3 per face), as Section 7 states; (2) the selected
+    eigenvalues are the pencil's three largest whatever tau; (3) with two
+    substructures and the edge average as initial constraint (Pi != I),
+    lambda_max(M S) after adding the three rows is lambda_{12,4} (Corollary 3.1)."""
+    prob = P.elasticity_cube(6, 2, channels=2, seed=3)
+    mf = oracle.Model(prob, averages=("edge", "face"))
+    m3 = oracle.Model(prob, averages=("edge",))
+    m3.schur()
+    ad = adapt(m3, tau=None, n_fixed=3)
+    nfaces = len(m3.globs.faces)
+    face_avg_rows = sum(g.rows.shape[0] for g in mf.constraints if g.kind == "face")
+    assert ad.n_added == 3 * nfaces == face_avg_rows
+    for r in ad.pairs.values():
+        assert r.selected == 3 and r.ties == 0
+        assert np.all(r.lam[:3] >= r.lam[3])
+
+    p2 = P.poisson_cube(6, 2, coef="lognormal", s_xyz=(2, 1, 1), seed=3)
+
+    def model():
+        m = oracle.Model(p2, averages=("face",))
+        m.schur()
+        return m
+
+    m = model()
+    lam = pair_problem(m, 0, 1, tau=1.0).lam
+    S = _dense_op(m.apply_S, m.nG)
+    m2 = model()
+    ad2 = adapt(m2, tau=None, n_fixed=3)
+    assert ad2.n_added == 3
+    M2 = _dense_op(m2.apply_M, m2.nG)
+    lmax2 = np.linalg.eigvals(M2 @ S).real.max()
+    assert abs(lmax2 - lam[3]) < 1e-7 * lam[3]
