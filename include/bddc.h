@@ -239,6 +239,15 @@ BDDC_API bddc_status bddc_setup(bddc_handle *h);
  * Errors: BDDC_ESTATE (no setup), BDDC_ENOTSPD, BDDC_EASSUMPTION. */
 BDDC_API bddc_status bddc_adapt(bddc_handle *h, double tau, bddc_adapt_info *info);
 
+/* As bddc_adapt, but every face gets the constraints of the n_per_face largest
+ * eigenvalues of its pair problem (all of them when there are fewer) instead of
+ * those above a threshold: the "c+e+f (3eigv)" constraints of Section 7 with
+ * n_per_face = 3 after bddc_set_averages(h, BDDC_AVG_EDGE).  info->n_ties counts
+ * faces whose last selected and first rejected eigenvalues agree to 1e-6
+ * (the selected subspace is then not unique).  Errors: BDDC_ESTATE (no setup),
+ * BDDC_EINVAL (n_per_face outside 1..48), BDDC_ENOTSPD, BDDC_EASSUMPTION. */
+BDDC_API bddc_status bddc_adapt_fixed(bddc_handle *h, int n_per_face, bddc_adapt_info *info);
+
 /* Solves sum_i R_i^T A_i R_i u = f: condensed right-hand side, PCG with the
  * BDDC preconditioner to ||r|| <= tol ||r_0|| from x_0 = 0, interior
  * recovery.  f and u are global free-dof vectors (length n_free) in memory

@@ -27,7 +27,7 @@ EXPORTS = ["bddc_default_options", "bddc_create", "bddc_destroy", "bddc_set_mesh
            "bddc_apply_preconditioner", "bddc_apply_schur", "bddc_launch_count", "bddc_status_str",
            "bddc_last_error", "bddc_get_phase_times", "bddc_get_local_matrix", "bddc_set_problem",
            "bddc_set_corners", "bddc_select_corners", "bddc_get_face_rows", "bddc_barrier_selftest",
-           "bddc_classify_q1"]
+           "bddc_classify_q1", "bddc_adapt_fixed"]
 PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
           "analysis_host", "condensed_rhs", "pcg", "recovery"]
 
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "bddc_select_corners": (i32, [vp, vp]),
         "bddc_get_face_rows": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
         "bddc_barrier_selftest": (i32, [vp, i32, dbl, vp]),
+        "bddc_adapt_fixed": (i32, [vp, i32, vp]),
         "bddc_classify_q1": (i32, [i32, i64, vp, i64, vp, vp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
@@ -249,6 +250,12 @@ class Solver:
     def adapt(self, tau):
         info = AdaptInfo()
         self._check(self.lib.bddc_adapt(self.h, float(tau), C.byref(info)))
+        return {"n_faces": info.n_faces, "n_added": info.n_added, "n_ties": info.n_ties, "omega": info.omega}
+
+    def adapt_fixed(self, n_per_face):
+        """The n_per_face dominant eigenvector constraints on every face (Section 7, "3eigv")."""
+        info = AdaptInfo()
+        self._check(self.lib.bddc_adapt_fixed(self.h, int(n_per_face), C.byref(info)))
         return {"n_faces": info.n_faces, "n_added": info.n_added, "n_ties": info.n_ties, "omega": info.omega}
 
     def solve(self, f, u=None, check=True):

@@ -2013,7 +2013,7 @@ void do_setup(bddc_handle *h) {
 // adapt
 namespace {
 
-void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
+void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0) {
     const int nf = (int)h->faces.size();
     reset_status(h);
     // the pair problems use the initial constraints only; drop rows of an earlier adapt
@@ -2389,8 +2389,8 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
     }
     run_gemm(h, gm2, "C", ff_mode);
     auto *ded = h->ar.upload("eigdesc", eds, h->stream);
-    launch_face_eig_n(ded, (int)eds.size(), nmax, tau, h->opt.drop_rel, h->opt.precision != BDDC_FP64 ? 1 : 0, h->dst,
-                      h->stream);
+    launch_face_eig_n(ded, (int)eds.size(), nmax, tau, h->opt.drop_rel, h->opt.precision != BDDC_FP64 ? 1 : 0, fixed_k,
+                      h->dst, h->stream);
     check_launch(h);
     phase_end(h, 4);
     fail_check(h, "adapt");
@@ -3043,6 +3043,16 @@ bddc_status bddc_adapt(bddc_handle *h, double tau, bddc_adapt_info *info) {
         BDDC_REQUIRE(h->have_setup, BDDC_ESTATE, "adapt before setup");
         BDDC_REQUIRE(tau > 0, BDDC_EINVAL, "tau must be positive");
         do_adapt(h, tau, info);
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+    });
+}
+
+bddc_status bddc_adapt_fixed(bddc_handle *h, int n_per_face, bddc_adapt_info *info) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(h->have_setup, BDDC_ESTATE, "adapt before setup");
+        BDDC_REQUIRE(n_per_face >= 1 && n_per_face <= 48, BDDC_EINVAL, "n_per_face must be in 1..48");
+        do_adapt(h, 1.0, info, n_per_face);
         BDDC_CUDA(cudaStreamSynchronize(h->stream));
     });
 }

@@ -259,7 +259,7 @@ __device__ void householder_ff_packed(double *A, int lda, int n, ff *F, double *
 
 __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *descs, int np, double tau,
                                                                double drop_rel, DevStatus *st, int use_smem,
-                                                               int use_ff, int packed_off) {
+                                                               int use_ff, int packed_off, int fixed_k) {
     extern __shared__ double sm[];
     __shared__ double scratch[32];
     __shared__ double sh_val[4];
@@ -371,9 +371,14 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     for (int w = 0; w < (nt >> 5); ++w) tnorm = fmax(tnorm, scratch[w]);
     __syncthreads();
     if (tid == 0) {
-        int less = sturm_less(dd, e2, n, tau);
-        int nsel = n - less;
-        int ties = sturm_less(dd, e2, n, tau * (1 + 1e-6)) - sturm_less(dd, e2, n, tau * (1 - 1e-6));
+        int nsel, ties = 0;
+        if (fixed_k > 0) {
+            nsel = min(fixed_k, n);   // the fixed_k dominant eigenvalues (Section 7, "3eigv")
+        } else {
+            const int less = sturm_less(dd, e2, n, tau);
+            nsel = n - less;
+            ties = sturm_less(dd, e2, n, tau * (1 + 1e-6)) - sturm_less(dd, e2, n, tau * (1 - 1e-6));
+        }
         int over = 0;
         if (nsel > kEigCap) {
             nsel = kEigCap;
@@ -408,6 +413,8 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
         if (lane == 0) lam[t] = 0.5 * (lo + hi);
     }
     __syncthreads();
+    // fixed count: a boundary lambda_k ~ lambda_{k+1} leaves the selected subspace not unique
+    if (fixed_k > 0 && tid == 0 && nsel > 0 && nsel < n && fabs(lam[nsel] / lam[nsel - 1] - 1.0) < 1e-6) sh_int[1] = 1;
     // ---- 3. inverse iteration on T (one warp per vector), back-transformation ----
     double *wbase = work + 10 * n;  // 6 n doubles per warp
     for (int mI = wid; mI < nsel; mI += nw) {
@@ -586,7 +593,7 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
 }
 
 void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, int use_ff,
-                       DevStatus *st, cudaStream_t s) {
+                       int fixed_k, DevStatus *st, cudaStream_t s) {
     if (npairs <= 0) return;
     size_t need = sizeof(double) * ((size_t)nmax * nmax + (10 + 6 * (EIG_THREADS / 32)) * (size_t)nmax + 16);
     int use_smem = need <= 200 * 1024;
@@ -600,7 +607,8 @@ void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, d
         smem += packed;
     }
     if (smem > 48 * 1024) cudaFuncSetAttribute(face_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    face_eig_kernel<<<npairs, EIG_THREADS, smem, s>>>(descs, npairs, tau, drop_rel, st, use_smem, use_ff, packed_off);
+    face_eig_kernel<<<npairs, EIG_THREADS, smem, s>>>(descs, npairs, tau, drop_rel, st, use_smem, use_ff, packed_off,
+                                                      fixed_k);
 }
 
 // ---------------------------------------------------------------------------

@@ -25,8 +25,9 @@ struct EigDesc {
 // 200 KB of shared memory the matrix is reduced in place and work (64 n + 16
 // doubles) is used from global memory.
 // use_ff: the Householder reduction runs in double-float on the FP32 pipe (mixed modes)
+// fixed_k > 0: select the fixed_k largest eigenvalues of every face instead of lambda > tau
 void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, int use_ff,
-                       DevStatus *st, cudaStream_t s);
+                       int fixed_k, DevStatus *st, cudaStream_t s);
 
 // Deflated pair matrix M3 (see adapt phase): adds sigma*c_blk*N0 N0^T to the
 // (w2,w2), (b,w2) and (b,b) blocks with c = 4, 2, 1; sigma = max diag(S^).

@@ -51,3 +51,44 @@ def test_adaptive_with_initial_averages(case, prec):
     kr = res.condition()[1] / res.condition()[0]
     assert abs(sinfo["kappa"] - kr) <= 0.01 * kr
     assert np.linalg.norm(u - res.u) <= 1e-7 * np.linalg.norm(res.u)
+
+
+CASES_FIXED = {
+    # Section 7's "c+e+f (3eigv)": corners, arithmetic edge averages, three dominant
+    # eigenvector constraints per face
+    "elast6_edge_3eigv": (lambda: P.elasticity_cube(6, 2, channels=2, seed=3), ("edge",), 3),
+    "poisson12_edge_3eigv": (lambda: P.poisson_cube(12, 2, coef="random_high", seed=2), ("edge",), 3),
+    "poisson10_corners_2eigv": (lambda: P.poisson_cube(10, 2, coef="lognormal", seed=4), (), 2),
+}
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
+@pytest.mark.parametrize("case", sorted(CASES_FIXED))
+def test_fixed_number_of_eigenvectors_per_face(case, prec):
+    make, av, k = CASES_FIXED[case]
+    prob = make()
+    m = oracle.Model(prob, averages=av)
+    m.schur()
+    ad = oracle.adapt(m, tau=None, n_fixed=k)
+    res = m.solve(tol=1e-8)
+    s = B.Solver(precision=prec)
+    s.set_mesh_problem(prob)
+    s.set_averages(edge="edge" in av, face="face" in av)
+    s.setup()
+    info = s.adapt_fixed(k)
+    assert info["n_ties"] == 0 and all(r.ties == 0 for r in ad.pairs.values())
+    for f, key in enumerate(sorted(ad.pairs)):
+        g = s.face_eigs(f)
+        r = ad.pairs[key]
+        assert g["pair"] == key
+        assert g["selected"] == r.selected == min(k, r.lam.size)
+        assert g["kept"] == ad.per_face[key]
+        n = min(len(g["lam"]), r.selected + 1)
+        assert np.allclose(g["lam"][:n], r.lam[:n], rtol=TOL_LAM), (key, g["lam"][:n], r.lam[:n])
+    assert info["n_added"] == ad.n_added
+    assert abs(info["omega"] - ad.omega) <= TOL_LAM * ad.omega
+    u, sinfo = s.solve(B.free_load_vector(prob))
+    assert abs(sinfo["iters"] - res.iters) <= 1
+    kr = res.condition()[1] / res.condition()[0]
+    assert abs(sinfo["kappa"] - kr) <= 0.01 * kr
+    assert np.linalg.norm(u - res.u) <= 1e-7 * np.linalg.norm(res.u)
