@@ -7,6 +7,8 @@ import, call or link anything here, and nothing here imports them.
 Modules: fe (Q1 elements, assembly), globs (faces/edges/corners, weights),
 bddc (Schur complements, Lemma 2.1 preconditioner, PCG, Lanczos estimate),
 adaptive (pair eigenproblems and face constraints, Algorithm 3.1),
+change_of_variables (Section 5: pivoted-QR change of variables, the saddle,
+projected and primal forms of the preconditioner in the new variables),
 native (the cyclic Jacobi helper in jacobi.c).
 """
 from .bddc import Model, pcg, lanczos_condition, lanczos_tridiagonal
