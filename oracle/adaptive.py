@@ -100,13 +100,15 @@ def pair_data(model, i, j):
                 s_nodes=s_nodes, face_mask=face_mask, di=di, dj=dj)
 
 
-def initial_rows_on_s(model, i, j, s_g):
-    """Rows of D^c_ij: initial glob constraints on globs inside s (both i and j share them)."""
+def initial_rows_on_s(model, i, j, s_g, include_adaptive=False):
+    """Rows of D^c_ij: initial glob constraints on globs inside s (both i and j share them).
+    include_adaptive: also the adaptive rows already added (the pair problem on the
+    final space W~, whose largest eigenvalue is omega_ij after adaptation)."""
     ns = s_g.size
     pos = {int(g): k for k, g in enumerate(s_g)}
     rows = []
     for gc in model.constraints:
-        if gc.kind == "adaptive" or not ({i, j} <= set(gc.subs)):
+        if (gc.kind.startswith("adaptive") and not include_adaptive) or not ({i, j} <= set(gc.subs)):
             continue
         if not all(int(g) in pos for g in gc.gdofs):
             continue
@@ -119,7 +121,7 @@ def initial_rows_on_s(model, i, j, s_g):
     return np.array(rows).reshape(-1, 2 * ns)
 
 
-def pair_problem(model, i, j, tau, keep_matrices=False, n_fixed=None):
+def pair_problem(model, i, j, tau, keep_matrices=False, n_fixed=None, include_adaptive=False):
     """tau: select lambda > tau (Algorithm 3.1).  n_fixed: instead select the n_fixed
     largest eigenvalues (all when there are fewer) -- the paper's "3eigv" constraints
     of Section 7, three dominant eigenvectors per face; ties then counts a boundary
@@ -152,12 +154,12 @@ def pair_problem(model, i, j, tau, keep_matrices=False, n_fixed=None):
     IE[ns + k, ns + k] = di
     L = IE.T @ Sblk @ IE
     L = 0.5 * (L + L.T)
-    D = initial_rows_on_s(model, i, j, pd["s_g"])
+    D = initial_rows_on_s(model, i, j, pd["s_g"], include_adaptive)
     if D.shape[0]:
-        Pi = np.eye(2 * ns) - D.T @ np.linalg.solve(D @ D.T, D)
         U, sv, Vt = np.linalg.svd(D)
         rank = int((sv > 1e-12 * sv[0]).sum())
         Q = Vt[rank:].T
+        Pi = Q @ Q.T                      # I - D^T (D D^T)^{-1} D, also for dependent rows
     else:
         Pi = np.eye(2 * ns)
         Q = np.eye(2 * ns)
@@ -219,15 +221,42 @@ class AdaptResult:
     per_face: dict
 
 
-def adapt(model, tau, n_fixed=None):
+def edge_rows(model, res):
+    """The edge parts of the rows d of one pair (Section 3, after Prop. 4.1: d split into
+    one row on the face and one row per edge, so that every row stays on one glob).
+    Returns [(edge nodes, rows)], the rows over the edge's dofs in global dof order; an
+    edge part below DROP_REL of its whole row's norm carries no constraint and is left out."""
+    ns = res.s_gdofs.size
+    c = model.ncomp
+    d_i = res.d_full[:, :ns]
+    full = np.linalg.norm(res.d_full, axis=1)
+    out = []
+    for key, nodes in sorted(model.globs.edges.items(), key=lambda kv: kv[1][0]):
+        if not set(res.pair) <= set(key):
+            continue
+        gd = model.glob_gdofs(nodes)
+        pos = np.searchsorted(res.s_gdofs, gd)
+        assert np.all(res.s_gdofs[pos] == gd), "an edge of the pair outside s"
+        part = d_i[:, pos]
+        keep = np.linalg.norm(part, axis=1) > DROP_REL * full
+        if keep.any():
+            out.append((np.asarray(nodes), orthonormal_rows(part[keep])))
+    return out
+
+
+def adapt(model, tau, n_fixed=None, keep_edges=False):
     """Algorithm 3.1 on every face pair; the new face rows are added to the model.
     With n_fixed, the n_fixed dominant eigenvectors of every face are used instead of
-    those above tau (Section 7, "3eigv")."""
+    those above tau (Section 7, "3eigv").  keep_edges: the edge parts of the rows d are
+    added too, as constraints between the pair on each edge (the split rows of Section
+    3), instead of being dropped as in the paper's experiments (the Remark closing
+    Section 3); then omega~ <= tau holds after adaptation."""
     pairs = {}
     for (i, j) in sorted(model.globs.faces):
         pairs[(i, j)] = pair_problem(model, i, j, tau, n_fixed=n_fixed)
     per_face = {}
     n_added = 0
+    n_edge_rows = 0
     c = model.ncomp
     for (i, j), res in pairs.items():
         if res.selected == 0:
@@ -239,5 +268,18 @@ def adapt(model, tau, n_fixed=None):
         model.add_constraint("adaptive", nodes, (i, j), rows)
         per_face[(i, j)] = rows.shape[0]
         n_added += rows.shape[0]
+        if keep_edges:
+            for enodes, erows in edge_rows(model, res):
+                model.add_constraint("adaptive_edge", enodes, (i, j), erows)
+                n_edge_rows += erows.shape[0]
     omega = max((r.lam[0] for r in pairs.values() if r.lam.size), default=0.0)
-    return AdaptResult(pairs, omega, n_added, per_face)
+    out = AdaptResult(pairs, omega, n_added, per_face)
+    out.n_edge_rows = n_edge_rows
+    return out
+
+
+def indicator(model, tau=np.inf):
+    """omega~ (eq. cond-ind) on the current space W~: the largest eigenvalue of every
+    face pair's problem with all constraints in place, adaptive rows included."""
+    return max((pair_problem(model, i, j, tau, include_adaptive=True).lam[:1].max(initial=0.0)
+                for (i, j) in sorted(model.globs.faces)), default=0.0)
