@@ -221,7 +221,7 @@ class AdaptResult:
     per_face: dict
 
 
-def edge_rows(model, res):
+def edge_rows(model, res, orthonormal=True):
     """The edge parts of the rows d of one pair (Section 3, after Prop. 4.1: d split into
     one row on the face and one row per edge, so that every row stays on one glob).
     Returns [(edge nodes, rows)], the rows over the edge's dofs in global dof order; an
@@ -240,7 +240,8 @@ def edge_rows(model, res):
         part = d_i[:, pos]
         keep = np.linalg.norm(part, axis=1) > DROP_REL * full
         if keep.any():
-            out.append((np.asarray(nodes), orthonormal_rows(part[keep])))
+            rows = part[keep]
+            out.append((np.asarray(nodes), orthonormal_rows(rows) if orthonormal else rows))
     return out
 
 
@@ -248,9 +249,14 @@ def adapt(model, tau, n_fixed=None, keep_edges=False):
     """Algorithm 3.1 on every face pair; the new face rows are added to the model.
     With n_fixed, the n_fixed dominant eigenvectors of every face are used instead of
     those above tau (Section 7, "3eigv").  keep_edges: the edge parts of the rows d are
-    added too, as constraints between the pair on each edge (the split rows of Section
-    3), instead of being dropped as in the paper's experiments (the Remark closing
-    Section 3); then omega~ <= tau holds after adaptation."""
+    added too, instead of being dropped as in the paper's experiments (the Remark
+    closing Section 3); then omega~ <= tau holds after adaptation.
+      keep_edges=True:   the split rows of Section 3, each a constraint between the
+                         pair's two substructures on one edge;
+      keep_edges="glob": per edge, one orthonormal basis of the span of every pair's
+                         edge rows on it, enforced on all substructures sharing the
+                         edge (a stronger constraint set, whose rows stay independent
+                         on every substructure, as a primal coarse space needs)."""
     pairs = {}
     for (i, j) in sorted(model.globs.faces):
         pairs[(i, j)] = pair_problem(model, i, j, tau, n_fixed=n_fixed)
@@ -258,6 +264,7 @@ def adapt(model, tau, n_fixed=None, keep_edges=False):
     n_added = 0
     n_edge_rows = 0
     c = model.ncomp
+    edge_stack = {}                # keep_edges="glob": edge nodes -> rows of every pair
     for (i, j), res in pairs.items():
         if res.selected == 0:
             per_face[(i, j)] = 0
@@ -268,10 +275,18 @@ def adapt(model, tau, n_fixed=None, keep_edges=False):
         model.add_constraint("adaptive", nodes, (i, j), rows)
         per_face[(i, j)] = rows.shape[0]
         n_added += rows.shape[0]
-        if keep_edges:
+        if keep_edges == "glob":
+            for enodes, erows in edge_rows(model, res, orthonormal=False):
+                edge_stack.setdefault(tuple(int(v) for v in enodes), []).append(erows)
+        elif keep_edges:
             for enodes, erows in edge_rows(model, res):
                 model.add_constraint("adaptive_edge", enodes, (i, j), erows)
                 n_edge_rows += erows.shape[0]
+    for key in sorted(edge_stack):
+        rows = orthonormal_rows(np.vstack(edge_stack[key]))
+        subs = sorted(model.globs.sets[key[0]])
+        model.add_constraint("adaptive_edge", np.array(key), subs, rows)
+        n_edge_rows += rows.shape[0]
     omega = max((r.lam[0] for r in pairs.values() if r.lam.size), default=0.0)
     out = AdaptResult(pairs, omega, n_added, per_face)
     out.n_edge_rows = n_edge_rows
