@@ -248,6 +248,29 @@ BDDC_API bddc_status bddc_adapt(bddc_handle *h, double tau, bddc_adapt_info *inf
  * BDDC_EINVAL (n_per_face outside 1..48), BDDC_ENOTSPD, BDDC_EASSUMPTION. */
 BDDC_API bddc_status bddc_adapt_fixed(bddc_handle *h, int n_per_face, bddc_adapt_info *info);
 
+/* keep = 1: every later bddc_adapt / bddc_adapt_fixed also keeps the edge parts of the
+ * selected rows d (Section 3 splits each d into one row on the face and one row per edge,
+ * so that every row stays on one glob; the paper's experiments drop the edge rows, the
+ * Remark closing Section 3, which is the default keep = 0).  Per edge, the edge parts
+ * of every face pair's rows on it (each normalised; a part below drop_rel * sqrt(2) |d|
+ * is left out) are orthonormalised with row pivoting, keeping rows while the pivot
+ * exceeds max(drop_rel, 1e-6) of the first (the pairs' rows on one edge overlap in exact
+ * arithmetic, and below 1e-6 the mixed modes' eigenvectors cannot tell a rounding
+ * direction from a real one), and the basis becomes a constraint on all substructures
+ * sharing the edge.  That is a stronger
+ * constraint set than the pairwise split rows, and with it every face pair's largest
+ * eigenvalue on the constrained space is still at most its lambda_{k+1} <= tau, so
+ * omega~ <= tau (the Courant-Fisher-Weyl principle with Algorithm 3.1); unlike the
+ * pairwise rows, the rows of every substructure stay independent, as the primal
+ * coarse space (Remark 5.1) needs.  Errors: BDDC_EINVAL (keep not 0 or 1); the adapt
+ * call fails with BDDC_EINVAL when an edge is shared by more than 8 face pairs. */
+BDDC_API bddc_status bddc_set_edge_rows(bddc_handle *h, int keep);
+
+/* Edge rows kept by the last adapt in total, and the number of edges that got rows
+ * (both 0 when bddc_set_edge_rows is off).  Either pointer may be NULL.
+ * Errors: BDDC_EINVAL (null handle). */
+BDDC_API bddc_status bddc_get_edge_rows(const bddc_handle *h, int *n_rows, int *n_edges);
+
 /* Solves sum_i R_i^T A_i R_i u = f: condensed right-hand side, PCG with the
  * BDDC preconditioner to ||r|| <= tol ||r_0|| from x_0 = 0, interior
  * recovery.  f and u are global free-dof vectors (length n_free) in memory

@@ -40,6 +40,11 @@ from .native import jacobi_eigh
 
 NULL_REL = 1e-12
 DROP_REL = 1e-10
+# Rank rule of the per-edge bases (keep_edges="glob"): the edge rows of the face pairs on
+# one edge overlap in exact arithmetic, and below this pivot a rounding-error direction of
+# the mixed-precision eigenvectors (~1e-7, double-float reduction) cannot be told from a
+# real one; the same rule holds for every precision.
+EDGE_DROP_REL = 1e-6
 TIE_REL = 1e-6
 
 
@@ -283,7 +288,7 @@ def adapt(model, tau, n_fixed=None, keep_edges=False):
                 model.add_constraint("adaptive_edge", enodes, (i, j), erows)
                 n_edge_rows += erows.shape[0]
     for key in sorted(edge_stack):
-        rows = orthonormal_rows(np.vstack(edge_stack[key]))
+        rows = orthonormal_rows(np.vstack(edge_stack[key]), EDGE_DROP_REL)
         subs = sorted(model.globs.sets[key[0]])
         model.add_constraint("adaptive_edge", np.array(key), subs, rows)
         n_edge_rows += rows.shape[0]

@@ -27,7 +27,7 @@ EXPORTS = ["bddc_default_options", "bddc_create", "bddc_destroy", "bddc_set_mesh
            "bddc_apply_preconditioner", "bddc_apply_schur", "bddc_launch_count", "bddc_status_str",
            "bddc_last_error", "bddc_get_phase_times", "bddc_get_local_matrix", "bddc_set_problem",
            "bddc_set_corners", "bddc_select_corners", "bddc_get_face_rows", "bddc_barrier_selftest",
-           "bddc_classify_q1", "bddc_adapt_fixed"]
+           "bddc_classify_q1", "bddc_adapt_fixed", "bddc_set_edge_rows", "bddc_get_edge_rows"]
 PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
           "analysis_host", "condensed_rhs", "pcg", "recovery"]
 
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
         "bddc_get_face_rows": (i32, [vp, i32, vp, vp, i32, i32, vp, vp]),
         "bddc_barrier_selftest": (i32, [vp, i32, dbl, vp]),
         "bddc_adapt_fixed": (i32, [vp, i32, vp]),
+        "bddc_set_edge_rows": (i32, [vp, i32]),
+        "bddc_get_edge_rows": (i32, [vp, vp, vp]),
         "bddc_classify_q1": (i32, [i32, i64, vp, i64, vp, vp, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
@@ -257,6 +259,17 @@ class Solver:
         info = AdaptInfo()
         self._check(self.lib.bddc_adapt_fixed(self.h, int(n_per_face), C.byref(info)))
         return {"n_faces": info.n_faces, "n_added": info.n_added, "n_ties": info.n_ties, "omega": info.omega}
+
+    def set_edge_rows(self, keep=True):
+        """Later adapt calls also keep the edge parts of the rows d (Section 3), one
+        orthonormal basis per edge on all substructures of the edge."""
+        self._check(self.lib.bddc_set_edge_rows(self.h, 1 if keep else 0))
+
+    def edge_rows(self):
+        """(edge rows kept by the last adapt, edges that got rows)."""
+        n, e = C.c_int(), C.c_int()
+        self._check(self.lib.bddc_get_edge_rows(self.h, C.byref(n), C.byref(e)))
+        return n.value, e.value
 
     def solve(self, f, u=None, check=True):
         """f: global free-dof load vector (numpy or torch CUDA).  Returns (u, info)."""

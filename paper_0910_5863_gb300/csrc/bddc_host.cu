@@ -80,6 +80,7 @@ struct GlobRows {               // one glob with constraint rows (c . w equal fo
     int nrows = 0;
     std::vector<double> rows;   // host rows (row-major nrows x gdofs) for averages
     int face = -1;              // >= 0: adaptive rows of that face (device buffer)
+    int edge = -1;              // >= 0: kept adaptive edge rows, bddc_handle::edge_rows[edge]
     int coarse0 = 0;            // first global coarse index
 };
 
@@ -154,6 +155,16 @@ struct bddc_handle {
     double omega = 0.0;
     std::vector<double *> face_rows_dev;
     int face_row_ld = 0;
+    // kept adaptive edge rows (Section 3's split rows; off unless bddc_set_edge_rows)
+    struct EdgeRows {
+        int edge_glob;           // index into edge_globs
+        const double *rowsT;     // column-major over the edge's dofs (ascending), ld = ld
+        int ld;                  // the edge's dofs
+        int nrows;
+    };
+    bool keep_edge_rows = false;
+    std::vector<EdgeRows> edge_rows;
+    int n_edge_rows = 0, n_edges_with_rows = 0;   // kept by the last adapt
     bool coarse_dirty = true;   // coarse operators are (re)built before the next solve
     bool assembled = false;     // dense local matrices hold the assembled A_i
     bool coarse_fp32 = false;   // the current coarse operators used the FP32 local saddle
@@ -1151,17 +1162,33 @@ void layout_constraints(bddc_handle *h) {
             auto &g = h->globs[sub_rows[s][m].first];
             int r = sub_rows[s][m].second;
             sd.row_coarse.push_back(g.coarse0 + r);
-            if (g.face >= 0) continue;
+            if (g.face >= 0 || g.edge >= 0) continue;
             for (size_t k = 0; k < g.gdofs.size(); ++k)
                 host[(size_t)pos[g.gdofs[k]] * sd.capA + m] = g.rows[(size_t)r * g.gdofs.size() + k];
         }
-        for (int k = 0; k < sd.nG; ++k) pos[sd.gG[k]] = -1;
         BDDC_CUDA(cudaMemcpyAsync(sd.Cb, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         // adaptive rows: one gather per (sub, face glob): Cb[m0 + l, facepos] = rows[l, f]
         for (int m = 0; m < sd.na;) {
             auto &g = h->globs[sub_rows[s][m].first];
-            if (g.face < 0) {
+            if (g.face < 0 && g.edge < 0) {
                 ++m;
+                continue;
+            }
+            if (g.edge >= 0) {
+                // kept edge rows: Cb[m + l, k] = rowsT(l, cmap[k]), ld = the edge's dofs
+                const auto &er = h->edge_rows[g.edge];
+                std::vector<int> cmap(sd.nG, -1);
+                for (size_t t = 0; t < g.gdofs.size(); ++t) {
+                    const int k = pos[g.gdofs[t]];
+                    BDDC_REQUIRE(k >= 0, BDDC_EINVAL, "internal: an edge dof outside a substructure of the edge");
+                    cmap[k] = (int)t;
+                }
+                int *dcm = h->ar.upload("ecmap_" + std::to_string(s) + "_" + std::to_string(g.edge), cmap, h->stream);
+                GatherOp o = gop(er.rowsT, er.ld, sd.Cb, sd.capA, g.nrows, sd.nG);
+                o.dst_row_off = m;
+                o.cmap = dcm;
+                ops.push_back(o);
+                m += g.nrows;
                 continue;
             }
             auto &fp = h->faces[g.face];
@@ -1180,6 +1207,7 @@ void layout_constraints(bddc_handle *h) {
             ops.push_back(o);
             m += g.nrows;
         }
+        for (int k = 0; k < sd.nG; ++k) pos[sd.gG[k]] = -1;
     }
     run_gathers(h, ops, "cons");
 }
@@ -2017,8 +2045,11 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
     const int nf = (int)h->faces.size();
     reset_status(h);
     // the pair problems use the initial constraints only; drop rows of an earlier adapt
-    h->globs.erase(std::remove_if(h->globs.begin(), h->globs.end(), [](const GlobRows &g) { return g.face >= 0; }),
+    h->globs.erase(std::remove_if(h->globs.begin(), h->globs.end(),
+                                  [](const GlobRows &g) { return g.face >= 0 || g.edge >= 0; }),
                    h->globs.end());
+    h->edge_rows.clear();
+    h->n_edge_rows = h->n_edges_with_rows = 0;
     if (nf == 0) {
         if (info) *info = bddc_adapt_info{0, 0, 0, 0.0};
         return;
@@ -2392,6 +2423,107 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
     launch_face_eig_n(ded, (int)eds.size(), nmax, tau, h->opt.drop_rel, h->opt.precision != BDDC_FP64 ? 1 : 0, fixed_k,
                       h->dst, h->stream);
     check_launch(h);
+    // kept edge rows (Section 3: d split into a face row and one row per edge), per edge:
+    // the edge parts of the same rows d from every face pair on the edge, stacked in the
+    // edge's slots (pairs in face order), then one orthonormal basis per edge
+    std::vector<int> eglob_ids, eglob_len; // edge globs with slots (ascending), their dofs
+    int *ekept_dev = nullptr;
+    if (h->keep_edge_rows && !eds.empty()) {
+        std::vector<int> dof_edge(h->nfree, -1);
+        for (size_t k = 0; k < h->edge_globs.size(); ++k)
+            for (int64_t v : h->edge_globs[k].second)
+                if (h->node_first[v] >= 0)
+                    for (int comp = 0; comp < h->ncomp; ++comp) dof_edge[h->node_first[v] + comp] = (int)k;
+        struct PairSegs {
+            size_t k;                                  // index into eds
+            std::vector<int> ptr, pos, eglob;
+        };
+        std::vector<PairSegs> ps;
+        std::map<int, int> nslot;                      // edge glob -> slots (face pairs on it)
+        std::map<int, int> elen;                       // edge glob -> dofs
+        for (size_t k = 0; k < eds.size(); ++k) {
+            const auto &fp = h->faces[eig_face[k]];
+            const int ns = (int)fp.s_g.size();
+            std::vector<char> on_face(ns, 0);
+            for (int q : fp.face_idx) on_face[q] = 1;
+            std::map<int, std::vector<int>> by_edge;   // edge glob -> s positions, ascending
+            for (int q = 0; q < ns; ++q) {
+                if (on_face[q]) continue;
+                const int eg = dof_edge[fp.s_g[q]];
+                BDDC_REQUIRE(eg >= 0, BDDC_EINVAL, "internal: a shared dof on no face and no edge");
+                by_edge[eg].push_back(q);
+            }
+            if (by_edge.empty()) continue;
+            PairSegs P;
+            P.k = k;
+            P.ptr.push_back(0);
+            for (auto &kv : by_edge) {
+                P.pos.insert(P.pos.end(), kv.second.begin(), kv.second.end());
+                P.ptr.push_back((int)P.pos.size());
+                P.eglob.push_back(kv.first);
+                const int len = (int)kv.second.size();
+                BDDC_REQUIRE(!elen.count(kv.first) || elen[kv.first] == len, BDDC_EINVAL,
+                             "internal: an edge seen with different lengths by two face pairs");
+                elen[kv.first] = len;
+                ++nslot[kv.first];
+            }
+            ps.push_back(std::move(P));
+        }
+        if (!ps.empty()) {
+            std::map<int, double *> stack;
+            std::map<int, int> next_slot;
+            std::vector<EdgeGlobDesc> egd;
+            ekept_dev = h->ar.get_t<int>("ekept_all", nslot.size());
+            for (auto &kv : nslot) {
+                const int eg = kv.first, len = elen[eg];
+                BDDC_REQUIRE(kv.second <= kMaxEdgeSlots, BDDC_EINVAL,
+                             "an edge shared by more than 8 face pairs (kept edge rows)");
+                const std::string tag = std::to_string(eg);
+                stack[eg] = h->ar.get_t<double>("estack_" + tag, (size_t)kv.second * kEigCap * len);
+                next_slot[eg] = 0;
+                EdgeGlobDesc g{};
+                g.R = stack[eg];
+                g.nrows = kv.second * kEigCap;
+                g.len = len;
+                g.rowsT = h->ar.get_t<double>("erowsT_" + tag, (size_t)len * len);
+                g.kept = ekept_dev + egd.size();
+                egd.push_back(g);
+                eglob_ids.push_back(eg);
+                eglob_len.push_back(len);
+            }
+            std::vector<EdgePartDesc> epd;
+            for (auto &P : ps) {
+                const auto &ed = eds[P.k];
+                const std::string tag = std::to_string(eig_face[P.k]);
+                std::vector<double *> slots;
+                for (size_t e = 0; e < P.eglob.size(); ++e) {
+                    const int eg = P.eglob[e];
+                    slots.push_back(stack[eg] + (size_t)(next_slot[eg]++) * kEigCap * elen[eg]);
+                }
+                EdgePartDesc d{};
+                d.W1 = ed.W1;
+                d.ldw = ed.ldw;
+                d.ns = (int)h->faces[eig_face[P.k]].s_g.size();
+                d.n = ed.n;
+                d.vec = ed.vec;
+                d.counts = ed.counts;
+                d.seg_ptr = h->ar.upload("eseg_ptr_" + tag, P.ptr, h->stream);
+                d.seg_pos = h->ar.upload("eseg_pos_" + tag, P.pos, h->stream);
+                d.nseg = (int)P.eglob.size();
+                d.slot = h->ar.upload("eslot_" + tag, slots, h->stream);
+                epd.push_back(d);
+            }
+            auto *dp = h->ar.upload("edgepartdesc", epd, h->stream);
+            launch_edge_parts(dp, (int)epd.size(), h->opt.drop_rel, h->stream);
+            check_launch(h);
+            auto *dg = h->ar.upload("edgeglobdesc", egd, h->stream);
+            // the rows of the pairs on one edge overlap in exact arithmetic; below 1e-6 of the first
+            // pivot a rounding direction of the mixed modes' eigenvectors (~1e-7) cannot be told
+            // from a real one, so every precision keeps rows only above that
+            launch_edge_globs(dg, (int)egd.size(), std::max(h->opt.drop_rel, 1e-6), h->stream);
+            check_launch(h);
+        }
+    }
     phase_end(h, 4);
     fail_check(h, "adapt");
     // results back to the host
@@ -2400,11 +2532,15 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
     h->face_rows_dev.assign(nf, nullptr);
     std::vector<int> cnt_all((size_t)nf * 8, 0);
     std::vector<double> lam_all((size_t)nf * (kEigCap + 1), 0.0);
+    std::vector<int> ekept(eglob_ids.size(), 0);
     if (!eds.empty()) {
         BDDC_CUDA(cudaMemcpyAsync(cnt_all.data(), h->ar.get_t<int>("fcnt_all", (size_t)nf * 8), cnt_all.size() * sizeof(int),
                                   cudaMemcpyDeviceToHost, h->stream));
         BDDC_CUDA(cudaMemcpyAsync(lam_all.data(), h->ar.get_t<double>("lam_all", (size_t)nf * (kEigCap + 1)),
                                   lam_all.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (ekept_dev)
+            BDDC_CUDA(cudaMemcpyAsync(ekept.data(), ekept_dev, ekept.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                                      h->stream));
         BDDC_CUDA(cudaStreamSynchronize(h->stream));
     }
     for (size_t k = 0; k < eds.size(); ++k) {
@@ -2430,6 +2566,26 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
             g.face = f;
             h->globs.push_back(g);
         }
+    }
+    // kept edge rows: one glob constraint per edge, on all substructures of the edge
+    for (size_t q = 0; q < eglob_ids.size(); ++q) {
+        if (ekept[q] <= 0) continue;
+        const int eg = eglob_ids[q];
+        const auto &E = h->edge_globs[eg];
+        GlobRows g;
+        g.subs = E.first;
+        for (int64_t v : E.second)
+            if (h->node_first[v] >= 0)
+                for (int comp = 0; comp < h->ncomp; ++comp) g.gdofs.push_back(h->node_first[v] + comp);
+        BDDC_REQUIRE((int)g.gdofs.size() == eglob_len[q] && ekept[q] <= eglob_len[q], BDDC_EINVAL,
+                     "internal: an edge's rows do not match its dofs");
+        g.nrows = ekept[q];
+        g.edge = (int)h->edge_rows.size();
+        h->edge_rows.push_back({eg, h->ar.get_t<double>("erowsT_" + std::to_string(eg), g.gdofs.size() * g.gdofs.size()),
+                                (int)g.gdofs.size(), ekept[q]});
+        h->n_edge_rows += ekept[q];
+        ++h->n_edges_with_rows;
+        h->globs.push_back(g);
     }
     h->omega = omega;
     // rows are stored row-major (l * nf + f); the constraint gather reads src(l, cmap[k]) = src[cmap[k] * ld + l]
@@ -3055,6 +3211,21 @@ bddc_status bddc_adapt_fixed(bddc_handle *h, int n_per_face, bddc_adapt_info *in
         do_adapt(h, 1.0, info, n_per_face);
         BDDC_CUDA(cudaStreamSynchronize(h->stream));
     });
+}
+
+bddc_status bddc_set_edge_rows(bddc_handle *h, int keep) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        BDDC_REQUIRE(keep == 0 || keep == 1, BDDC_EINVAL, "keep must be 0 or 1");
+        h->keep_edge_rows = keep != 0;
+    });
+}
+
+bddc_status bddc_get_edge_rows(const bddc_handle *h, int *n_rows, int *n_edges) {
+    if (!h) return BDDC_EINVAL;
+    if (n_rows) *n_rows = h->n_edge_rows;
+    if (n_edges) *n_edges = h->n_edges_with_rows;
+    return BDDC_OK;
 }
 
 bddc_status bddc_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_info *info) {

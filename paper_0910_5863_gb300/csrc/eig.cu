@@ -612,6 +612,118 @@ void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, d
 }
 
 // ---------------------------------------------------------------------------
+// Kept adaptive edge rows (see eig.h).  Stage 1: the edge parts of every face pair's
+// selected rows d, filtered and normalised, into the pair's slot of each edge.
+__global__ void __launch_bounds__(EIG_THREADS) edge_parts_kernel(const EdgePartDesc *descs, int np, double drop_rel) {
+    const EdgePartDesc D = descs[blockIdx.x];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    __shared__ double full[kEigCap], scl[kEigCap];
+    int nsel = D.counts[0];
+    nsel = nsel < 0 ? 0 : (nsel > kEigCap ? kEigCap : nsel);
+    // |d_l| over all of s (side i), one warp per row
+    for (int l = wid; l < nsel; l += nw) {
+        const double *y = D.vec + (size_t)l * D.n;
+        double s2 = 0.0;
+        for (int p = lane; p < D.ns; p += 32) {
+            double v = 0.0;
+            for (int j = 0; j < D.n; ++j) v += D.W1[p + (size_t)j * D.ldw] * y[j];
+            s2 += v * v;
+        }
+        s2 = warp_sum(s2);
+        if (lane == 0) full[l] = sqrt(s2);
+    }
+    __syncthreads();
+    for (int e = 0; e < D.nseg; ++e) {
+        const int p0 = D.seg_ptr[e], len = D.seg_ptr[e + 1] - p0;
+        double *R = D.slot[e];
+        for (int idx = tid; idx < kEigCap * len; idx += nt) {
+            const int l = idx / len, k = idx - l * len;
+            double v = 0.0;
+            if (l < nsel) {
+                const int p = D.seg_pos[p0 + k];
+                const double *y = D.vec + (size_t)l * D.n;
+                for (int j = 0; j < D.n; ++j) v += D.W1[p + (size_t)j * D.ldw] * y[j];
+            }
+            R[idx] = v;
+        }
+        __syncthreads();
+        for (int l = wid; l < nsel; l += nw) {
+            double s2 = 0.0;
+            for (int k = lane; k < len; k += 32) s2 += R[(size_t)l * len + k] * R[(size_t)l * len + k];
+            s2 = warp_sum(s2);
+            if (lane == 0) {
+                const double nr = sqrt(s2);
+                scl[l] = nr > drop_rel * 1.4142135623730951 * full[l] ? 1.0 / nr : 0.0;
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nsel * len; idx += nt) R[idx] *= scl[idx / len];
+        __syncthreads();
+    }
+}
+
+// Stage 2: Gram-Schmidt with row pivoting over the stacked slots of one edge.
+constexpr int kEdgeRowsMax = kMaxEdgeSlots * kEigCap;
+__global__ void __launch_bounds__(EIG_THREADS) edge_globs_kernel(const EdgeGlobDesc *descs, int ne, double drop_rel) {
+    const EdgeGlobDesc D = descs[blockIdx.x];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    __shared__ double nrm[kEdgeRowsMax];
+    __shared__ int sh_best;
+    __shared__ double sh_pn;
+    const int nr = D.nrows < kEdgeRowsMax ? D.nrows : kEdgeRowsMax, len = D.len;
+    double *R = D.R;
+    int kept = 0;
+    double first = -1.0;
+    for (int step = 0; step < nr && step < len; ++step) {
+        for (int l = step + wid; l < nr; l += nw) {
+            double s2 = 0.0;
+            for (int k = lane; k < len; k += 32) s2 += R[(size_t)l * len + k] * R[(size_t)l * len + k];
+            s2 = warp_sum(s2);
+            if (lane == 0) nrm[l] = sqrt(s2);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int best = step;
+            for (int l = step + 1; l < nr; ++l)
+                if (nrm[l] > nrm[best]) best = l;
+            sh_best = best;
+            sh_pn = nrm[best];
+        }
+        __syncthreads();
+        const int best = sh_best;
+        const double pn = sh_pn;
+        if (first < 0) first = pn;
+        if (!(pn > drop_rel * first) || pn == 0.0) break;
+        for (int k = tid; k < len; k += nt) {
+            const double a = R[(size_t)best * len + k], b = R[(size_t)step * len + k];
+            R[(size_t)best * len + k] = b;
+            R[(size_t)step * len + k] = a / pn;
+        }
+        __syncthreads();
+        for (int l = step + 1 + wid; l < nr; l += nw) {
+            double dot = 0.0;
+            for (int k = lane; k < len; k += 32) dot += R[(size_t)l * len + k] * R[(size_t)step * len + k];
+            dot = warp_sum(dot);
+            for (int k = lane; k < len; k += 32) R[(size_t)l * len + k] -= dot * R[(size_t)step * len + k];
+        }
+        __syncthreads();
+        kept = step + 1;
+    }
+    for (int idx = tid; idx < kept * len; idx += nt) {
+        const int l = idx / len, k = idx - l * len;
+        D.rowsT[(size_t)k * len + l] = R[(size_t)l * len + k];
+    }
+    if (tid == 0) *D.kept = kept;
+}
+
+void launch_edge_parts(const EdgePartDesc *d, int npairs, double drop_rel, cudaStream_t s) {
+    if (npairs > 0) edge_parts_kernel<<<npairs, EIG_THREADS, 0, s>>>(d, npairs, drop_rel);
+}
+void launch_edge_globs(const EdgeGlobDesc *d, int nedges, double drop_rel, cudaStream_t s) {
+    if (nedges > 0) edge_globs_kernel<<<nedges, EIG_THREADS, 0, s>>>(d, nedges, drop_rel);
+}
+
+// ---------------------------------------------------------------------------
 __global__ void deflate_kernel(const DeflateDesc *dd, int np) {
     __shared__ double scratch[32];
     const DeflateDesc d = dd[blockIdx.x];

@@ -29,6 +29,40 @@ struct EigDesc {
 void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, int use_ff,
                        int fixed_k, DevStatus *st, cudaStream_t s);
 
+// Kept adaptive edge rows (Section 3: every row d split into a face row and one row
+// per edge), in the per-edge form: on each edge, one orthonormal basis of the span of the
+// edge parts of every face pair's selected rows, a constraint on all substructures of
+// the edge.  Two launches:
+//   launch_edge_parts: one CTA per face pair, after launch_face_eig_n on the same W1
+//     and eigenvectors.  d_l = W1 y_l over the pair's s dofs (side i), l < selected.
+//     For every edge of the pair (a segment of s positions) row l of the pair's slot
+//     gets the edge part of d_l normalised, or zeros when that part is negligible,
+//     |d_l|_edge| <= drop_rel * sqrt(2) |d_l| (the whole row has d_i and -d_i), or
+//     l >= selected.  A slot is kEigCap rows x the segment's length, row-major.
+//   launch_edge_globs: one CTA per edge, over the slots of all pairs on it (stacked,
+//     nrows = slots x kEigCap): Gram-Schmidt with row pivoting, rows whose pivot falls
+//     below drop_rel of the first dropped (the caller passes 1e-6: the pairs' rows on
+//     one edge overlap in exact arithmetic).
+constexpr int kMaxEdgeSlots = 8;   // face pairs per edge
+struct EdgePartDesc {
+    const double *W1;     // ns x n, ld ldw (the face kernel's W1)
+    int ldw, ns, n;
+    const double *vec;    // the face kernel's eigenvectors: y_l at vec + l * n
+    const int *counts;    // the face kernel's counts: [0] = selected rows
+    const int *seg_ptr;   // (nseg + 1) offsets into seg_pos
+    const int *seg_pos;   // s positions (< ns) of every edge's dofs, in global dof order
+    int nseg;
+    double *const *slot;  // (nseg) the segment's slot: kEigCap x len, row-major
+};
+struct EdgeGlobDesc {
+    double *R;            // nrows x len, row-major: the stacked slots (destroyed)
+    int nrows, len;       // nrows <= kMaxEdgeSlots * kEigCap
+    double *rowsT;        // out: kept row l, dof k at rowsT[k * len + l] (ld len)
+    int *kept;            // out: rows kept
+};
+void launch_edge_parts(const EdgePartDesc *d, int npairs, double drop_rel, cudaStream_t s);
+void launch_edge_globs(const EdgeGlobDesc *d, int nedges, double drop_rel, cudaStream_t s);
+
 // Deflated pair matrix M3 (see adapt phase): adds sigma*c_blk*N0 N0^T to the
 // (w2,w2), (b,w2) and (b,b) blocks with c = 4, 2, 1; sigma = max diag(S^).
 struct DeflateDesc {

@@ -1,0 +1,73 @@
+"""Kept adaptive edge rows on the GPU (Section 3: every row d split into a face row and
+one row per edge; bddc_set_edge_rows) against the oracle's per-edge form
+(oracle.adaptive.adapt(keep_edges="glob")): the face and edge row counts, the
+preconditioner, PCG iterations, kappa and the solution.  On the channel problem the
+face rows alone leave kappa ~ 4e4; with the edge rows it falls below tau."""
+import numpy as np
+import pytest
+
+from paper_0910_5863_gb300 import problems as P
+from paper_0910_5863_gb300 import bddc as B
+import oracle
+from oracle.adaptive import adapt
+
+pytestmark = pytest.mark.gpu
+
+TAU = 10.0
+CASES = {
+    "elast8_channels_2x2x2": lambda: P.elasticity_cube(8, 2, channels=2, seed=3),
+    "elast12_channels_3x3x3": lambda: P.elasticity_cube(12, 3, channels=3, seed=1),
+    "poisson6_jumps_2x2x2": lambda: P.poisson_cube(6, 2, coef="random_high", seed=5),
+    "poisson9_jumps_3x3x3": lambda: P.poisson_cube(9, 3, coef="random_high", seed=7),
+}
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_kept_edge_rows_match_the_oracle(case, prec):
+    prob = CASES[case]()
+    m = oracle.Model(prob)
+    m.schur()
+    ad = adapt(m, TAU, keep_edges="glob")
+    n_edges_ref = sum(1 for g in m.constraints if g.kind == "adaptive_edge")
+    res = m.solve(tol=1e-8)
+    s = B.Solver(precision=prec)
+    s.set_mesh_problem(prob)
+    s.set_edge_rows(True)
+    s.setup()
+    info = s.adapt(TAU)
+    assert info["n_ties"] == 0
+    assert info["n_added"] == ad.n_added
+    assert s.edge_rows() == (ad.n_edge_rows, n_edges_ref)
+    # the constraint rows span the oracle's to the row tolerance of the face rows (1e-6)
+    rng = np.random.default_rng(0)
+    for _ in range(2):
+        x = rng.standard_normal(m.nG)
+        assert _rel(s.apply_preconditioner(x), m.apply_M(x)) < 1e-6
+    u, sinfo = s.solve(B.free_load_vector(prob))
+    assert abs(sinfo["iters"] - res.iters) <= 1
+    kr = res.condition()[1] / res.condition()[0]
+    assert abs(sinfo["kappa"] - kr) <= 0.01 * kr
+    assert _rel(u, res.u) <= 1e-7
+
+
+def test_edge_rows_bring_kappa_below_tau_on_channels():
+    prob = CASES["elast8_channels_2x2x2"]()
+    f = B.free_load_vector(prob)
+    kappa = {}
+    for keep in (False, True):
+        s = B.Solver(precision=B.FP64)
+        s.set_mesh_problem(prob)
+        s.set_edge_rows(keep)
+        s.setup()
+        s.adapt(TAU)
+        _, info = s.solve(f)
+        kappa[keep] = info["kappa"]
+        n_rows, n_edges = s.edge_rows()
+        assert (n_rows > 0 and n_edges > 0) if keep else (n_rows, n_edges) == (0, 0)
+    assert kappa[True] < TAU
+    assert kappa[False] > 100 * kappa[True]
