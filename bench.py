@@ -135,6 +135,8 @@ def _arm(args, precision, prob, dev_arrays, f_host, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     solver = B.Solver(precision=precision, tol=1e-8, stream=stream.cuda_stream)
+    if args.edge_rows:
+        solver.set_edge_rows(True)
 
     def step():
         solver.set_mesh(prob.ncomp, d_xyz, d_el, d_coef, prob.nu, d_sub, prob.nsub, d_dir)
@@ -355,6 +357,9 @@ def run_gpu(args, rank, world, local_rank):
     }
     line["config"]["precision"] = ("mixed (interior: FP32 factorization + FP64 refinement; pair condensations and "
                                    "local saddle: double-float partial Cholesky; eigen, coarse inverse, PCG: FP64)")
+    line["config"]["edge_rows"] = bool(args.edge_rows)
+    if args.edge_rows:
+        line["n_edge_rows"] = solver.edge_rows()[0]
     return line
 
 
@@ -406,6 +411,9 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="poisson24", choices=sorted(WORKLOADS))
+    ap.add_argument("--edge-rows", action="store_true",
+                    help="also keep the adaptive edge rows (Section 3's split rows, one basis per edge); "
+                         "poisson24 and elast32 workloads")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
