@@ -47,3 +47,5 @@ def test_host_only_calls(lib):
     assert B._lib.bddc_set_corners(None, 0, None) == 1
     assert B._lib.bddc_select_corners(None, None) == 1
     assert B._lib.bddc_set_problem(None, 1, 1, 1, None, None, 0) == 1
+    assert B._lib.bddc_set_edge_rows(None, 1) == 1
+    assert B._lib.bddc_get_edge_rows(None, None, None) == 1
