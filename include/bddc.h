@@ -235,7 +235,8 @@ BDDC_API bddc_status bddc_setup(bddc_handle *h);
  * pair eigenproblem (eq. (eig-matrix)) and adds, for every eigenvalue
  * lambda > tau, the face part of d = w^T (I-E)^T S^c (I-E) (eq. (d-def))
  * as a weighted-average face constraint (edge parts dropped, Remark of
- * Section 3), then rebuilds the preconditioner.  info may be NULL.
+ * Section 3, unless bddc_set_edge_rows keeps them), then rebuilds the
+ * preconditioner.  info may be NULL.
  * Errors: BDDC_ESTATE (no setup), BDDC_ENOTSPD, BDDC_EASSUMPTION. */
 BDDC_API bddc_status bddc_adapt(bddc_handle *h, double tau, bddc_adapt_info *info);
 

@@ -9,8 +9,9 @@ is solved in the factorspace modulo null(Pi S^c_ij Pi) (eq. (eig-nullspace)),
 and for every eigenvalue above tau (Algorithm 3.1: smallest k_ij with
 lambda_{k_ij+1} <= tau) the row d = w^T Pi (I-E)^T S^c (I-E) Pi (eq. (d-def)) is
 kept.  Its face part becomes a new weighted-average constraint (the edge
-parts are dropped, Remark at the end of Section 3).  omega_ij = lambda_1 and
-the indicator is omega~ = max omega_ij (eq. (cond-ind)).
+parts are dropped, Remark at the end of Section 3, unless adapt(keep_edges=...)
+keeps them as edge rows).  omega_ij = lambda_1 and the indicator is
+omega~ = max omega_ij (eq. (cond-ind)).
 
 Steps, in the paper's notation:
   1. S^c_ij: diag(S_i, S_j) on the interface dofs of the pair, assembled at

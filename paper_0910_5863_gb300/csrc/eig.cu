@@ -10,9 +10,10 @@
 //      gives lambda_1..lambda_{k+1},
 //   3. inverse iteration on T (LU with row interchanges) for the k vectors,
 //      re-orthogonalised inside clusters, and back-transformation,
-//   4. face rows d = (W1 y)|face (the face part of eq. (d-def); edge parts
-//      are dropped as in the paper's Remark), normalised and orthogonalised
-//      with row pivoting; rows whose pivot is below drop_rel are dropped.
+//   4. face rows d = (W1 y)|face (the face part of eq. (d-def); the edge
+//      parts are dropped as in the paper's Remark, or kept by the edge-row
+//      kernels further down), normalised and orthogonalised with row
+//      pivoting; rows whose pivot is below drop_rel are dropped.
 #include "common.cuh"
 #include <algorithm>
 #include "eig.h"
