@@ -233,7 +233,6 @@ def edge_rows(model, res, orthonormal=True):
     Returns [(edge nodes, rows)], the rows over the edge's dofs in global dof order; an
     edge part below DROP_REL of its whole row's norm carries no constraint and is left out."""
     ns = res.s_gdofs.size
-    c = model.ncomp
     d_i = res.d_full[:, :ns]
     full = np.linalg.norm(res.d_full, axis=1)
     out = []
@@ -241,7 +240,7 @@ def edge_rows(model, res, orthonormal=True):
         if not set(res.pair) <= set(key):
             continue
         gd = model.glob_gdofs(nodes)
-        pos = np.searchsorted(res.s_gdofs, gd)
+        pos = np.minimum(np.searchsorted(res.s_gdofs, gd), ns - 1)
         assert np.all(res.s_gdofs[pos] == gd), "an edge of the pair outside s"
         part = d_i[:, pos]
         keep = np.linalg.norm(part, axis=1) > DROP_REL * full
