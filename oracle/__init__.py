@@ -9,7 +9,8 @@ bddc (Schur complements, Lemma 2.1 preconditioner, PCG, Lanczos estimate),
 adaptive (pair eigenproblems and face constraints, Algorithm 3.1),
 change_of_variables (Section 5: pivoted-QR change of variables, the saddle,
 projected and primal forms of the preconditioner in the new variables),
-native (the cyclic Jacobi helper in jacobi.c).
+lobpcg (Section 3: LOBPCG on the pair pencil in the factorspace, plain or
+preconditioned by B^+), native (the cyclic Jacobi helper in jacobi.c).
 """
 from .bddc import Model, pcg, lanczos_condition, lanczos_tridiagonal
 from .adaptive import adapt, pair_problem, orthonormal_rows

@@ -64,6 +64,7 @@ class PairResult:
     W: np.ndarray = None
     L: np.ndarray = None
     Shat: np.ndarray = None
+    Q: np.ndarray = None       # orthonormal basis of range(Pi) (2 n_s x dim)
 
 
 def pair_data(model, i, j):
@@ -190,7 +191,7 @@ def pair_problem(model, i, j, tau, keep_matrices=False, n_fixed=None, include_ad
     res = PairResult((i, j), lam, n_null, sel, face_rows, np.unique(pd["s_nodes"][pd["face_mask"]]),
                      d, pd["s_g"], pd["face_mask"], ties)
     if keep_matrices:
-        res.W, res.L, res.Shat = W, L, Shat
+        res.W, res.L, res.Shat, res.Q = W, L, Shat, Q
     return res
 
 
