@@ -486,3 +486,28 @@ def test_three_dominant_eigenvectors_per_face():
     M2 = _dense_op(m2.apply_M, m2.nG)
     lmax2 = np.linalg.eigvals(M2 @ S).real.max()
     assert abs(lmax2 - lam[3]) < 1e-7 * lam[3]
+
+
+def test_pair_elimination_is_singular_on_two_element_substructures():
+    """6^3 elasticity in 3 x 3 x 3 substructures (2 elements wide) with stiff channels:
+    the block that the pair problems around the central substructure (13) eliminate,
+    S^c_ij without s and the shared corners, is singular to rounding, so a Cholesky of
+    it (the library's pair condensation) must stop with a non-positive pivot; with
+    substructures 4 elements wide the same blocks are positive definite."""
+    from oracle.adaptive import pair_data
+
+    def min_ratio(prob, pairs):
+        m = oracle.Model(prob)
+        m.schur()
+        worst = np.inf
+        for (i, j) in pairs:
+            pd = pair_data(m, i, j)
+            Sc = pd["Sc"]
+            mask = np.ones(Sc.shape[0], dtype=bool)
+            mask[np.concatenate([pd["pos_i"], pd["pos_j"]])] = False
+            w = np.linalg.eigvalsh(Sc[np.ix_(mask, mask)])
+            worst = min(worst, w[0] / w[-1])
+        return worst
+
+    assert min_ratio(P.elasticity_cube(6, 3, channels=3, seed=1), [(13, 14), (13, 16), (13, 22)]) < 1e-13
+    assert min_ratio(P.elasticity_cube(12, 3, channels=3, seed=1), [(13, 14), (13, 16), (13, 22)]) > 1e-12
