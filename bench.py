@@ -36,6 +36,9 @@ WORKLOADS = {
     # 32^3 elasticity, 64 substructures, 8 stiff channels E = 1e6, clamped z = 0
     "elast32": ("elast32_4x4x4_channels1e6_adaptive_tau10", "32x32x32 Q1 hex, 3 dofs/node",
                 "config_elasticity_channels"),
+    # 48x48x24 elasticity, 64 region-grown irregular substructures, E in {1, 1e3} by z-layers of 4
+    "irregular48": ("elast48x48x24_irregular64_layers1e3_adaptive_tau10", "48x48x24 Q1 hex, 3 dofs/node",
+                    "config_irregular_elasticity"),
     # 256 independent Poisson problems (2^3 or 3^3 substructures of 6^3..10^3 elements,
     # lognormal coefficients sigma = 2), solved by concurrent handles on separate streams
     "batch256": ("batch256_poisson_lognormal_adaptive_tau10", "256 problems, 12^3..30^3 Q1 hex",
@@ -301,6 +304,16 @@ def run_gpu(args, rank, world, local_rank):
                   torch.from_numpy(np.ascontiguousarray(prob.elem_sub, dtype=np.int32)).to(dev),
                   torch.from_numpy(np.ascontiguousarray(prob.dirichlet, dtype=np.uint8)).to(dev))
     f_host = B.free_load_vector(prob)
+    if args.arm != "both":   # one arm alone (profiling runs): its step time and phases only
+        prec = B.MIXED if args.arm == "mixed" else B.FP64
+        solver, t, ph, ad, info, launches, clk = _arm(args, prec, prob, dev_arrays, f_host, world, local_rank)
+        return {"metric": METRIC, "value": t, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if args.arm == "mixed" else "f64", "data": "synthetic",
+                "config": dict(_config(prob, args.seed, args.workload), precision=args.arm), "arm": args.arm,
+                "gpu_launches": int(launches), "clocks": clk, "phase_ms": _phase_summary(ph),
+                "iters": info["iters"], "kappa": info["kappa"], "relres": info.get("relres"),
+                "n_added": ad["n_added"], "omega": ad["omega"]}
     solver, t_mixed, ph_mixed, ad, info, launches, clk = _arm(args, B.MIXED, prob, dev_arrays, f_host, world,
                                                               local_rank)
     _, t_fp64, ph_fp64, ad64, info64, launches64, clk64 = _arm(args, B.FP64, prob, dev_arrays, f_host, world,
@@ -412,6 +425,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="poisson24", choices=sorted(WORKLOADS))
+    ap.add_argument("--arm", default="both", choices=["both", "mixed", "fp64"],
+                    help="precision arms to time (the fp64 sub-object needs both)")
     ap.add_argument("--edge-rows", action="store_true",
                     help="also keep the adaptive edge rows (Section 3's split rows, one basis per edge); "
                          "poisson24 and elast32 workloads")

@@ -41,11 +41,6 @@ from .native import jacobi_eigh
 
 NULL_REL = 1e-12
 DROP_REL = 1e-10
-# Rank rule of the per-edge bases (keep_edges="glob"): the edge rows of the face pairs on
-# one edge overlap in exact arithmetic, and below this pivot a rounding-error direction of
-# the mixed-precision eigenvectors (~1e-7, double-float reduction) cannot be told from a
-# real one; the same rule holds for every precision.
-EDGE_DROP_REL = 1e-6
 TIE_REL = 1e-6
 
 
@@ -195,6 +190,30 @@ def pair_problem(model, i, j, tau, keep_matrices=False, n_fixed=None, include_ad
     return res
 
 
+def row_pivots(rows):
+    """The pivots of Gram-Schmidt with row pivoting on the normalised rows, relative to
+    the first (non-increasing, as in a column-pivoted QR): the rows kept at a drop
+    threshold t are those whose pivot is >= t."""
+    if rows.shape[0] == 0:
+        return np.zeros(0)
+    R = rows / np.linalg.norm(rows, axis=1, keepdims=True)
+    piv = []
+    remaining = list(range(R.shape[0]))
+    while remaining:
+        norms = np.array([np.linalg.norm(R[k]) for k in remaining])
+        kk = int(np.argmax(norms))
+        p = norms[kk]
+        piv.append(p)
+        if p == 0.0:
+            break
+        q = R[remaining[kk]] / p
+        remaining.pop(kk)
+        for k in remaining:
+            R[k] = R[k] - (R[k] @ q) * q
+    piv = np.array(piv)
+    return piv / piv[0]
+
+
 def orthonormal_rows(rows, drop_rel=DROP_REL):
     """Normalise rows, then Gram-Schmidt with row pivoting; drop rows whose
     pivot is below drop_rel relative to the first pivot."""
@@ -251,7 +270,7 @@ def edge_rows(model, res, orthonormal=True):
     return out
 
 
-def adapt(model, tau, n_fixed=None, keep_edges=False):
+def adapt(model, tau, n_fixed=None, keep_edges=False, edge_drop_rel=DROP_REL):
     """Algorithm 3.1 on every face pair; the new face rows are added to the model.
     With n_fixed, the n_fixed dominant eigenvectors of every face are used instead of
     those above tau (Section 7, "3eigv").  keep_edges: the edge parts of the rows d are
@@ -262,7 +281,9 @@ def adapt(model, tau, n_fixed=None, keep_edges=False):
       keep_edges="glob": per edge, one orthonormal basis of the span of every pair's
                          edge rows on it, enforced on all substructures sharing the
                          edge (a stronger constraint set, whose rows stay independent
-                         on every substructure, as a primal coarse space needs)."""
+                         on every substructure, as a primal coarse space needs).
+    edge_drop_rel: the rank rule of those per-edge bases (the rank drop of Section 5, as
+    for the face rows); every edge's relative pivots are returned in edge_pivots."""
     pairs = {}
     for (i, j) in sorted(model.globs.faces):
         pairs[(i, j)] = pair_problem(model, i, j, tau, n_fixed=n_fixed)
@@ -288,14 +309,18 @@ def adapt(model, tau, n_fixed=None, keep_edges=False):
             for enodes, erows in edge_rows(model, res):
                 model.add_constraint("adaptive_edge", enodes, (i, j), erows)
                 n_edge_rows += erows.shape[0]
+    edge_pivots = {}
     for key in sorted(edge_stack):
-        rows = orthonormal_rows(np.vstack(edge_stack[key]), EDGE_DROP_REL)
+        stacked = np.vstack(edge_stack[key])
+        edge_pivots[key] = row_pivots(stacked)
+        rows = orthonormal_rows(stacked, edge_drop_rel)
         subs = sorted(model.globs.sets[key[0]])
         model.add_constraint("adaptive_edge", np.array(key), subs, rows)
         n_edge_rows += rows.shape[0]
     omega = max((r.lam[0] for r in pairs.values() if r.lam.size), default=0.0)
     out = AdaptResult(pairs, omega, n_added, per_face)
     out.n_edge_rows = n_edge_rows
+    out.edge_pivots = edge_pivots
     return out
 
 

@@ -2517,10 +2517,13 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
             launch_edge_parts(dp, (int)epd.size(), h->opt.drop_rel, h->stream);
             check_launch(h);
             auto *dg = h->ar.upload("edgeglobdesc", egd, h->stream);
-            // the rows of the pairs on one edge overlap in exact arithmetic; below 1e-6 of the first
-            // pivot a rounding direction of the mixed modes' eigenvectors (~1e-7) cannot be told
-            // from a real one, so every precision keeps rows only above that
-            launch_edge_globs(dg, (int)egd.size(), std::max(h->opt.drop_rel, 1e-6), h->stream);
+            // the rows of the pairs on one edge overlap in exact arithmetic.  The FP64 path keeps
+            // the rank rule of the face rows (drop_rel).  The mixed modes' eigenvectors carry
+            // rounding directions of ~1e-8 relative (double-float reduction), which that rule
+            // would keep as rows; they keep pivots above 1e-6 of the first only
+            const double edge_drop = h->opt.precision == BDDC_FP64 || h->fp64_class_forced
+                                         ? h->opt.drop_rel : std::max(h->opt.drop_rel, 1e-6);
+            launch_edge_globs(dg, (int)egd.size(), edge_drop, h->stream);
             check_launch(h);
         }
     }

@@ -511,3 +511,32 @@ def test_pair_elimination_is_singular_on_two_element_substructures():
 
     assert min_ratio(P.elasticity_cube(6, 3, channels=3, seed=1), [(13, 14), (13, 16), (13, 22)]) < 1e-13
     assert min_ratio(P.elasticity_cube(12, 3, channels=3, seed=1), [(13, 14), (13, 16), (13, 22)]) > 1e-12
+
+
+# --- averaging weights (Section 7) ---------------------------------------------------
+
+def test_weights_are_the_diagonal_stiffness_before_interior_elimination():
+    """Section 7 takes the averaging weights proportional to the diagonal entries of the
+    stiffness before the interiors are eliminated.  Two substructures of a 6^3 Poisson
+    mesh split at x = 3h: substructure 0 has k1 on its layer of elements touching the
+    face and 100 k1 deeper in, substructure 1 has k2.  A face node touches as many
+    elements on each side, each adding k h / 3 to the diagonal (the Q1 element closed
+    form), so delta_0 = k1 / (k1 + k2) exactly at every interface dof, for the global
+    weights and for the pair weights of E_ij.  Weights from diag(S_i) (after the
+    elimination) differ here, so this pin tells the two readings apart."""
+    k1, k2 = 3.0, 7.0
+    prob = P.poisson_cube(6, 2, s_xyz=(2, 1, 1))
+    ex = np.arange(prob.ne) % 6
+    prob.coef = np.where(ex < 2, 100.0 * k1, np.where(ex == 2, k1, k2))
+    m = oracle.Model(prob)
+    s0, s1 = m.subs
+    expect = k1 / (k1 + k2)
+    assert s0.G.size > 0 and np.abs(s0.deltaG - expect).max() < 1e-14
+    assert np.abs(s1.deltaG - (1.0 - expect)).max() < 1e-14
+    m.schur()
+    pd = pair_data(m, 0, 1)
+    assert np.abs(pd["di"] - expect).max() < 1e-14 and np.abs(pd["dj"] - (1 - expect)).max() < 1e-14
+    # the other reading, diag(S_i) normalised over the pair, is not k1 / (k1 + k2)
+    dS0 = s0.S.diagonal()
+    dS1 = s1.S.diagonal()[[s1.gposG[int(g)] for g in s0.gdof[s0.G]]]
+    assert np.abs(dS0 / (dS0 + dS1) - expect).max() > 1e-2
