@@ -227,8 +227,10 @@ void check_launch(bddc_handle *h) {
 
 // ---- batched partial Cholesky ------------------------------------------------
 // batch tags reported with a failed pivot
-int pchol_tag(const std::string &name) {
+// (a batch name may carry a '#' suffix that keeps its buffers apart, e.g. "E1#2")
+int pchol_tag(const std::string &name_in) {
     static const char *names[] = {"", "AII", "M1", "M1f", "M2", "MC", "E1", "E2", "E3", "F"};
+    const std::string name = name_in.substr(0, name_in.find('#'));
     for (int k = 1; k < 10; ++k)
         if (name == names[k]) return k;
     return 0;
@@ -257,8 +259,16 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const 
             if (kb >= d.nstop) continue;
             int nb = std::min(kPanelNB, d.nstop - kb);
             int below = d.n - kb - nb;
+            // rows [z0, z1) are identity rows that this step leaves untouched (PcholDesc::id0)
+            const int z0 = d.id0 > 0 ? d.id0 + std::max(0, kb + nb - d.idc) : d.n;
+            const int z1 = d.id0 > 0 ? std::min(d.n, d.id0 + d.nstop - d.idc) : d.n;
+            auto idle = [&](int r0, int r1) { return r0 >= z0 && std::min(r1, d.n) <= z1; };
             int np = std::max(1, (below + kPanelRows - 1) / kPanelRows);
-            for (int r = 0; r < np; ++r) pitems.push_back(make_int2(m, r));
+            for (int r = 0; r < np; ++r) {
+                const int r0 = kb + nb + r * kPanelRows;
+                if (r > 0 && idle(r0, r0 + kPanelRows)) continue;
+                pitems.push_back(make_int2(m, r));
+            }
             uitems.push_back(make_int4(m, -1, -1, 0));  // copy of the factored diagonal block
             int tn = d.n - kb - nb;
             int nt = (tn + kTile - 1) / kTile;
@@ -267,8 +277,15 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const 
                 const int cw = std::min(d.ncol, d.n) - kb - nb;
                 ct = cw > 0 ? (cw + kTile - 1) / kTile : 0;
             }
-            for (int ti = 0; ti < nt; ++ti)
-                for (int tj = 0; tj <= ti && tj < ct; ++tj) uitems.push_back(make_int4(m, ti, tj, 0));
+            for (int ti = 0; ti < nt; ++ti) {
+                const int i0 = kb + nb + ti * kTile;
+                if (idle(i0, i0 + kTile)) continue;
+                for (int tj = 0; tj <= ti && tj < ct; ++tj) {
+                    const int j0 = kb + nb + tj * kTile;
+                    if (idle(j0, j0 + kTile)) continue;
+                    uitems.push_back(make_int4(m, ti, tj, 0));
+                }
+            }
         }
     }
     poff[nsteps] = (int)pitems.size();
@@ -303,7 +320,9 @@ void run_pchol_fp64class(bddc_handle *h, const std::vector<PcholDesc<double>> &d
     launch_ff_convert(dd, di, (int)items.size(), 1, h->stream);
     check_launch(h);
     std::vector<PcholDesc<ff>> fd;
-    for (const auto &d : descs) fd.push_back(PcholDesc<ff>{reinterpret_cast<ff *>(d.A), d.n, d.ld, d.nstop, d.tag, nullptr});
+    for (const auto &d : descs)
+        fd.push_back(PcholDesc<ff>{reinterpret_cast<ff *>(d.A), d.n, d.ld, d.nstop, d.tag, nullptr, d.ncol, d.id0,
+                                   d.idc, d.fail});
     run_pchol<ff>(h, fd, tag);
     launch_ff_convert(dd, di, (int)items.size(), 0, h->stream);
     check_launch(h);
@@ -1311,9 +1330,9 @@ void coarse_setup(bddc_handle *h, bool allow_fp32) {
         DiagOp dop{M1[s], ld1[s], nr, 0, nr, 1.0, mixed ? 1 : 0, 0};
         id1.push_back(dop);
         if (mixed)
-            d1f.push_back(PcholDesc<float>{reinterpret_cast<float *>(M1[s]), N1[s], ld1[s], nr, 0});
+            d1f.push_back(PcholDesc<float>{reinterpret_cast<float *>(M1[s]), N1[s], ld1[s], nr, 0, nullptr, 0, nr});
         else
-            d1.push_back(PcholDesc<double>{M1[s], N1[s], ld1[s], nr, 0});
+            d1.push_back(PcholDesc<double>{M1[s], N1[s], ld1[s], nr, 0, nullptr, 0, nr});
     }
     zero_all(h, zl, "M12");
     run_gathers(h, g1, "M1");
@@ -1479,7 +1498,7 @@ void coarse_setup(bddc_handle *h, bool allow_fp32) {
     g5[0].dst_lower = 1;
     run_gathers(h, g5, "MC");
     run_diag(h, {DiagOp{MC, ldm, nC, 0, nC, 1.0}}, "MC");
-    run_pchol<double>(h, {PcholDesc<double>{MC, 2 * nC, ldm, nC, 0}}, "MC");
+    run_pchol<double>(h, {PcholDesc<double>{MC, 2 * nC, ldm, nC, 0, nullptr, 0, nC}}, "MC");
     double *SCinv = h->ar.get_t<double>("SCinv", (size_t)nC * nC);
     GatherOp o = gop(MC, ldm, SCinv, nC, nC, nC);
     o.src_row_off = nC;
@@ -2059,7 +2078,14 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
         fp.nsel = fp.nkept = fp.ties = 0;
     }
     phase_begin(h, 3);
-    // E1: per (sub, face) Schur complement of S_i onto t = [s (s order); shared corners]
+    // E1: per (sub, face) Schur complement of S_i onto t = [s (s order); shared corners],
+    // by nested condensation.  The faces of every substructure are split into a binary
+    // tree; a tree node holds the Schur complement of S_i onto the union R of its faces'
+    // target sets, formed from its parent's by eliminating the parent's dofs outside R
+    // (a gather + a partial Cholesky).  By the quotient property of Schur complements a
+    // leaf's matrix is the Schur complement of S_i onto its target, as a direct
+    // elimination would give it; with halving sets the tree costs ~0.8 n^3 flop per
+    // substructure where one elimination per face costs ~n^3/3 each.
     std::vector<PcholDesc<double>> dE1, dE2, dE3;
     std::vector<GatherOp> gE1, gE2, gE3, gQ;
     std::vector<DiagOp> idE3;
@@ -2079,48 +2105,157 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
     };
     std::vector<PairBufs> pbufs(nf);
     int nmax = 0;
-    for (int f = 0; f < nf; ++f) {
-        auto &fp = h->faces[f];
-        auto &B = pbufs[f];
-        const int ns = (int)fp.s_g.size(), nc = (int)fp.ci_pos.size();
-        B.ns = ns;
-        B.nc = nc;
-        nmax = std::max(nmax, ns);
-        for (int side = 0; side < 2; ++side) {
-            int s = side ? fp.j : fp.i;
-            auto &sd = h->subs[s];
-            const auto &spos = side ? fp.pos_j : fp.pos_i;
-            const auto &cpos = side ? fp.cj_pos : fp.ci_pos;
-            std::vector<char> in_t(sd.nG, 0);
-            for (int p : spos) in_t[p] = 1;
-            for (int p : cpos) in_t[p] = 1;
-            std::vector<int> perm;
-            for (int k = 0; k < sd.nG; ++k)
-                if (!in_t[k]) perm.push_back(k);
-            int no = (int)perm.size();
-            perm.insert(perm.end(), spos.begin(), spos.end());
-            perm.insert(perm.end(), cpos.begin(), cpos.end());
-            int n = (int)perm.size();
-            B.nT[side] = n;
-            B.no[side] = no;
-            B.ldT[side] = round_up(std::max(n, 1), 8);
-            B.T[side] = h->ar.get_t<double>("E1_" + std::to_string(f) + "_" + std::to_string(side), (size_t)B.ldT[side] * n);
-            int *dp = h->ar.upload("E1p_" + std::to_string(f) + "_" + std::to_string(side), perm, h->stream);
-            GatherOp o = gop(sd.S, sd.ldS, B.T[side], B.ldT[side], n, n);
-            o.rmap = dp;
-            o.cmap = dp;
-            o.dst_lower = 1;
-            gE1.push_back(o);
-            dE1.push_back(PcholDesc<double>{B.T[side], n, B.ldT[side], no, 0});
-        }
-    }
-    run_gathers(h, gE1, "E1");
-    run_pchol_fp64class(h, dE1, "E1");
     // algorithmic FP64 flops of the condensations: partial Cholesky of n with nstop = m
     // (m^3/3 + m^2 (n - m) + m (n - m)^2), for the E1 matrices here and E2, E3 below
     auto pchol_flop = [](double n, double m) { return m * m * m / 3.0 + m * m * (n - m) + m * (n - m) * (n - m); };
     double cflop = 0.0;
-    for (auto &dd : dE1) cflop += pchol_flop(dd.n, dd.nstop);
+    struct CondNode {
+        int sub = 0, parent = -1, leaf = -1, depth = 0;
+        std::vector<int> R;          // retained interface positions, in the node's matrix order
+        const double *base = nullptr;
+        int ld = 0, off = 0, n = 0;  // matrix (lower triangle) at base[off + a + (off + b) ld], a, b < |R|
+    };
+    std::vector<CondNode> cn;
+    std::vector<std::vector<int>> leaf_t(2 * nf);   // leaf (2 f + side): target [s (s order); corners]
+    std::vector<std::vector<int>> sub_leaves(h->nsub);
+    for (int f = 0; f < nf; ++f) {
+        auto &fp = h->faces[f];
+        pbufs[f].ns = (int)fp.s_g.size();
+        pbufs[f].nc = (int)fp.ci_pos.size();
+        nmax = std::max(nmax, pbufs[f].ns);
+        for (int side = 0; side < 2; ++side) {
+            const auto &spos = side ? fp.pos_j : fp.pos_i;
+            const auto &cpos = side ? fp.cj_pos : fp.ci_pos;
+            auto &t = leaf_t[2 * f + side];
+            t.assign(spos.begin(), spos.end());
+            t.insert(t.end(), cpos.begin(), cpos.end());
+            sub_leaves[side ? fp.j : fp.i].push_back(2 * f + side);
+        }
+    }
+    int max_depth = 0;
+    for (int s = 0; s < h->nsub; ++s) {
+        auto &leaves = sub_leaves[s];
+        if (leaves.empty()) continue;
+        // leaves ordered by the mean interface position of their targets (interface
+        // positions follow the global dof order, so nearby faces stay together)
+        std::vector<double> key(2 * nf, 0.0);
+        for (int l : leaves) {
+            double m = 0.0;
+            for (int p : leaf_t[l]) m += p;
+            key[l] = m / std::max<size_t>(1, leaf_t[l].size());
+        }
+        std::stable_sort(leaves.begin(), leaves.end(), [&](int a, int b) { return key[a] < key[b]; });
+        // recursive split into halves of about equal target size
+        struct Range { int lo, hi, parent, depth; };
+        std::vector<Range> todo{{0, (int)leaves.size(), -1, 0}};
+        std::vector<std::pair<int, std::pair<int, int>>> made;   // node -> leaf range
+        while (!todo.empty()) {
+            Range r = todo.back();
+            todo.pop_back();
+            CondNode nd;
+            nd.sub = s;
+            nd.parent = r.parent;
+            nd.depth = r.depth;
+            max_depth = std::max(max_depth, r.depth);
+            const int id = (int)cn.size();
+            if (r.hi - r.lo == 1) {
+                nd.leaf = leaves[r.lo];
+                nd.R = leaf_t[nd.leaf];
+            } else {
+                std::vector<char> in(h->subs[s].nG, 0);
+                size_t tot = 0;
+                for (int k = r.lo; k < r.hi; ++k) tot += leaf_t[leaves[k]].size();
+                for (int k = r.lo; k < r.hi; ++k)
+                    for (int p : leaf_t[leaves[k]]) in[p] = 1;
+                for (int p = 0; p < h->subs[s].nG; ++p)
+                    if (in[p]) nd.R.push_back(p);
+                size_t acc = 0;
+                int mid = r.lo + 1;
+                for (int k = r.lo; k < r.hi - 1; ++k) {
+                    acc += leaf_t[leaves[k]].size();
+                    mid = k + 1;
+                    if (2 * acc >= tot) break;
+                }
+                todo.push_back({r.lo, mid, id, r.depth + 1});
+                todo.push_back({mid, r.hi, id, r.depth + 1});
+            }
+            cn.push_back(std::move(nd));
+        }
+    }
+    // level by level: every node's matrix from its parent's (the roots from S_i)
+    for (int d = 0; d <= max_depth; ++d) {
+        std::vector<GatherOp> g;
+        std::vector<PcholDesc<double>> dd;
+        for (int v = 0; v < (int)cn.size(); ++v) {
+            auto &nd = cn[v];
+            if (nd.depth != d) continue;
+            const auto &sd = h->subs[nd.sub];
+            std::vector<int> perm;           // parent-local indices: [eliminated; R in node order]
+            const double *src;
+            int ld_src, off_src, n_par;
+            if (nd.parent < 0) {
+                src = sd.S;
+                ld_src = sd.ldS;
+                off_src = 0;
+                n_par = sd.nG;
+                if (nd.leaf < 0 && (int)nd.R.size() == sd.nG) {   // all of S_i retained: the root is S_i
+                    nd.base = sd.S;
+                    nd.ld = sd.ldS;
+                    nd.off = 0;
+                    nd.n = sd.nG;
+                    continue;
+                }
+                std::vector<char> in(sd.nG, 0);
+                for (int p : nd.R) in[p] = 1;
+                for (int p = 0; p < sd.nG; ++p)
+                    if (!in[p]) perm.push_back(p);
+                perm.insert(perm.end(), nd.R.begin(), nd.R.end());
+            } else {
+                const auto &pn = cn[nd.parent];
+                src = pn.base;
+                ld_src = pn.ld;
+                off_src = pn.off;
+                n_par = (int)pn.R.size();
+                std::vector<int> loc(sd.nG, -1);
+                for (int k = 0; k < n_par; ++k) loc[pn.R[k]] = k;
+                std::vector<char> in(n_par, 0);
+                for (int p : nd.R) in[loc[p]] = 1;
+                for (int k = 0; k < n_par; ++k)
+                    if (!in[k]) perm.push_back(k);
+                for (int p : nd.R) perm.push_back(loc[p]);
+            }
+            const int n = n_par, no = n - (int)nd.R.size();
+            nd.ld = round_up(std::max(n, 1), 8);
+            nd.n = n;
+            nd.off = no;
+            double *buf = h->ar.get_t<double>("E1n_" + std::to_string(v), (size_t)nd.ld * std::max(n, 1));
+            nd.base = buf;
+            int *dp = h->ar.upload("E1p_" + std::to_string(v), perm, h->stream);
+            GatherOp o = gop(src, ld_src, buf, nd.ld, n, n);
+            o.rmap = dp;
+            o.cmap = dp;
+            o.src_row_off = off_src;
+            o.src_col_off = off_src;
+            o.src_sym = 1;
+            o.dst_lower = 1;
+            g.push_back(o);
+            if (no > 0) {
+                dd.push_back(PcholDesc<double>{buf, n, nd.ld, no, 0});
+                cflop += pchol_flop(n, no);
+            }
+        }
+        run_gathers(h, g, "E1#" + std::to_string(d));
+        run_pchol_fp64class(h, dd, "E1#" + std::to_string(d));
+    }
+    for (const auto &nd : cn) {
+        if (nd.leaf < 0) continue;
+        auto &B = pbufs[nd.leaf / 2];
+        const int side = nd.leaf % 2;
+        B.T[side] = const_cast<double *>(nd.base);
+        B.nT[side] = nd.n;
+        B.ldT[side] = nd.ld;
+        B.no[side] = nd.off;
+    }
     // E2: pair matrix [C; s_i; s_j], eliminate C -> S^ (2 ns)
     ZeroList zy;
     for (int f = 0; f < nf; ++f) {
@@ -2228,7 +2363,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
             }
         }
         if (groups.empty()) {
-            dE3.push_back(PcholDesc<double>{B.M3, n3, B.ldM3, 2 * ns, 0});
+            dE3.push_back(PcholDesc<double>{B.M3, n3, B.ldM3, 2 * ns, 0, nullptr, 0, 2 * ns, ns});
         } else {
             std::vector<int> newidx(ns, 0), lead(ns, -1), grp(ns, -1), keep, gptr{0}, gidx;
             for (size_t g = 0; g < groups.size(); ++g) {

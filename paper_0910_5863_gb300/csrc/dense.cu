@@ -78,7 +78,12 @@ __global__ void __launch_bounds__(PANEL_ROWS) pchol_panel_kernel(const PcholDesc
         else if (i == j) Ld[j][j] *= inv_d[j];  // a_jj / sqrt(a_jj)
     }
     __syncthreads();
-    if (bad && tid == 0 && w.y == 0) dev_fail(st, BDDC_DEV_ERR_NOTSPD, d.tag * 100000 + w.x, kb);
+    if (bad && tid == 0 && w.y == 0) {
+        if (d.fail)
+            *d.fail = 1;
+        else
+            dev_fail(st, BDDC_DEV_ERR_NOTSPD, d.tag * 100000 + w.x, kb);
+    }
     // Every CTA of this matrix factors the diagonal block from A, so the factor
     // must not be written into A during this launch: CTA 0 leaves it in the
     // scratch and the update launch of the same step copies it into A.

@@ -16,6 +16,14 @@ struct PcholDesc {
     int tag;    // batch tag reported with a failed pivot (item = tag * 100000 + matrix)
     T *diag;    // NB x NB scratch: the factored diagonal block of the current step
     int ncol;   // > 0: the trailing updates stop at column ncol (a block-column panel)
+    // Rows [id0, id0 + nstop - idc) start as an identity block under the eliminated
+    // columns: row id0 + q = e_{idc + q}^T (as in [[M, .], [I, 0]] with idc = 0; id0 = 0:
+    // none).  Such a row stays zero in every column before idc + q, so at the step of
+    // columns [kb, kb + nb) the rows with idc + q >= kb + nb take no part: their work
+    // items are skipped.
+    int id0;
+    int idc;
+    int *fail;  // non-NULL: a non-positive pivot sets *fail = 1 instead of the device status
 };
 
 // dst[p + dst_row_off, q + dst_col_off] (+)= scale * rscale[p] * cscale[q] * src(rmap[p], cmap[q])
