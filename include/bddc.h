@@ -93,6 +93,20 @@ typedef struct {
      * in the energy form, whose error R^T A_II^-1 R is second order in that residual,
      * so the default 1e-8 already gives S_i to ~1e-13 relative). */
     double refine_tol;
+    /* Pair eigenproblems (Section 3).  By default every face is solved densely
+     * (Householder reduction, by several CTAs per face above order 200, then Sturm
+     * counts, bisection and inverse iteration).  Faces whose reduced problem has
+     * order above eig_large_n (default -1: none) are instead solved by batched LOBPCG
+     * (the eigensolver the paper names for them):
+     * blocks of 16 (then 32) Ritz vectors, FP64 products and Rayleigh-Ritz, until every
+     * selected pair and the largest rejected one has ||C x - theta x|| <= eig_tol |theta|
+     * (default 1e-8) or eig_maxit iterations (default 240) have run.  The number of
+     * eigenvalues above tau is then certified by a Cholesky factorization (see
+     * bddc_adapt); a face that does not converge or fails the certificate is solved by
+     * the dense kernel.  Both paths select the same constraints. */
+    int eig_large_n;
+    double eig_tol;
+    int eig_maxit;
 } bddc_options;
 
 /* One substructure of an algebraic problem (bddc_set_problem): its local matrix
@@ -114,12 +128,18 @@ typedef struct {
     int n_added;           /* adaptive constraints added (after rank drop) */
     int n_ties;            /* eigenvalues within 1e-6 relative of tau */
     double omega;          /* condition number indicator max_ij lambda_ij,1 (eq. (cond-ind)) */
+    int n_lobpcg;          /* faces solved by LOBPCG (order above bddc_options.eig_large_n) */
+    int lobpcg_iters;      /* the most LOBPCG iterations any of them needed */
+    int n_dense_fallback;  /* of those, faces handed to the dense kernel (no convergence,
+                              block too small, or a failed count certificate) */
 } bddc_adapt_info;
 
 typedef struct {
     int iters;             /* PCG iterations */
     int converged;         /* 1 if ||r_k|| <= tol ||r_0|| */
-    double relres;         /* ||r_k|| / ||r_0|| of the recurrence */
+    double relres;         /* true relative residual ||g - S u_G|| / ||g|| of the condensed
+                              interface problem (eq. (reduced-problem)), recomputed on the
+                              device from the local S_i after PCG */
     double kappa;          /* Lanczos estimate lambda_max / lambda_min */
     double setup_ms;       /* last bddc_setup + bddc_adapt, device time */
     double solve_ms;       /* this solve, device time */
@@ -127,6 +147,7 @@ typedef struct {
     int coarse_fp32;       /* 1: the local saddle operators came from the FP32 factorization */
     int refine_steps;      /* mixed modes: corrections of the interior refinement */
     double refine_relres;  /* mixed modes: its final largest relative residual */
+    double relres_recurrence; /* ||r_k|| / ||r_0|| of the PCG recurrence (the stopping test) */
 } bddc_solve_info;
 
 /* Fills *opt with the defaults above. */
@@ -255,10 +276,10 @@ BDDC_API bddc_status bddc_adapt_fixed(bddc_handle *h, int n_per_face, bddc_adapt
  * Remark closing Section 3, which is the default keep = 0).  Per edge, the edge parts
  * of every face pair's rows on it (each normalised; a part below drop_rel * sqrt(2) |d|
  * is left out) are orthonormalised with row pivoting, keeping rows while the pivot
- * exceeds max(drop_rel, 1e-6) of the first (the pairs' rows on one edge overlap in exact
- * arithmetic, and below 1e-6 the mixed modes' eigenvectors cannot tell a rounding
- * direction from a real one), and the basis becomes a constraint on all substructures
- * sharing the edge.  That is a stronger
+ * exceeds drop_rel of the first (BDDC_FP64), or max(drop_rel, 1e-6) in the mixed modes
+ * (the pairs' rows on one edge overlap in exact arithmetic, and below 1e-6 the mixed
+ * modes' eigenvectors cannot tell a rounding direction from a real one), and the basis
+ * becomes a constraint on all substructures sharing the edge.  That is a stronger
  * constraint set than the pairwise split rows, and with it every face pair's largest
  * eigenvalue on the constrained space is still at most its lambda_{k+1} <= tau, so
  * omega~ <= tau (the Courant-Fisher-Weyl principle with Algorithm 3.1); unlike the
@@ -351,6 +372,26 @@ BDDC_API bddc_status bddc_apply_schur(bddc_handle *h, const double *x, double *y
  * Cholesky factorizations (order n, m columns eliminated); other phases
  * report 0 FLOPs.  ms[cap], flop[cap] may be NULL; *n = 9. */
 BDDC_API bddc_status bddc_get_phase_times(const bddc_handle *h, double *ms, double *flop, int cap, int *n);
+
+/* Kernel timers for roofline measurements.  on = 1 starts them (and clears the
+ * totals), on = 0 stops them.  While on, every launch of the kernels below is
+ * bracketed by CUDA events on the handle's stream.  Errors: BDDC_EINVAL. */
+BDDC_API bddc_status bddc_set_kernel_timing(bddc_handle *h, int on);
+
+/* Totals since the last bddc_set_kernel_timing(h, 1), one entry per class:
+ *   0 trailing updates of the double-float partial Cholesky (pchol_update_kernel<ff>)
+ *   1 trailing updates of the FP64 partial Cholesky
+ *   2 trailing updates of the FP32 partial Cholesky
+ *   3 tensor-core 3xTF32 GEMMs (tc_gemm_kernel)
+ *   4 the persistent PCG kernel (solve launches)
+ *   5 the face reductions (face_eig_kernel, tridiag_multi_kernel)
+ * ms: summed device time of the launches; work: their algorithmic flop (partial
+ * Cholesky updates: 2 x the multiply-adds of the lower-triangle tiles launched;
+ * GEMMs: 2 M N K, one of the three TF32 products; reductions: 4/3 n^3 per face;
+ * PCG: 0); launches: their count.  *n = 6; cap limits the entries written.  The call
+ * waits for the recorded events.  Errors: BDDC_EINVAL (NULL handle). */
+BDDC_API bddc_status bddc_get_kernel_times(bddc_handle *h, double *ms, double *work, int64_t *launches, int cap,
+                                           int *n);
 
 /* Number of kernel launches made by the handle so far (all phases). */
 BDDC_API int64_t bddc_launch_count(const bddc_handle *h);

@@ -27,7 +27,8 @@ EXPORTS = ["bddc_default_options", "bddc_create", "bddc_destroy", "bddc_set_mesh
            "bddc_apply_preconditioner", "bddc_apply_schur", "bddc_launch_count", "bddc_status_str",
            "bddc_last_error", "bddc_get_phase_times", "bddc_get_local_matrix", "bddc_set_problem",
            "bddc_set_corners", "bddc_select_corners", "bddc_get_face_rows", "bddc_barrier_selftest",
-           "bddc_classify_q1", "bddc_adapt_fixed", "bddc_set_edge_rows", "bddc_get_edge_rows"]
+           "bddc_classify_q1", "bddc_adapt_fixed", "bddc_set_edge_rows", "bddc_get_edge_rows",
+           "bddc_set_kernel_timing", "bddc_get_kernel_times"]
 PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
           "analysis_host", "condensed_rhs", "pcg", "recovery"]
 
@@ -35,7 +36,8 @@ PHASES = ["assembly", "interior_elimination", "coarse_setup", "pair_condensation
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int), ("drop_rel", C.c_double),
                 ("timeout_s", C.c_double), ("stream", C.c_void_p), ("dev_alloc", C.c_void_p),
-                ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p), ("refine_tol", C.c_double)]
+                ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p), ("refine_tol", C.c_double),
+                ("eig_large_n", C.c_int), ("eig_tol", C.c_double), ("eig_maxit", C.c_int)]
 
 
 class Subdomain(C.Structure):
@@ -48,13 +50,20 @@ _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 
 class AdaptInfo(C.Structure):
-    _fields_ = [("n_faces", C.c_int), ("n_added", C.c_int), ("n_ties", C.c_int), ("omega", C.c_double)]
+    _fields_ = [("n_faces", C.c_int), ("n_added", C.c_int), ("n_ties", C.c_int), ("omega", C.c_double),
+                ("n_lobpcg", C.c_int), ("lobpcg_iters", C.c_int), ("n_dense_fallback", C.c_int)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("relres", C.c_double), ("kappa", C.c_double),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("interior_fp32", C.c_int),
-                ("coarse_fp32", C.c_int), ("refine_steps", C.c_int), ("refine_relres", C.c_double)]
+                ("coarse_fp32", C.c_int), ("refine_steps", C.c_int), ("refine_relres", C.c_double),
+                ("relres_recurrence", C.c_double)]
+
+
+def _adapt_dict(info):
+    return {"n_faces": info.n_faces, "n_added": info.n_added, "n_ties": info.n_ties, "omega": info.omega,
+            "n_lobpcg": info.n_lobpcg, "lobpcg_iters": info.lobpcg_iters, "n_dense_fallback": info.n_dense_fallback}
 
 
 class BddcError(RuntimeError):
@@ -96,6 +105,8 @@ def load(path: str = LIB_PATH):
         "bddc_status_str": (C.c_char_p, [i32]),
         "bddc_last_error": (C.c_char_p, [vp]),
         "bddc_get_phase_times": (i32, [vp, vp, vp, i32, vp]),
+        "bddc_set_kernel_timing": (i32, [vp, i32]),
+        "bddc_get_kernel_times": (i32, [vp, vp, vp, vp, i32, vp]),
         "bddc_get_local_matrix": (i32, [vp, i32, vp, i32, i32]),
         "bddc_set_problem": (i32, [vp, i64, i32, C.c_int32, vp, vp, i32]),
         "bddc_set_corners": (i32, [vp, i64, vp]),
@@ -147,13 +158,15 @@ class Solver:
     """One handle of the library (one GPU, one stream)."""
 
     def __init__(self, precision=FP64, tol=1e-8, maxit=1000, drop_rel=1e-10, timeout_s=10.0, stream=None,
-                 allocator=None, refine_tol=None):
+                 allocator=None, refine_tol=None, eig_large_n=None, eig_tol=None, eig_maxit=None):
         """allocator: None (the library's cudaMalloc) or "torch" (device memory from
-        PyTorch's caching allocator on the handle's stream)."""
+        PyTorch's caching allocator on the handle's stream).  eig_large_n / eig_tol /
+        eig_maxit: the batched LOBPCG of the pair problems (bddc_options); None = default."""
         self.lib = load()
         opt = Options()
         self.lib.bddc_default_options(C.byref(opt))
         opt.precision = precision
+        self.precision = precision
         opt.tol = tol
         opt.maxit = maxit
         opt.drop_rel = drop_rel
@@ -161,6 +174,12 @@ class Solver:
         opt.stream = stream
         if refine_tol is not None:
             opt.refine_tol = refine_tol
+        if eig_large_n is not None:
+            opt.eig_large_n = int(eig_large_n)
+        if eig_tol is not None:
+            opt.eig_tol = float(eig_tol)
+        if eig_maxit is not None:
+            opt.eig_maxit = int(eig_maxit)
         self._callbacks = None
         if allocator == "torch":
             self._callbacks = _torch_allocator(stream)
@@ -252,13 +271,13 @@ class Solver:
     def adapt(self, tau):
         info = AdaptInfo()
         self._check(self.lib.bddc_adapt(self.h, float(tau), C.byref(info)))
-        return {"n_faces": info.n_faces, "n_added": info.n_added, "n_ties": info.n_ties, "omega": info.omega}
+        return _adapt_dict(info)
 
     def adapt_fixed(self, n_per_face):
         """The n_per_face dominant eigenvector constraints on every face (Section 7, "3eigv")."""
         info = AdaptInfo()
         self._check(self.lib.bddc_adapt_fixed(self.h, int(n_per_face), C.byref(info)))
-        return {"n_faces": info.n_faces, "n_added": info.n_added, "n_ties": info.n_ties, "omega": info.omega}
+        return _adapt_dict(info)
 
     def set_edge_rows(self, keep=True):
         """Later adapt calls also keep the edge parts of the rows d (Section 3), one
@@ -286,7 +305,8 @@ class Solver:
         st = self.lib.bddc_solve(self.h, pf, pu, mem, C.byref(info))
         out = {"iters": info.iters, "converged": bool(info.converged), "relres": info.relres, "kappa": info.kappa,
                "interior_fp32": bool(info.interior_fp32), "coarse_fp32": bool(info.coarse_fp32),
-               "refine_steps": info.refine_steps, "refine_relres": info.refine_relres}
+               "refine_steps": info.refine_steps, "refine_relres": info.refine_relres,
+               "relres_recurrence": info.relres_recurrence}
         if check or st not in (0, 5):
             self._check(st)
         out["status"] = STATUS.get(st, st)
@@ -367,6 +387,22 @@ class Solver:
         y = np.zeros_like(x)
         self._check(self.lib.bddc_apply_schur(self.h, x.ctypes.data, y.ctypes.data, MEM_HOST))
         return y
+
+    KERNEL_CLASSES = ["pchol_update_ff", "pchol_update_fp64", "pchol_update_fp32", "tc_gemm_3xtf32", "pcg_kernel",
+                      "face_reduction"]
+
+    def set_kernel_timing(self, on=True):
+        self._check(self.lib.bddc_set_kernel_timing(self.h, 1 if on else 0))
+
+    def kernel_times(self):
+        """{class: (ms, algorithmic flop, launches)} since set_kernel_timing(True)."""
+        ms = np.zeros(8)
+        wk = np.zeros(8)
+        nl = np.zeros(8, dtype=np.int64)
+        n = C.c_int()
+        self._check(self.lib.bddc_get_kernel_times(self.h, ms.ctypes.data, wk.ctypes.data, nl.ctypes.data, 8,
+                                                   C.byref(n)))
+        return {self.KERNEL_CLASSES[k]: (ms[k], wk[k], int(nl[k])) for k in range(n.value)}
 
     def phase_times(self):
         """{phase: (ms, algorithmic flop)} of the last setup / adapt / solve."""

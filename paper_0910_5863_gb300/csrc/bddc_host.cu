@@ -27,6 +27,7 @@
 #include <set>
 #include <string>
 #include <vector>
+#include <type_traits>
 
 #include "../../include/bddc.h"
 #include "assembly.h"
@@ -37,6 +38,7 @@
 #include "host_util.h"
 #include "tc_gemm.h"
 #include "mixed.h"
+#include "lobpcg.h"
 #include "pcg.h"
 
 using namespace bddc;
@@ -86,6 +88,10 @@ struct GlobRows {               // one glob with constraint rows (c . w equal fo
 
 struct PhaseTimer {
     cudaEvent_t a = nullptr, b = nullptr;
+};
+
+struct LobStats {   // batched LOBPCG of the last adapt: large faces, most iterations, dense fallbacks
+    int faces = 0, iters = 0, fallback = 0;
 };
 
 }  // namespace
@@ -153,6 +159,7 @@ struct bddc_handle {
     double setup_ms = 0.0, adapt_ms = 0.0;
     // adapt results
     double omega = 0.0;
+    LobStats lob_stats;   // the last adapt's batched LOBPCG (large faces)
     std::vector<double *> face_rows_dev;
     int face_row_ld = 0;
     // kept adaptive edge rows (Section 3's split rows; off unless bddc_set_edge_rows)
@@ -176,6 +183,19 @@ struct bddc_handle {
     bool factored = false;      // FP64 mode: A_i factored in place
     int mixed_iters = 0;        // refinement steps the interior elimination needed (mixed mode)
     double mixed_relres = 0.0;  // largest relative residual of the refined A_II X = A_IG
+    // kernel timers (bddc_set_kernel_timing): event pairs around the launches of a few
+    // kernels, on the handle's stream; the work of every launch is counted on the host
+    static constexpr int kKClasses = 6;
+    bool ktiming = false;
+    std::vector<cudaEvent_t> kev;
+    size_t kev_used = 0;
+    struct KPending {
+        int cls;
+        size_t ev;
+    };
+    std::vector<KPending> kpend;
+    double kt_ms[kKClasses] = {}, kt_work[kKClasses] = {};
+    int64_t kt_n[kKClasses] = {};
     // phase timing: events [2k, 2k+1] bracket phase k
     static constexpr int kPhases = 9;
     cudaEvent_t ev[2 * kPhases] = {};
@@ -223,6 +243,43 @@ void check_launch(bddc_handle *h) {
     h->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error{BDDC_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
+// ---- kernel timers: classes of bddc_get_kernel_times --------------------------
+enum KClass { KT_PCHOL_FF = 0, KT_PCHOL_F64 = 1, KT_PCHOL_F32 = 2, KT_TC_GEMM = 3, KT_PCG = 4, KT_FACE_RED = 5 };
+
+void kt_collect(bddc_handle *h) {
+    for (const auto &p : h->kpend) {
+        float ms = 0.f;
+        BDDC_CUDA(cudaEventSynchronize(h->kev[p.ev + 1]));
+        BDDC_CUDA(cudaEventElapsedTime(&ms, h->kev[p.ev], h->kev[p.ev + 1]));
+        h->kt_ms[p.cls] += ms;
+    }
+    h->kpend.clear();
+    h->kev_used = 0;
+}
+
+// records the start event of a timed launch; returns its index (or -1 when timing is off)
+long kt_begin(bddc_handle *h) {
+    if (!h->ktiming) return -1;
+    if (h->kev_used + 2 > 4096) kt_collect(h);
+    while (h->kev.size() < h->kev_used + 2) {
+        cudaEvent_t e;
+        BDDC_CUDA(cudaEventCreate(&e));
+        h->kev.push_back(e);
+    }
+    const size_t i = h->kev_used;
+    h->kev_used += 2;
+    BDDC_CUDA(cudaEventRecord(h->kev[i], h->stream));
+    return (long)i;
+}
+
+void kt_end(bddc_handle *h, long tok, int cls, double work) {
+    if (tok < 0) return;
+    BDDC_CUDA(cudaEventRecord(h->kev[tok + 1], h->stream));
+    h->kpend.push_back({cls, (size_t)tok});
+    h->kt_work[cls] += work;
+    h->kt_n[cls] += 1;
 }
 
 // ---- batched partial Cholesky ------------------------------------------------
@@ -293,12 +350,27 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const 
     auto *dd = h->ar.upload("pc_desc_" + tag, descs, h->stream);
     auto *dp = h->ar.upload("pc_pit_" + tag, pitems, h->stream);
     auto *du = h->ar.upload("pc_uit_" + tag, uitems, h->stream);
+    const int cls = std::is_same<T, ff>::value ? KT_PCHOL_FF : (std::is_same<T, double>::value ? KT_PCHOL_F64 : KT_PCHOL_F32);
     for (int s = 0; s < nsteps; ++s) {
         int kb = s * kPanelNB;
         launch_pchol_panel<T>(dd, dp + poff[s], poff[s + 1] - poff[s], kb, h->dst, h->stream);
         check_launch(h);
+        double work = 0.0;   // the trailing update's multiply-adds x 2 (lower triangle of diagonal tiles)
+        if (h->ktiming)
+            for (int u = uoff[s]; u < uoff[s + 1]; ++u) {
+                const int4 w = uitems[u];
+                if (w.y < 0) continue;
+                const auto &d = descs[w.x];
+                const int nb = std::min(kPanelNB, d.nstop - kb), t0 = kb + nb;
+                const int cend = d.ncol > 0 ? std::min(d.ncol, d.n) : d.n;
+                const double r = std::min(kTile, d.n - (t0 + w.y * kTile));
+                const double c = std::min(kTile, cend - (t0 + w.z * kTile));
+                work += 2.0 * nb * (w.y == w.z ? r * (r + 1) / 2 : r * c);
+            }
+        const long tok = kt_begin(h);
         launch_pchol_update<T>(dd, du + uoff[s], uoff[s + 1] - uoff[s], kb, h->stream);
         check_launch(h);
+        kt_end(h, tok, cls, work);
     }
 }
 
@@ -396,8 +468,13 @@ void run_tc_gemm(bddc_handle *h, const std::vector<TcGemm> &jobs, const std::str
     if (items.empty()) return;
     auto *dj = h->ar.upload("tcj_" + tag, jobs, h->stream);
     auto *di = h->ar.upload("tci_" + tag, items, h->stream);
+    double work = 0.0;   // effective multiply-adds x 2 (each executed as three TF32 products)
+    for (const auto &g : jobs)
+        if (g.M > 0 && g.N > 0 && g.K > 0) work += 2.0 * g.M * g.N * g.K * (lower_only ? 0.5 : 1.0);
+    const long tok = kt_begin(h);
     launch_tc_gemm(dj, di, (int)items.size(), h->dst, h->opt.timeout_s, h->stream);
     check_launch(h);
+    kt_end(h, tok, KT_TC_GEMM, work);
 }
 
 // FP32 partial Cholesky, left-looking in block columns of 128 with the long
@@ -2060,6 +2137,275 @@ void do_setup(bddc_handle *h) {
 // adapt
 namespace {
 
+// Face eigenproblems C y = lambda y (eig.h).  Faces of order <= opt.eig_large_n go to the dense
+// kernel (Householder + Sturm counts, one CTA each).  Larger faces, whose one-CTA reduction
+// would set the length of the phase, run the batched LOBPCG of lobpcg.h: k = 16, then 32
+// for faces whose block held no rejected Ritz value, each converged face checked by the
+// Cholesky certificate of its count; a face that does not converge or whose certificate
+// fails is solved by the dense kernel.  The face rows of the LOBPCG faces are then formed
+// by the face kernel from the supplied eigenpairs.
+constexpr int kTriMultiN = 200;
+
+void run_face_eigs(bddc_handle *h, const std::vector<EigDesc> &eds, double tau, int fixed_k, LobStats *stats) {
+    const int use_ff = h->opt.precision != BDDC_FP64 ? 1 : 0;
+    std::vector<EigDesc> small, big;
+    const int large_n = h->opt.eig_large_n;
+    // LOBPCG needs a trial space [X P R] narrower than the problem: n > 3 x 16
+    for (const auto &e : eds) (large_n >= 0 && e.n > large_n && e.n > 48 && fixed_k + 1 < kLobMaxK
+                                   ? big : small).push_back(e);
+    auto dense1 = [&](const std::vector<EigDesc> &v, const std::string &tag, int ff) {
+        if (v.empty()) return;
+        int nmax = 0;
+        for (const auto &e : v) nmax = std::max(nmax, e.n);
+        auto *d = h->ar.upload("eigdesc_" + tag, v, h->stream);
+        double work = 0.0;   // the Householder reduction, 4/3 n^3 flop per face it reduces
+        for (const auto &e : v)
+            if (e.given == 0) work += 4.0 / 3.0 * (double)e.n * e.n * e.n;
+        const long tok = kt_begin(h);
+        launch_face_eig_n(d, (int)v.size(), nmax, tau, h->opt.drop_rel, ff, fixed_k, h->dst, h->stream);
+        check_launch(h);
+        kt_end(h, tok, KT_FACE_RED, work);
+    };
+    // the dense kernel; faces above kTriMultiN get their Householder reduction from
+    // several CTAs each (tridiag.cu), then the kernel's remaining steps
+    auto dense = [&](const std::vector<EigDesc> &v, const std::string &tag, int ff) {
+        std::vector<EigDesc> one, multi;
+        for (const auto &e : v) (e.n > kTriMultiN ? multi : one).push_back(e);
+        dense1(one, tag, ff);
+        if (multi.empty()) return;
+        std::stable_sort(multi.begin(), multi.end(), [](const EigDesc &a, const EigDesc &b) { return a.n > b.n; });
+        int nmax = multi.front().n;
+        const int cap = tridiag_multi_capacity(nmax);
+        BDDC_REQUIRE(cap >= 2, BDDC_ECUDA, "no co-resident CTAs for the face reduction");
+        unsigned *bar = h->ar.get_t<unsigned>("tri_bar_" + tag, 2 * multi.size());
+        size_t pos = 0;
+        int wave = 0;
+        while (pos < multi.size()) {   // waves of faces whose CTAs fit co-resident
+            std::vector<TridiagDesc> td;
+            std::vector<int2> items;
+            int used = 0;
+            for (; pos < multi.size(); ++pos) {
+                const EigDesc &e = multi[pos];
+                const int G = std::min(std::max((e.n + 63) / 64, 2), std::min(16, cap));
+                if (used + G > cap) break;
+                for (int g = 0; g < G; ++g) items.push_back(make_int2((int)td.size(), g));
+                td.push_back(TridiagDesc{e.C, e.n, e.ld, e.work, G, bar + 2 * pos});
+                used += G;
+            }
+            const std::string ws = tag + "_" + std::to_string(wave++);
+            BDDC_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2 * multi.size(), h->stream));
+            auto *dtd = h->ar.upload("tri_desc_" + ws, td, h->stream);
+            auto *dti = h->ar.upload("tri_it_" + ws, items, h->stream);
+            double work = 0.0;
+            for (const auto &t : td) work += 4.0 / 3.0 * (double)t.n * t.n * t.n;
+            const long tok = kt_begin(h);
+            cudaError_t err = launch_tridiag_multi(dtd, dti, (int)items.size(), nmax, ff, h->dst, h->opt.timeout_s,
+                                                   h->stream);
+            BDDC_REQUIRE(err == cudaSuccess, BDDC_ECUDA, std::string("face reduction launch: ") + cudaGetErrorString(err));
+            h->launches++;
+            kt_end(h, tok, KT_FACE_RED, work);
+        }
+        for (auto &e : multi) e.given = 2;
+        dense1(multi, tag + "_tri", 0);
+    };
+    dense(small, "small", use_ff);
+    if (stats) *stats = LobStats{(int)big.size(), 0, 0};
+    if (big.empty()) return;
+    // batched FP64 GEMMs with the descriptors and tile items uploaded once
+    struct GemmBatch {
+        GemmDesc *d = nullptr;
+        int4 *it = nullptr;
+        int n = 0;
+    };
+    auto prep_gemm = [&](const std::vector<GemmDesc> &g, const std::string &tag) {
+        GemmBatch b;
+        std::vector<int4> items;
+        for (int q = 0; q < (int)g.size(); ++q)
+            for (int a = 0; a < (g[q].m + kTile - 1) / kTile; ++a)
+                for (int c = 0; c < (g[q].n + kTile - 1) / kTile; ++c) items.push_back(make_int4(q, a, c, 0));
+        b.d = h->ar.upload("lobg_" + tag, g, h->stream);
+        b.it = h->ar.upload("lobi_" + tag, items, h->stream);
+        b.n = (int)items.size();
+        return b;
+    };
+    auto gemm = [&](const GemmBatch &b) {
+        launch_gemm(b.d, b.it, b.n, 0, h->stream);
+        check_launch(h);
+    };
+    std::vector<int> todo(big.size());
+    std::iota(todo.begin(), todo.end(), 0);
+    std::vector<char> solved(big.size(), 0);
+    std::vector<int> fallback;
+    for (int pass = 0; pass < 2 && !todo.empty(); ++pass) {
+        const int k = pass == 0 ? 16 : kLobMaxK, m = 3 * k;
+        const int nb = (int)todo.size();
+        const std::string ps = std::to_string(pass);
+        std::vector<size_t> off(nb + 1, 0);
+        std::vector<int> lds(nb);
+        for (int b = 0; b < nb; ++b) {
+            const int n = big[todo[b]].n;
+            lds[b] = round_up(n, 8);
+            off[b + 1] = off[b] + 4 * (size_t)lds[b] * m + 6 * (size_t)m * m + 2 * (size_t)k * m + 2 * k;
+        }
+        double *pool = h->ar.get_t<double>("lob_pool" + ps, off[nb]);
+        int *ipool = h->ar.get_t<int>("lob_ipool" + ps, (size_t)nb * 4 + 1);
+        std::vector<LobDesc> ld(nb);
+        std::vector<GemmDesc> gar[2], ggram[2], gupd[2], gax[2];
+        for (int b = 0; b < nb; ++b) {
+            const EigDesc &e = big[todo[b]];
+            const int n = e.n;
+            double *p = pool + off[b];
+            LobDesc &d = ld[b];
+            d.C = e.C;
+            d.n = n;
+            d.ldc = e.ld;
+            d.k = k;
+            d.lds = lds[b];
+            for (int c = 0; c < 2; ++c) {
+                d.S[c] = p;
+                p += (size_t)lds[b] * m;
+                d.AS[c] = p;
+                p += (size_t)lds[b] * m;
+            }
+            d.G = p;
+            p += 2 * (size_t)m * m;
+            d.coef = p;
+            p += 2 * (size_t)k * m;
+            d.theta = p;
+            p += k;
+            d.rnorm = p;
+            p += k;
+            d.scratch = p;
+            d.state = ipool + 4 * b;
+            for (int c = 0; c < 2; ++c) {
+                const size_t r0 = (size_t)2 * k * d.lds;
+                gar[c].push_back(GemmDesc{e.C, d.S[c] + r0, d.AS[c] + r0, e.ld, d.lds, d.lds, n, k, n, 0, 0, 1.0, 0.0});
+                ggram[c].push_back(GemmDesc{d.S[c], d.AS[c], d.G, d.lds, d.lds, m, m, m, n, 1, 0, 1.0, 0.0});
+                ggram[c].push_back(GemmDesc{d.S[c], d.S[c], d.G + (size_t)m * m, d.lds, d.lds, m, m, m, n, 1, 0, 1.0, 0.0});
+                gupd[c].push_back(GemmDesc{d.S[c], d.coef, d.S[1 - c], d.lds, m, d.lds, n, 2 * k, m, 0, 0, 1.0, 0.0});
+                // C P by the same combination; C X is recomputed from X every iteration (below),
+                // so rounding in the combined products never enters the residual test
+                gupd[c].push_back(GemmDesc{d.AS[c], d.coef + (size_t)k * m, d.AS[1 - c] + (size_t)k * d.lds, d.lds, m,
+                                           d.lds, n, k, m, 0, 0, 1.0, 0.0});
+                gax[c].push_back(GemmDesc{e.C, d.S[c], d.AS[c], e.ld, d.lds, d.lds, n, k, n, 0, 0, 1.0, 0.0});
+            }
+        }
+        auto *dl = h->ar.upload("lob_desc" + ps, ld, h->stream);
+        GemmBatch b_ar[2], b_gram[2], b_upd[2], b_ax[2];
+        for (int c = 0; c < 2; ++c) {
+            const std::string cs = ps + "_" + std::to_string(c);
+            b_ar[c] = prep_gemm(gar[c], "ar" + cs);
+            b_gram[c] = prep_gemm(ggram[c], "gram" + cs);
+            b_upd[c] = prep_gemm(gupd[c], "upd" + cs);
+            b_ax[c] = prep_gemm(gax[c], "ax" + cs);
+        }
+        if (pass == 0) {
+            std::vector<int2> sym;
+            for (int b = 0; b < nb; ++b)
+                for (int c = 0; c < (ld[b].n + 63) / 64; ++c) sym.push_back(make_int2(b, c));
+            auto *dsy = h->ar.upload("lob_sym", sym, h->stream);
+            launch_lob_symmetrize(dl, dsy, (int)sym.size(), h->stream);
+            check_launch(h);
+        }
+        launch_lob_init(dl, nb, 0, h->stream);
+        check_launch(h);
+        int cur = 0, it = 0;
+        std::vector<int> st((size_t)nb * 4);
+        for (; it < h->opt.eig_maxit; ++it) {
+            gemm(b_ax[cur]);
+            launch_lob_prep(dl, nb, cur, tau, fixed_k, h->opt.eig_tol, 0, h->stream);
+            check_launch(h);
+            gemm(b_ar[cur]);
+            gemm(b_gram[cur]);
+            launch_lob_rr(dl, nb, h->stream);
+            check_launch(h);
+            gemm(b_upd[cur]);
+            cur ^= 1;
+            if (it % 4 == 3) {
+                BDDC_CUDA(cudaMemcpyAsync(st.data(), ipool, st.size() * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+                BDDC_CUDA(cudaStreamSynchronize(h->stream));
+                bool all = true;
+                for (int b = 0; b < nb; ++b) all = all && st[4 * b] != 0;
+                if (all) break;
+            }
+        }
+        // fresh C X, the final residual test, the outputs and the certificate
+        gemm(b_ax[cur]);
+        launch_lob_prep(dl, nb, cur, tau, fixed_k, h->opt.eig_tol, 1, h->stream);
+        check_launch(h);
+        std::vector<LobOutDesc> od(nb);
+        std::vector<LobCertDesc> cd(nb);
+        std::vector<int2> citems;
+        std::vector<PcholDesc<double>> chol(nb);
+        int *fails = h->ar.get_t<int>("lob_fail" + ps, nb);
+        BDDC_CUDA(cudaMemsetAsync(fails, 0, sizeof(int) * nb, h->stream));
+        for (int b = 0; b < nb; ++b) {
+            const EigDesc &e = big[todo[b]];
+            const int n = e.n, ldm = round_up(n, 8);
+            od[b] = LobOutDesc{ld[b].S[cur], n, ld[b].lds, k, ld[b].theta, e.lam, e.vec, e.counts, kEigCap, ld[b].state};
+            double *M = h->ar.get_t<double>("lob_cert" + ps + "_" + std::to_string(b), (size_t)ldm * n);
+            cd[b] = LobCertDesc{e.C, n, e.ld, ld[b].S[cur], ld[b].lds, k, ld[b].theta, e.counts, M, ldm, 1e-6};
+            for (int c = 0; c < (n + 63) / 64; ++c) citems.push_back(make_int2(b, c));
+            chol[b] = PcholDesc<double>{M, n, ldm, n, 0, nullptr, 0, 0, 0, fails + b};
+        }
+        auto *dod = h->ar.upload("lob_out" + ps, od, h->stream);
+        launch_lob_select(dod, nb, tau, fixed_k, h->stream);
+        check_launch(h);
+        auto *dcd = h->ar.upload("lob_certd" + ps, cd, h->stream);
+        auto *dci = h->ar.upload("lob_certi" + ps, citems, h->stream);
+        launch_lob_cert(dcd, dci, (int)citems.size(), h->stream);
+        check_launch(h);
+        run_pchol<double>(h, chol, "F#lob" + ps);
+        std::vector<int> fl(nb);
+        BDDC_CUDA(cudaMemcpyAsync(st.data(), ipool, st.size() * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaMemcpyAsync(fl.data(), fails, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        std::vector<int> next;
+        if (getenv("BDDC_LOB_DEBUG")) {
+            int cnt[6] = {0, 0, 0, 0, 0, 0}, nf = 0;
+            for (int b = 0; b < nb; ++b) {
+                cnt[std::min(std::max(st[4 * b + 2], 0), 5)]++;
+                nf += fl[b] != 0;
+            }
+            fprintf(stderr, "lobpcg pass %d: %d faces k=%d loop %d; states run %d conv %d small %d rank %d final %d; cert fails %d\n",
+                    pass, nb, k, it, cnt[0], cnt[1], cnt[2], cnt[3], cnt[4], nf);
+            for (int b = 0; b < nb; ++b)
+                if (st[4 * b + 2] != 1 || fl[b]) {
+                    std::vector<double> th(k), rn(k);
+                    BDDC_CUDA(cudaMemcpy(th.data(), ld[b].theta, k * sizeof(double), cudaMemcpyDeviceToHost));
+                    BDDC_CUDA(cudaMemcpy(rn.data(), ld[b].rnorm, k * sizeof(double), cudaMemcpyDeviceToHost));
+                    fprintf(stderr, "  face n=%d state %d iters %d fail %d:", big[todo[b]].n, st[4 * b + 2],
+                            st[4 * b + 1], fl[b]);
+                    for (int j = 0; j < std::min(k, 8); ++j) fprintf(stderr, " (%.6g %.2e)", th[j], rn[j]);
+                    fprintf(stderr, "\n");
+                }
+        }
+        for (int b = 0; b < nb; ++b) {
+            if (stats) stats->iters = std::max(stats->iters, st[4 * b + 1]);
+            if (st[4 * b + 2] == 1 && fl[b] == 0)
+                solved[todo[b]] = 1;
+            else if (st[4 * b + 2] == 2 && pass == 0 && big[todo[b]].n > 3 * kLobMaxK)
+                next.push_back(todo[b]);   // block too small: again with the larger block
+            else
+                fallback.push_back(todo[b]);
+        }
+        todo = next;
+    }
+    for (int b : todo) fallback.push_back(b);
+    std::vector<EigDesc> given, dense_big;
+    for (size_t b = 0; b < big.size(); ++b) {
+        if (solved[b]) {
+            EigDesc e = big[b];
+            e.given = 1;
+            given.push_back(e);
+        }
+    }
+    for (int b : fallback) dense_big.push_back(big[b]);
+    if (stats) stats->fallback = (int)dense_big.size();
+    dense(dense_big, "fallback", use_ff);
+    dense(given, "given", 0);
+}
+
 void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0) {
     const int nf = (int)h->faces.size();
     reset_status(h);
@@ -2070,7 +2416,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
     h->edge_rows.clear();
     h->n_edge_rows = h->n_edges_with_rows = 0;
     if (nf == 0) {
-        if (info) *info = bddc_adapt_info{0, 0, 0, 0.0};
+        if (info) *info = bddc_adapt_info{};
         return;
     }
     for (auto &fp : h->faces) {
@@ -2522,7 +2868,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
         gm2.push_back(g2);
         int nface = (int)fp.face_idx.size();
         int *fpos = h->ar.upload("fpos_" + std::to_string(f), fp.face_idx, h->stream);
-        EigDesc e;
+        EigDesc e{};
         e.C = B.C;
         e.n = ne;
         e.ld = ldq;
@@ -2554,10 +2900,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
         check_launch(h);
     }
     run_gemm(h, gm2, "C", ff_mode);
-    auto *ded = h->ar.upload("eigdesc", eds, h->stream);
-    launch_face_eig_n(ded, (int)eds.size(), nmax, tau, h->opt.drop_rel, h->opt.precision != BDDC_FP64 ? 1 : 0, fixed_k,
-                      h->dst, h->stream);
-    check_launch(h);
+    run_face_eigs(h, eds, tau, fixed_k, &h->lob_stats);
     // kept edge rows (Section 3: d split into a face row and one row per edge), per edge:
     // the edge parts of the same rows d from every face pair on the edge, stacked in the
     // edge's slots (pairs in face order), then one orthonormal basis per edge
@@ -2764,6 +3107,9 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
         info->n_added = n_added;
         info->n_ties = n_ties;
         info->omega = omega;
+        info->n_lobpcg = h->lob_stats.faces;
+        info->lobpcg_iters = h->lob_stats.iters;
+        info->n_dense_fallback = h->lob_stats.fallback;
     }
 }
 
@@ -2833,11 +3179,25 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
     check_launch(h);
     phase_end(h, 6);
     phase_begin(h, 7);
+    // the condensed right-hand side g, kept for the true residual after PCG
+    double *gsave = h->ar.get_t<double>("g_save", std::max(h->nG, 1));
+    double *nrm2 = h->ar.get_t<double>("relres_nrm2", 2);
+    BDDC_CUDA(cudaMemcpyAsync(gsave, h->pb.r, h->nG * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     int nblocks = 0;
+    const long tok_pcg = kt_begin(h);
     cudaError_t e = launch_pcg(h->ops, h->pb, PCG_SOLVE, h->opt.tol, h->opt.maxit, h->dst, h->opt.timeout_s,
                                h->stream, &nblocks);
     BDDC_REQUIRE(e == cudaSuccess, BDDC_ECUDA, std::string("PCG launch: ") + cudaGetErrorString(e));
     h->launches++;
+    kt_end(h, tok_pcg, KT_PCG, 0.0);
+    // true residual ||g - S u_G|| / ||g||: one more application of the local S_i
+    BDDC_CUDA(cudaMemcpyAsync(h->pb.z, h->pb.x, h->nG * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    e = launch_pcg(h->ops, h->pb, PCG_APPLY_S, h->opt.tol, h->opt.maxit, h->dst, h->opt.timeout_s, h->stream,
+                   &nblocks);
+    BDDC_REQUIRE(e == cudaSuccess, BDDC_ECUDA, std::string("residual launch: ") + cudaGetErrorString(e));
+    h->launches++;
+    launch_residual_norms2(gsave, h->pb.q, h->nG, nrm2, h->stream);
+    check_launch(h);
     phase_end(h, 7);
     phase_begin(h, 8);
     // recovery: t = y - L21^T u_G ; u_I = L11^-T t
@@ -2877,9 +3237,11 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
     else
         BDDC_CUDA(cudaMemcpyAsync(u, du, h->nfree * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     int it[2];
-    double rr;
+    double rr, tr[2];
     BDDC_CUDA(cudaMemcpyAsync(it, h->pb.iters, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     BDDC_CUDA(cudaMemcpyAsync(&rr, h->pb.relres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    BDDC_CUDA(cudaMemcpyAsync(tr, h->ar.get_t<double>("relres_nrm2", 2), 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
     BDDC_CUDA(cudaStreamSynchronize(h->stream));
     fail_check(h, "solve");
     phase_collect(h, 6, 8);
@@ -2891,7 +3253,8 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
     if (info) {
         info->iters = it[0];
         info->converged = it[1];
-        info->relres = rr;
+        info->relres = tr[1] > 0.0 ? std::sqrt(tr[0] / tr[1]) : 0.0;
+        info->relres_recurrence = rr;
         double lmin = 1, lmax = 1;
         bddc_condition_estimate(h, &lmin, &lmax);
         info->kappa = lmax / lmin;
@@ -2924,6 +3287,9 @@ void bddc_default_options(bddc_options *opt) {
     opt->dev_free = nullptr;
     opt->alloc_ctx = nullptr;
     opt->refine_tol = 1e-8;
+    opt->eig_large_n = -1;
+    opt->eig_tol = 1e-8;
+    opt->eig_maxit = 240;
 }
 
 const char *bddc_status_str(bddc_status s) {
@@ -3001,6 +3367,7 @@ void bddc_destroy(bddc_handle *h) {
     h->ar.release();
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : h->kev) cudaEventDestroy(e);
     delete h;
 }
 
@@ -3570,6 +3937,31 @@ bddc_status bddc_apply_schur(bddc_handle *h, const double *x, double *y, int mem
 }
 
 int64_t bddc_launch_count(const bddc_handle *h) { return h ? h->launches : 0; }
+
+bddc_status bddc_set_kernel_timing(bddc_handle *h, int on) {
+    if (!h || (on != 0 && on != 1)) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        kt_collect(h);
+        h->ktiming = on != 0;
+        for (int k = 0; k < bddc_handle::kKClasses; ++k) {
+            h->kt_ms[k] = h->kt_work[k] = 0.0;
+            h->kt_n[k] = 0;
+        }
+    });
+}
+
+bddc_status bddc_get_kernel_times(bddc_handle *h, double *ms, double *work, int64_t *launches, int cap, int *n) {
+    if (!h) return BDDC_EINVAL;
+    BDDC_TRY(h, {
+        kt_collect(h);
+        if (n) *n = bddc_handle::kKClasses;
+        for (int k = 0; k < bddc_handle::kKClasses && k < cap; ++k) {
+            if (ms) ms[k] = h->kt_ms[k];
+            if (work) work[k] = h->kt_work[k];
+            if (launches) launches[k] = h->kt_n[k];
+        }
+    });
+}
 
 bddc_status bddc_get_phase_times(const bddc_handle *h, double *ms, double *flop, int cap, int *n) {
     if (!h) return BDDC_EINVAL;

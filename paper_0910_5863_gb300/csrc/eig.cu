@@ -276,7 +276,11 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     double *A;
     int lda;
     double *work;
-    if (use_smem) {
+    if (D.given) {   // eigenpairs (1) or the tridiagonal form (2) supplied: C stays in place
+        A = D.C;
+        lda = D.ld;
+        work = D.work;
+    } else if (use_smem) {
         A = sm;
         lda = n;
         work = sm + (size_t)n * n;
@@ -287,7 +291,18 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
         work = D.work;
     }
     double *dd = work, *ee = work + n, *bet = work + 2 * n, *P = work + 3 * n, *Wv = work + 4 * n;
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     __syncthreads();
+    if (D.given == 1) {
+        if (tid == 0) {
+            sh_int[0] = counts[0];
+            sh_int[1] = counts[3];
+            sh_int[2] = counts[4];
+            sh_int[3] = counts[2];
+        }
+        __syncthreads();
+    } else {
+    if (D.given != 2) {   // given == 2: the tridiagonal form comes from tridiag.cu
     // ---- 1. Householder tridiagonalisation: A = Q T Q^T ----
     if (use_ff && packed_off >= 0)
         householder_ff_packed(A, lda, n, reinterpret_cast<ff *>(reinterpret_cast<char *>(sm) + packed_off), dd, ee, bet,
@@ -356,6 +371,7 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
         bet[n - 1] = 0.0;
         ee[n - 1] = 0.0;
     }
+    }   // D.given != 2
     __syncthreads();
     // ---- 2. counts and bisection ----
     double *e2 = work + 5 * n;
@@ -393,7 +409,6 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     __syncthreads();
     const int nsel = sh_int[0], nval = sh_int[3];
     double *lam = D.lam;
-    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     // 32-way multisection, one warp per eigenvalue: lanes 0..30 count at 31 interior points
     for (int t = wid; t < nval; t += nw) {
         const int j = n - 1 - t;  // index among ascending eigenvalues
@@ -522,6 +537,8 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
         }
     }
     __syncthreads();
+    }   // !D.given
+    const int nsel = sh_int[0], nval = sh_int[3];
     // ---- 4. face rows and their pivoted orthonormalisation ----
     const int nf = D.nface;
     double *R = D.rows;

@@ -19,7 +19,28 @@ struct EigDesc {
     double *work;         // scratch: 64 n + 16
     double *rows;         // out: face rows, row l at rows[l * nface + f] (orthonormal)
     int *counts;          // out: [0] selected, [1] kept, [2] values in lam, [3] ties, [4] overflow
+    int given;            // 1: lam, vec and counts [0], [2], [3], [4] are supplied (the batched
+                          // LOBPCG, lobpcg.h); only the face rows are formed (C is not read).
+                          // 2: the Householder reduction is supplied (launch_tridiag_multi):
+                          // reflectors in C, dd / ee / bet in work; steps 2-4 run
 };
+
+// Householder tridiagonalisation of large face matrices by several CTAs per face
+// (tridiag.cu): the face's G CTAs share every reduction step, with a bounded barrier of
+// the face's CTAs between the matrix-vector product and the rank-2 update.  One
+// cooperative launch; items = (descriptor, rank g < G) per CTA.  Leaves C and work as
+// the face kernel's step 1 does (EigDesc::given = 2).  bar: 2 zeroed counters per face.
+struct TridiagDesc {
+    double *A;            // n x n, ld lda, both triangles (overwritten)
+    int n, lda;
+    double *work;         // the face's EigDesc::work
+    int G;                // CTAs of this face
+    unsigned *bar;
+};
+cudaError_t launch_tridiag_multi(const TridiagDesc *descs, const int2 *items, int nitems, int nmax, int use_ff,
+                                 DevStatus *st, double timeout_s, cudaStream_t s);
+// CTAs of launch_tridiag_multi that can be co-resident (one cooperative launch at most)
+int tridiag_multi_capacity(int nmax);
 
 // nmax: largest n of the batch; when the matrix and work arrays do not fit in
 // 200 KB of shared memory the matrix is reduced in place and work (64 n + 16

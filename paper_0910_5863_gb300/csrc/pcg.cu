@@ -373,6 +373,36 @@ __global__ void weights_kernel(IfaceOps o, const double *diag, const double *tot
     }
 }
 
+__global__ void __launch_bounds__(1024) residual_norms2_kernel(const double *g, const double *q, int n, double *out) {
+    __shared__ double sa[32], sb[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double d = g[i] - q[i];
+        a += d * d;
+        b += g[i] * g[i];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            ta += sa[w];
+            tb += sb[w];
+        }
+        out[0] = ta;
+        out[1] = tb;
+    }
+}
+
+void launch_residual_norms2(const double *g, const double *q, int n, double *out, cudaStream_t s) {
+    residual_norms2_kernel<<<1, 1024, 0, s>>>(g, q, n, out);
+}
+
 void launch_iface_assemble(const IfaceOps &ops, const double *packed, double *out, cudaStream_t s) {
     int blocks = (ops.nG + 255) / 256;
     if (blocks > 0) iface_assemble_kernel<<<blocks, 256, 0, s>>>(ops, packed, out);

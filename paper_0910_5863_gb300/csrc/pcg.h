@@ -73,5 +73,7 @@ void launch_weights(const IfaceOps &ops, const double *diag_packed, double *tota
                     cudaStream_t s);
 // Deterministic assembly of a packed local interface vector: out[x] = sum over entries.
 void launch_iface_assemble(const IfaceOps &ops, const double *packed, double *out, cudaStream_t s);
+// out[0] = ||g - q||^2, out[1] = ||g||^2 (one block, fixed summation order).
+void launch_residual_norms2(const double *g, const double *q, int n, double *out, cudaStream_t s);
 
 }  // namespace bddc
