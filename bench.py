@@ -483,8 +483,52 @@ def run_oracle(args, sample_note):
 _ORACLE_SAMPLE = {}
 
 
+def measure_peaks(local_rank=0):
+    """Library (cuBLAS) GEMM throughput per dtype at 8192^3 and the device copy bandwidth
+    (CUDA events, best of several runs): the denominators quoted beside the derived ALU peaks."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    out = {}
+    n = 8192
+    for name, dt, tf32 in (("fp64", torch.float64, False), ("fp32_simt", torch.float32, False),
+                           ("tf32", torch.float32, True), ("bf16", torch.bfloat16, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device=dev, dtype=torch.float32).to(dt)
+        b = torch.randn(n, n, device=dev, dtype=torch.float32).to(dt)
+        reps = 2 if dt == torch.float64 else 10
+        best = 1e30
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3 / reps)
+        out[name + "_tflops"] = 2.0 * n ** 3 / best / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    x = torch.empty(1 << 28, dtype=torch.float64, device=dev)   # 2 GiB
+    y = torch.empty_like(x)
+    best = 1e30
+    for _ in range(5):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        y.copy_(x)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    out["copy_gbs"] = 2 * x.numel() * 8 / best / 1e9
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--peaks", action="store_true",
+                    help="print the cuBLAS GEMM rates (FP64, FP32, TF32, BF16) and the copy bandwidth and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -501,6 +545,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.peaks:
+        print(json.dumps(measure_peaks(local_rank)), flush=True)
+        return
 
     if args.impl == "reference":
         if rank != 0:

@@ -34,6 +34,15 @@ __device__ __forceinline__ void tri_fma(ff &acc, ff a, ff b) { ff_fma_acc(acc, a
 __device__ __forceinline__ double tri_norm(double a) { return a; }
 __device__ __forceinline__ ff tri_norm(ff a) { return ff_norm(a); }
 
+// Loads of data that other CTAs of the face write during the launch bypass L1 (.cg):
+// the SMs' L1 caches are not coherent with each other, and a column changes owner as
+// the trailing block shrinks, so a line read in an earlier step may be stale.
+__device__ __forceinline__ double tri_ld(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ ff tri_ld(const ff *p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return ff(v.x, v.y);
+}
+
 __device__ __forceinline__ double tri_warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -132,7 +141,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const Tridia
         T acc = tri_from<T>(0.0);
         int cnt = 0;
         for (int i = tid; i < m; i += nt) {
-            const T v = x[i];
+            const T v = tri_ld(x + i);
             xs[i] = v;
             tri_fma(acc, v, v);
             if ((++cnt & 15) == 0) acc = tri_norm(acc);
@@ -164,7 +173,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const Tridia
             T a = tri_from<T>(0.0);
             int c = 0;
             for (int j = lane; j < m; j += 32) {
-                tri_fma(a, col[j], xs[j]);
+                tri_fma(a, tri_ld(col + j), xs[j]);
                 if ((++c & 15) == 0) a = tri_norm(a);
             }
             a = tri_warp_sum(tri_norm(a));
@@ -174,18 +183,18 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const Tridia
         T pa = tri_from<T>(0.0);
         cnt = 0;
         for (int i = tid; i < m; i += nt) {
-            tri_fma(pa, P[i], xs[i]);
+            tri_fma(pa, tri_ld(P + i), xs[i]);
             if ((++cnt & 15) == 0) pa = tri_norm(pa);
         }
         const double pv = tri_block_sum(tri_to(tri_norm(pa)), scratch);
         const T K = tri_from<T>(0.5 * beta * pv);
-        for (int i = tid; i < m; i += nt) Ws[i] = P[i] - K * xs[i];
+        for (int i = tid; i < m; i += nt) Ws[i] = tri_ld(P + i) - K * xs[i];
         __syncthreads();
         // columns [i0, i1) of B -= x W^T + W x^T, one warp per column
         for (int j = i0 + wid; j < i1; j += nw) {
             const T wj = Ws[j], xj = xs[j];
             T *col = B + (size_t)j * lda;
-            for (int i = lane; i < m; i += 32) col[i] -= xs[i] * wj + Ws[i] * xj;
+            for (int i = lane; i < m; i += 32) col[i] = tri_ld(col + i) - (xs[i] * wj + Ws[i] * xj);
         }
         if (g == 0 && tid == 0) {
             F[(size_t)k * lda + k + 1] = tri_from<T>(v0);   // the reflector's leading entry
@@ -196,10 +205,10 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const Tridia
     }
     // diagonal, last off-diagonal, and (double-float) the reflectors back to doubles
     slice(n, c0, c1);
-    for (int i = c0 + tid; i < c1; i += nt) dd[i] = tri_to(F[(size_t)i * lda + i]);
+    for (int i = c0 + tid; i < c1; i += nt) dd[i] = tri_to(tri_ld(F + (size_t)i * lda + i));
     if (g == 0 && tid == 0) {
         if (n >= 2) {
-            ee[n - 2] = tri_to(F[(size_t)(n - 2) * lda + n - 1]);
+            ee[n - 2] = tri_to(tri_ld(F + (size_t)(n - 2) * lda + n - 1));
             bet[n - 2] = 0.0;
         }
         bet[n - 1] = 0.0;
@@ -208,7 +217,8 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const Tridia
     if constexpr (std::is_same<T, ff>::value) {
         if (!face_barrier(bar, G, st, timeout_ns)) return;   // every diagonal read before rewriting
         for (int c = c0; c < c1; ++c)
-            for (int i = c + 1 + tid; i < n; i += nt) Ad[(size_t)c * lda + i] = ff_to_double(F[(size_t)c * lda + i]);
+            for (int i = c + 1 + tid; i < n; i += nt)
+                Ad[(size_t)c * lda + i] = ff_to_double(tri_ld(F + (size_t)c * lda + i));
     }
 }
 
