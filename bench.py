@@ -225,7 +225,14 @@ def _kernel_table(kt, steps, solver, info, workload):
             continue
         e = {"kernel": name, "launches_per_step": n / steps, "ms_per_step": ms / steps, "ms_per_launch": ms / n,
              "traffic": TRAFFIC.get((workload, name))}
-        if name == "pcg_kernel":
+        if name in ("oz_split", "pchol_panel"):   # latency-bound helpers: time only
+            e.update(bound="latency", unit="ms", work_per_launch=0.0, achieved=0.0, peak=1.0, peak_source="time only")
+        elif name == "oz_syrk_bf16":
+            w = 28.0 * work / n   # 28 bf16 digit products per effective multiply-add
+            e.update(bound="tensor", unit="TFLOP/s", work_per_launch=w, achieved=w / (ms / n / 1e3) / 1e12, peak=bf16,
+                     effective_tflops=work / n / (ms / n / 1e3) / 1e12,
+                     peak_source=f"{src} bf16 {bf16} TFLOP/s (of {src}); executed bf16 flop of the 28 digit products")
+        elif name == "pcg_kernel":
             # per launch (one whole PCG solve): every iteration reads every S_i and P~_i once
             gemv = sum(2 * 8 * solver.interface_dofs(i).size ** 2 for i in range(solver.nsub))
             b = gemv * info["iters"]

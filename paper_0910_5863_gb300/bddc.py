@@ -37,7 +37,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int), ("drop_rel", C.c_double),
                 ("timeout_s", C.c_double), ("stream", C.c_void_p), ("dev_alloc", C.c_void_p),
                 ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p), ("refine_tol", C.c_double),
-                ("eig_large_n", C.c_int), ("eig_tol", C.c_double), ("eig_maxit", C.c_int)]
+                ("eig_large_n", C.c_int), ("eig_tol", C.c_double), ("eig_maxit", C.c_int),
+                ("mixed_updates", C.c_int)]
 
 
 class Subdomain(C.Structure):
@@ -158,7 +159,8 @@ class Solver:
     """One handle of the library (one GPU, one stream)."""
 
     def __init__(self, precision=FP64, tol=1e-8, maxit=1000, drop_rel=1e-10, timeout_s=10.0, stream=None,
-                 allocator=None, refine_tol=None, eig_large_n=None, eig_tol=None, eig_maxit=None):
+                 allocator=None, refine_tol=None, eig_large_n=None, eig_tol=None, eig_maxit=None,
+                 mixed_updates=None):
         """allocator: None (the library's cudaMalloc) or "torch" (device memory from
         PyTorch's caching allocator on the handle's stream).  eig_large_n / eig_tol /
         eig_maxit: the batched LOBPCG of the pair problems (bddc_options); None = default."""
@@ -180,6 +182,8 @@ class Solver:
             opt.eig_tol = float(eig_tol)
         if eig_maxit is not None:
             opt.eig_maxit = int(eig_maxit)
+        if mixed_updates is not None:
+            opt.mixed_updates = int(mixed_updates)
         self._callbacks = None
         if allocator == "torch":
             self._callbacks = _torch_allocator(stream)
@@ -389,18 +393,18 @@ class Solver:
         return y
 
     KERNEL_CLASSES = ["pchol_update_ff", "pchol_update_fp64", "pchol_update_fp32", "tc_gemm_3xtf32", "pcg_kernel",
-                      "face_reduction"]
+                      "face_reduction", "oz_syrk_bf16", "oz_split", "pchol_panel"]
 
     def set_kernel_timing(self, on=True):
         self._check(self.lib.bddc_set_kernel_timing(self.h, 1 if on else 0))
 
     def kernel_times(self):
         """{class: (ms, algorithmic flop, launches)} since set_kernel_timing(True)."""
-        ms = np.zeros(8)
-        wk = np.zeros(8)
-        nl = np.zeros(8, dtype=np.int64)
+        ms = np.zeros(16)
+        wk = np.zeros(16)
+        nl = np.zeros(16, dtype=np.int64)
         n = C.c_int()
-        self._check(self.lib.bddc_get_kernel_times(self.h, ms.ctypes.data, wk.ctypes.data, nl.ctypes.data, 8,
+        self._check(self.lib.bddc_get_kernel_times(self.h, ms.ctypes.data, wk.ctypes.data, nl.ctypes.data, 16,
                                                    C.byref(n)))
         return {self.KERNEL_CLASSES[k]: (ms[k], wk[k], int(nl[k])) for k in range(n.value)}
 

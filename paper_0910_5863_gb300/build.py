@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbddc.so")
-SOURCES = ["bddc_host.cu", "dense.cu", "assembly.cu", "pcg.cu", "eig.cu", "noalloc.cu", "mixed.cu", "tc_gemm.cu", "lobpcg.cu", "tridiag.cu"]
+SOURCES = ["bddc_host.cu", "dense.cu", "assembly.cu", "pcg.cu", "eig.cu", "noalloc.cu", "mixed.cu", "tc_gemm.cu", "lobpcg.cu", "tridiag.cu", "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

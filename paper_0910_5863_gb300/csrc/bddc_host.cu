@@ -39,6 +39,7 @@
 #include "tc_gemm.h"
 #include "mixed.h"
 #include "lobpcg.h"
+#include "ozaki.h"
 #include "pcg.h"
 
 using namespace bddc;
@@ -185,7 +186,7 @@ struct bddc_handle {
     double mixed_relres = 0.0;  // largest relative residual of the refined A_II X = A_IG
     // kernel timers (bddc_set_kernel_timing): event pairs around the launches of a few
     // kernels, on the handle's stream; the work of every launch is counted on the host
-    static constexpr int kKClasses = 6;
+    static constexpr int kKClasses = 9;
     bool ktiming = false;
     std::vector<cudaEvent_t> kev;
     size_t kev_used = 0;
@@ -246,7 +247,10 @@ void check_launch(bddc_handle *h) {
 }
 
 // ---- kernel timers: classes of bddc_get_kernel_times --------------------------
-enum KClass { KT_PCHOL_FF = 0, KT_PCHOL_F64 = 1, KT_PCHOL_F32 = 2, KT_TC_GEMM = 3, KT_PCG = 4, KT_FACE_RED = 5 };
+enum KClass {
+    KT_PCHOL_FF = 0, KT_PCHOL_F64 = 1, KT_PCHOL_F32 = 2, KT_TC_GEMM = 3, KT_PCG = 4, KT_FACE_RED = 5, KT_OZAKI = 6,
+    KT_OZ_SPLIT = 7, KT_PANEL = 8
+};
 
 void kt_collect(bddc_handle *h) {
     for (const auto &p : h->kpend) {
@@ -353,8 +357,10 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const 
     const int cls = std::is_same<T, ff>::value ? KT_PCHOL_FF : (std::is_same<T, double>::value ? KT_PCHOL_F64 : KT_PCHOL_F32);
     for (int s = 0; s < nsteps; ++s) {
         int kb = s * kPanelNB;
+        const long tokp = kt_begin(h);
         launch_pchol_panel<T>(dd, dp + poff[s], poff[s + 1] - poff[s], kb, h->dst, h->stream);
         check_launch(h);
+        kt_end(h, tokp, KT_PANEL, 0.0);
         double work = 0.0;   // the trailing update's multiply-adds x 2 (lower triangle of diagonal tiles)
         if (h->ktiming)
             for (int u = uoff[s]; u < uoff[s + 1]; ++u) {
@@ -374,10 +380,90 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const 
     }
 }
 
+// Double-float partial Cholesky in block columns of kOzK = 128: each block column is
+// factored by the SIMT kernels with their updates confined to its columns, its rows below
+// are split into bf16 digit planes, and the trailing block is updated on the tensor cores
+// (ozaki.h).  Rows of an identity block that are still zero in the block column
+// (PcholDesc::id0) take no part in the update: their tiles are skipped.
+void run_pchol_oz(bddc_handle *h, const std::vector<PcholDesc<ff>> &descs, const std::string &tag) {
+    constexpr int W = kOzK;
+    int nJ = 0;
+    for (const auto &d : descs) nJ = std::max(nJ, (d.nstop + W - 1) / W);
+    for (int jb = 0; jb < nJ; ++jb) {
+        const int J = jb * W;
+        const std::string t = tag + "_oz" + std::to_string(jb);
+        std::vector<PcholDesc<ff>> pv;
+        std::vector<OzSplitDesc> sd;
+        std::vector<OzSyrkDesc> yd;
+        std::vector<int2> sitems;
+        std::vector<int4> yitems;
+        size_t nsl = 0, nex = 0;
+        for (const auto &d : descs) {
+            if (J >= d.nstop) continue;
+            const int w = std::min(W, d.nstop - J), rows = d.n - J - w;
+            pv.push_back(PcholDesc<ff>{d.A + (size_t)J * d.ld + J, d.n - J, d.ld, w, d.tag, nullptr, w, 0, 0, d.fail});
+            if (rows > 0) {
+                nsl += (size_t)oz_rows_pad(rows) * kOzSlices * W;
+                nex += rows;
+            }
+        }
+        uint16_t *slices = h->ar.get_t<uint16_t>("oz_sl_" + tag, std::max<size_t>(nsl, 8));
+        int *rexp = h->ar.get_t<int>("oz_ex_" + tag, std::max<size_t>(nex, 1));
+        size_t osl = 0, oex = 0;
+        double work = 0.0;
+        for (const auto &d : descs) {
+            if (J >= d.nstop) continue;
+            const int w = std::min(W, d.nstop - J), rows = d.n - J - w;
+            if (rows <= 0) continue;
+            const size_t ld = (size_t)d.ld;
+            const int k = (int)sd.size();
+            sd.push_back(OzSplitDesc{d.A + (size_t)J * ld + J + w, d.ld, rows, w, slices + osl, rexp + oex});
+            yd.push_back(OzSyrkDesc{d.A + (size_t)(J + w) * ld + J + w, d.ld, rows, slices + osl, rexp + oex});
+            osl += (size_t)oz_rows_pad(rows) * kOzSlices * W;
+            oex += rows;
+            for (int g = 0; g < (oz_rows_pad(rows) + 255) / 256; ++g) sitems.push_back(make_int2(k, g));
+            // identity rows still zero in this block column (row id0 + q with idc + q >= J + w):
+            // view rows [z0, z1) of the trailing block, whose origin is row J + w
+            int z0 = rows, z1 = rows;
+            if (d.id0 > 0) {
+                z0 = std::max(0, std::max(d.id0 - J - w, d.id0 - d.idc));
+                z1 = std::min(rows, d.id0 + d.nstop - d.idc - J - w);
+                if (z0 >= z1) z0 = z1 = rows;
+            }
+            auto idle = [&](int a, int b) { return a >= z0 && std::min(b, rows) <= z1; };
+            for (int a = 0; a * kOzTileM < rows; ++a) {
+                if (idle(a * kOzTileM, (a + 1) * kOzTileM)) continue;
+                for (int c = 0; c * kOzTileN < rows && c * kOzTileN <= a * kOzTileM + kOzTileM - 1; ++c) {
+                    if (idle(c * kOzTileN, (c + 1) * kOzTileN)) continue;
+                    yitems.push_back(make_int4(k, a, c, 0));
+                    const double r = std::min(kOzTileM, rows - a * kOzTileM);
+                    const double cc = std::min(kOzTileN, rows - c * kOzTileN);
+                    work += 2.0 * w * r * cc;
+                }
+            }
+        }
+        run_pchol<ff>(h, pv, tag + "#p");
+        if (sd.empty()) continue;
+        auto *dsd = h->ar.upload("oz_sd_" + t, sd, h->stream);
+        auto *dsi = h->ar.upload("oz_si_" + t, sitems, h->stream);
+        const long toks = kt_begin(h);
+        launch_oz_split(dsd, dsi, (int)sitems.size(), h->stream);
+        check_launch(h);
+        kt_end(h, toks, KT_OZ_SPLIT, 0.0);
+        auto *dyd = h->ar.upload("oz_yd_" + t, yd, h->stream);
+        auto *dyi = h->ar.upload("oz_yi_" + t, yitems, h->stream);
+        const long tok = kt_begin(h);
+        launch_oz_syrk(dyd, dyi, (int)yitems.size(), h->dst, h->opt.timeout_s, h->stream);
+        check_launch(h);
+        kt_end(h, tok, KT_OZAKI, work);
+    }
+}
+
 // Partial Cholesky of FP64 matrices in the FP64-class arithmetic of the precision
-// mode: FP64 in BDDC_FP64; in the mixed modes double-float on the FP32 pipe (the
-// lower triangles are converted in place before and after, the upper triangles
-// are not touched).
+// mode: FP64 in BDDC_FP64; in the mixed modes double-float (the lower triangles are
+// converted in place before and after, the upper triangles are not touched), with the
+// trailing updates on the tensor cores (run_pchol_oz) unless mixed_updates selects the
+// FP32 pipe.
 void run_pchol_fp64class(bddc_handle *h, const std::vector<PcholDesc<double>> &descs, const std::string &tag) {
     if (descs.empty()) return;
     if (h->opt.precision == BDDC_FP64 || h->fp64_class_forced) {
@@ -395,7 +481,10 @@ void run_pchol_fp64class(bddc_handle *h, const std::vector<PcholDesc<double>> &d
     for (const auto &d : descs)
         fd.push_back(PcholDesc<ff>{reinterpret_cast<ff *>(d.A), d.n, d.ld, d.nstop, d.tag, nullptr, d.ncol, d.id0,
                                    d.idc, d.fail});
-    run_pchol<ff>(h, fd, tag);
+    if (h->opt.mixed_updates == 0)
+        run_pchol_oz(h, fd, tag);
+    else
+        run_pchol<ff>(h, fd, tag);
     launch_ff_convert(dd, di, (int)items.size(), 0, h->stream);
     check_launch(h);
 }
@@ -3290,6 +3379,7 @@ void bddc_default_options(bddc_options *opt) {
     opt->eig_large_n = -1;
     opt->eig_tol = 1e-8;
     opt->eig_maxit = 240;
+    opt->mixed_updates = 0;
 }
 
 const char *bddc_status_str(bddc_status s) {

@@ -1,0 +1,331 @@
+// Double-float trailing updates on the tensor cores by exact bf16 slicing (see ozaki.h).
+//
+// oz_split: one thread per row of the factored block column.  e_r from the largest
+//   |L[r, k]| (frexp), then exactly, u = L[r, k] 2^-e_r and for p = 1..7:
+//   d_p = rint(u 2^7p), u -= d_p 2^-7p, with u kept as a double-float remainder on the
+//   FP32 pipe.  Digit plane p goes to the pre-swizzled layout of ozaki.h as bf16 (16-byte
+//   stores of 8 digits).
+//
+// oz_syrk: persistent, one CTA per SM (210 KB of shared memory, all 512 TMEM columns),
+//   output tiles of 128 x 32 taken round robin, three warp roles:
+//   * warps 0-6 copy, per tile and 32-value K chunk, the 7 digit planes of rows i0..
+//     (A operand, 128 x 32 bf16 each) and of rows j0.. (B operand, 32 x 32) into one of
+//     three shared-memory stages (cp.async, K-major with 64-byte swizzling: row r's
+//     16-byte chunk c at chunk c ^ ((r / 2) mod 4)) and arrive on the stage's mbarrier;
+//   * one thread of warp 7 issues the 28 digit products (p + q <= 8) of the chunk, two
+//     K = 16 MMAs each (tcgen05.mma kind::f16, bf16 inputs, FP32 accumulate), into
+//     accumulator t = p + q of the tile's set (TMEM columns 224 set + 32 (t - 2) ..),
+//     commits them to the stage's "empty" mbarrier and, after the last chunk, to the
+//     set's "full" mbarrier; two accumulator sets let the drain of one tile overlap the
+//     products of the next;
+//   * warps 8-11 (warp w reads TMEM lanes 32 (w mod 4) .., i.e. those rows) combine the
+//     seven accumulators in double-float from t = 8 to t = 2, release the set, scale by
+//     2^(e_i + e_j) and subtract from C.
+// Every mbarrier wait is bounded; on a timeout the CTA records BDDC_DEV_ERR_TIMEOUT,
+// waits (bounded) for the MMAs it issued, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include "common.cuh"
+#include "ozaki.h"
+#include "tcgen05.cuh"
+
+namespace bddc {
+
+namespace {
+
+using namespace tc;
+
+// warp roles: 0 copies the digit planes into the stages (one thread), 1 issues the MMAs (one
+// thread; the warp owns the tensor memory), 2-5 drain the accumulators (warp w reads TMEM
+// lanes 32 (w mod 4) ..)
+constexpr int OZ_PRODUCER_WARP = 0;
+constexpr int OZ_MMA_WARP = 1;
+constexpr int OZ_EPI_WARP0 = 2;
+constexpr int OZ_THREADS = 192;
+constexpr int OZ_EPI_THREADS = 128;
+constexpr int OZ_KC = kOzKC;                               // K per stage: 64-byte rows (64-byte swizzle)
+constexpr int OZ_STAGES = kOzTileN == 32 ? 3 : 2;
+constexpr int OZ_SETS = kOzTileN == 32 ? 2 : 1;             // accumulator sets in tensor memory
+constexpr int OZ_A_BYTES = kOzTileM * OZ_KC * 2;           // one digit plane of the A operand (8 KB)
+constexpr int OZ_B_BYTES = kOzTileN * OZ_KC * 2;           // (2 KB)
+constexpr int OZ_STAGE_BYTES = kOzSlices * (OZ_A_BYTES + OZ_B_BYTES);
+
+// global -> shared bulk copy (bytes a multiple of 16, both addresses 16-byte aligned), its
+// completion counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024;
+constexpr int OZ_SET_COLS = kOzSlices * kOzTileN;          // one accumulator set (7 x N columns)
+constexpr uint32_t OZ_TMEM_COLS = 512;                     // two sets: the drain of a tile overlaps the next
+
+// shared-memory matrix descriptor, K-major with 64-byte swizzling: start address >> 4,
+// leading byte offset 16 (unused), stride byte offset 512 (8-row atoms of 64-byte rows),
+// descriptor version 1 at bits 46-47, swizzle mode 4 (64 bytes) at bits 61-63
+__device__ __forceinline__ uint64_t oz_sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// tcgen05 instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9 =
+// bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t oz_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzTileN >> 3) << 17) | ((uint32_t)(kOzTileM >> 4) << 24);
+}
+
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    // two-sum of a.h and b, then the low parts (b is exact; a.l carries the old tail)
+    const float s = a.h + b;
+    const float bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b - bb);
+    const float t = e + a.l;
+    const float h = s + t;
+    return ff(h, t - (h - s));
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitDesc *descs, const int2 *items, int nitems) {
+    const int2 w = items[blockIdx.x];
+    const OzSplitDesc d = descs[w.x];
+    const int r = w.y * 256 + threadIdx.x;
+    const int rows_pad = oz_rows_pad(d.rows);
+    if (r >= rows_pad) return;
+    float mx = 0.f;
+    if (r < d.rows)
+        for (int c = 0; c < d.k; ++c) mx = fmaxf(mx, fabsf(d.L[(size_t)c * d.ldl + r].h));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);   // mx = f 2^e, f in [0.5, 1): 2^e > max |x_h|, so |x| 2^-e < 1
+    if (r < d.rows) d.rexp[r] = e;
+    // 16-byte chunk ch (8 digits) of row r within K chunk kc, stored at chunk ch ^ ((r / 2) mod 4)
+    // of the row's 64 bytes: the shared-memory layout the tensor cores read, so that one
+    // contiguous copy moves a whole (plane, chunk, row tile) block.  The digits are taken
+    // from the double-float remainder (h, l) on the FP32 pipe: with d = rint(h 2^7p),
+    // h - d 2^-7p is exact (Sterbenz), and a two-sum keeps the remainder normalised.
+    for (int c0 = 0; c0 < kOzK; c0 += 8) {
+        uint16_t dig[kOzSlices][8];
+        for (int cc = 0; cc < 8; ++cc) {
+            const int c = c0 + cc;
+            float rh = 0.f, rl = 0.f;
+            if (r < d.rows && c < d.k && mx > 0.f) {
+                const ff v = d.L[(size_t)c * d.ldl + r];
+                rh = ldexpf(v.h, -e);
+                rl = ldexpf(v.l, -e);
+            }
+#pragma unroll
+            for (int p = 0; p < kOzSlices; ++p) {
+                const float sc = __int_as_float((127 + 7 * (p + 1)) << 23);    // 2^7(p+1)
+                const float isc = __int_as_float((127 - 7 * (p + 1)) << 23);   // 2^-7(p+1)
+                const float dp = rintf(rh * sc);
+                const float a = rh - dp * isc;   // exact
+                const float s2 = a + rl, bb = s2 - a;
+                const float err = (a - (s2 - bb)) + (rl - bb);
+                rh = s2;
+                rl = err;
+                dig[p][cc] = __bfloat16_as_ushort(__float2bfloat16_rn(dp));
+            }
+        }
+        const int kc = c0 / kOzKC, ch = (c0 % kOzKC) / 8;
+        const int sch = ch ^ ((r >> 1) & 3);
+#pragma unroll
+        for (int p = 0; p < kOzSlices; ++p) {
+            uint4 pk;
+            pk.x = (uint32_t)dig[p][0] | ((uint32_t)dig[p][1] << 16);
+            pk.y = (uint32_t)dig[p][2] | ((uint32_t)dig[p][3] << 16);
+            pk.z = (uint32_t)dig[p][4] | ((uint32_t)dig[p][5] << 16);
+            pk.w = (uint32_t)dig[p][6] | ((uint32_t)dig[p][7] << 16);
+            *reinterpret_cast<uint4 *>(d.slices + (((size_t)p * (kOzK / kOzKC) + kc) * rows_pad + r) * kOzKC +
+                                       sch * 8) = pk;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_syrk_kernel(const OzSyrkDesc *descs, const int4 *items, int nitems, DevStatus *st, uint64_t timeout_ns) {
+    extern __shared__ uint8_t oz_smem_raw[];
+    __shared__ uint64_t full[OZ_STAGES], empty[OZ_STAGES], accfull[OZ_SETS], accempty[OZ_SETS], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t raw = smem_u32(oz_smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;   // swizzle atoms need aligned tiles
+
+    if (warp == OZ_MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(OZ_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < OZ_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int a = 0; a < OZ_SETS; ++a) {
+            mbar_init(smem_u32(&accfull[a]), 1);
+            mbar_init(smem_u32(&accempty[a]), OZ_EPI_THREADS);
+        }
+        mbar_init(smem_u32(&done), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint64_t deadline = globaltimer_ns() + timeout_ns;
+    auto wait = [&](uint64_t &bar, uint32_t parity) -> bool {
+        unsigned spins = 0;
+        while (!mbar_try_wait(smem_u32(&bar), parity)) {
+            if ((++spins & 1023u) == 0 && (abort_flag || globaltimer_ns() > deadline)) {
+                abort_flag = 1;
+                return false;
+            }
+        }
+        return true;
+    };
+    if (warp == OZ_PRODUCER_WARP) {
+        // ---- one thread copies, per tile and 32-value K chunk, the 7 digit-plane blocks of rows
+        // i0.. (A, 8 KB each) and of rows j0.. (B, 2 KB each) into a stage (bulk copies; the stage's
+        // mbarrier completes when all their bytes have landed) ----
+        if (lane == 0) {
+            int g = 0;
+            for (int it = blockIdx.x; it < nitems && !abort_flag; it += gridDim.x) {
+                const int4 w = items[it];
+                const OzSyrkDesc d = descs[w.x];
+                const int i0 = w.y * kOzTileM, j0 = w.z * kOzTileN, rows_pad = oz_rows_pad(d.n);
+                for (int kc = 0; kc < kOzK / kOzKC; ++kc, ++g) {
+                    const int s = g % OZ_STAGES;
+                    if (g >= OZ_STAGES && !wait(empty[s], (uint32_t)(((g / OZ_STAGES) - 1) & 1))) break;
+                    const uint32_t a_base = sbase + s * OZ_STAGE_BYTES, b_base = a_base + kOzSlices * OZ_A_BYTES;
+                    const uint32_t fb = smem_u32(&full[s]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                 "r"((uint32_t)OZ_STAGE_BYTES)
+                                 : "memory");
+                    for (int p = 0; p < kOzSlices; ++p) {
+                        const uint16_t *plane = d.slices + ((size_t)p * (kOzK / kOzKC) + kc) * rows_pad * kOzKC;
+                        bulk_g2s(a_base + p * OZ_A_BYTES, plane + (size_t)i0 * kOzKC, OZ_A_BYTES, fb);
+                        bulk_g2s(b_base + p * OZ_B_BYTES, plane + (size_t)j0 * kOzKC, OZ_B_BYTES, fb);
+                    }
+                }
+            }
+        }
+    } else if (warp == OZ_MMA_WARP) {
+        // ---- one thread issues the 28 digit products per K chunk into the tile's accumulator set ----
+        if (lane == 0) {
+            const uint32_t idesc = oz_idesc();
+            int g = 0, li = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
+                const int a = li % OZ_SETS;
+                if (li >= OZ_SETS && !wait(accempty[a], (uint32_t)(((li / OZ_SETS) - 1) & 1))) break;
+                tc_fence_after();
+                const uint32_t abase = tmem + (uint32_t)(a * OZ_SET_COLS);
+                for (int kc = 0; kc < kOzK / OZ_KC && ok; ++kc, ++g) {
+                    const int s = g % OZ_STAGES;
+                    if (!wait(full[s], (uint32_t)((g / OZ_STAGES) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_base = sbase + s * OZ_STAGE_BYTES, b_base = a_base + kOzSlices * OZ_A_BYTES;
+                    for (int t = 2; t <= kOzSlices + 1; ++t) {
+                        const uint32_t dacc = abase + (uint32_t)(kOzTileN * (t - 2));
+                        bool first = kc == 0;
+                        for (int p = 1; p <= kOzSlices; ++p) {
+                            const int q = t - p;
+                            if (q < 1 || q > kOzSlices) continue;
+#pragma unroll
+                            for (int kk = 0; kk < OZ_KC / 16; ++kk) {
+                                const uint32_t koff = kk * 32;   // 16 bf16 = 32 bytes of the 64-byte row
+                                tc_mma_f16(dacc, oz_sdesc(a_base + (p - 1) * OZ_A_BYTES + koff),
+                                           oz_sdesc(b_base + (q - 1) * OZ_B_BYTES + koff), idesc, first ? 0u : 1u);
+                                first = false;
+                            }
+                        }
+                    }
+                    tc_commit(smem_u32(&empty[s]));   // frees the stage when these products are done
+                }
+                if (!ok) break;
+                tc_commit(smem_u32(&accfull[a]));     // the tile's accumulators are complete
+            }
+            tc_commit(smem_u32(&done));               // every issued product has completed
+            if (!wait(done, 0u)) {
+                // bounded again: the tensor memory is freed only after the last products
+                const uint64_t dl = globaltimer_ns() + timeout_ns;
+                while (!mbar_try_wait(smem_u32(&done), 0u) && globaltimer_ns() < dl) {
+                }
+            }
+        }
+    } else if (warp >= OZ_EPI_WARP0) {
+        // ---- epilogue: combine the seven accumulators in double-float, scale, subtract from C ----
+        const int q4 = warp & 3;
+        int li = 0;
+        for (int it = blockIdx.x; it < nitems && !abort_flag; it += gridDim.x, ++li) {
+            const int a = li % OZ_SETS;
+            if (!wait(accfull[a], (uint32_t)((li / OZ_SETS) & 1))) break;
+            tc_fence_after();
+            const int4 w = items[it];
+            const OzSyrkDesc d = descs[w.x];
+            const int i = w.y * kOzTileM + 32 * q4 + lane, j0 = w.z * kOzTileN;
+            ff acc[kOzTileN];
+#pragma unroll
+            for (int jj = 0; jj < kOzTileN; ++jj) acc[jj] = ff(0.f, 0.f);
+            for (int t = kOzSlices + 1; t >= 2; --t) {
+                uint32_t v[32];
+                const float sc = __int_as_float((127 - 7 * t) << 23);   // 2^-7t
+#pragma unroll
+                for (int g32 = 0; g32 < kOzTileN / 32; ++g32) {
+                    tc_ld32(tmem + ((uint32_t)(32 * q4) << 16) +
+                                (uint32_t)(a * OZ_SET_COLS + kOzTileN * (t - 2) + 32 * g32),
+                            v);
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj)
+                        acc[32 * g32 + jj] = ff_add_f(acc[32 * g32 + jj], __uint_as_float(v[jj]) * sc);
+                }
+            }
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accempty[a])) : "memory");
+            if (i < d.n) {
+                const int ei = d.rexp[i];
+#pragma unroll
+                for (int jj = 0; jj < kOzTileN; ++jj) {
+                    const int j = j0 + jj;
+                    if (j > i || j >= d.n) continue;
+                    const int sh = ei + d.rexp[j];
+                    const ff upd(ldexpf(acc[jj].h, sh), ldexpf(acc[jj].l, sh));
+                    ff *cp = d.C + (size_t)j * d.ldc + i;
+                    *cp = *cp - upd;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) dev_fail(st, BDDC_DEV_ERR_TIMEOUT, blockIdx.x, -3);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == OZ_MMA_WARP) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+void launch_oz_split(const OzSplitDesc *d, const int2 *items, int nitems, cudaStream_t s) {
+    if (nitems > 0) oz_split_kernel<<<nitems, 256, 0, s>>>(d, items, nitems);
+}
+
+void launch_oz_syrk(const OzSyrkDesc *d, const int4 *items, int nitems, DevStatus *st, double timeout_s,
+                    cudaStream_t s) {
+    if (nitems <= 0) return;
+    cudaFuncSetAttribute(oz_syrk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nitems < nsm ? nitems : nsm;   // persistent: one CTA per SM, tiles round robin
+    const uint64_t tns = (uint64_t)(timeout_s * 1e9);
+    oz_syrk_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(d, items, nitems, st, tns);
+}
+
+}  // namespace bddc
