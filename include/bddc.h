@@ -107,6 +107,12 @@ typedef struct {
     int eig_large_n;
     double eig_tol;
     int eig_maxit;
+    /* Mixed modes: the trailing updates of the double-float factorizations (pair
+     * condensations, local saddle).  0 (default): on the tensor cores, by exact bf16
+     * slicing of the factored block columns (7 digit planes of 7 bits, FP32 accumulation
+     * of integer digit products, double-float combination; ~2^-49 per product);
+     * 1: double-float on the FP32 pipe. */
+    int mixed_updates;
 } bddc_options;
 
 /* One substructure of an algebraic problem (bddc_set_problem): its local matrix
@@ -385,10 +391,14 @@ BDDC_API bddc_status bddc_set_kernel_timing(bddc_handle *h, int on);
  *   3 tensor-core 3xTF32 GEMMs (tc_gemm_kernel)
  *   4 the persistent PCG kernel (solve launches)
  *   5 the face reductions (face_eig_kernel, tridiag_multi_kernel)
+ *   6 tensor-core trailing updates of the double-float factorizations (oz_syrk_kernel;
+ *     work = 2 x the multiply-adds of the block update, computed as 28 bf16 digit products)
+ *   7 the digit splitting of their block columns (oz_split_kernel; work 0)
+ *   8 the panel steps of every partial Cholesky (pchol_panel_kernel; work 0)
  * ms: summed device time of the launches; work: their algorithmic flop (partial
  * Cholesky updates: 2 x the multiply-adds of the lower-triangle tiles launched;
  * GEMMs: 2 M N K, one of the three TF32 products; reductions: 4/3 n^3 per face;
- * PCG: 0); launches: their count.  *n = 6; cap limits the entries written.  The call
+ * PCG: 0); launches: their count.  *n = 9; cap limits the entries written.  The call
  * waits for the recorded events.  Errors: BDDC_EINVAL (NULL handle). */
 BDDC_API bddc_status bddc_get_kernel_times(bddc_handle *h, double *ms, double *work, int64_t *launches, int cap,
                                            int *n);
@@ -412,8 +422,10 @@ BDDC_API int64_t bddc_launch_count(const bddc_handle *h);
  *   stream    cudaStream_t (NULL = default stream); the call synchronizes it
  *   msg       optional buffer (msg_cap bytes) for a one-line error reason
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (once per device, with that device current); make
- * that first call before any stream capture.  All calls share the one array:
+ * cudaGetSymbolAddress (once per device, with that device current).  The CUDA
+ * runtime loads device code lazily, so that first call is also when the array's
+ * memory is taken on that device: make it at start-up (and before any stream
+ * capture); later calls allocate nothing.  All calls share the one array:
  * calls whose work overlaps on the GPU (other threads or streams) race and
  * must be serialized by the caller.  Errors: BDDC_EINVAL (sizes, null
  * pointers, n > 1024), BDDC_ENOTSPD (A_II not positive definite), BDDC_ECUDA. */
