@@ -38,12 +38,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BDDC setup+solve s at rel.res 1e-8, mixed vs FP64 GPU; % tensor-core peak"
 WORKLOADS = {
-    # the timed workload: 24^3 Poisson, 27 substructures, 20% of elements at k = 1e4
+    # 24^3 Poisson, 27 substructures, 20% of elements at k = 1e4
     "poisson24": ("poisson24_3x3x3_jump1e4_adaptive_tau10", "24x24x24 Q1 hex", "config_adaptive_poisson"),
     # 32^3 elasticity, 64 substructures, 8 stiff channels E = 1e6, clamped z = 0
     "elast32": ("elast32_4x4x4_channels1e6_adaptive_tau10", "32x32x32 Q1 hex, 3 dofs/node",
                 "config_elasticity_channels"),
-    # 48x48x24 elasticity, 64 region-grown irregular substructures, E in {1, 1e3} by z-layers of 4
+    # the default workload: 48x48x24 elasticity, 64 region-grown irregular substructures,
+    # E in {1, 1e3} by z-layers of 4
     "irregular48": ("elast48x48x24_irregular64_layers1e3_adaptive_tau10", "48x48x24 Q1 hex, 3 dofs/node",
                     "config_irregular_elasticity"),
     # 256 independent Poisson problems (2^3 or 3^3 substructures of 6^3..10^3 elements,

@@ -58,8 +58,12 @@ typedef enum { BDDC_MEM_HOST = 0, BDDC_MEM_DEVICE = 1 } bddc_mem;
 typedef enum {
     BDDC_FP64 = 0,         /* every dense factorization in FP64 */
     BDDC_MIXED = 1,        /* interior elimination: FP32 factorization + FP64 refinement (S_i to
-                              1e-11 relative); local saddle, coarse, pair problems, eigen, PCG
-                              in FP64.  The preconditioner matches the FP64 one to ~1e-9. */
+                              1e-11 relative); the local saddle and coarse inverses and the pair
+                              condensations in double-float (unit roundoff 2^-48), their trailing
+                              updates on the bf16 tensor cores by exact digit slicing
+                              (mixed_updates = 0); face eigenproblems in double-float with FP64
+                              Sturm counts and Rayleigh quotients; PCG in FP64.  The
+                              preconditioner matches the FP64 one to ~1e-9. */
     BDDC_MIXED_FP32_SADDLE = 2  /* as BDDC_MIXED, and the local saddle operators of the
                               preconditioner (Lemma 2.1) from an equilibrated FP32
                               factorization (rebuilt in FP64 if a pivot falls below 1e-5).
@@ -108,7 +112,7 @@ typedef struct {
     double eig_tol;
     int eig_maxit;
     /* Mixed modes: the trailing updates of the double-float factorizations (pair
-     * condensations, local saddle).  0 (default): on the tensor cores, by exact bf16
+     * condensations, local saddle and coarse inverses).  0 (default): on the tensor cores, by exact bf16
      * slicing of the factored block columns (7 digit planes of 7 bits, FP32 accumulation
      * of integer digit products, double-float combination; ~2^-49 per product);
      * 1: double-float on the FP32 pipe. */

@@ -1659,12 +1659,13 @@ void coarse_setup(bddc_handle *h, bool allow_fp32) {
     auto *dcad = h->ar.upload("cad", cad, h->stream);
     launch_coarse_assemble(dcad, ns, SC, nC, h->stream);
     check_launch(h);
-    // inverse by partial Cholesky of [[S_C, .]; [I, 0]]
+    // inverse by partial Cholesky of [[S_C, .]; [I, 0]], in the FP64-class arithmetic of the
+    // precision mode (double-float with tensor-core updates in the mixed modes)
     std::vector<GatherOp> g5{gop(SC, nC, MC, ldm, nC, nC)};
     g5[0].dst_lower = 1;
     run_gathers(h, g5, "MC");
     run_diag(h, {DiagOp{MC, ldm, nC, 0, nC, 1.0}}, "MC");
-    run_pchol<double>(h, {PcholDesc<double>{MC, 2 * nC, ldm, nC, 0, nullptr, 0, nC}}, "MC");
+    run_pchol_fp64class(h, {PcholDesc<double>{MC, 2 * nC, ldm, nC, 0, nullptr, 0, nC}}, "MC");
     double *SCinv = h->ar.get_t<double>("SCinv", (size_t)nC * nC);
     GatherOp o = gop(MC, ldm, SCinv, nC, nC, nC);
     o.src_row_off = nC;
@@ -1729,12 +1730,10 @@ void alloc_solver_buffers(bddc_handle *h) {
     h->ops.maxGi = 0;
     for (auto &sd : h->subs) h->ops.maxGi = std::max(h->ops.maxGi, sd.nG);
     std::vector<int> nGi(ns), ldS(ns), RG;
-    std::vector<int2> rb;
     for (int s = 0; s < ns; ++s) {
         nGi[s] = h->subs[s].nG;
         ldS[s] = h->subs[s].ldS;
         RG.insert(RG.end(), h->subs[s].RG.begin(), h->subs[s].RG.end());
-        for (int r = 0; r < nGi[s]; r += 64) rb.push_back(make_int2(s, r));
     }
     {   // S_i and P~_i together larger than about 3/4 of L2 (126 MB): stream them
         size_t bytes = 0;
@@ -1750,11 +1749,11 @@ void alloc_solver_buffers(bddc_handle *h) {
     h->ops.gptr = h->ar.upload("gptr", h->gptr, h->stream);
     h->ops.gent = h->ar.upload("gent", h->gent, h->stream);
     h->ops.gsub = h->ar.upload("gsub", h->gsub, h->stream);
-    h->ops.rowblk = h->ar.upload("rowblk", rb, h->stream);
-    h->ops.nrowblk = (int)rb.size();
+    h->ops.sumG = h->sumG;
     const int nG = std::max(h->nG, 1);
     h->pb.x = h->ar.get_t<double>("x", nG);
     h->pb.r = h->ar.get_t<double>("r", nG);
+    h->pb.r2 = h->ar.get_t<double>("r2", nG);
     h->pb.z = h->ar.get_t<double>("z", nG);
     h->pb.p0 = h->ar.get_t<double>("p0", nG);
     h->pb.p1 = h->ar.get_t<double>("p1", nG);
@@ -2450,25 +2449,6 @@ void run_face_eigs(bddc_handle *h, const std::vector<EigDesc> &eds, double tau, 
         BDDC_CUDA(cudaMemcpyAsync(fl.data(), fails, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream));
         BDDC_CUDA(cudaStreamSynchronize(h->stream));
         std::vector<int> next;
-        if (getenv("BDDC_LOB_DEBUG")) {
-            int cnt[6] = {0, 0, 0, 0, 0, 0}, nf = 0;
-            for (int b = 0; b < nb; ++b) {
-                cnt[std::min(std::max(st[4 * b + 2], 0), 5)]++;
-                nf += fl[b] != 0;
-            }
-            fprintf(stderr, "lobpcg pass %d: %d faces k=%d loop %d; states run %d conv %d small %d rank %d final %d; cert fails %d\n",
-                    pass, nb, k, it, cnt[0], cnt[1], cnt[2], cnt[3], cnt[4], nf);
-            for (int b = 0; b < nb; ++b)
-                if (st[4 * b + 2] != 1 || fl[b]) {
-                    std::vector<double> th(k), rn(k);
-                    BDDC_CUDA(cudaMemcpy(th.data(), ld[b].theta, k * sizeof(double), cudaMemcpyDeviceToHost));
-                    BDDC_CUDA(cudaMemcpy(rn.data(), ld[b].rnorm, k * sizeof(double), cudaMemcpyDeviceToHost));
-                    fprintf(stderr, "  face n=%d state %d iters %d fail %d:", big[todo[b]].n, st[4 * b + 2],
-                            st[4 * b + 1], fl[b]);
-                    for (int j = 0; j < std::min(k, 8); ++j) fprintf(stderr, " (%.6g %.2e)", th[j], rn[j]);
-                    fprintf(stderr, "\n");
-                }
-        }
         for (int b = 0; b < nb; ++b) {
             if (stats) stats->iters = std::max(stats->iters, st[4 * b + 1]);
             if (st[4 * b + 2] == 1 && fl[b] == 0)

@@ -6,21 +6,24 @@
 //   FP32 pipe.  Digit plane p goes to the pre-swizzled layout of ozaki.h as bf16 (16-byte
 //   stores of 8 digits).
 //
-// oz_syrk: persistent, one CTA per SM (210 KB of shared memory, all 512 TMEM columns),
+// oz_syrk: persistent, one CTA per SM (211 KB of shared memory, all 512 TMEM columns),
 //   output tiles of 128 x 32 taken round robin, three warp roles:
-//   * warps 0-6 copy, per tile and 32-value K chunk, the 7 digit planes of rows i0..
-//     (A operand, 128 x 32 bf16 each) and of rows j0.. (B operand, 32 x 32) into one of
-//     three shared-memory stages (cp.async, K-major with 64-byte swizzling: row r's
-//     16-byte chunk c at chunk c ^ ((r / 2) mod 4)) and arrive on the stage's mbarrier;
-//   * one thread of warp 7 issues the 28 digit products (p + q <= 8) of the chunk, two
-//     K = 16 MMAs each (tcgen05.mma kind::f16, bf16 inputs, FP32 accumulate), into
-//     accumulator t = p + q of the tile's set (TMEM columns 224 set + 32 (t - 2) ..),
-//     commits them to the stage's "empty" mbarrier and, after the last chunk, to the
-//     set's "full" mbarrier; two accumulator sets let the drain of one tile overlap the
-//     products of the next;
-//   * warps 8-11 (warp w reads TMEM lanes 32 (w mod 4) .., i.e. those rows) combine the
-//     seven accumulators in double-float from t = 8 to t = 2, release the set, scale by
-//     2^(e_i + e_j) and subtract from C.
+//   * one thread of warp 0 copies, per tile and 32-value K chunk, the 7 digit planes of rows
+//     i0.. (A operand, 128 x 32 bf16 each, 8 KB) and of rows j0.. (B operand, 32 x 32, 2 KB)
+//     into one of three shared-memory stages with bulk copies (cp.async.bulk; the planes are
+//     stored pre-swizzled, K-major with 64-byte swizzling: row r's 16-byte chunk c at chunk
+//     c ^ ((r / 2) mod 4)); the stage's mbarrier completes when all bytes have landed;
+//   * one thread of warp 1 issues per K = 16 step one MMA per A plane p (tcgen05.mma
+//     kind::f16, bf16 inputs, FP32 accumulate): the B planes q = 1 .. 8 - p lie back to back
+//     in the stage, so A_p against all of them is one MMA of N = 32 (8 - p) whose 32-column
+//     blocks land on the accumulators t = p + q (TMEM columns 224 set + 32 (t - 2) ..); it
+//     commits them to the stage's "empty" mbarrier and, after the last chunk, to the set's
+//     "full" mbarrier; two accumulator sets let the drain of one tile overlap the products of
+//     the next;
+//   * warps 2-9 (warp w reads TMEM lanes 32 (w mod 4) .., i.e. those rows, and 16 of the 32
+//     columns) fetch the tile's C values while its products run, combine the seven
+//     accumulators from t = 8 to t = 2, release the set, scale by 2^(e_i + e_j) and subtract
+//     from C.
 // Every mbarrier wait is bounded; on a timeout the CTA records BDDC_DEV_ERR_TIMEOUT,
 // waits (bounded) for the MMAs it issued, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -40,11 +43,16 @@ using namespace tc;
 constexpr int OZ_PRODUCER_WARP = 0;
 constexpr int OZ_MMA_WARP = 1;
 constexpr int OZ_EPI_WARP0 = 2;
-constexpr int OZ_THREADS = 192;
-constexpr int OZ_EPI_THREADS = 128;
+constexpr int OZ_EPI_WARPS = 8;                            // two per TMEM lane quarter, 16 columns each
+constexpr int OZ_EPI_THREADS = 32 * OZ_EPI_WARPS;
+constexpr int OZ_THREADS = 32 * OZ_EPI_WARP0 + OZ_EPI_THREADS;
 constexpr int OZ_KC = kOzKC;                               // K per stage: 64-byte rows (64-byte swizzle)
-constexpr int OZ_STAGES = kOzTileN == 32 ? 3 : 2;
-constexpr int OZ_SETS = kOzTileN == 32 ? 2 : 1;             // accumulator sets in tensor memory
+constexpr int OZ_STAGES = 3;
+constexpr int OZ_SETS = 2;                                 // accumulator sets in tensor memory
+// one MMA takes all B planes of a stage (N = 7 x 32 at most: M = 128 allows N <= 256), and two
+// sets of seven accumulators fill the 512 TMEM columns
+static_assert(kOzTileN == 32 && kOzTileN * kOzSlices <= 256 && OZ_SETS * kOzSlices * kOzTileN <= 512,
+              "tile shape: one MMA per A plane, two sets in 512 TMEM columns");
 constexpr int OZ_A_BYTES = kOzTileM * OZ_KC * 2;           // one digit plane of the A operand (8 KB)
 constexpr int OZ_B_BYTES = kOzTileN * OZ_KC * 2;           // (2 KB)
 constexpr int OZ_STAGE_BYTES = kOzSlices * (OZ_A_BYTES + OZ_B_BYTES);
@@ -70,8 +78,17 @@ __device__ __forceinline__ uint64_t oz_sdesc(uint32_t saddr) {
 
 // tcgen05 instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9 =
 // bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
-__host__ __device__ constexpr uint32_t oz_idesc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzTileN >> 3) << 17) | ((uint32_t)(kOzTileM >> 4) << 24);
+__host__ __device__ constexpr uint32_t oz_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kOzTileM >> 4) << 24);
+}
+
+// a 2^e (exact unless the result leaves the normal range, where it rounds like ldexpf)
+__device__ __forceinline__ ff ff_scale2(ff a, int e) {
+    if (e >= -126 && e <= 127) {
+        const float p = __int_as_float((e + 127) << 23);
+        return ff(a.h * p, a.l * p);
+    }
+    return ff(ldexpf(a.h, e), ldexpf(a.l, e));
 }
 
 __device__ __forceinline__ ff ff_add_f(ff a, float b) {
@@ -214,7 +231,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     } else if (warp == OZ_MMA_WARP) {
         // ---- one thread issues the 28 digit products per K chunk into the tile's accumulator set ----
         if (lane == 0) {
-            const uint32_t idesc = oz_idesc();
             int g = 0, li = 0;
             bool ok = true;
             for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
@@ -230,20 +246,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t a_base = sbase + s * OZ_STAGE_BYTES, b_base = a_base + kOzSlices * OZ_A_BYTES;
-                    for (int t = 2; t <= kOzSlices + 1; ++t) {
-                        const uint32_t dacc = abase + (uint32_t)(kOzTileN * (t - 2));
-                        bool first = kc == 0;
-                        for (int p = 1; p <= kOzSlices; ++p) {
-                            const int q = t - p;
-                            if (q < 1 || q > kOzSlices) continue;
+                    // plane p of A against the B planes q = 1 .. 8 - p at once: they are consecutive
+                    // 32-row blocks of the stage, i.e. one B operand of N = 32 (8 - p) rows, whose
+                    // output block q lands on accumulator p + q (columns 32 (p + q - 2) ..) when the
+                    // product starts at column 32 (p - 1).  The first product of a tile (p = 1, all
+                    // seven accumulators) overwrites, every later one accumulates.
 #pragma unroll
-                            for (int kk = 0; kk < OZ_KC / 16; ++kk) {
-                                const uint32_t koff = kk * 32;   // 16 bf16 = 32 bytes of the 64-byte row
-                                tc_mma_f16(dacc, oz_sdesc(a_base + (p - 1) * OZ_A_BYTES + koff),
-                                           oz_sdesc(b_base + (q - 1) * OZ_B_BYTES + koff), idesc, first ? 0u : 1u);
-                                first = false;
-                            }
-                        }
+                    for (int kk = 0; kk < OZ_KC / 16; ++kk) {
+                        const uint32_t koff = kk * 32;   // 16 bf16 = 32 bytes of the 64-byte row
+#pragma unroll
+                        for (int p = 1; p <= kOzSlices; ++p)
+                            tc_mma_f16(abase + (uint32_t)(kOzTileN * (p - 1)),
+                                       oz_sdesc(a_base + (p - 1) * OZ_A_BYTES + koff), oz_sdesc(b_base + koff),
+                                       oz_idesc(kOzTileN * (kOzSlices + 1 - p)),
+                                       (kc == 0 && kk == 0 && p == 1) ? 0u : 1u);
                     }
                     tc_commit(smem_u32(&empty[s]));   // frees the stage when these products are done
                 }
@@ -259,44 +275,74 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             }
         }
     } else if (warp >= OZ_EPI_WARP0) {
-        // ---- epilogue: combine the seven accumulators in double-float, scale, subtract from C ----
-        const int q4 = warp & 3;
+        // ---- epilogue: combine the seven accumulators, scale, subtract from C ----
+        // Warp w reads TMEM lanes 32 (w mod 4) .. (rows of the tile) and 16 of its 32 columns.
+        // The tile's C values and column exponents are fetched before its accumulators are
+        // waited for (no other CTA touches this tile), so their latency overlaps the products;
+        // lane l holds the exponent of column j0 + l and hands it out by shuffle.
+        // Combination, in units of 2^(e_i + e_j): acc_8, acc_7, acc_6 (integers below 2^23) in
+        // plain FP32, Horner in 2^-7, with a rounding error below 2^-43, under the 2^-41 of the
+        // digit products p + q > 8 that the scheme drops; then acc_5 .. acc_2 one by one in
+        // double-float.
+        const int q4 = warp & 3, c16 = 16 * ((warp - OZ_EPI_WARP0) >> 2);
         int li = 0;
         for (int it = blockIdx.x; it < nitems && !abort_flag; it += gridDim.x, ++li) {
             const int a = li % OZ_SETS;
-            if (!wait(accfull[a], (uint32_t)((li / OZ_SETS) & 1))) break;
-            tc_fence_after();
             const int4 w = items[it];
             const OzSyrkDesc d = descs[w.x];
-            const int i = w.y * kOzTileM + 32 * q4 + lane, j0 = w.z * kOzTileN;
-            ff acc[kOzTileN];
+            const int i = w.y * kOzTileM + 32 * q4 + lane, j0 = w.z * kOzTileN + c16;
+            const bool row_ok = i < d.n;
+            const int ej = w.z * kOzTileN + lane < d.n ? d.rexp[w.z * kOzTileN + lane] : 0;
+            const int ei = row_ok ? d.rexp[i] : 0;
+            ff cv[16];
 #pragma unroll
-            for (int jj = 0; jj < kOzTileN; ++jj) acc[jj] = ff(0.f, 0.f);
-            for (int t = kOzSlices + 1; t >= 2; --t) {
-                uint32_t v[32];
-                const float sc = __int_as_float((127 - 7 * t) << 23);   // 2^-7t
+            for (int jj = 0; jj < 16; ++jj) {
+                const int j = j0 + jj;
+                cv[jj] = (row_ok && j <= i) ? d.C[(size_t)j * d.ldc + i] : ff(0.f, 0.f);
+            }
+            if (!wait(accfull[a], (uint32_t)((li / OZ_SETS) & 1))) break;
+            tc_fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(a * OZ_SET_COLS + c16);
+            auto col = [&](int t) { return tbase + (uint32_t)(kOzTileN * (t - 2)); };
+            float tail[16];
+            {
+                uint32_t v8[16], v7[16], v6[16];
+                tc_ld16_nowait(col(8), v8);
+                tc_ld16_nowait(col(7), v7);
+                tc_ld16_nowait(col(6), v6);
+                tc_wait_ld();
+                const float s7 = __int_as_float((127 - 7) << 23);   // 2^-7
 #pragma unroll
-                for (int g32 = 0; g32 < kOzTileN / 32; ++g32) {
-                    tc_ld32(tmem + ((uint32_t)(32 * q4) << 16) +
-                                (uint32_t)(a * OZ_SET_COLS + kOzTileN * (t - 2) + 32 * g32),
-                            v);
+                for (int jj = 0; jj < 16; ++jj)
+                    tail[jj] = fmaf(fmaf(__uint_as_float(v8[jj]), s7, __uint_as_float(v7[jj])), s7,
+                                    __uint_as_float(v6[jj])) * __int_as_float((127 - 42) << 23);   // 2^-42
+            }
+            ff acc[16];
+            {
+                uint32_t v5[16], v4[16], v3[16], v2[16];
+                tc_ld16_nowait(col(5), v5);
+                tc_ld16_nowait(col(4), v4);
+                tc_ld16_nowait(col(3), v3);
+                tc_ld16_nowait(col(2), v2);
+                tc_wait_ld();
+                tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accempty[a])) : "memory");
 #pragma unroll
-                    for (int jj = 0; jj < 32; ++jj)
-                        acc[32 * g32 + jj] = ff_add_f(acc[32 * g32 + jj], __uint_as_float(v[jj]) * sc);
+                for (int jj = 0; jj < 16; ++jj) {
+                    ff x(tail[jj], 0.f);
+                    x = ff_add_f(x, __uint_as_float(v5[jj]) * __int_as_float((127 - 35) << 23));
+                    x = ff_add_f(x, __uint_as_float(v4[jj]) * __int_as_float((127 - 28) << 23));
+                    x = ff_add_f(x, __uint_as_float(v3[jj]) * __int_as_float((127 - 21) << 23));
+                    acc[jj] = ff_add_f(x, __uint_as_float(v2[jj]) * __int_as_float((127 - 14) << 23));
                 }
             }
-            tc_fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accempty[a])) : "memory");
-            if (i < d.n) {
-                const int ei = d.rexp[i];
 #pragma unroll
-                for (int jj = 0; jj < kOzTileN; ++jj) {
-                    const int j = j0 + jj;
-                    if (j > i || j >= d.n) continue;
-                    const int sh = ei + d.rexp[j];
-                    const ff upd(ldexpf(acc[jj].h, sh), ldexpf(acc[jj].l, sh));
-                    ff *cp = d.C + (size_t)j * d.ldc + i;
-                    *cp = *cp - upd;
+            for (int jj = 0; jj < 16; ++jj) {
+                const int j = j0 + jj;
+                const int sh = ei + __shfl_sync(0xffffffffu, ej, c16 + jj);
+                if (row_ok && j <= i) {   // j <= i < n
+                    const ff upd = ff_scale2(acc[jj], sh);
+                    d.C[(size_t)j * d.ldc + i] = cv[jj] - upd;
                 }
             }
         }

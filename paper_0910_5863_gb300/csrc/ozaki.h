@@ -9,9 +9,10 @@
 // products of two digit matrices, summed over K <= 128, are integers below 2^24 and so
 // exact in the FP32 accumulators of the tensor cores whatever the order of summation;
 // all products with the same p + q = t share one accumulator (at most 7 of them:
-// 9 x 2^12 x 128 < 2^24).  The seven accumulators t = 2..8 are then combined in
-// double-float, t = 8 first, scaled by 2^(e_r + e_c) and subtracted from C.  Terms with
-// p + q > 8 are dropped: the result carries ~2^-49 of 2^(e_r + e_c) per product.
+// 9 x 2^12 x 128 < 2^24).  The seven accumulators t = 2..8 are then combined, t = 8 first
+// (t = 8..6 in FP32, whose rounding stays below the dropped terms, t = 5..2 in
+// double-float), scaled by 2^(e_r + e_c) and subtracted from C.  Terms with p + q > 8 are
+// dropped: the result carries ~2^-49 of 2^(e_r + e_c) per product.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

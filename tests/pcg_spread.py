@@ -44,3 +44,27 @@ def iterations_agree(it, m, kappa, tol=1e-8):
     lo, hi = perturbed_iteration_range(m, tol, seeds=16, delta=1e-12)
     w = max(1, hi - lo)
     return lo - w <= it <= hi + w
+
+
+def perturbed_rows_iteration_range(m, tol=1e-8, seeds=8, delta=1e-9):
+    """(lo, hi) of the oracle's iteration count over the unperturbed run and `seeds` runs
+    with every adaptive constraint row r -> r + delta |r| e / |e|, e Gaussian: the
+    preconditioner then moves by ~delta, the size of the difference between two FP64
+    implementations whose face eigenvectors agree to that level."""
+    saved = [(g, g.rows.copy()) for g in m.constraints if g.kind.startswith("adaptive")]
+    m._M = None
+    its = [m.solve(tol=tol).iters]
+    try:
+        for seed in range(seeds):
+            rng = np.random.default_rng(1000 + seed)
+            for g, R in saved:
+                E = rng.standard_normal(R.shape)
+                g.rows = R + delta * (np.linalg.norm(R, axis=1, keepdims=True) * E
+                                      / np.linalg.norm(E, axis=1, keepdims=True))
+            m._M = None
+            its.append(m.solve(tol=tol).iters)
+    finally:
+        for g, R in saved:
+            g.rows = R
+        m._M = None
+    return min(its), max(its)

@@ -17,13 +17,10 @@ from test_gpu_parity import check_face_rows
 pytestmark = pytest.mark.gpu
 
 TAU = 10.0
-# Eigenvalues against the oracle: the FP64 path meets 1e-6 on every face.  The mixed
-# path condenses the pairs in double-float (unit roundoff 2^-48, 32 times FP64's);
-# on this problem the worst faces amplify rounding by ~1e9 (the FP64 path's own
-# deviation from the oracle reaches 1.3e-7 there), so the mixed path is held to
-# 32 x 1.3e-7 ~ 4e-6, rounded up to 1e-5.
-TOL_LAM = {B.FP64: 1e-6, B.MIXED: 1e-5}
-TOL_SPAN = {B.FP64: 1e-6, B.MIXED: 1e-5}
+# Eigenvalues (the selected ones and the next) and the spans of the face rows against the
+# oracle, both paths at 1e-6 on every face.
+TOL_LAM = {B.FP64: 1e-6, B.MIXED: 1e-6}
+TOL_SPAN = {B.FP64: 1e-6, B.MIXED: 1e-6}
 
 
 @pytest.fixture(scope="module")
