@@ -1730,10 +1730,12 @@ void alloc_solver_buffers(bddc_handle *h) {
     h->ops.maxGi = 0;
     for (auto &sd : h->subs) h->ops.maxGi = std::max(h->ops.maxGi, sd.nG);
     std::vector<int> nGi(ns), ldS(ns), RG;
+    std::vector<int2> rb;
     for (int s = 0; s < ns; ++s) {
         nGi[s] = h->subs[s].nG;
         ldS[s] = h->subs[s].ldS;
         RG.insert(RG.end(), h->subs[s].RG.begin(), h->subs[s].RG.end());
+        for (int r = 0; r < nGi[s]; r += 64) rb.push_back(make_int2(s, r));
     }
     {   // S_i and P~_i together larger than about 3/4 of L2 (126 MB): stream them
         size_t bytes = 0;
@@ -1749,11 +1751,11 @@ void alloc_solver_buffers(bddc_handle *h) {
     h->ops.gptr = h->ar.upload("gptr", h->gptr, h->stream);
     h->ops.gent = h->ar.upload("gent", h->gent, h->stream);
     h->ops.gsub = h->ar.upload("gsub", h->gsub, h->stream);
-    h->ops.sumG = h->sumG;
+    h->ops.rowblk = h->ar.upload("rowblk", rb, h->stream);
+    h->ops.nrowblk = (int)rb.size();
     const int nG = std::max(h->nG, 1);
     h->pb.x = h->ar.get_t<double>("x", nG);
     h->pb.r = h->ar.get_t<double>("r", nG);
-    h->pb.r2 = h->ar.get_t<double>("r2", nG);
     h->pb.z = h->ar.get_t<double>("z", nG);
     h->pb.p0 = h->ar.get_t<double>("p0", nG);
     h->pb.p1 = h->ar.get_t<double>("p1", nG);

@@ -37,92 +37,84 @@ struct PcgParams {
     uint64_t timeout_ns;
 };
 
-// y_i = Mats_i v_i for every substructure.  S_i and P~_i are symmetric and stored in
-// full, so entry c of the product is column c dotted with v_i: the columns of all
-// substructures, concatenated (sum nGi of them), are split into one contiguous range per
-// block, and each warp streams whole columns (16-byte loads, eight per lane in flight:
-// 64 KB per SM) against v_i staged in shared memory once per substructure of the range.
-// No block-wide synchronisation is needed between columns.  When the matrices do not fit
-// in L2 they are read with the evict-first policy, which keeps the vectors and the coarse
-// data resident.  val(g) gives v at interface dof g.
-__device__ __forceinline__ double2 ld_mat2(const double2 *p, bool stream) {
-    return stream ? __ldcs(p) : __ldg(p);
+// y_i = Mats_i * v_i for every (substructure, 64-row block); v_i = R_i v is
+// staged in shared memory once per substructure, then the warps split the
+// columns and every lane reads two consecutive rows of a column with one
+// 16-byte load (512 coalesced bytes per warp and column).  Eight columns per
+// warp are loaded before they are used, so 64 KB per SM are in flight: the
+// matrices are streamed from HBM once per application.  When they do not fit
+// in L2 they are read with the evict-first policy, which keeps the vectors and
+// the coarse data resident.
+// If pold != nullptr, v[g] = z[g] + beta * pold[g] (the new search direction).
+__device__ __forceinline__ double2 ld_mat2(const double *p, bool stream) {
+    return stream ? __ldcs(reinterpret_cast<const double2 *>(p)) : __ldg(reinterpret_cast<const double2 *>(p));
 }
 
-// The block's column range [c0, c1) of the concatenated local vectors and the substructure
-// holding c0 (the last s with off[s] <= c0: empty substructures share the next one's offset).
-struct ColRange {
-    int64_t c0, c1;
-    int s0;
-};
-
-__device__ ColRange col_range(const IfaceOps &o) {
-    ColRange cr;
-    cr.c0 = o.sumG * blockIdx.x / gridDim.x;
-    cr.c1 = o.sumG * (blockIdx.x + 1) / gridDim.x;
-    int lo = 0, hi = o.nsub - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
-        if (o.off[mid] <= cr.c0) lo = mid;
-        else hi = mid - 1;
-    }
-    cr.s0 = lo;
-    return cr;
-}
-
-// Returns this thread's share of sum_i v_i . y_i (the entries it stored), which for
+// Returns this thread's share of sum_i v_i . y_i (the rows it stored), which for
 // Mats = S gives p^T S p without assembling S p.
-template <class V>
-__device__ double local_gemv(const PcgParams &P, const ColRange &cr, double *const *Mats, V val, double *yout,
-                             double *vs) {
+__device__ double local_gemv(const PcgParams &P, double *const *Mats, const double *vin, const double *pold,
+                             double beta, double *yout, double *red, double *vs) {
     double vy = 0.0;
     const IfaceOps &o = P.o;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const bool stream = o.stream_mats != 0;
-    for (int s = cr.s0; s < o.nsub; ++s) {
-        const int64_t base = o.off[s];
-        if (base >= cr.c1) break;
+    int cur = -1;
+    for (int it = blockIdx.x; it < o.nrowblk; it += gridDim.x) {
+        int2 w = o.rowblk[it];
+        const int s = w.x, r0 = w.y;
         const int n = o.nGi[s], ld = o.ldS[s];
-        const int64_t lo = cr.c0 > base ? cr.c0 : base, hi = cr.c1 < base + n ? cr.c1 : base + n;
-        if (lo >= hi) continue;
-        const int *RG = o.RG + base;
-        __syncthreads();   // the previous substructure's v is no longer read
-        for (int c = threadIdx.x; c < n; c += blockDim.x) vs[c] = val(RG[c]);
-        __syncthreads();
-        const double2 *vs2 = reinterpret_cast<const double2 *>(vs);
+        if (s != cur) {
+            const int *RG = o.RG + o.off[s];
+            __syncthreads();
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                int g = RG[c];
+                vs[c] = pold ? ldx(vin + g) + beta * ldx(pold + g) : ldx(vin + g);
+            }
+            __syncthreads();
+            cur = s;
+        }
         const double *A = Mats[s];
-        const int np = n >> 1;   // whole row pairs; ld is even, so every column is 16-byte aligned
-        for (int c = (int)(lo - base) + wid; c < (int)(hi - base); c += PCG_WARPS) {
-            const double2 *col = reinterpret_cast<const double2 *>(A + (size_t)c * ld);
-            double a0 = 0.0, a1 = 0.0;
-            for (int pi = lane; pi < np; pi += 8 * 32) {
+        const int r = r0 + 2 * lane;   // ld is even, so A + c * ld + r is 16-byte aligned
+        double a0 = 0.0, a1 = 0.0;
+        if (r < n) {   // rows r + 1 < ld stay inside the allocation; a row r + 1 >= n is ignored
+            int c = wid;
+            for (; c + 7 * PCG_WARPS < n; c += 8 * PCG_WARPS) {
                 double2 v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    v[u] = pi + 32 * u < np ? ld_mat2(col + pi + 32 * u, stream) : make_double2(0.0, 0.0);
+                for (int u = 0; u < 8; ++u) v[u] = ld_mat2(A + (size_t)(c + u * PCG_WARPS) * ld + r, stream);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    if (pi + 32 * u < np) {
-                        const double2 x = vs2[pi + 32 * u];
-                        a0 = fma(v[u].x, x.x, a0);
-                        a1 = fma(v[u].y, x.y, a1);
-                    }
+                    const double x = vs[c + u * PCG_WARPS];
+                    a0 += v[u].x * x;
+                    a1 += v[u].y * x;
                 }
             }
-            if ((n & 1) && lane == 0) a0 = fma(A[(size_t)c * ld + n - 1], vs[n - 1], a0);
-            const double y = warp_sum(a0 + a1);
-            if (lane == 0) {
-                yout[base + c] = y;
-                vy = fma(vs[c], y, vy);
+            for (; c < n; c += PCG_WARPS) {
+                const double2 v = ld_mat2(A + (size_t)c * ld + r, stream);
+                const double x = vs[c];
+                a0 += v.x * x;
+                a1 += v.y * x;
             }
         }
+        red[wid * 64 + 2 * lane] = a0;
+        red[wid * 64 + 2 * lane + 1] = a1;
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            double sum = 0.0;
+#pragma unroll
+            for (int k = 0; k < PCG_WARPS; ++k) sum += red[k * 64 + threadIdx.x];
+            if (r0 + threadIdx.x < n) {
+                yout[o.off[s] + r0 + threadIdx.x] = sum;
+                vy += vs[r0 + threadIdx.x] * sum;
+            }
+        }
+        __syncthreads();
     }
     return vy;
 }
 
-// c_i[m] = Phi~_i[:, m] . r_i, r at interface dof g given by val(g)
-template <class V>
-__device__ void coarse_dots(const PcgParams &P, V val) {
+// c_i[m] = Phi~_i[:, m] . r_i
+__device__ void coarse_dots(const PcgParams &P, const double *rin) {
     const IfaceOps &o = P.o;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int it = blockIdx.x; it < o.ncdot; it += gridDim.x) {
@@ -141,27 +133,17 @@ __device__ void coarse_dots(const PcgParams &P, V val) {
                 double rv[4], cv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    rv[u] = val(g[u]);
+                    rv[u] = ldx(rin + g[u]);
                     cv[u] = col[k + 32 * u];
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) acc += cv[u] * rv[u];
             }
-            for (; k < n; k += 32) acc += col[k] * val(RG[k]);
+            for (; k < n; k += 32) acc += col[k] * ldx(rin + RG[k]);
             acc = warp_sum(acc);
             if (lane == 0) P.b.cl[o.offc[s] + m] = acc;
         }
     }
-}
-
-// r_k[g] = r_{k-1}[g] - alpha q[g], q = S p assembled from the local products: the owner of g
-// stores it, and the blocks that need it before then form it the same way (same operands,
-// same order, explicit fma), so every block sees the same value.
-__device__ __forceinline__ double r_next(const IfaceOps &o, const double *yl, const double *rprev, double alpha,
-                                         int g) {
-    double q = 0.0;
-    for (int e = o.gptr[g]; e < o.gptr[g + 1]; ++e) q += ldx(yl + o.gent[e]);
-    return fma(-alpha, q, ldx(rprev + g));
 }
 
 // u_c = S_C^{-1} r_c; r_c is assembled redundantly in every block (shared memory)
@@ -228,19 +210,18 @@ __device__ double reduce_partials(const double *partial, int nb) {
 
 __global__ void __launch_bounds__(PCG_THREADS, 1) pcg_kernel(PcgParams P) {
     extern __shared__ double smem[];
-    double *rc = smem;    // nC (coarse phase) ...
-    double *vs = smem;    // ... or max nGi (local products)
+    double *red = smem;                    // PCG_WARPS * 64
+    double *rc = smem + PCG_WARPS * 64;    // nC (coarse phase) ...
+    double *vs = rc;                       // ... or max nGi (local products)
     __shared__ double scratch[32];
     const IfaceOps &o = P.o;
     PcgBuffers &b = P.b;
     const unsigned nb = gridDim.x;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
-    const ColRange cr = col_range(o);
 
     if (P.mode == PCG_APPLY_M) {
-        auto rv = [&](int g) { return ldx(b.r + g); };
-        local_gemv(P, cr, o.P, rv, b.zl, vs);
-        coarse_dots(P, rv);
+        local_gemv(P, o.P, b.r, nullptr, 0.0, b.zl, red, vs);
+        coarse_dots(P, b.r);
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
         coarse_solve(P, rc);
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
@@ -248,7 +229,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) pcg_kernel(PcgParams P) {
         return;
     }
     if (P.mode == PCG_APPLY_S) {
-        local_gemv(P, cr, o.S, [&](int g) { return ldx(b.z + g); }, b.yl, vs);
+        local_gemv(P, o.S, b.z, nullptr, 0.0, b.yl, red, vs);
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
         for (int x = gtid; x < o.nG; x += gstride) {
             double v = 0.0;
@@ -258,11 +239,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) pcg_kernel(PcgParams P) {
         return;
     }
 
-    // ---- PCG: four grid barriers per iteration ----
-    // (1) local products and coarse dots of M r_k done; (2) u_c done; (3) z and r . z done;
-    // (4) S p and p . S p done.  r_k = r_{k-1} - alpha q is not stored before (1): the owner
-    // of each dof stores it while every block forms the values it stages (r_next), and
-    // ||r_k|| is reduced at (1), after which the iteration stops or goes on with M r_k.
+    // ---- PCG ----
     double part = 0.0;
     for (int x = gtid; x < o.nG; x += gstride) {
         b.x[x] = 0.0;
@@ -273,60 +250,29 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) pcg_kernel(PcgParams P) {
     if (threadIdx.x == 0) b.partial[blockIdx.x] = part;
     if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
     const double r0 = sqrt(reduce_partials(b.partial, nb));
-    double rz_old = 1.0, rr = r0 * r0, alpha = 0.0;
+    double rz_old = 1.0, rr = r0 * r0;
     int k = 0;
     bool conv = (r0 == 0.0);
-    double *rcur = b.r, *rnew = b.r2;   // r_{k-1} (complete), r_k (being stored)
     double *pold = b.p0, *pnew = b.p1;
-    bool pend = false;                  // r_k, x_k not yet stored
-    while (!conv) {
-        if (pend) {   // store r_k and x_k = x_{k-1} + alpha p_k (p_k is pold here); ||r_k||^2
-            part = 0.0;
-            for (int x = gtid; x < o.nG; x += gstride) {
-                const double rv = r_next(o, b.yl, rcur, alpha, x);
-                rnew[x] = rv;
-                b.x[x] = fma(alpha, pold[x], b.x[x]);
-                part += rv * rv;
-            }
-            part = block_sum(part, scratch);
-            if (threadIdx.x == 0) b.partial[blockIdx.x] = part;
-        }
-        const bool more = k < P.maxit;
-        if (more) {   // z = M r_k, first half: local products and coarse dots
-            if (pend) {
-                auto rv = [&](int g) { return r_next(o, b.yl, rcur, alpha, g); };
-                local_gemv(P, cr, o.P, rv, b.zl, vs);
-                coarse_dots(P, rv);
-            } else {
-                auto rv = [&](int g) { return ldx(rcur + g); };
-                local_gemv(P, cr, o.P, rv, b.zl, vs);
-                coarse_dots(P, rv);
-            }
-        }
-        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
-        if (pend) {
-            rr = reduce_partials(b.partial, nb);
-            conv = sqrt(rr) <= P.tol * r0;
-            double *t = rcur;
-            rcur = rnew;
-            rnew = t;
-            pend = false;
-            if (conv) break;
-        }
-        if (!more) break;
+    while (!conv && k < P.maxit) {
         ++k;
+        // z = M r
+        local_gemv(P, o.P, b.r, nullptr, 0.0, b.zl, red, vs);
+        coarse_dots(P, b.r);
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
         coarse_solve(P, rc);
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
-        part = assemble_z(P, rcur, b.z);   // r_k[x] was stored by this very thread
+        part = assemble_z(P, b.r, b.z);
         part = block_sum(part, scratch);
         if (threadIdx.x == 0) b.partial[blockIdx.x] = part;
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
-        // beta, p = z + beta p, y_i = S_i p_i; p . S p = sum_i p_i . S_i p_i comes out of the
-        // local products (second partials buffer: other blocks may still be reading r . z)
+        // beta, p = z + beta p, y_i = S_i p_i
         const double rz = reduce_partials(b.partial, nb);
         const double beta = (k == 1) ? 0.0 : rz / rz_old;
-        for (int x = gtid; x < o.nG; x += gstride) pnew[x] = fma(beta, pold[x], b.z[x]);
-        part = local_gemv(P, cr, o.S, [&](int g) { return fma(beta, ldx(pold + g), ldx(b.z + g)); }, b.yl, vs);
+        // p . S p = sum_i p_i . S_i p_i comes out of the local products (second partials
+        // buffer: other blocks may still be reading r . z from the first)
+        for (int x = gtid; x < o.nG; x += gstride) pnew[x] = b.z[x] + beta * pold[x];
+        part = local_gemv(P, o.S, b.z, pold, beta, b.yl, red, vs);
         part = block_sum(part, scratch);
         if (threadIdx.x == 0) b.partial[PCG_PARTIALS + blockIdx.x] = part;
         if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
@@ -335,16 +281,30 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) pcg_kernel(PcgParams P) {
             --k;
             break;
         }
-        alpha = rz / pq;
+        const double alpha = rz / pq;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             b.alpha[k - 1] = alpha;
             if (k > 1) b.beta[k - 2] = beta;
         }
+        // q = sum R_i^T y_i assembled on the fly; x += alpha p, r -= alpha q
+        part = 0.0;
+        for (int x = gtid; x < o.nG; x += gstride) {
+            double q = 0.0;
+            for (int e = o.gptr[x]; e < o.gptr[x + 1]; ++e) q += ldx(b.yl + o.gent[e]);
+            b.x[x] += alpha * pnew[x];
+            double rv = b.r[x] - alpha * q;
+            b.r[x] = rv;
+            part += rv * rv;
+        }
+        part = block_sum(part, scratch);
+        if (threadIdx.x == 0) b.partial[blockIdx.x] = part;
+        if (!grid_barrier(P.st, nb, P.timeout_ns)) return;
+        rr = reduce_partials(b.partial, nb);
+        conv = sqrt(rr) <= P.tol * r0;
         rz_old = rz;
         double *t = pold;
         pold = pnew;
         pnew = t;
-        pend = true;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *b.iters = k;
@@ -363,7 +323,7 @@ cudaError_t launch_pcg(const IfaceOps &ops, const PcgBuffers &buf, int mode, dou
     P.maxit = maxit;
     P.st = st;
     P.timeout_ns = (uint64_t)(timeout_s * 1e9);
-    size_t smem = sizeof(double) * ((size_t)std::max(std::max(ops.nC, ops.maxGi), 1));
+    size_t smem = sizeof(double) * (PCG_WARPS * 64 + (size_t)std::max(std::max(ops.nC, ops.maxGi), 1));
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

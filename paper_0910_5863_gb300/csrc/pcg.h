@@ -39,14 +39,15 @@ struct IfaceOps {
     const ZEntry *zent;      // the entries again, as assembly records
     const int *cptr;         // (nC+1)
     const int64_t *cent;     // packed local coarse index of each entry
-    int64_t sumG;            // sum nGi: the local products split these columns evenly over the blocks
+    const int2 *rowblk;      // (sub, first row) GEMV work items, 64 rows each
+    int nrowblk;
     int stream_mats;         // S_i and P~_i exceed L2: read them with the evict-first policy
     const int2 *cdot;        // (sub, first coarse column) items, 16 columns each
     int ncdot;
 };
 
 struct PcgBuffers {
-    double *x, *r, *r2, *z, *p0, *p1, *q;  // nG (r2: the second residual buffer of PCG)
+    double *x, *r, *z, *p0, *p1, *q;  // nG
     double *zl, *yl;                  // sum nGi
     double *cl;                       // sum nci
     double *uc;                       // nC
