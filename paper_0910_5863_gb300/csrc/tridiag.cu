@@ -3,13 +3,23 @@
 //
 // One CTA reduces a matrix of order n in n - 2 dependent steps, each a matrix-vector
 // product and a symmetric rank-2 update of the trailing block: order n^3 memory
-// traffic through a single SM.  Here the G CTAs of a face share every step: CTA g
-// forms the rows [i0, i1) of P = beta B x and, after a barrier of the face's CTAs,
-// updates the columns [i0, i1) of B -= x W^T + W x^T (both triangles are kept, as the
-// one-CTA reduction keeps them).  Each step's scalars (|x|, alpha, beta, p.x) are
-// recomputed by every CTA in the same order, so all CTAs take the same decisions.
-// The grid is one cooperative launch (all CTAs co-resident); the barrier of a face
-// spins with a bound and records BDDC_DEV_ERR_TIMEOUT instead of hanging.
+// traffic through a single SM.  Here the G CTAs of a face share every step, and each
+// step costs one pass over the trailing block and one barrier of the face's CTAs:
+//   * CTA g owns the columns c = g, g + G, ... for the whole reduction;
+//   * step k starts with P = beta B x complete (B the trailing block after step k - 1,
+//     x the reflector of column k).  Every CTA reads all of P and forms W = P - K x,
+//     then column k + 1 after this step's update, x' (the next reflector's column),
+//     and its Householder scalars: the same operands in the same order in every CTA,
+//     so all CTAs take the same decisions.  Column k + 1 itself is never written in
+//     step k, so reading it needs no extra barrier;
+//   * each CTA then updates its columns c >= k + 2, B -= x W^T + W x^T, and in the same
+//     pass dots them with x' (the next step's P entries), and all CTAs meet once.
+// Each step's reflector is written into its column by all CTAs (a share each) at the
+// start of the next step, after every CTA has read that column.  Both triangles of the
+// trailing block are kept below row k + 1 (the row of the current pivot is not updated:
+// nothing reads it again).  The grid is one cooperative launch (all CTAs co-resident);
+// the barrier of a face spins with a bound and records BDDC_DEV_ERR_TIMEOUT instead of
+// hanging.
 //
 // Output, as the face kernel's step 1 leaves it: the reflectors below the
 // subdiagonal of C (as doubles), and in the face's work array dd (diagonal),
@@ -33,6 +43,15 @@ __device__ __forceinline__ void tri_fma(double &acc, double a, double b) { acc =
 __device__ __forceinline__ void tri_fma(ff &acc, ff a, ff b) { ff_fma_acc(acc, a, b); }
 __device__ __forceinline__ double tri_norm(double a) { return a; }
 __device__ __forceinline__ ff tri_norm(ff a) { return ff_norm(a); }
+// c - (a b + d e): two accumulated products, one renormalisation (double-float)
+__device__ __forceinline__ double tri_sub2(double c, double a, double b, double d, double e) {
+    return fma(-d, e, fma(-a, b, c));
+}
+__device__ __forceinline__ ff tri_sub2(ff c, ff a, ff b, ff d, ff e) {
+    ff_fma_acc(c, -a, b);
+    ff_fma_acc(c, -d, e);
+    return ff_norm(c);
+}
 
 // Loads of data that other CTAs of the face write during the launch bypass L1 (.cg):
 // the SMs' L1 caches are not coherent with each other, and a column changes owner as
@@ -108,6 +127,31 @@ __device__ __forceinline__ bool face_barrier(unsigned *bar, unsigned G, DevStatu
     return ok != 0;
 }
 
+// Householder scalars of the vector v (length len >= 2, shared memory, every thread):
+// alpha (the new off-diagonal), v0 (the reflector's leading entry) and beta = 2 / |v|^2;
+// beta = 0 (and v0 = alpha = x0) when v is already reduced.
+struct TriHh {
+    double alpha, v0, beta;
+};
+template <typename T>
+__device__ TriHh tri_householder(const T *v, int len, double *scratch) {
+    T acc = tri_from<T>(0.0);
+    int cnt = 0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const T x = v[i];
+        tri_fma(acc, x, x);
+        if ((++cnt & 15) == 0) acc = tri_norm(acc);
+    }
+    const double s = tri_block_sum(tri_to(tri_norm(acc)), scratch);
+    const double x0 = tri_to(v[0]);
+    const double rest = s - x0 * x0;
+    if (rest <= 1e-300 * (s + 1e-300)) return TriHh{x0, x0, 0.0};
+    const double nrm = sqrt(s);
+    const double alpha = x0 > 0 ? -nrm : nrm;
+    const double v0 = x0 - alpha;
+    return TriHh{alpha, v0, 2.0 / (rest + v0 * v0)};
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const TridiagDesc *descs, const int2 *items,
                                                                     DevStatus *st, uint64_t timeout_ns) {
@@ -120,103 +164,114 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const Tridia
     const size_t lda = D.lda;
     double *Ad = D.A;
     T *F = reinterpret_cast<T *>(Ad);   // ff: a double slot holds one double-float
-    T *xs = reinterpret_cast<T *>(tri_sm), *Ws = xs + n;
+    T *xs = reinterpret_cast<T *>(tri_sm), *Ws = xs + n, *xn = Ws + n;
     double *dd = D.work, *ee = D.work + n, *bet = D.work + 2 * n;
-    T *P = reinterpret_cast<T *>(D.work + 3 * n);   // shared between the face's CTAs
+    T *Pbuf = reinterpret_cast<T *>(D.work + 3 * n);   // P of the even / odd steps, n each, shared by the face
     unsigned *bar = D.bar;
-    auto slice = [&](int len, int &a, int &b) {
-        a = (int)((long long)len * g / G);
-        b = (int)((long long)len * (g + 1) / G);
-    };
-    int c0, c1;
+    auto first_own = [&](int c0) { return c0 + ((g - c0) % G + G) % G; };   // first c >= c0 with c = g mod G
     if constexpr (std::is_same<T, ff>::value) {   // to double-float in place, this CTA's columns
-        slice(n, c0, c1);
-        for (int c = c0; c < c1; ++c)
+        for (int c = g; c < n; c += G)
             for (int i = tid; i < n; i += nt) F[(size_t)c * lda + i] = ff_from_double(Ad[(size_t)c * lda + i]);
     }
     if (!face_barrier(bar, G, st, timeout_ns)) return;
-    for (int k = 0; k + 2 < n; ++k) {
-        const int m = n - k - 1;
-        const T *x = F + (size_t)k * lda + k + 1;   // column k below the diagonal
-        T acc = tri_from<T>(0.0);
-        int cnt = 0;
-        for (int i = tid; i < m; i += nt) {
-            const T v = tri_ld(x + i);
-            xs[i] = v;
-            tri_fma(acc, v, v);
-            if ((++cnt & 15) == 0) acc = tri_norm(acc);
-        }
-        const double s = tri_block_sum(tri_to(tri_norm(acc)), scratch);
-        const double x0 = tri_to(xs[0]);
-        const double rest = s - x0 * x0;
-        if (rest <= 1e-300 * (s + 1e-300)) {   // already reduced: every CTA takes this branch
-            if (g == 0 && tid == 0) {
-                bet[k] = 0.0;
-                ee[k] = x0;
-            }
-            continue;
-        }
-        const double nrm = sqrt(s);
-        const double alpha = x0 > 0 ? -nrm : nrm;
-        const double v0 = x0 - alpha;
-        const double beta = 2.0 / (rest + v0 * v0);
-        if (tid == 0) xs[0] = tri_from<T>(v0);
-        __syncthreads();
-        const T fbeta = tri_from<T>(beta);
-        T *B = F + (size_t)(k + 1) * lda + k + 1;
-        int i0, i1;
-        slice(m, i0, i1);
-        // entries [i0, i1) of P = beta B x; B is kept symmetric, so P_i is column i of B
-        // against x: one warp per column, contiguous loads
-        for (int i = i0 + wid; i < i1; i += nw) {
-            const T *col = B + (size_t)i * lda;
+    // step 0's reflector (column 0 below the diagonal) and P_0 over the original columns 1..
+    for (int i = tid; i < n - 1; i += nt) xs[i] = tri_ld(F + 1 + i);
+    __syncthreads();
+    const TriHh h0 = tri_householder(xs, n - 1, scratch);
+    if (tid == 0) xs[0] = tri_from<T>(h0.v0);
+    __syncthreads();
+    if (g == 0 && tid == 0) {
+        dd[0] = tri_to(tri_ld(F));
+        F[1] = tri_from<T>(h0.v0);
+    }
+    double beta = h0.beta, alpha = h0.alpha;
+    {
+        const T fb = tri_from<T>(beta);
+        for (int c = first_own(1) + wid * G; c < n; c += nw * G) {
+            const T *col = F + (size_t)c * lda + 1;
             T a = tri_from<T>(0.0);
-            int c = 0;
-            for (int j = lane; j < m; j += 32) {
-                tri_fma(a, tri_ld(col + j), xs[j]);
-                if ((++c & 15) == 0) a = tri_norm(a);
+            int cnt = 0;
+            for (int i = lane; i < n - 1; i += 32) {
+                tri_fma(a, col[i], xs[i]);
+                if ((++cnt & 15) == 0) a = tri_norm(a);
             }
             a = tri_warp_sum(tri_norm(a));
-            if (lane == 0) P[i] = fbeta * a;
+            if (lane == 0) Pbuf[c - 1] = fb * a;
         }
-        if (!face_barrier(bar, G, st, timeout_ns)) return;
+    }
+    if (!face_barrier(bar, G, st, timeout_ns)) return;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;   // trailing rows / columns k + 1 .. n - 1, local index 0 .. m - 1
+        const T *Pk = Pbuf + (size_t)(k & 1) * n;
+        T *Pn = Pbuf + (size_t)((k + 1) & 1) * n;
+        if (k > 0)   // step k's reflector into column k (every CTA has read that column in step k - 1)
+            for (int i = g * nt + tid; i < m; i += G * nt) F[(size_t)k * lda + k + 1 + i] = xs[i];
+        // (a) W = P - K x, K = beta (P . x) / 2
         T pa = tri_from<T>(0.0);
-        cnt = 0;
+        int cnt = 0;
         for (int i = tid; i < m; i += nt) {
-            tri_fma(pa, tri_ld(P + i), xs[i]);
+            tri_fma(pa, tri_ld(Pk + i), xs[i]);
             if ((++cnt & 15) == 0) pa = tri_norm(pa);
         }
         const double pv = tri_block_sum(tri_to(tri_norm(pa)), scratch);
         const T K = tri_from<T>(0.5 * beta * pv);
-        for (int i = tid; i < m; i += nt) Ws[i] = tri_ld(P + i) - K * xs[i];
+        for (int i = tid; i < m; i += nt) Ws[i] = tri_ld(Pk + i) - K * xs[i];
         __syncthreads();
-        // columns [i0, i1) of B -= x W^T + W x^T, one warp per column
-        for (int j = i0 + wid; j < i1; j += nw) {
-            const T wj = Ws[j], xj = xs[j];
-            T *col = B + (size_t)j * lda;
-            for (int i = lane; i < m; i += 32) col[i] = tri_ld(col + i) - (xs[i] * wj + Ws[i] * xj);
+        // (b) column k + 1 after this step: its diagonal and, below, the next reflector's column
+        const T *cn = F + (size_t)(k + 1) * lda + (k + 1);
+        for (int t = tid; t < m - 1; t += nt) xn[t] = tri_sub2(tri_ld(cn + 1 + t), xs[1 + t], Ws[0], Ws[1 + t], xs[0]);
+        if (g == 0 && tid == 0) dd[k + 1] = tri_to(tri_sub2(tri_ld(cn), xs[0], Ws[0], Ws[0], xs[0]));
+        __syncthreads();
+        const bool more = k + 3 < n;   // a step k + 1 follows
+        TriHh hn{0.0, 0.0, 0.0};
+        if (more) {
+            hn = tri_householder(xn, m - 1, scratch);
+            if (tid == 0) xn[0] = tri_from<T>(hn.v0);
+            __syncthreads();
         }
         if (g == 0 && tid == 0) {
-            F[(size_t)k * lda + k + 1] = tri_from<T>(v0);   // the reflector's leading entry
             bet[k] = beta;
             ee[k] = alpha;
+            if (!more) {   // k + 1 = n - 2: the last off-diagonal, no reflection
+                ee[k + 1] = tri_to(xn[0]);
+                bet[k + 1] = 0.0;
+            }
         }
+        // (c) own columns c >= k + 2: B -= x W^T + W x^T below row k + 1, and the next P entries
+        const T fbn = tri_from<T>(more ? hn.beta : 0.0);
+        for (int c = first_own(k + 2) + wid * G; c < n; c += nw * G) {
+            const int j = c - (k + 1);
+            T *col = F + (size_t)c * lda + (k + 1);
+            const T wj = Ws[j], xj = xs[j];
+            T a = tri_from<T>(0.0);
+            cnt = 0;
+            for (int i = 1 + lane; i < m; i += 32) {
+                const T v = tri_sub2(col[i], xs[i], wj, Ws[i], xj);
+                col[i] = v;
+                if (more) {
+                    tri_fma(a, v, xn[i - 1]);
+                    if ((++cnt & 15) == 0) a = tri_norm(a);
+                }
+            }
+            if (more) {
+                a = tri_warp_sum(tri_norm(a));
+                if (lane == 0) Pn[c - (k + 2)] = fbn * a;
+            }
+        }
+        beta = more ? hn.beta : 0.0;
+        alpha = hn.alpha;
+        __syncthreads();   // xs, Ws and xn read by every warp
+        for (int t = tid; t < m - 1; t += nt) xs[t] = xn[t];
         if (!face_barrier(bar, G, st, timeout_ns)) return;
     }
-    // diagonal, last off-diagonal, and (double-float) the reflectors back to doubles
-    slice(n, c0, c1);
-    for (int i = c0 + tid; i < c1; i += nt) dd[i] = tri_to(tri_ld(F + (size_t)i * lda + i));
+    // the last diagonal entry (updated by its owner in the last step)
     if (g == 0 && tid == 0) {
-        if (n >= 2) {
-            ee[n - 2] = tri_to(tri_ld(F + (size_t)(n - 2) * lda + n - 1));
-            bet[n - 2] = 0.0;
-        }
+        dd[n - 1] = tri_to(tri_ld(F + (size_t)(n - 1) * lda + n - 1));
         bet[n - 1] = 0.0;
         ee[n - 1] = 0.0;
     }
-    if constexpr (std::is_same<T, ff>::value) {
-        if (!face_barrier(bar, G, st, timeout_ns)) return;   // every diagonal read before rewriting
-        for (int c = c0; c < c1; ++c)
+    if constexpr (std::is_same<T, ff>::value) {   // the reflectors back to doubles, this CTA's columns
+        for (int c = g; c < n; c += G)
             for (int i = c + 1 + tid; i < n; i += nt)
                 Ad[(size_t)c * lda + i] = ff_to_double(tri_ld(F + (size_t)c * lda + i));
     }
@@ -226,7 +281,7 @@ int tridiag_multi_capacity(int nmax) {
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = 2 * sizeof(double) * (size_t)nmax;
+    const size_t smem = 3 * sizeof(double) * (size_t)nmax;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_multi_kernel<ff>, TRI_THREADS, smem);
     int per_sm64 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm64, tridiag_multi_kernel<double>, TRI_THREADS, smem);
@@ -236,7 +291,7 @@ int tridiag_multi_capacity(int nmax) {
 cudaError_t launch_tridiag_multi(const TridiagDesc *descs, const int2 *items, int nitems, int nmax, int use_ff,
                                  DevStatus *st, double timeout_s, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    const size_t smem = 2 * sizeof(double) * (size_t)nmax;
+    const size_t smem = 3 * sizeof(double) * (size_t)nmax;
     uint64_t tns = (uint64_t)(timeout_s * 1e9);
     void *args[] = {&descs, &items, &st, &tns};
     if (smem > 48 * 1024) {
