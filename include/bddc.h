@@ -111,10 +111,11 @@ typedef struct {
     int eig_large_n;
     double eig_tol;
     int eig_maxit;
-    /* Mixed modes: the trailing updates of the double-float factorizations (pair
-     * condensations, local saddle and coarse inverses).  0 (default): on the tensor cores, by exact bf16
-     * slicing of the factored block columns (7 digit planes of 7 bits, FP32 accumulation
-     * of integer digit products, double-float combination; ~2^-49 per product);
+    /* Mixed modes: the double-float factorizations (pair condensations, local saddle and
+     * coarse inverses).  0 (default): in block columns of 128 whose triangular solves
+     * (against the inverse of the diagonal block's factor) and trailing updates run on the
+     * tensor cores, by exact bf16 slicing (7 digit planes of 7 bits, FP32 accumulation of
+     * integer digit products, double-float combination; ~2^-49 per product);
      * 1: double-float on the FP32 pipe. */
     int mixed_updates;
 } bddc_options;

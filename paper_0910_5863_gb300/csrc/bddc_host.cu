@@ -380,11 +380,14 @@ void run_pchol(bddc_handle *h, const std::vector<PcholDesc<T>> &descs_in, const 
     }
 }
 
-// Double-float partial Cholesky in block columns of kOzK = 128: each block column is
-// factored by the SIMT kernels with their updates confined to its columns, its rows below
-// are split into bf16 digit planes, and the trailing block is updated on the tensor cores
-// (ozaki.h).  Rows of an identity block that are still zero in the block column
-// (PcholDesc::id0) take no part in the update: their tiles are skipped.
+// Double-float partial Cholesky in block columns of kOzK = 128, every block column in
+// five launches: (1) the w x w diagonal block factored in shared memory, with the inverse
+// of its factor (one CTA per matrix); (2) the rows below and that inverse split into bf16
+// digit planes; (3) those rows times the inverse's transpose on the tensor cores, which is
+// the block column of the factor, L21 = A21 L11^-T; (4) L21 split; (5) the trailing block
+// updated on the tensor cores, C -= L21 L21^T (ozaki.h).  Rows of an identity block that
+// are still zero in the block column (PcholDesc::id0) take no part in (3) and (5): their
+// tiles are skipped (zero rows of A21 give zero rows of L21).
 void run_pchol_oz(bddc_handle *h, const std::vector<PcholDesc<ff>> &descs, const std::string &tag) {
     constexpr int W = kOzK;
     int nJ = 0;
@@ -392,36 +395,56 @@ void run_pchol_oz(bddc_handle *h, const std::vector<PcholDesc<ff>> &descs, const
     for (int jb = 0; jb < nJ; ++jb) {
         const int J = jb * W;
         const std::string t = tag + "_oz" + std::to_string(jb);
-        std::vector<PcholDesc<ff>> pv;
-        std::vector<OzSplitDesc> sd;
-        std::vector<OzSyrkDesc> yd;
-        std::vector<int2> sitems;
-        std::vector<int4> yitems;
-        size_t nsl = 0, nex = 0;
+        std::vector<OzDiagDesc> dg;
+        std::vector<OzSplitDesc> sd1, sd2;
+        std::vector<OzSyrkDesc> gd, yd;
+        std::vector<int2> si1, si2;
+        std::vector<int4> gi, yi;
+        size_t nsl = 0, nex = 0, ndg = 0;
         for (const auto &d : descs) {
             if (J >= d.nstop) continue;
             const int w = std::min(W, d.nstop - J), rows = d.n - J - w;
-            pv.push_back(PcholDesc<ff>{d.A + (size_t)J * d.ld + J, d.n - J, d.ld, w, d.tag, nullptr, w, 0, 0, d.fail});
+            ++ndg;
             if (rows > 0) {
                 nsl += (size_t)oz_rows_pad(rows) * kOzSlices * W;
                 nex += rows;
             }
         }
+        ff *linv = h->ar.get_t<ff>("oz_linv_" + tag, std::max<size_t>(ndg, 1) * W * W);
+        const size_t lsl = (size_t)oz_rows_pad(W) * kOzSlices * W;   // digit planes of one inverse
         uint16_t *slices = h->ar.get_t<uint16_t>("oz_sl_" + tag, std::max<size_t>(nsl, 8));
+        uint16_t *lslices = h->ar.get_t<uint16_t>("oz_lsl_" + tag, std::max<size_t>(ndg, 1) * lsl);
         int *rexp = h->ar.get_t<int>("oz_ex_" + tag, std::max<size_t>(nex, 1));
+        int *lrexp = h->ar.get_t<int>("oz_lex_" + tag, std::max<size_t>(ndg, 1) * W);
         size_t osl = 0, oex = 0;
-        double work = 0.0;
+        double work = 0.0, gwork = 0.0;
         for (const auto &d : descs) {
             if (J >= d.nstop) continue;
             const int w = std::min(W, d.nstop - J), rows = d.n - J - w;
-            if (rows <= 0) continue;
             const size_t ld = (size_t)d.ld;
-            const int k = (int)sd.size();
-            sd.push_back(OzSplitDesc{d.A + (size_t)J * ld + J + w, d.ld, rows, w, slices + osl, rexp + oex});
-            yd.push_back(OzSyrkDesc{d.A + (size_t)(J + w) * ld + J + w, d.ld, rows, slices + osl, rexp + oex});
+            const int q = (int)dg.size();
+            ff *Li = linv + (size_t)q * W * W;
+            dg.push_back(OzDiagDesc{d.A + (size_t)J * ld + J, d.ld, w, Li, d.tag, d.fail});
+            if (rows <= 0) continue;
+            const int k1 = (int)sd1.size();
+            ff *A21 = d.A + (size_t)J * ld + J + w;
+            // (2): A21 and the inverse; (4): L21 again into the same planes, after (3) consumed them
+            sd1.push_back(OzSplitDesc{A21, d.ld, rows, w, slices + osl, rexp + oex});
+            for (int g = 0; g < (oz_rows_pad(rows) + 255) / 256; ++g) si1.push_back(make_int2(k1, g));
+            const int k1b = (int)sd1.size();
+            sd1.push_back(OzSplitDesc{Li, W, w, w, lslices + (size_t)q * lsl, lrexp + (size_t)q * W});
+            si1.push_back(make_int2(k1b, 0));
+            const int k2 = (int)sd2.size();
+            sd2.push_back(OzSplitDesc{A21, d.ld, rows, w, slices + osl, rexp + oex});
+            for (int g = 0; g < (oz_rows_pad(rows) + 255) / 256; ++g) si2.push_back(make_int2(k2, g));
+            const int kg = (int)gd.size();
+            gd.push_back(OzSyrkDesc{A21, d.ld, rows, slices + osl, rexp + oex, lslices + (size_t)q * lsl,
+                                    lrexp + (size_t)q * W, w, 1});
+            const int ky = (int)yd.size();
+            yd.push_back(OzSyrkDesc{d.A + (size_t)(J + w) * ld + J + w, d.ld, rows, slices + osl, rexp + oex,
+                                    slices + osl, rexp + oex, rows, 0});
             osl += (size_t)oz_rows_pad(rows) * kOzSlices * W;
             oex += rows;
-            for (int g = 0; g < (oz_rows_pad(rows) + 255) / 256; ++g) sitems.push_back(make_int2(k, g));
             // identity rows still zero in this block column (row id0 + q with idc + q >= J + w):
             // view rows [z0, z1) of the trailing block, whose origin is row J + w
             int z0 = rows, z1 = rows;
@@ -433,29 +456,46 @@ void run_pchol_oz(bddc_handle *h, const std::vector<PcholDesc<ff>> &descs, const
             auto idle = [&](int a, int b) { return a >= z0 && std::min(b, rows) <= z1; };
             for (int a = 0; a * kOzTileM < rows; ++a) {
                 if (idle(a * kOzTileM, (a + 1) * kOzTileM)) continue;
+                const double r = std::min(kOzTileM, rows - a * kOzTileM);
+                for (int c = 0; c * kOzTileN < w; ++c) {
+                    gi.push_back(make_int4(kg, a, c, 0));
+                    gwork += 2.0 * w * r * std::min(kOzTileN, w - c * kOzTileN);
+                }
                 for (int c = 0; c * kOzTileN < rows && c * kOzTileN <= a * kOzTileM + kOzTileM - 1; ++c) {
                     if (idle(c * kOzTileN, (c + 1) * kOzTileN)) continue;
-                    yitems.push_back(make_int4(k, a, c, 0));
-                    const double r = std::min(kOzTileM, rows - a * kOzTileM);
-                    const double cc = std::min(kOzTileN, rows - c * kOzTileN);
-                    work += 2.0 * w * r * cc;
+                    yi.push_back(make_int4(ky, a, c, 0));
+                    work += 2.0 * w * r * std::min(kOzTileN, rows - c * kOzTileN);
                 }
             }
         }
-        run_pchol<ff>(h, pv, tag + "#p");
-        if (sd.empty()) continue;
-        auto *dsd = h->ar.upload("oz_sd_" + t, sd, h->stream);
-        auto *dsi = h->ar.upload("oz_si_" + t, sitems, h->stream);
-        const long toks = kt_begin(h);
-        launch_oz_split(dsd, dsi, (int)sitems.size(), h->stream);
+        auto *ddg = h->ar.upload("oz_dg_" + t, dg, h->stream);
+        const long tokd = kt_begin(h);
+        launch_oz_diag(ddg, (int)dg.size(), h->dst, h->stream);
         check_launch(h);
-        kt_end(h, toks, KT_OZ_SPLIT, 0.0);
-        auto *dyd = h->ar.upload("oz_yd_" + t, yd, h->stream);
-        auto *dyi = h->ar.upload("oz_yi_" + t, yitems, h->stream);
-        const long tok = kt_begin(h);
-        launch_oz_syrk(dyd, dyi, (int)yitems.size(), h->dst, h->opt.timeout_s, h->stream);
-        check_launch(h);
-        kt_end(h, tok, KT_OZAKI, work);
+        kt_end(h, tokd, KT_PANEL, 0.0);
+        if (sd1.empty()) continue;
+        auto split = [&](const std::vector<OzSplitDesc> &v, const std::vector<int2> &it, const std::string &nm) {
+            auto *dd = h->ar.upload("oz_sd" + nm + "_" + t, v, h->stream);
+            auto *di = h->ar.upload("oz_si" + nm + "_" + t, it, h->stream);
+            const long tok = kt_begin(h);
+            launch_oz_split(dd, di, (int)it.size(), h->stream);
+            check_launch(h);
+            kt_end(h, tok, KT_OZ_SPLIT, 0.0);
+        };
+        auto products = [&](const std::vector<OzSyrkDesc> &v, const std::vector<int4> &it, const std::string &nm,
+                            double wk) {
+            if (it.empty()) return;
+            auto *dd = h->ar.upload("oz_yd" + nm + "_" + t, v, h->stream);
+            auto *di = h->ar.upload("oz_yi" + nm + "_" + t, it, h->stream);
+            const long tok = kt_begin(h);
+            launch_oz_syrk(dd, di, (int)it.size(), h->dst, h->opt.timeout_s, h->stream);
+            check_launch(h);
+            kt_end(h, tok, KT_OZAKI, wk);
+        };
+        split(sd1, si1, "1");
+        products(gd, gi, "g", gwork);
+        split(sd2, si2, "2");
+        products(yd, yi, "y", work);
     }
 }
 

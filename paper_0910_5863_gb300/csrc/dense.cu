@@ -568,18 +568,27 @@ __global__ void ff_convert_kernel(const PcholDesc<double> *descs, const int2 *it
     const PcholDesc<double> d = descs[w.x];
     const int j = w.y;
     double *col = d.A + (size_t)j * d.ld;
-    for (int i = j + threadIdx.x; i < d.n; i += blockDim.x) {
-        if (to_ff) {
-            const ff v = ff_from_double(col[i]);
-            reinterpret_cast<ff *>(col)[i] = v;
-        } else {
-            const ff v = reinterpret_cast<const ff *>(col)[i];
-            col[i] = ff_to_double(v);
+    const int nb = blockDim.x;
+    // four independent loads per thread in flight before any store
+    for (int i0 = j + threadIdx.x; i0 < d.n; i0 += 4 * nb) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = i0 + u * nb < d.n ? col[i0 + u * nb] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * nb;
+            if (i >= d.n) break;
+            if (to_ff) {
+                reinterpret_cast<ff *>(col)[i] = ff_from_double(v[u]);
+            } else {
+                const long long b = __double_as_longlong(v[u]);   // the two words, h first in memory
+                col[i] = ff_to_double(ff(__int_as_float((int)(b & 0xffffffffLL)), __int_as_float((int)(b >> 32))));
+            }
         }
     }
 }
 void launch_ff_convert(const PcholDesc<double> *descs, const int2 *items, int nitems, int to_ff, cudaStream_t s) {
-    if (nitems > 0) ff_convert_kernel<<<nitems, 128, 0, s>>>(descs, items, nitems, to_ff);
+    if (nitems > 0) ff_convert_kernel<<<nitems, 256, 0, s>>>(descs, items, nitems, to_ff);
 }
 
 template void launch_pchol_panel<double>(const PcholDesc<double> *, const int2 *, int, int, DevStatus *, cudaStream_t);

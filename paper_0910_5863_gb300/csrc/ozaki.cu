@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int it = blockIdx.x; it < nitems && !abort_flag; it += gridDim.x) {
                 const int4 w = items[it];
                 const OzSyrkDesc d = descs[w.x];
-                const int i0 = w.y * kOzTileM, j0 = w.z * kOzTileN, rows_pad = oz_rows_pad(d.n);
+                const int i0 = w.y * kOzTileM, j0 = w.z * kOzTileN, rows_pad = oz_rows_pad(d.n),
+                          rows_pad_b = oz_rows_pad(d.nb);
                 for (int kc = 0; kc < kOzK / kOzKC; ++kc, ++g) {
                     const int s = g % OZ_STAGES;
                     if (g >= OZ_STAGES && !wait(empty[s], (uint32_t)(((g / OZ_STAGES) - 1) & 1))) break;
@@ -221,9 +222,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                                  "r"((uint32_t)OZ_STAGE_BYTES)
                                  : "memory");
                     for (int p = 0; p < kOzSlices; ++p) {
-                        const uint16_t *plane = d.slices + ((size_t)p * (kOzK / kOzKC) + kc) * rows_pad * kOzKC;
-                        bulk_g2s(a_base + p * OZ_A_BYTES, plane + (size_t)i0 * kOzKC, OZ_A_BYTES, fb);
-                        bulk_g2s(b_base + p * OZ_B_BYTES, plane + (size_t)j0 * kOzKC, OZ_B_BYTES, fb);
+                        const size_t blk = (size_t)p * (kOzK / kOzKC) + kc;
+                        bulk_g2s(a_base + p * OZ_A_BYTES, d.slices + (blk * rows_pad + i0) * kOzKC, OZ_A_BYTES, fb);
+                        bulk_g2s(b_base + p * OZ_B_BYTES, d.slices_b + (blk * rows_pad_b + j0) * kOzKC, OZ_B_BYTES,
+                                 fb);
                     }
                 }
             }
@@ -291,14 +293,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const int4 w = items[it];
             const OzSyrkDesc d = descs[w.x];
             const int i = w.y * kOzTileM + 32 * q4 + lane, j0 = w.z * kOzTileN + c16;
-            const bool row_ok = i < d.n;
-            const int ej = w.z * kOzTileN + lane < d.n ? d.rexp[w.z * kOzTileN + lane] : 0;
+            const bool row_ok = i < d.n, sub = d.mode == 0;
+            const int ej = w.z * kOzTileN + lane < d.nb ? d.rexp_b[w.z * kOzTileN + lane] : 0;
             const int ei = row_ok ? d.rexp[i] : 0;
             ff cv[16];
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) {
                 const int j = j0 + jj;
-                cv[jj] = (row_ok && j <= i) ? d.C[(size_t)j * d.ldc + i] : ff(0.f, 0.f);
+                cv[jj] = (sub && row_ok && j <= i) ? d.C[(size_t)j * d.ldc + i] : ff(0.f, 0.f);
             }
             if (!wait(accfull[a], (uint32_t)((li / OZ_SETS) & 1))) break;
             tc_fence_after();
@@ -340,9 +342,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int jj = 0; jj < 16; ++jj) {
                 const int j = j0 + jj;
                 const int sh = ei + __shfl_sync(0xffffffffu, ej, c16 + jj);
-                if (row_ok && j <= i) {   // j <= i < n
+                if (row_ok && (sub ? j <= i : j < d.nb)) {   // mode 0: j <= i < n
                     const ff upd = ff_scale2(acc[jj], sh);
-                    d.C[(size_t)j * d.ldc + i] = cv[jj] - upd;
+                    d.C[(size_t)j * d.ldc + i] = sub ? cv[jj] - upd : upd;
                 }
             }
         }
@@ -356,6 +358,83 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS)
                      : "memory");
     }
+}
+
+constexpr int OZD_THREADS = 512;
+constexpr int OZD_PITCH = kOzK + 1;   // shared-memory row pitch (ff)
+
+__global__ void __launch_bounds__(OZD_THREADS) oz_diag_kernel(const OzDiagDesc *descs, DevStatus *st) {
+    extern __shared__ ff ozd_sm[];
+    const OzDiagDesc d = descs[blockIdx.x];
+    ff *S = ozd_sm;                        // S[r * pitch + c]: L[r][c] for r >= c, Y[r][c] at S[c * pitch + r]
+    ff *yd = ozd_sm + kOzK * OZD_PITCH;     // diagonal of Y
+    __shared__ ff sinv;
+    __shared__ int bad;
+    const int w = d.w, tid = threadIdx.x, nt = blockDim.x;
+    auto at = [&](int r, int c) -> ff & { return S[r * OZD_PITCH + c]; };
+    for (int e = tid; e < w * w; e += nt) {
+        const int r = e % w, c = e / w;
+        if (r >= c) at(r, c) = d.A[(size_t)c * d.ld + r];
+        else at(r, c) = ff(0.f, 0.f);   // Y[c][r] = 0
+    }
+    for (int k = tid; k < w; k += nt) yd[k] = ff(1.f, 0.f);
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < w; ++k) {
+        if (tid == 0) {
+            ff dk = at(k, k);
+            if (!(dk > ff(0.f, 0.f))) {
+                bad = 1;
+                dk = ff(1.f, 0.f);
+            }
+            const ff inv = ff_rsqrt(dk);
+            at(k, k) = dk * inv;   // sqrt(d_k)
+            sinv = inv;
+        }
+        __syncthreads();
+        const ff inv = sinv;
+        for (int r = k + 1 + tid; r < w; r += nt) at(r, k) *= inv;           // column k of L
+        for (int c = tid; c <= k; c += nt) {                                 // row k of Y
+            if (c < k) at(c, k) *= inv;
+            else yd[k] *= inv;
+        }
+        __syncthreads();
+        // trailing block of L (lower triangle, a warp per column) and the rows below k of Y
+        // (columns <= k, a warp per column)
+        const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+        for (int c = k + 1 + wid; c < w; c += nw) {
+            const ff lck = at(c, k);
+            for (int r = c + lane; r < w; r += 32) at(r, c) -= at(r, k) * lck;
+        }
+        for (int c = wid; c <= k; c += nw) {
+            const ff yk = c < k ? at(c, k) : yd[k];
+            for (int r = k + 1 + lane; r < w; r += 32) at(c, r) -= at(r, k) * yk;
+        }
+        __syncthreads();
+    }
+    if (bad && tid == 0) {
+        if (d.fail)
+            *d.fail = 1;
+        else
+            dev_fail(st, BDDC_DEV_ERR_NOTSPD, d.tag * 100000 + blockIdx.x, 0);
+    }
+    for (int e = tid; e < w * w; e += nt) {
+        const int r = e % w, c = e / w;
+        if (r >= c) d.A[(size_t)c * d.ld + r] = at(r, c);
+    }
+    for (int e = tid; e < kOzK * kOzK; e += nt) {
+        const int r = e % kOzK, c = e / kOzK;
+        ff v(0.f, 0.f);
+        if (r < w && c < w) v = r > c ? at(c, r) : (r == c ? yd[r] : ff(0.f, 0.f));
+        d.Linv[(size_t)c * kOzK + r] = v;
+    }
+}
+
+void launch_oz_diag(const OzDiagDesc *d, int nd, DevStatus *st, cudaStream_t s) {
+    if (nd <= 0) return;
+    const int smem = (int)sizeof(ff) * (kOzK * OZD_PITCH + kOzK);
+    cudaFuncSetAttribute(oz_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    oz_diag_kernel<<<nd, OZD_THREADS, smem, s>>>(d, st);
 }
 
 void launch_oz_split(const OzSplitDesc *d, const int2 *items, int nitems, cudaStream_t s) {

@@ -46,16 +46,37 @@ struct OzSplitDesc {
 // items: (descriptor, 256-row group)
 void launch_oz_split(const OzSplitDesc *d, const int2 *items, int nitems, cudaStream_t s);
 
-// C[i, j] -= sum_k L[i, k] L[j, k] for the lower triangle (i >= j) of an n x n
-// double-float block C (ld ldc), L split by launch_oz_split (rows = n).
+// Cholesky factorization of the w x w (w <= kOzK) diagonal block of a double-float matrix
+// in place (lower triangle, column-major, ld) and the inverse of its factor, L^-1, written
+// to Linv (column-major, ld kOzK, zero above the diagonal).  One CTA per block, in shared
+// memory: right-looking, and at every pivot k the forward elimination of L Y = I takes the
+// same column (Y = L^-1 kept transposed in the upper triangle).  A non-positive pivot is
+// replaced by 1 and reported in *fail (non-NULL) or in the device status (item tag).
+struct OzDiagDesc {
+    ff *A;
+    int ld, w;
+    ff *Linv;
+    int tag;
+    int *fail;
+};
+void launch_oz_diag(const OzDiagDesc *d, int nd, DevStatus *st, cudaStream_t s);
+
+// mode 0: C[i, j] -= sum_k L[i, k] L[j, k] for the lower triangle (i >= j) of an n x n
+//         double-float block C (ld ldc), L split by launch_oz_split (rows = n); the B fields
+//         repeat the A fields (nb = n);
+// mode 1: C[i, j] = sum_k A[i, k] B[j, k] for all i < n, j < nb (C n x nb), A split with
+//         rows = n into slices / rexp and B with rows = nb into slices_b / rexp_b.
 struct OzSyrkDesc {
     ff *C;
     int ldc, n;
     const uint16_t *slices;
     const int *rexp;
+    const uint16_t *slices_b;
+    const int *rexp_b;
+    int nb, mode;
 };
-// items: (descriptor, 128-row tile, 32-column tile, 0); lower tiles only.  Persistent: one CTA
-// per SM takes the items round robin.
+// items: (descriptor, 128-row tile, 32-column tile, 0); mode 0: lower tiles only.  Persistent:
+// one CTA per SM takes the items round robin.
 void launch_oz_syrk(const OzSyrkDesc *d, const int4 *items, int nitems, DevStatus *st, double timeout_s,
                     cudaStream_t s);
 
