@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(OZD_THREADS) oz_diag_kernel(const OzDiagDesc *
     const OzDiagDesc d = descs[blockIdx.x];
     ff *S = ozd_sm;                        // S[r * pitch + c]: L[r][c] for r >= c, Y[r][c] at S[c * pitch + r]
     ff *yd = ozd_sm + kOzK * OZD_PITCH;     // diagonal of Y
-    __shared__ ff sinv;
+    __shared__ ff invs[kOzK];
     __shared__ int bad;
     const int w = d.w, tid = threadIdx.x, nt = blockDim.x;
     auto at = [&](int r, int c) -> ff & { return S[r * OZD_PITCH + c]; };
@@ -378,37 +378,56 @@ __global__ void __launch_bounds__(OZD_THREADS) oz_diag_kernel(const OzDiagDesc *
         else at(r, c) = ff(0.f, 0.f);   // Y[c][r] = 0
     }
     for (int k = tid; k < w; k += nt) yd[k] = ff(1.f, 0.f);
-    if (tid == 0) bad = 0;
-    __syncthreads();
-    for (int k = 0; k < w; ++k) {
-        if (tid == 0) {
-            ff dk = at(k, k);
-            if (!(dk > ff(0.f, 0.f))) {
-                bad = 1;
-                dk = ff(1.f, 0.f);
-            }
-            const ff inv = ff_rsqrt(dk);
-            at(k, k) = dk * inv;   // sqrt(d_k)
-            sinv = inv;
+    // Pivot k: column k of L and row k of Y scaled by 1 / sqrt(d_k), then the trailing block of L
+    // and the rows of Y below k updated.  The thread that updates the next diagonal entry forms
+    // its reciprocal square root at once, so every pivot costs two barriers.
+    auto pivot = [&](int k) {
+        ff dk = at(k, k);
+        if (!(dk > ff(0.f, 0.f))) {
+            bad = 1;
+            dk = ff(1.f, 0.f);
+            at(k, k) = dk;
         }
-        __syncthreads();
-        const ff inv = sinv;
+        invs[k] = ff_rsqrt(dk);
+    };
+    if (tid == 0) {
+        bad = 0;
+        if (w > 0) pivot(0);
+    }
+    __syncthreads();
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int k = 0; k < w; ++k) {
+        const ff inv = invs[k];
+        if (tid == 0) at(k, k) = at(k, k) * inv;                              // sqrt(d_k)
         for (int r = k + 1 + tid; r < w; r += nt) at(r, k) *= inv;           // column k of L
         for (int c = tid; c <= k; c += nt) {                                 // row k of Y
             if (c < k) at(c, k) *= inv;
             else yd[k] *= inv;
         }
         __syncthreads();
-        // trailing block of L (lower triangle, a warp per column) and the rows below k of Y
-        // (columns <= k, a warp per column)
-        const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+        const int m = w - k - 1;
+        // trailing block of L: lower triangle, a warp per column
         for (int c = k + 1 + wid; c < w; c += nw) {
             const ff lck = at(c, k);
-            for (int r = c + lane; r < w; r += 32) at(r, c) -= at(r, k) * lck;
+            for (int r = c + lane; r < w; r += 32) {
+                at(r, c) -= at(r, k) * lck;
+                if (r == k + 1 && c == k + 1) pivot(k + 1);   // thread 0
+            }
         }
-        for (int c = wid; c <= k; c += nw) {
-            const ff yk = c < k ? at(c, k) : yd[k];
-            for (int r = k + 1 + lane; r < w; r += 32) at(c, r) -= at(r, k) * yk;
+        // rows below k of Y, columns <= k (flattened, rows fastest: contiguous in shared memory)
+        if (m > 0) {
+            const int tot = m * (k + 1), dc = nt / m, dr = nt % m;
+            int c = tid / m, r = tid % m;
+            for (int e = tid; e < tot; e += nt) {
+                const ff yk = c < k ? at(c, k) : yd[k];
+                at(c, k + 1 + r) -= at(k + 1 + r, k) * yk;
+                r += dr;
+                c += dc;
+                if (r >= m) {
+                    r -= m;
+                    ++c;
+                }
+            }
         }
         __syncthreads();
     }
