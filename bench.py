@@ -234,11 +234,19 @@ def _kernel_table(kt, steps, solver, info, workload):
                      effective_tflops=work / n / (ms / n / 1e3) / 1e12,
                      peak_source=f"{src} bf16 {bf16} TFLOP/s (of {src}); executed bf16 flop of the 28 digit products")
         elif name == "pcg_kernel":
-            # per launch (one whole PCG solve): every iteration reads every S_i and P~_i once
+            # per launch (one whole PCG solve): every iteration reads every S_i and P~_i once, one
+            # FP64 multiply-add per 8-byte entry, so the FP64 pipe caps the stream at
+            # PEAK_FP64 / 2 x 8 bytes per second, below the HBM copy rate
             gemv = sum(2 * 8 * solver.interface_dofs(i).size ** 2 for i in range(solver.nsub))
             b = gemv * info["iters"]
-            e.update(bound="hbm", unit="GB/s", work_per_launch=b, achieved=b / (ms / n / 1e3) / 1e9, peak=hbm,
-                     peak_source=f"{src} HBM copy bandwidth (of {src})")
+            fp64_gbs = PEAK_FP64_TFLOPS * 1e12 / 2 * 8 / 1e9
+            if fp64_gbs < hbm:
+                bound, peak, ps = "alu", fp64_gbs, ("derived FP64 pipe rate as GEMV bytes (one multiply-add per "
+                                                     f"8-byte entry), below the {src} HBM copy bandwidth {hbm} GB/s")
+            else:
+                bound, peak, ps = "hbm", hbm, f"{src} HBM copy bandwidth (of {src})"
+            e.update(bound=bound, unit="GB/s", work_per_launch=b, achieved=b / (ms / n / 1e3) / 1e9, peak=peak,
+                     peak_source=ps)
         elif name == "tc_gemm_3xtf32":
             w = 3.0 * work / n   # three TF32 products per effective product
             e.update(bound="tensor", unit="TFLOP/s", work_per_launch=w, achieved=w / (ms / n / 1e3) / 1e12,
