@@ -2472,7 +2472,7 @@ void run_face_eigs(bddc_handle *h, const std::vector<EigDesc> &eds, double tau, 
         for (int b = 0; b < nb; ++b) {
             const EigDesc &e = big[todo[b]];
             const int n = e.n, ldm = round_up(n, 8);
-            od[b] = LobOutDesc{ld[b].S[cur], n, ld[b].lds, k, ld[b].theta, e.lam, e.vec, e.counts, kEigCap, ld[b].state};
+            od[b] = LobOutDesc{ld[b].S[cur], n, ld[b].lds, k, ld[b].theta, e.lam, e.vec, e.counts, e.cap, ld[b].state};
             double *M = h->ar.get_t<double>("lob_cert" + ps + "_" + std::to_string(b), (size_t)ldm * n);
             cd[b] = LobCertDesc{e.C, n, e.ld, ld[b].S[cur], ld[b].lds, k, ld[b].theta, e.counts, M, ldm, 1e-6};
             for (int c = 0; c < (n + 63) / 64; ++c) citems.push_back(make_int2(b, c));
@@ -2992,6 +2992,7 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
         e.work = h->ar.get_t<double>("ework_" + std::to_string(f), (size_t)64 * ns + 16);
         e.rows = h->ar.get_t<double>("frows_" + std::to_string(f), (size_t)kEigCap * std::max(nface, 1));
         e.counts = h->ar.get_t<int>("fcnt_all", (size_t)nf * 8) + (size_t)f * 8;
+        e.cap = kEigCap;
         eds.push_back(e);
         eig_face.push_back(f);
     }
@@ -3012,6 +3013,36 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
     }
     run_gemm(h, gm2, "C", ff_mode);
     run_face_eigs(h, eds, tau, fixed_k, &h->lob_stats);
+    {   // faces with more than kEigCap eigenvalues above tau: their matrix C formed again (the
+        // first pass reduced it in place) and the dense path run once more with room for all
+        std::vector<int> cnt0((size_t)nf * 8, 0);
+        BDDC_CUDA(cudaMemcpyAsync(cnt0.data(), h->ar.get_t<int>("fcnt_all", (size_t)nf * 8), cnt0.size() * sizeof(int),
+                                  cudaMemcpyDeviceToHost, h->stream));
+        BDDC_CUDA(cudaStreamSynchronize(h->stream));
+        std::vector<EigDesc> redo;
+        std::vector<GemmDesc> gredo;
+        for (size_t k = 0; k < eds.size(); ++k) {
+            const int f = eig_face[k], over = cnt0[(size_t)f * 8 + 4];
+            if (over <= 0) continue;
+            EigDesc &e = eds[k];
+            const int ns = pbufs[f].ns;
+            e.cap = over;
+            e.lam = h->ar.get_t<double>("lamx_" + std::to_string(f), (size_t)over + 1);
+            e.vec = h->ar.get_t<double>("vec_" + std::to_string(f), (size_t)over * ns);
+            e.rows = h->ar.get_t<double>("frows_" + std::to_string(f), (size_t)over * std::max(e.nface, 1));
+            redo.push_back(e);
+            gredo.push_back(gm2[k]);
+        }
+        if (!redo.empty()) {
+            BDDC_REQUIRE(!h->keep_edge_rows, BDDC_EINVAL,
+                         "kept edge rows allow at most 48 selected eigenvectors per face");
+            run_gemm(h, gredo, "Cx", ff_mode);
+            const int keep = h->opt.eig_large_n;
+            h->opt.eig_large_n = -1;   // the dense path forms every selected pair
+            run_face_eigs(h, redo, tau, fixed_k, nullptr);
+            h->opt.eig_large_n = keep;
+        }
+    }
     // kept edge rows (Section 3: d split into a face row and one row per edge), per edge:
     // the edge parts of the same rows d from every face pair on the edge, stacked in the
     // edge's slots (pairs in face order), then one orthonormal basis per edge
@@ -3139,16 +3170,23 @@ void do_adapt(bddc_handle *h, double tau, bddc_adapt_info *info, int fixed_k = 0
         int f = eig_face[k];
         auto &fp = h->faces[f];
         const int *cnt = &cnt_all[(size_t)f * 8];
-        std::vector<double> lam(lam_all.begin() + (size_t)f * (kEigCap + 1), lam_all.begin() + (size_t)(f + 1) * (kEigCap + 1));
+        std::vector<double> lam;
+        if (eds[k].cap > kEigCap) {   // a face redone with a larger capacity
+            lam.resize(cnt[2]);
+            if (cnt[2] > 0)
+                BDDC_CUDA(cudaMemcpy(lam.data(), eds[k].lam, cnt[2] * sizeof(double), cudaMemcpyDeviceToHost));
+        } else {
+            lam.assign(lam_all.begin() + (size_t)f * (kEigCap + 1), lam_all.begin() + (size_t)(f + 1) * (kEigCap + 1));
+            lam.resize(cnt[2]);
+        }
         fp.nsel = cnt[0];
         fp.nkept = cnt[1];
         fp.ties = cnt[3];
-        lam.resize(cnt[2]);
         fp.lam = lam;
         if (!lam.empty()) omega = std::max(omega, lam[0]);
         n_added += fp.nkept;
         n_ties += fp.ties;
-        BDDC_REQUIRE(cnt[4] == 0, BDDC_EINVAL, "more than 48 eigenvalues above tau on one face");
+        BDDC_REQUIRE(cnt[4] == 0, BDDC_ECUDA, "internal: a face's eigenpairs exceed its capacity");
         h->face_rows_dev[f] = eds[k].rows;
         if (fp.nkept > 0) {
             GlobRows g;

@@ -396,10 +396,10 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
             nsel = n - less;
             ties = sturm_less(dd, e2, n, tau * (1 + 1e-6)) - sturm_less(dd, e2, n, tau * (1 - 1e-6));
         }
-        int over = 0;
-        if (nsel > kEigCap) {
-            nsel = kEigCap;
-            over = 1;
+        int over = 0;   // > 0: the selected count when it exceeds the face's capacity
+        if (nsel > D.cap) {
+            over = nsel;
+            nsel = D.cap;
         }
         sh_int[0] = nsel;
         sh_int[1] = ties;

@@ -5,7 +5,7 @@
 
 namespace bddc {
 
-constexpr int kEigCap = 48;   // most eigenpairs above tau kept per face
+constexpr int kEigCap = 48;   // eigenpairs formed per face in the first pass (a face with more is redone)
 
 struct EigDesc {
     double *C;            // n x n symmetric standard-form matrix (destroyed)
@@ -14,11 +14,13 @@ struct EigDesc {
     int ldw;
     const int *face_pos;  // positions of the face dofs among the n rows
     int nface;
-    double *lam;          // out: eigenvalues, descending (selected + largest rejected), kEigCap + 1
-    double *vec;          // scratch: kEigCap x n eigenvectors of C
+    double *lam;          // out: eigenvalues, descending (selected + largest rejected), cap + 1
+    double *vec;          // scratch: cap x n eigenvectors of C
     double *work;         // scratch: 64 n + 16
     double *rows;         // out: face rows, row l at rows[l * nface + f] (orthonormal)
-    int *counts;          // out: [0] selected, [1] kept, [2] values in lam, [3] ties, [4] overflow
+    int *counts;          // out: [0] selected, [1] kept, [2] values in lam, [3] ties, [4] overflow:
+                          // the selected count when it exceeds cap (then only cap are formed), else 0
+    int cap;              // most eigenpairs formed (lam, vec and rows are sized by it)
     int given;            // 1: lam, vec and counts [0], [2], [3], [4] are supplied (the batched
                           // LOBPCG, lobpcg.h); only the face rows are formed (C is not read).
                           // 2: the Householder reduction is supplied (launch_tridiag_multi):

@@ -399,10 +399,10 @@ __global__ void lob_select_kernel(const LobOutDesc *descs, int nd, double tau, i
                 ties += fabs(d.theta[j] / tau - 1.0) < 1e-6 ? 1 : 0;
             }
         }
-        int over = 0;
+        int over = 0;   // > 0: the selected count when it exceeds the capacity
         if (nsel > d.cap) {
+            over = nsel;
             nsel = d.cap;
-            over = 1;
         }
         nsel_sh = nsel;
         ties_sh = ties;
