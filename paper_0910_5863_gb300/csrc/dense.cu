@@ -403,8 +403,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const 
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    for (int k0 = 0; k0 < d.k; k0 += 16) {
-        for (int e = tid; e < 16 * TILE; e += 256) {
+    // The next K step's tile entries are loaded into registers while the current one is
+    // multiplied (8 of A and 8 of B per thread), then staged after the barrier.
+    constexpr int PER = 16 * TILE / 256;
+    double ra[PER], rb[PER];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * 256;
             int r, k;
             // A tile: rows m0..m0+63, k0..k0+15
             if (!d.transA) {
@@ -414,13 +420,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const 
                 k = e % 16;
                 r = e / 16;
             }
-            double v = 0.0;
-            if (m0 + r < d.m && k0 + k < d.k)
-                v = d.transA ? d.A[(size_t)(m0 + r) * d.lda + k0 + k] : d.A[(size_t)(k0 + k) * d.lda + m0 + r];
-            if constexpr (FF)
-                As[k][r] = ff_from_double(v);
-            else
-                As[k][r] = v;
+            ra[q] = (m0 + r < d.m && k0 + k < d.k)
+                        ? (d.transA ? d.A[(size_t)(m0 + r) * d.lda + k0 + k] : d.A[(size_t)(k0 + k) * d.lda + m0 + r])
+                        : 0.0;
             int c;
             if (d.transB) {
                 c = e % TILE;
@@ -429,15 +431,31 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc *descs, const 
                 k = e % 16;
                 c = e / 16;
             }
-            v = 0.0;
-            if (n0 + c < d.n && k0 + k < d.k)
-                v = d.transB ? d.B[(size_t)(k0 + k) * d.ldb + n0 + c] : d.B[(size_t)(n0 + c) * d.ldb + k0 + k];
-            if constexpr (FF)
-                Bs[k][c] = ff_from_double(v);
-            else
-                Bs[k][c] = v;
+            rb[q] = (n0 + c < d.n && k0 + k < d.k)
+                        ? (d.transB ? d.B[(size_t)(k0 + k) * d.ldb + n0 + c] : d.B[(size_t)(n0 + c) * d.ldb + k0 + k])
+                        : 0.0;
         }
+    };
+    auto stage = [&]() {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = tid + q * 256;
+            const int ra_r = d.transA ? e / 16 : e % TILE, ra_k = d.transA ? e % 16 : e / TILE;
+            const int rb_c = d.transB ? e % TILE : e / 16, rb_k = d.transB ? e / TILE : e % 16;
+            if constexpr (FF) {
+                As[ra_k][ra_r] = ff_from_double(ra[q]);
+                Bs[rb_k][rb_c] = ff_from_double(rb[q]);
+            } else {
+                As[ra_k][ra_r] = ra[q];
+                Bs[rb_k][rb_c] = rb[q];
+            }
+        }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < d.k; k0 += 16) {
+        stage();
         __syncthreads();
+        if (k0 + 16 < d.k) fetch(k0 + 16);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             T a[4], b[4];
