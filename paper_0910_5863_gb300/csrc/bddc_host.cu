@@ -1197,101 +1197,123 @@ void classify(bddc_handle *h) {
     // element positions read the substructure dof lists, which are final now; the face
     // pairs below only read them as well
     if (!h->csr_mode) epos_task.start([h]() { h->epos = element_positions(h); });
-    // face pairs
-    h->faces.clear();
-    h->faces.reserve(face_list.size());
-    std::vector<int> pj(h->nfree, -1);   // position of a dof in sj's interface list
-    // per set: the face (index + 1) it was last tested for, and whether it holds both substructures
-    std::vector<int> set_stamp(h->sets.size(), 0);
-    std::vector<char> set_both(h->sets.size(), 0);
-    int face_no = 0;
-    for (auto &fl : face_list) {
-        FacePair fp;
-        fp.i = fl.first.first;
-        fp.j = fl.first.second;
-        ++face_no;
-        auto &si = h->subs[fp.i], &sj = h->subs[fp.j];
-        for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = k;
-        std::vector<int64_t> cn;
-        for (int k = 0; k < si.nG; ++k) {
-            int64_t g = si.gG[k];
-            int64_t v = dof_node[g];
-            const int sid = h->node_set[v];
-            if (set_stamp[sid] != face_no) {
-                const auto &S = h->sets[sid];
-                set_stamp[sid] = face_no;
-                set_both[sid] = std::binary_search(S.begin(), S.end(), fp.i) && std::binary_search(S.begin(), S.end(), fp.j);
+    // face pairs: independent of each other, built by a few host threads (each with its own
+    // scratch); the failure reported is the first face's in face order, as a serial loop would
+    const size_t nfl = face_list.size();
+    h->faces.assign(nfl, FacePair());
+    std::vector<std::string> face_err(nfl);
+    auto build_faces = [&](size_t t0, size_t tstep) {
+        std::vector<int> pj(h->nfree, -1);   // position of a dof in sj's interface list
+        // per set: the face (index + 1) it was last tested for, and whether it holds both substructures
+        std::vector<int> set_stamp(h->sets.size(), 0);
+        std::vector<char> set_both(h->sets.size(), 0);
+        for (size_t q = t0; q < nfl; q += tstep) {
+            const auto &fl = face_list[q];
+            const int face_no = (int)q + 1;
+            FacePair fp;
+            fp.i = fl.first.first;
+            fp.j = fl.first.second;
+            auto &si = h->subs[fp.i], &sj = h->subs[fp.j];
+            for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = k;
+            std::vector<int64_t> cn;
+            for (int k = 0; k < si.nG; ++k) {
+                int64_t g = si.gG[k];
+                int64_t v = dof_node[g];
+                const int sid = h->node_set[v];
+                if (set_stamp[sid] != face_no) {
+                    const auto &S = h->sets[sid];
+                    set_stamp[sid] = face_no;
+                    set_both[sid] = std::binary_search(S.begin(), S.end(), fp.i) && std::binary_search(S.begin(), S.end(), fp.j);
+                }
+                if (!set_both[sid]) continue;
+                if (h->is_corner[v]) {
+                    fp.ci_pos.push_back(k);
+                    fp.cj_pos.push_back(pj[g]);
+                    if (g % c == 0 || c == 1) cn.push_back(v);
+                    continue;
+                }
+                fp.s_g.push_back(g);
+                fp.pos_i.push_back(k);
             }
-            if (!set_both[sid]) continue;
-            if (h->is_corner[v]) {
-                fp.ci_pos.push_back(k);
-                fp.cj_pos.push_back(pj[g]);
-                if (g % c == 0 || c == 1) cn.push_back(v);
-                continue;
-            }
-            fp.s_g.push_back(g);
-            fp.pos_i.push_back(k);
-        }
-        // s sorted by global dof (si.gG is sorted so s_g is too)
-        for (size_t k = 0; k < fp.s_g.size(); ++k) {
-            int64_t g = fp.s_g[k];
-            fp.pos_j.push_back(pj[g]);
-            const auto &S = h->sets[h->node_set[dof_node[g]]];
-            if (S.size() == 2) fp.face_idx.push_back((int)k);
-        }
-        fp.floating = si.floating && sj.floating;
-        const int nsd = (int)fp.s_g.size();
-        if (si.floating || sj.floating) {
-            // with one floating member the pair matrix is singular unless the shared corners fix its rigid modes
-            int need = (c == 1) ? 1 : 3;
-            std::vector<int64_t> cnu;
-            for (size_t k = 0; k < fp.ci_pos.size(); k += c) cnu.push_back(dof_node[si.gG[fp.ci_pos[k]]]);
-            if (rank_corners(cnu) < need)
-                throw Error{BDDC_EASSUMPTION, "Assumption 2: corners shared by substructures " + std::to_string(fp.i) +
-                                                  " and " + std::to_string(fp.j) + " do not fix relative rigid motions"};
-        }
-        if (fp.floating) {
-            // null space of S^ on s: rigid modes, identical on both sides; N0 orthonormal with N = [N0; N0]
-            int nr = (c == 1) ? 1 : 6;
-            std::vector<double> R((size_t)nsd * nr, 0.0);
-            for (int k = 0; k < nsd; ++k) {
+            // s sorted by global dof (si.gG is sorted so s_g is too)
+            for (size_t k = 0; k < fp.s_g.size(); ++k) {
                 int64_t g = fp.s_g[k];
-                int comp = (int)(g % c);
-                const double *x = &h->xyz[dof_node[g] * 3];
-                if (c == 1) {
-                    R[k] = 1.0;
-                } else {
-                    R[(size_t)comp * nsd + k] = 1.0;  // translations
-                    // rotations omega x x: e_a x x, component comp
-                    double rot[3][3] = {{0, -x[2], x[1]}, {x[2], 0, -x[0]}, {-x[1], x[0], 0}};
-                    // omega = e_a: (e_a x x)_comp = rot[comp][a]... (e_a x x) = -x x e_a
-                    for (int a = 0; a < 3; ++a) R[(size_t)(3 + a) * nsd + k] = -rot[comp][a];
+                fp.pos_j.push_back(pj[g]);
+                const auto &S = h->sets[h->node_set[dof_node[g]]];
+                if (S.size() == 2) fp.face_idx.push_back((int)k);
+            }
+            fp.floating = si.floating && sj.floating;
+            const int nsd = (int)fp.s_g.size();
+            for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = -1;
+            if (si.floating || sj.floating) {
+                // with one floating member the pair matrix is singular unless the shared corners fix its rigid modes
+                int need = (c == 1) ? 1 : 3;
+                std::vector<int64_t> cnu;
+                for (size_t k = 0; k < fp.ci_pos.size(); k += c) cnu.push_back(dof_node[si.gG[fp.ci_pos[k]]]);
+                if (rank_corners(cnu) < need) {
+                    face_err[q] = "Assumption 2: corners shared by substructures " + std::to_string(fp.i) + " and " +
+                                  std::to_string(fp.j) + " do not fix relative rigid motions";
+                    continue;
                 }
             }
-            // modified Gram-Schmidt, then scale by 1/sqrt(2)
-            int kept = 0;
-            std::vector<double> Q;
-            for (int a = 0; a < nr; ++a) {
-                std::vector<double> v(R.begin() + (size_t)a * nsd, R.begin() + (size_t)(a + 1) * nsd);
-                for (int b = 0; b < kept; ++b) {
-                    double d = 0;
-                    for (int k = 0; k < nsd; ++k) d += v[k] * Q[(size_t)b * nsd + k];
-                    for (int k = 0; k < nsd; ++k) v[k] -= d * Q[(size_t)b * nsd + k];
+            if (fp.floating) {
+                // null space of S^ on s: rigid modes, identical on both sides; N0 orthonormal with N = [N0; N0]
+                int nr = (c == 1) ? 1 : 6;
+                std::vector<double> R((size_t)nsd * nr, 0.0);
+                for (int k = 0; k < nsd; ++k) {
+                    int64_t g = fp.s_g[k];
+                    int comp = (int)(g % c);
+                    const double *x = &h->xyz[dof_node[g] * 3];
+                    if (c == 1) {
+                        R[k] = 1.0;
+                    } else {
+                        R[(size_t)comp * nsd + k] = 1.0;  // translations
+                        // rotations omega x x: e_a x x, component comp
+                        double rot[3][3] = {{0, -x[2], x[1]}, {x[2], 0, -x[0]}, {-x[1], x[0], 0}};
+                        // omega = e_a: (e_a x x)_comp = rot[comp][a]... (e_a x x) = -x x e_a
+                        for (int a = 0; a < 3; ++a) R[(size_t)(3 + a) * nsd + k] = -rot[comp][a];
+                    }
                 }
-                double nrm = 0;
-                for (double t : v) nrm += t * t;
-                nrm = std::sqrt(nrm);
-                if (nrm < 1e-10) continue;
-                for (double &t : v) t /= nrm;
-                Q.insert(Q.end(), v.begin(), v.end());
-                kept++;
+                // modified Gram-Schmidt, then scale by 1/sqrt(2)
+                int kept = 0;
+                std::vector<double> Q;
+                for (int a = 0; a < nr; ++a) {
+                    std::vector<double> v(R.begin() + (size_t)a * nsd, R.begin() + (size_t)(a + 1) * nsd);
+                    for (int b = 0; b < kept; ++b) {
+                        double d = 0;
+                        for (int k = 0; k < nsd; ++k) d += v[k] * Q[(size_t)b * nsd + k];
+                        for (int k = 0; k < nsd; ++k) v[k] -= d * Q[(size_t)b * nsd + k];
+                    }
+                    double nrm = 0;
+                    for (double t : v) nrm += t * t;
+                    nrm = std::sqrt(nrm);
+                    if (nrm < 1e-10) continue;
+                    for (double &t : v) t /= nrm;
+                    Q.insert(Q.end(), v.begin(), v.end());
+                    kept++;
+                }
+                for (double &t : Q) t /= std::sqrt(2.0);
+                fp.N0 = Q;
+                fp.nnull = kept;
             }
-            for (double &t : Q) t /= std::sqrt(2.0);
-            fp.N0 = Q;
-            fp.nnull = kept;
+            h->faces[q] = std::move(fp);
         }
-        for (int k = 0; k < sj.nG; ++k) pj[sj.gG[k]] = -1;
-        h->faces.push_back(std::move(fp));
+    };
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const size_t nthr = std::max<size_t>(1, std::min<size_t>({8, hw > 0 ? (size_t)hw : 1, (nfl + 15) / 16}));
+        std::vector<HostTask> tasks(nthr - 1);
+        for (size_t t = 1; t < nthr; ++t) tasks[t - 1].start([&build_faces, t, nthr]() { build_faces(t, nthr); });
+        std::exception_ptr err0;
+        try {
+            build_faces(0, nthr);
+        } catch (...) {
+            err0 = std::current_exception();
+        }
+        for (auto &t : tasks) t.rethrow();
+        if (err0) std::rethrow_exception(err0);
+        for (size_t q = 0; q < nfl; ++q)
+            if (!face_err[q].empty()) throw Error{BDDC_EASSUMPTION, face_err[q]};
     }
     const auto tc_color = std::chrono::steady_clock::now();
     colour_task.rethrow();
@@ -2308,6 +2330,20 @@ void run_face_eigs(bddc_handle *h, const std::vector<EigDesc> &eds, double tau, 
         const int cap = tridiag_multi_capacity(nmax);
         BDDC_REQUIRE(cap >= 2, BDDC_ECUDA, "no co-resident CTAs for the face reduction");
         unsigned *bar = h->ar.get_t<unsigned>("tri_bar_" + tag, 2 * multi.size());
+        // CTAs per face in proportion to its reduction work (n^3), so that the largest faces,
+        // whose n - 2 dependent steps are the launch's critical path, get the most: all faces in
+        // one cooperative launch when 2 CTAs each fit, at most 64 for one face
+        std::vector<int> Gf(multi.size(), 2);
+        if (2 * multi.size() <= (size_t)cap) {
+            double w3 = 0.0;
+            for (const auto &e : multi) w3 += (double)e.n * e.n * e.n;
+            const int spare = cap - 2 * (int)multi.size();
+            for (size_t q = 0; q < multi.size(); ++q) {
+                const double n = multi[q].n;
+                Gf[q] = 2 + (int)std::floor(spare * (n * n * n) / w3);
+                Gf[q] = std::min(Gf[q], std::min(64, std::max(2, (multi[q].n + 15) / 16)));
+            }
+        }
         size_t pos = 0;
         int wave = 0;
         while (pos < multi.size()) {   // waves of faces whose CTAs fit co-resident
@@ -2316,7 +2352,7 @@ void run_face_eigs(bddc_handle *h, const std::vector<EigDesc> &eds, double tau, 
             int used = 0;
             for (; pos < multi.size(); ++pos) {
                 const EigDesc &e = multi[pos];
-                const int G = std::min(std::max((e.n + 63) / 64, 2), std::min(16, cap));
+                const int G = std::min(Gf[pos], cap);
                 if (used + G > cap) break;
                 for (int g = 0; g < G; ++g) items.push_back(make_int2((int)td.size(), g));
                 td.push_back(TridiagDesc{e.C, e.n, e.ld, e.work, G, bar + 2 * pos});
@@ -2335,7 +2371,28 @@ void run_face_eigs(bddc_handle *h, const std::vector<EigDesc> &eds, double tau, 
             h->launches++;
             kt_end(h, tok, KT_FACE_RED, work);
         }
+        // eigenpairs and face rows of these faces, several CTAs each; the face kernel finishes them
         for (auto &e : multi) e.given = 2;
+        {
+            const int G = kFaceVecCTAs;
+            std::vector<int2> vit;
+            std::vector<size_t> off(multi.size() + 1, 0);
+            for (size_t q = 0; q < multi.size(); ++q) {
+                off[q + 1] = off[q] + (size_t)G * 8 * 6 * multi[q].n;
+                for (int g = 0; g < G; ++g) vit.push_back(make_int2((int)q, g));
+            }
+            double *scr_all = h->ar.get_t<double>("fvscr_" + tag, std::max<size_t>(off.back(), 1));
+            std::vector<double *> scr(multi.size());
+            for (size_t q = 0; q < multi.size(); ++q) scr[q] = scr_all + off[q];
+            auto *dvd = h->ar.upload("fvdesc_" + tag, multi, h->stream);
+            auto *dvi = h->ar.upload("fvit_" + tag, vit, h->stream);
+            auto *dvs = h->ar.upload("fvscrp_" + tag, scr, h->stream);
+            const long tok = kt_begin(h);
+            launch_face_vec(dvd, dvi, (int)vit.size(), G, nmax, tau, fixed_k, dvs, h->stream);
+            check_launch(h);
+            kt_end(h, tok, KT_FACE_RED, 0.0);
+        }
+        for (auto &e : multi) e.given = 3;
         dense1(multi, tag + "_tri", 0);
     };
     dense(small, "small", use_ff);

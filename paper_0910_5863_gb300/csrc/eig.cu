@@ -258,6 +258,112 @@ __device__ void householder_ff_packed(double *A, int lda, int n, ff *F, double *
     __syncthreads();
 }
 
+// The per-eigenvalue steps of the face problem, one warp each, shared by face_eig_kernel and
+// face_vec_kernel (bit-identical results whichever runs them).
+// Eigenvalue j (ascending) of T by 32-way multisection: lanes 0..30 count at 31 interior points.
+__device__ double tri_multisect(const double *dd, const double *e2, int n, int j, double tnorm) {
+    const int lane = threadIdx.x & 31;
+    double lo = -tnorm - 1.0, hi = tnorm + 1.0;
+    for (int round = 0; round < 40; ++round) {
+        const double w = hi - lo;
+        if (w <= 1e-15 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
+        const double x = lo + w * (double)(lane + 1) * (1.0 / 32.0);
+        const bool above = lane < 31 && sturm_less(dd, e2, n, x) > j;
+        const unsigned mask = __ballot_sync(0xffffffffu, above);
+        const int first = mask ? __ffs(mask) - 1 : 31;
+        const double nlo = first == 0 ? lo : lo + w * (double)first * (1.0 / 32.0);
+        const double nhi = first == 31 ? hi : lo + w * (double)(first + 1) * (1.0 / 32.0);
+        if (!(nlo > lo || nhi < hi)) break;
+        lo = nlo;
+        hi = nhi;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Inverse iteration on T - lm I (LU with row interchanges by lane 0, three solves), the
+// normalised vector written to out.  wb: 6 n doubles of scratch for the warp.
+__device__ void tri_inverse_iteration(const double *dd, const double *ee, int n, double lm, int mI, double tnorm,
+                                      double *wb, double *out) {
+    const int lane = threadIdx.x & 31;
+    double *dl = wb, *du = dl + n, *dv = du + n, *du2 = dv + n, *xv = du2 + n;
+    int *piv = (int *)(xv + n);
+    if (lane == 0) {
+        // LU with row interchanges of T - lm I; the reciprocals of the pivots are kept in dv
+        const double small = 2.2e-16 * fmax(tnorm, 1e-300);
+        for (int i = 0; i < n; ++i) {
+            dv[i] = dd[i] - lm;
+            du[i] = (i + 1 < n) ? ee[i] : 0.0;
+            dl[i] = (i + 1 < n) ? ee[i] : 0.0;
+            du2[i] = 0.0;
+        }
+        for (int i = 0; i + 1 < n; ++i) {
+            if (fabs(dv[i]) >= fabs(dl[i])) {
+                piv[i] = 0;
+                if (dv[i] == 0.0) dv[i] = small;
+                double f = dl[i] / dv[i];
+                dl[i] = f;
+                dv[i + 1] -= f * du[i];
+            } else {
+                piv[i] = 1;
+                double f = dv[i] / dl[i];
+                dv[i] = dl[i];
+                dl[i] = f;
+                double t = du[i];
+                du[i] = dv[i + 1];
+                dv[i + 1] = t - f * dv[i + 1];
+                if (i + 2 < n) {
+                    du2[i] = du[i + 1];
+                    du[i + 1] = -f * du[i + 1];
+                }
+            }
+        }
+        if (dv[n - 1] == 0.0) dv[n - 1] = small;
+        for (int i = 0; i < n; ++i) dv[i] = 1.0 / dv[i];
+    }
+    for (int i = lane; i < n; i += 32) xv[i] = 1.0 + 0.1 * (double)((i * 7919 + mI * 104729) % 17) / 17.0;
+    __syncwarp();
+    for (int itr = 0; itr < 3; ++itr) {
+        if (lane == 0) {
+            for (int i = 0; i + 1 < n; ++i) {
+                if (piv[i] == 0) {
+                    xv[i + 1] -= dl[i] * xv[i];
+                } else {
+                    double t = xv[i];
+                    xv[i] = xv[i + 1];
+                    xv[i + 1] = t - dl[i] * xv[i + 1];
+                }
+            }
+            xv[n - 1] *= dv[n - 1];
+            if (n >= 2) xv[n - 2] = (xv[n - 2] - du[n - 2] * xv[n - 1]) * dv[n - 2];
+            for (int i = n - 3; i >= 0; --i) xv[i] = (xv[i] - du[i] * xv[i + 1] - du2[i] * xv[i + 2]) * dv[i];
+        }
+        __syncwarp();
+        double s2 = 0.0;
+        for (int i = lane; i < n; i += 32) s2 += xv[i] * xv[i];
+        s2 = warp_sum(s2);
+        const double inv = s2 > 0 ? 1.0 / sqrt(s2) : 0.0;
+        for (int i = lane; i < n; i += 32) xv[i] *= inv;
+        __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) out[i] = xv[i];
+    __syncwarp();
+}
+
+// y = H_0 H_1 ... H_{n-3} y with the reflectors below the subdiagonal of A (read-only)
+__device__ void tri_back_transform(const double *A, int lda, const double *bet, int n, double *y) {
+    const int lane = threadIdx.x & 31;
+    for (int k = n - 3; k >= 0; --k) {
+        const double b = bet[k];
+        if (b == 0.0) continue;
+        const double *v = A + (size_t)k * lda + k + 1;
+        double dot = 0.0;
+        for (int i = lane; i < n - k - 1; i += 32) dot += v[i] * y[k + 1 + i];
+        dot = warp_sum(dot) * b;
+        for (int i = lane; i < n - k - 1; i += 32) y[k + 1 + i] -= dot * v[i];
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *descs, int np, double tau,
                                                                double drop_rel, DevStatus *st, int use_smem,
                                                                int use_ff, int packed_off, int fixed_k) {
@@ -293,7 +399,7 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     double *dd = work, *ee = work + n, *bet = work + 2 * n, *P = work + 3 * n, *Wv = work + 4 * n;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     __syncthreads();
-    if (D.given == 1) {
+    if (D.given == 1 || D.given == 3) {
         if (tid == 0) {
             sh_int[0] = counts[0];
             sh_int[1] = counts[3];
@@ -409,95 +515,18 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
     __syncthreads();
     const int nsel = sh_int[0], nval = sh_int[3];
     double *lam = D.lam;
-    // 32-way multisection, one warp per eigenvalue: lanes 0..30 count at 31 interior points
+    // 32-way multisection, one warp per eigenvalue
     for (int t = wid; t < nval; t += nw) {
-        const int j = n - 1 - t;  // index among ascending eigenvalues
-        double lo = -tnorm - 1.0, hi = tnorm + 1.0;
-        for (int round = 0; round < 40; ++round) {
-            const double w = hi - lo;
-            if (w <= 1e-15 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
-            const double x = lo + w * (double)(lane + 1) * (1.0 / 32.0);
-            const bool above = lane < 31 && sturm_less(dd, e2, n, x) > j;
-            const unsigned mask = __ballot_sync(0xffffffffu, above);
-            const int first = mask ? __ffs(mask) - 1 : 31;
-            const double nlo = first == 0 ? lo : lo + w * (double)first * (1.0 / 32.0);
-            const double nhi = first == 31 ? hi : lo + w * (double)(first + 1) * (1.0 / 32.0);
-            if (!(nlo > lo || nhi < hi)) break;
-            lo = nlo;
-            hi = nhi;
-        }
-        if (lane == 0) lam[t] = 0.5 * (lo + hi);
+        const double l = tri_multisect(dd, e2, n, n - 1 - t, tnorm);
+        if (lane == 0) lam[t] = l;
     }
     __syncthreads();
     // fixed count: a boundary lambda_k ~ lambda_{k+1} leaves the selected subspace not unique
     if (fixed_k > 0 && tid == 0 && nsel > 0 && nsel < n && fabs(lam[nsel] / lam[nsel - 1] - 1.0) < 1e-6) sh_int[1] = 1;
     // ---- 3. inverse iteration on T (one warp per vector), back-transformation ----
     double *wbase = work + 10 * n;  // 6 n doubles per warp
-    for (int mI = wid; mI < nsel; mI += nw) {
-        double *dl = wbase + (size_t)wid * 6 * n, *du = dl + n, *dv = du + n, *du2 = dv + n, *xv = du2 + n;
-        int *piv = (int *)(xv + n);
-        const double lm = lam[mI];
-        if (lane == 0) {
-            // LU with row interchanges of T - lm I; the reciprocals of the pivots are kept in dv
-            const double small = 2.2e-16 * fmax(tnorm, 1e-300);
-            for (int i = 0; i < n; ++i) {
-                dv[i] = dd[i] - lm;
-                du[i] = (i + 1 < n) ? ee[i] : 0.0;
-                dl[i] = (i + 1 < n) ? ee[i] : 0.0;
-                du2[i] = 0.0;
-            }
-            for (int i = 0; i + 1 < n; ++i) {
-                if (fabs(dv[i]) >= fabs(dl[i])) {
-                    piv[i] = 0;
-                    if (dv[i] == 0.0) dv[i] = small;
-                    double f = dl[i] / dv[i];
-                    dl[i] = f;
-                    dv[i + 1] -= f * du[i];
-                } else {
-                    piv[i] = 1;
-                    double f = dv[i] / dl[i];
-                    dv[i] = dl[i];
-                    dl[i] = f;
-                    double t = du[i];
-                    du[i] = dv[i + 1];
-                    dv[i + 1] = t - f * dv[i + 1];
-                    if (i + 2 < n) {
-                        du2[i] = du[i + 1];
-                        du[i + 1] = -f * du[i + 1];
-                    }
-                }
-            }
-            if (dv[n - 1] == 0.0) dv[n - 1] = small;
-            for (int i = 0; i < n; ++i) dv[i] = 1.0 / dv[i];
-        }
-        for (int i = lane; i < n; i += 32) xv[i] = 1.0 + 0.1 * (double)((i * 7919 + mI * 104729) % 17) / 17.0;
-        __syncwarp();
-        for (int itr = 0; itr < 3; ++itr) {
-            if (lane == 0) {
-                for (int i = 0; i + 1 < n; ++i) {
-                    if (piv[i] == 0) {
-                        xv[i + 1] -= dl[i] * xv[i];
-                    } else {
-                        double t = xv[i];
-                        xv[i] = xv[i + 1];
-                        xv[i + 1] = t - dl[i] * xv[i + 1];
-                    }
-                }
-                xv[n - 1] *= dv[n - 1];
-                if (n >= 2) xv[n - 2] = (xv[n - 2] - du[n - 2] * xv[n - 1]) * dv[n - 2];
-                for (int i = n - 3; i >= 0; --i) xv[i] = (xv[i] - du[i] * xv[i + 1] - du2[i] * xv[i + 2]) * dv[i];
-            }
-            __syncwarp();
-            double s2 = 0.0;
-            for (int i = lane; i < n; i += 32) s2 += xv[i] * xv[i];
-            s2 = warp_sum(s2);
-            const double inv = s2 > 0 ? 1.0 / sqrt(s2) : 0.0;
-            for (int i = lane; i < n; i += 32) xv[i] *= inv;
-            __syncwarp();
-        }
-        double *vout = D.vec + (size_t)mI * n;
-        for (int i = lane; i < n; i += 32) vout[i] = xv[i];
-    }
+    for (int mI = wid; mI < nsel; mI += nw)
+        tri_inverse_iteration(dd, ee, n, lam[mI], mI, tnorm, wbase + (size_t)wid * 6 * n, D.vec + (size_t)mI * n);
     __syncthreads();
     // clusters (eigenvalues within 1e-5 relative): orthonormalise in order (rare)
     for (int mI = 1; mI < nsel; ++mI) {
@@ -523,32 +552,53 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
         }
     }
     // back-transformation y = H_0 H_1 ... H_{n-3} x, one warp per vector (reflectors are read-only)
-    for (int mI = wid; mI < nsel; mI += nw) {
-        double *y = D.vec + (size_t)mI * n;
-        for (int k = n - 3; k >= 0; --k) {
-            const double b = bet[k];
-            if (b == 0.0) continue;
-            const double *v = A + (size_t)k * lda + k + 1;
-            double dot = 0.0;
-            for (int i = lane; i < n - k - 1; i += 32) dot += v[i] * y[k + 1 + i];
-            dot = warp_sum(dot) * b;
-            for (int i = lane; i < n - k - 1; i += 32) y[k + 1 + i] -= dot * v[i];
-            __syncwarp();
-        }
-    }
+    for (int mI = wid; mI < nsel; mI += nw) tri_back_transform(A, lda, bet, n, D.vec + (size_t)mI * n);
     __syncthreads();
     }   // !D.given
     const int nsel = sh_int[0], nval = sh_int[3];
     // ---- 4. face rows and their pivoted orthonormalisation ----
     const int nf = D.nface;
     double *R = D.rows;
-    for (int e = tid; e < nsel * nf; e += nt) {
-        int l = e / nf, f = e % nf;
-        const double *y = D.vec + (size_t)l * n;
-        const double *wr = D.W1 + D.face_pos[f];
-        double acc = 0.0;
-        for (int j = 0; j < n; ++j) acc += wr[(size_t)j * D.ldw] * y[j];
-        R[(size_t)l * nf + f] = acc;
+    if (D.given != 3) {
+        for (int e = tid; e < nsel * nf; e += nt) {
+            int l = e / nf, f = e % nf;
+            const double *y = D.vec + (size_t)l * n;
+            const double *wr = D.W1 + D.face_pos[f];
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc += wr[(size_t)j * D.ldw] * y[j];
+            R[(size_t)l * nf + f] = acc;
+        }
+    } else {
+        // eigenpairs and rows from face_vec_kernel: the boundary test of the fixed count, and
+        // clusters (eigenvalues within 1e-5 relative) orthonormalised in order, the rows with
+        // the same combinations (they are linear in the vectors)
+        const double *lam = D.lam;
+        if (fixed_k > 0 && tid == 0 && nsel > 0 && nsel < n && fabs(lam[nsel] / lam[nsel - 1] - 1.0) < 1e-6)
+            sh_int[1] = 1;
+        for (int mI = 1; mI < nsel; ++mI) {
+            double *x = D.vec + (size_t)mI * n;
+            bool any = false;
+            for (int q = 0; q < mI; ++q) {
+                if (fabs(lam[q] - lam[mI]) > 1e-5 * fabs(lam[mI])) continue;
+                any = true;
+                const double *vq = D.vec + (size_t)q * n;
+                double dot = 0.0;
+                for (int i = tid; i < n; i += nt) dot += vq[i] * x[i];
+                dot = block_sum(dot, scratch);
+                for (int i = tid; i < n; i += nt) x[i] -= dot * vq[i];
+                for (int f = tid; f < nf; f += nt) R[(size_t)mI * nf + f] -= dot * R[(size_t)q * nf + f];
+                __syncthreads();
+            }
+            if (any) {
+                double s2 = 0.0;
+                for (int i = tid; i < n; i += nt) s2 += x[i] * x[i];
+                s2 = block_sum(s2, scratch);
+                const double inv = s2 > 0 ? 1.0 / sqrt(s2) : 0.0;
+                for (int i = tid; i < n; i += nt) x[i] *= inv;
+                for (int f = tid; f < nf; f += nt) R[(size_t)mI * nf + f] *= inv;
+                __syncthreads();
+            }
+        }
     }
     __syncthreads();
     // normalise every row
@@ -608,6 +658,85 @@ __global__ void __launch_bounds__(EIG_THREADS) face_eig_kernel(const EigDesc *de
         counts[3] = sh_int[1];
         counts[4] = sh_int[2];
     }
+}
+
+// Eigenpairs and face rows of the faces whose Householder reduction is supplied (EigDesc::given
+// == 2), several CTAs per face: item (face, g) of G; CTA g takes the eigenvalue indices g, g + G,
+// ..., one warp each: multisection, and for the selected ones inverse iteration,
+// back-transformation and the face row.  Every CTA forms the counts from the same Sturm counts;
+// CTA 0 stores them.  The face kernel finishes these faces with given = 3.
+__global__ void __launch_bounds__(EIG_THREADS) face_vec_kernel(const EigDesc *descs, const int2 *items, int G,
+                                                               double tau, int fixed_k, double *const *scr) {
+    extern __shared__ double fv_e2[];
+    __shared__ double scratch[32];
+    __shared__ int sh_int[4];
+    const int2 it = items[blockIdx.x];
+    const EigDesc D = descs[it.x];
+    const int g = it.y, n = D.n, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    if (n <= 0) return;
+    const double *dd = D.work, *ee = D.work + n, *bet = D.work + 2 * n;
+    double tn = 0.0;
+    for (int i = tid; i < n; i += nt) {
+        const double a = i > 0 ? fabs(ee[i - 1]) : 0.0, b = i + 1 < n ? fabs(ee[i]) : 0.0;
+        tn = fmax(tn, fabs(dd[i]) + a + b);
+        if (i + 1 < n) fv_e2[i] = ee[i] * ee[i];
+    }
+    tn = warp_max(tn);
+    if (lane == 0) scratch[wid] = tn;
+    __syncthreads();
+    double tnorm = 0.0;
+    for (int w = 0; w < nw; ++w) tnorm = fmax(tnorm, scratch[w]);
+    if (tid == 0) {
+        int nsel, ties = 0;
+        if (fixed_k > 0) {
+            nsel = min(fixed_k, n);
+        } else {
+            const int less = sturm_less(dd, fv_e2, n, tau);
+            nsel = n - less;
+            ties = sturm_less(dd, fv_e2, n, tau * (1 + 1e-6)) - sturm_less(dd, fv_e2, n, tau * (1 - 1e-6));
+        }
+        int over = 0;
+        if (nsel > D.cap) {
+            over = nsel;
+            nsel = D.cap;
+        }
+        sh_int[0] = nsel;
+        sh_int[1] = ties;
+        sh_int[2] = over;
+        sh_int[3] = min(nsel + 1, n);
+    }
+    __syncthreads();
+    const int nsel = sh_int[0], nval = sh_int[3], nf = D.nface;
+    double *wb = scr[it.x] + (size_t)(g * nw + wid) * 6 * n;
+    for (int t = g + G * wid; t < nval; t += G * nw) {
+        const double l = tri_multisect(dd, fv_e2, n, n - 1 - t, tnorm);
+        if (lane == 0) D.lam[t] = l;
+        if (t >= nsel) continue;
+        double *y = D.vec + (size_t)t * n;
+        tri_inverse_iteration(dd, ee, n, l, t, tnorm, wb, y);
+        tri_back_transform(D.C, D.ld, bet, n, y);
+        for (int f = lane; f < nf; f += 32) {
+            const double *wr = D.W1 + D.face_pos[f];
+            double acc = 0.0;
+            for (int j = 0; j < n; ++j) acc += wr[(size_t)j * D.ldw] * y[j];
+            D.rows[(size_t)t * nf + f] = acc;
+        }
+    }
+    if (g == 0 && tid == 0) {
+        D.counts[0] = nsel;
+        D.counts[1] = 0;
+        D.counts[2] = nval;
+        D.counts[3] = sh_int[1];
+        D.counts[4] = sh_int[2];
+    }
+}
+
+void launch_face_vec(const EigDesc *descs, const int2 *items, int nitems, int G, int nmax, double tau, int fixed_k,
+                     double *const *scr, cudaStream_t s) {
+    if (nitems <= 0) return;
+    const size_t smem = sizeof(double) * (size_t)std::max(nmax, 1);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(face_vec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    face_vec_kernel<<<nitems, EIG_THREADS, smem, s>>>(descs, items, G, tau, fixed_k, scr);
 }
 
 void launch_face_eig_n(const EigDesc *descs, int npairs, int nmax, double tau, double drop_rel, int use_ff,

@@ -24,7 +24,9 @@ struct EigDesc {
     int given;            // 1: lam, vec and counts [0], [2], [3], [4] are supplied (the batched
                           // LOBPCG, lobpcg.h); only the face rows are formed (C is not read).
                           // 2: the Householder reduction is supplied (launch_tridiag_multi):
-                          // reflectors in C, dd / ee / bet in work; steps 2-4 run
+                          // reflectors in C, dd / ee / bet in work; steps 2-4 run.
+                          // 3: as 1 with the face rows supplied too (launch_face_vec): the
+                          // clusters are orthonormalised and the rows reduced
 };
 
 // Householder tridiagonalisation of large face matrices by several CTAs per face
@@ -43,6 +45,13 @@ cudaError_t launch_tridiag_multi(const TridiagDesc *descs, const int2 *items, in
                                  DevStatus *st, double timeout_s, cudaStream_t s);
 // CTAs of launch_tridiag_multi that can be co-resident (one cooperative launch at most)
 int tridiag_multi_capacity(int nmax);
+
+// The eigenpairs and face rows of faces whose Householder reduction launch_tridiag_multi
+// supplied (given == 2), G CTAs per face (items = (descriptor, g)); scr[descriptor]: G x 8 x 6 n
+// doubles of scratch.  launch_face_eig_n with given = 3 then finishes them.
+void launch_face_vec(const EigDesc *descs, const int2 *items, int nitems, int G, int nmax, double tau, int fixed_k,
+                     double *const *scr, cudaStream_t s);
+constexpr int kFaceVecCTAs = 7;   // CTAs per face: 7 x 8 warps cover 49 eigenvalues, one each
 
 // nmax: largest n of the batch; when the matrix and work arrays do not fit in
 // 200 KB of shared memory the matrix is reduced in place and work (64 n + 16

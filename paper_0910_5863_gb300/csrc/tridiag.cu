@@ -237,25 +237,46 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const Tridia
                 bet[k + 1] = 0.0;
             }
         }
-        // (c) own columns c >= k + 2: B -= x W^T + W x^T below row k + 1, and the next P entries
+        // (c) own columns c >= k + 2: B -= x W^T + W x^T below row k + 1, and the next P entries.
+        // A warp takes two of its columns at a time, so x, W and x' are read from shared memory
+        // once for both.
         const T fbn = tri_from<T>(more ? hn.beta : 0.0);
-        for (int c = first_own(k + 2) + wid * G; c < n; c += nw * G) {
-            const int j = c - (k + 1);
+        const int cstep = nw * G;
+        for (int c = first_own(k + 2) + wid * G; c < n; c += 2 * cstep) {
+            const int c2 = c + cstep;
+            const bool two = c2 < n;
+            const int j = c - (k + 1), j2 = two ? c2 - (k + 1) : j;
             T *col = F + (size_t)c * lda + (k + 1);
-            const T wj = Ws[j], xj = xs[j];
-            T a = tri_from<T>(0.0);
+            T *col2 = F + (size_t)(two ? c2 : c) * lda + (k + 1);
+            const T wj = Ws[j], xj = xs[j], wj2 = Ws[j2], xj2 = xs[j2];
+            T a = tri_from<T>(0.0), a2 = tri_from<T>(0.0);
             cnt = 0;
             for (int i = 1 + lane; i < m; i += 32) {
-                const T v = tri_sub2(col[i], xs[i], wj, Ws[i], xj);
+                const T xi = xs[i], wi = Ws[i];
+                const T v = tri_sub2(col[i], xi, wj, wi, xj);
                 col[i] = v;
+                T v2 = v;
+                if (two) {
+                    v2 = tri_sub2(col2[i], xi, wj2, wi, xj2);
+                    col2[i] = v2;
+                }
                 if (more) {
-                    tri_fma(a, v, xn[i - 1]);
-                    if ((++cnt & 15) == 0) a = tri_norm(a);
+                    const T xni = xn[i - 1];
+                    tri_fma(a, v, xni);
+                    tri_fma(a2, v2, xni);
+                    if ((++cnt & 15) == 0) {
+                        a = tri_norm(a);
+                        a2 = tri_norm(a2);
+                    }
                 }
             }
             if (more) {
                 a = tri_warp_sum(tri_norm(a));
-                if (lane == 0) Pn[c - (k + 2)] = fbn * a;
+                a2 = tri_warp_sum(tri_norm(a2));
+                if (lane == 0) {
+                    Pn[c - (k + 2)] = fbn * a;
+                    if (two) Pn[c2 - (k + 2)] = fbn * a2;
+                }
             }
         }
         beta = more ? hn.beta : 0.0;
