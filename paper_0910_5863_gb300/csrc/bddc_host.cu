@@ -512,7 +512,7 @@ void run_pchol_fp64class(bddc_handle *h, const std::vector<PcholDesc<double>> &d
     }
     std::vector<int2> items;
     for (int m = 0; m < (int)descs.size(); ++m)
-        for (int j = 0; j < descs[m].n; ++j) items.push_back(make_int2(m, j));
+        for (int j = 0; j < descs[m].n; j += kConvertCols) items.push_back(make_int2(m, j));
     auto *dd = h->ar.upload("ffc_desc_" + tag, descs, h->stream);
     auto *di = h->ar.upload("ffc_it_" + tag, items, h->stream);
     launch_ff_convert(dd, di, (int)items.size(), 1, h->stream);

@@ -584,23 +584,25 @@ __global__ void ff_convert_kernel(const PcholDesc<double> *descs, const int2 *it
     if (it >= nitems) return;
     const int2 w = items[it];
     const PcholDesc<double> d = descs[w.x];
-    const int j = w.y;
-    double *col = d.A + (size_t)j * d.ld;
     const int nb = blockDim.x;
-    // four independent loads per thread in flight before any store
-    for (int i0 = j + threadIdx.x; i0 < d.n; i0 += 4 * nb) {
-        double v[4];
+    // kConvertCols columns per block, four independent loads per thread in flight before any store
+    for (int j = w.y; j < min(w.y + kConvertCols, d.n); ++j) {
+        double *col = d.A + (size_t)j * d.ld;
+        for (int i0 = j + threadIdx.x; i0 < d.n; i0 += 4 * nb) {
+            double v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = i0 + u * nb < d.n ? col[i0 + u * nb] : 0.0;
+            for (int u = 0; u < 4; ++u) v[u] = i0 + u * nb < d.n ? col[i0 + u * nb] : 0.0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * nb;
-            if (i >= d.n) break;
-            if (to_ff) {
-                reinterpret_cast<ff *>(col)[i] = ff_from_double(v[u]);
-            } else {
-                const long long b = __double_as_longlong(v[u]);   // the two words, h first in memory
-                col[i] = ff_to_double(ff(__int_as_float((int)(b & 0xffffffffLL)), __int_as_float((int)(b >> 32))));
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * nb;
+                if (i >= d.n) break;
+                if (to_ff) {
+                    reinterpret_cast<ff *>(col)[i] = ff_from_double(v[u]);
+                } else {
+                    const long long b = __double_as_longlong(v[u]);   // the two words, h first in memory
+                    col[i] = ff_to_double(
+                        ff(__int_as_float((int)(b & 0xffffffffLL)), __int_as_float((int)(b >> 32))));
+                }
             }
         }
     }

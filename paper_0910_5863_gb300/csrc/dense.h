@@ -89,7 +89,8 @@ void launch_pchol_panel(const PcholDesc<T> *descs, const int2 *items, int nitems
 template <typename T>
 void launch_pchol_update(const PcholDesc<T> *descs, const int4 *items, int nitems, int kb, cudaStream_t s);
 // in-place conversion of the lower triangles between FP64 (to_ff = 0) and double-float
-// (to_ff = 1; struct ff of ff.cuh); items = (matrix, column)
+// (to_ff = 1; struct ff of ff.cuh); items = (matrix, first of kConvertCols columns)
+constexpr int kConvertCols = 8;
 void launch_ff_convert(const PcholDesc<double> *descs, const int2 *items, int nitems, int to_ff, cudaStream_t s);
 void launch_gather(const GatherOp *ops, const int2 *items, int nitems, cudaStream_t s);
 void launch_diag_set(const DiagOp *ops, int nops, cudaStream_t s);
