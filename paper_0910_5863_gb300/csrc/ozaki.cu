@@ -113,7 +113,14 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitDesc *descs,
     if (r < d.rows)
         for (int c = 0; c < d.k; ++c) mx = fmaxf(mx, fabsf(d.L[(size_t)c * d.ldl + r].h));
     int e = 0;
-    if (mx > 0.f) frexpf(mx, &e);   // mx = f 2^e, f in [0.5, 1): 2^e > max |x_h|, so |x| 2^-e < 1
+    if (mx > 0.f) {   // mx = f 2^e, f in [0.5, 1): 2^e > max |x_h|, so |x| 2^-e < 1
+        const int be = (__float_as_int(mx) >> 23) & 0xff;
+        if (be > 0) e = be - 126;   // normal: read off the exponent field
+        else frexpf(mx, &e);
+    }
+    // 2^-e as a float when it is a normal number (then x 2^-e is exactly ldexpf(x, -e))
+    const bool pow2_ok = -e >= -126 && -e <= 127;
+    const float sce = pow2_ok ? __int_as_float((127 - e) << 23) : 0.f;
     if (r < d.rows) d.rexp[r] = e;
     // 16-byte chunk ch (8 digits) of row r within K chunk kc, stored at chunk ch ^ ((r / 2) mod 4)
     // of the row's 64 bytes: the shared-memory layout the tensor cores read, so that one
@@ -127,8 +134,8 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitDesc *descs,
             float rh = 0.f, rl = 0.f;
             if (r < d.rows && c < d.k && mx > 0.f) {
                 const ff v = d.L[(size_t)c * d.ldl + r];
-                rh = ldexpf(v.h, -e);
-                rl = ldexpf(v.l, -e);
+                rh = pow2_ok ? v.h * sce : ldexpf(v.h, -e);
+                rl = pow2_ok ? v.l * sce : ldexpf(v.l, -e);
             }
 #pragma unroll
             for (int p = 0; p < kOzSlices; ++p) {
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
 }
 
-constexpr int OZD_THREADS = 512;
+constexpr int OZD_THREADS = 1024;
 constexpr int OZD_PITCH = kOzK + 1;   // shared-memory row pitch (ff)
 
 __global__ void __launch_bounds__(OZD_THREADS) oz_diag_kernel(const OzDiagDesc *descs, DevStatus *st) {
