@@ -212,8 +212,11 @@ PEAK_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 # TF32 dense tensor rate: the measured bf16 rate x the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 
-# DRAM bytes (read + write) per launch from committed ncu captures: {(workload, kernel class): bytes}
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch from committed ncu captures: {(workload, kernel class): bytes}.
+# The digit products on the 48x48x24 irregular mixed step: 318 launches, 137.5 GB read + 93.8 GB
+# written (profiles/oz_syrk_elast32.md gives the command): the trailing blocks are read and written
+# once per 128-wide block column.
+TRAFFIC = {("irregular48", "oz_syrk_bf16"): (137.53e9 + 93.79e9) / 318}
 
 
 def _kernel_table(kt, steps, solver, info, workload):
