@@ -38,6 +38,8 @@ def test_kernel_table_bounds_and_rates():
     # 28 executed digit products per effective multiply-add, per launch, over the mean launch time
     assert abs(oz["achieved"] - 28 * 4e12 / 10 / (20.0 / 10 / 1e3) / 1e12) < 1e-9 * oz["achieved"]
     assert abs(oz["frac"] - oz["achieved"] / bf16) < 1e-12
+    assert oz["traffic"] == bench.TRAFFIC[("irregular48", "oz_syrk_bf16")]   # measured DRAM bytes per launch
+    assert out["pcg_kernel"]["traffic"] is None                              # not measured: null
     pcg = out["pcg_kernel"]
     # one FP64 multiply-add per 8-byte entry of S_i and P~_i: the FP64 pipe caps the stream below HBM
     fp64_gbs = bench.PEAK_FP64_TFLOPS * 1e12 / 2 * 8 / 1e9
