@@ -37,8 +37,10 @@ struct PcgParams {
     uint64_t timeout_ns;
 };
 
-// y_i = Mats_i * v_i for every (substructure, 64-row block); v_i = R_i v is
-// staged in shared memory once per substructure, then the warps split the
+// y_i = Mats_i * v_i for every (substructure, 64-row block); the blocks take
+// the host's bins of items (equal cost within ~2%, the items of a bin ordered
+// by substructure), v_i = R_i v is staged in shared memory once per
+// substructure of a bin, then the warps split the
 // columns and every lane reads two consecutive rows of a column with one
 // 16-byte load (512 coalesced bytes per warp and column).  Eight columns per
 // warp are loaded before they are used, so 64 KB per SM are in flight: the
@@ -59,7 +61,8 @@ __device__ double local_gemv(const PcgParams &P, double *const *Mats, const doub
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const bool stream = o.stream_mats != 0;
     int cur = -1;
-    for (int it = blockIdx.x; it < o.nrowblk; it += gridDim.x) {
+    for (int bin = blockIdx.x; bin < o.nbins; bin += gridDim.x)
+    for (int it = o.binptr[bin]; it < o.binptr[bin + 1]; ++it) {
         int2 w = o.rowblk[it];
         const int s = w.x, r0 = w.y;
         const int n = o.nGi[s], ld = o.ldS[s];

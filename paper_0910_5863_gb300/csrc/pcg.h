@@ -39,8 +39,10 @@ struct IfaceOps {
     const ZEntry *zent;      // the entries again, as assembly records
     const int *cptr;         // (nC+1)
     const int64_t *cent;     // packed local coarse index of each entry
-    const int2 *rowblk;      // (sub, first row) GEMV work items, 64 rows each
+    const int2 *rowblk;      // (sub, first row) GEMV work items, 64 rows each, grouped by bin
     int nrowblk;
+    const int *binptr;       // (nbins + 1) items of each bin: block b takes bins b, b + grid, ...
+    int nbins;               // bins of near-equal cost (longest item first onto the lightest bin)
     int stream_mats;         // S_i and P~_i exceed L2: read them with the evict-first policy
     const int2 *cdot;        // (sub, first coarse column) items, 16 columns each
     int ncdot;
