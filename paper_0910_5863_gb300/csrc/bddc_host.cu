@@ -24,7 +24,6 @@
 #include <memory>
 #include <thread>
 #include <numeric>
-#include <queue>
 #include <set>
 #include <string>
 #include <vector>
@@ -42,6 +41,7 @@
 #include "lobpcg.h"
 #include "ozaki.h"
 #include "pcg.h"
+#include "schedule.h"
 
 using namespace bddc;
 
@@ -1777,37 +1777,6 @@ void coarse_setup(bddc_handle *h, bool allow_fp32) {
     h->pb.uc = h->ar.get_t<double>("uc", nC);
 }
 
-// Bins of the PCG local-product items (one 64-row block of S_i or P~_i each):
-// every item costs about its substructure's column count (the warps' multiply-
-// adds issue per column whatever the rows left in a ragged last block), and the
-// items go longest first onto the least loaded of nbins bins (ties to the lower
-// bin), which evens the blocks' work between the grid barriers to ~2% where
-// handing the items out in turn left ~10%.  Within a bin the items keep their
-// (substructure, row) order, so a block stages each v_i once per bin.
-void bin_row_blocks(const std::vector<int2> &rb, const std::vector<int> &nGi, int nbins,
-                    std::vector<int2> &out, std::vector<int> &binptr) {
-    std::vector<int> order(rb.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return nGi[rb[a].x] > nGi[rb[b].x]; });
-    using Load = std::pair<int64_t, int>;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> q;
-    for (int b = 0; b < nbins; ++b) q.push({0, b});
-    std::vector<int> bin_of(rb.size());
-    for (int k : order) {
-        Load l = q.top();
-        q.pop();
-        bin_of[k] = l.second;
-        q.push({l.first + nGi[rb[k].x], l.second});
-    }
-    binptr.assign(nbins + 1, 0);
-    for (size_t k = 0; k < rb.size(); ++k) ++binptr[bin_of[k] + 1];
-    for (int b = 0; b < nbins; ++b) binptr[b + 1] += binptr[b];
-    std::vector<int> fill(binptr.begin(), binptr.end() - 1);
-    out.resize(rb.size());
-    for (size_t k = 0; k < rb.size(); ++k) out[fill[bin_of[k]]++] = rb[k];   // (sub, row) order kept
-}
-
 void alloc_solver_buffers(bddc_handle *h) {
     const int ns = h->nsub;
     std::vector<double *> S(ns), P(ns), Phi(ns);
@@ -1845,14 +1814,18 @@ void alloc_solver_buffers(bddc_handle *h) {
     h->ops.gptr = h->ar.upload("gptr", h->gptr, h->stream);
     h->ops.gent = h->ar.upload("gent", h->gent, h->stream);
     h->ops.gsub = h->ar.upload("gsub", h->gsub, h->stream);
-    {   // one bin per SM: the PCG kernel runs one block per SM
+    {   // The PCG kernel runs one block per SM; one bin of row blocks per SM.  An item
+        // costs about its substructure's column count (the warps' multiply-adds issue per
+        // column whatever the rows left in a ragged last block); binned by cost, the
+        // blocks' shares between grid barriers differ by ~2%, where handing the items out
+        // in turn left ~10%.  A bin keeps the (substructure, row) order, so a block stages
+        // each v_i once per bin.
         int dev = 0, nsm = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) throw Error{7, std::string("SM count: ") + cudaGetErrorString(e)};
+        BDDC_CUDA(cudaGetDevice(&dev));
+        BDDC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         std::vector<int2> rbs;
         std::vector<int> bp;
-        bin_row_blocks(rb, nGi, std::max(nsm, 1), rbs, bp);
+        bin_by_cost(rb, [&](const int2 &w) { return (int64_t)nGi[w.x]; }, std::max(nsm, 1), rbs, bp);
         h->ops.rowblk = h->ar.upload("rowblk", rbs, h->stream);
         h->ops.nrowblk = (int)rbs.size();
         h->ops.binptr = h->ar.upload("binptr", bp, h->stream);
