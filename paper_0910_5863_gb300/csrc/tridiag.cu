@@ -15,7 +15,8 @@
 //   * each CTA then updates its columns c >= k + 2, B -= x W^T + W x^T, and in the same
 //     pass dots them with x' (the next step's P entries), and all CTAs meet once.
 // Each step's reflector is written into its column by all CTAs (a share each) at the
-// start of the next step, after every CTA has read that column.  Both triangles of the
+// start of the next step, after every CTA has read that column (column 0's, one entry,
+// after the barrier that follows P_0).  Both triangles of the
 // trailing block are kept below row k + 1 (the row of the current pivot is not updated:
 // nothing reads it again).  The grid is one cooperative launch (all CTAs co-resident);
 // the barrier of a face spins with a bound and records BDDC_DEV_ERR_TIMEOUT instead of
@@ -180,10 +181,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const Tridia
     const TriHh h0 = tri_householder(xs, n - 1, scratch);
     if (tid == 0) xs[0] = tri_from<T>(h0.v0);
     __syncthreads();
-    if (g == 0 && tid == 0) {
-        dd[0] = tri_to(tri_ld(F));
-        F[1] = tri_from<T>(h0.v0);
-    }
+    if (g == 0 && tid == 0) dd[0] = tri_to(tri_ld(F));
     double beta = h0.beta, alpha = h0.alpha;
     {
         const T fb = tri_from<T>(beta);
@@ -200,6 +198,10 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_multi_kernel(const Tridia
         }
     }
     if (!face_barrier(bar, G, st, timeout_ns)) return;
+    // column 0's reflector: only its leading entry differs from the column, and it is stored
+    // only now, when every CTA of the face has read column 0 (a store before this barrier could
+    // reach a CTA still loading the column)
+    if (g == 0 && tid == 0) F[1] = tri_from<T>(h0.v0);
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;   // trailing rows / columns k + 1 .. n - 1, local index 0 .. m - 1
         const T *Pk = Pbuf + (size_t)(k & 1) * n;
