@@ -2394,7 +2394,7 @@ void run_face_eigs(bddc_handle *h, const std::vector<EigDesc> &eds, double tau, 
             std::vector<int2> vit;
             std::vector<size_t> off(multi.size() + 1, 0);
             for (size_t q = 0; q < multi.size(); ++q) {
-                off[q + 1] = off[q] + (size_t)G * 8 * 6 * multi[q].n;
+                off[q + 1] = off[q] + (size_t)G * kFaceVecWarps * 6 * multi[q].n;
                 for (int g = 0; g < G; ++g) vit.push_back(make_int2((int)q, g));
             }
             double *scr_all = h->ar.get_t<double>("fvscr_" + tag, std::max<size_t>(off.back(), 1));

@@ -22,6 +22,7 @@
 namespace bddc {
 
 constexpr int EIG_THREADS = 256;
+static_assert(EIG_THREADS == 32 * kFaceVecWarps, "face_vec scratch is sized for kFaceVecWarps warps per CTA");
 
 __device__ __forceinline__ int lane_of(int tid) { return tid & 31; }
 // threads per row for a matrix-vector product of order m on nt threads: the largest

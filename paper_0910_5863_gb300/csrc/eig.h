@@ -52,6 +52,7 @@ int tridiag_multi_capacity(int nmax);
 void launch_face_vec(const EigDesc *descs, const int2 *items, int nitems, int G, int nmax, double tau, int fixed_k,
                      double *const *scr, cudaStream_t s);
 constexpr int kFaceVecCTAs = 7;   // CTAs per face: 7 x 8 warps cover 49 eigenvalues, one each
+constexpr int kFaceVecWarps = 8;  // warps per CTA of launch_face_vec (its scratch is per warp)
 
 // nmax: largest n of the batch; when the matrix and work arrays do not fit in
 // 200 KB of shared memory the matrix is reduced in place and work (64 n + 16
