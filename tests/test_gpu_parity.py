@@ -82,6 +82,27 @@ def test_solve(case):
     assert abs(info8["kappa"] - k_ref) <= 0.01 * k_ref
 
 
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
+def test_zero_load_gives_zero_solution(prec):
+    """The degenerate right-hand side f = 0: the solution of K u = 0 is u = 0, PCG stops
+    before its first iteration (r_0 = 0) and reports a zero residual; with no Lanczos
+    coefficients the condition estimate is 1."""
+    prob = P.config_small()
+    s = B.Solver(precision=prec, tol=1e-8)
+    s.set_mesh_problem(prob)
+    s.setup()
+    s.adapt(10.0)
+    f = B.free_load_vector(prob)
+    u = np.full_like(f, np.nan)            # every entry must be written by the solve
+    u, info = s.solve(np.zeros_like(f), u=u)
+    assert np.all(u == 0.0)
+    assert info["converged"] and info["iters"] == 0
+    assert info["relres"] == 0.0 and info["kappa"] == 1.0
+    # the handle solves a nonzero load normally afterwards
+    u1, info1 = s.solve(f)
+    assert info1["converged"] and info1["iters"] > 0 and np.linalg.norm(u1) > 0
+
+
 def _adaptive_case(prob, tau=10.0):
     m = oracle.Model(prob)
     m.schur()
