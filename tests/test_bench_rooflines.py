@@ -1,6 +1,6 @@
-"""Host logic of the bench's kernel table (CPU): the bound, peak and achieved rate of every
-kernel class are formed from the timers' (ms, algorithmic work, launches) as the design notes
-state them, and the dominant class becomes the roofline entry."""
+"""Host logic of the bench (CPU): the bound, peak and achieved rate of every kernel class are
+formed from the timers' (ms, algorithmic work, launches) as the design notes state them, the
+dominant class becomes the roofline entry, and the nvidia-smi clock samples are summarised."""
 import os
 import sys
 
@@ -66,3 +66,20 @@ def test_derived_peaks():
     assert abs(bench.PEAK_FP64_TFLOPS - 1.25856) < 1e-9
     assert abs(bench.PEAK_FP32_TFLOPS - 80.54784) < 1e-9
     assert abs(bench.PEAK_FF_TFLOPS - 6.71232) < 1e-9
+
+
+def test_clock_samples_summary():
+    # columns: index, clocks.sm, clocks.max.sm, power.draw, active reasons (bit mask), hw_slowdown,
+    # hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    lines = [
+        "0, 2070, 2070, 950.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.7, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, [N/A], 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",   # skipped
+        "0, 2070, 2070",                                                                  # short: skipped
+        "0, 2055, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+    ]
+    c = bench.parse_clocks(lines)
+    assert c == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = bench.parse_clocks(["0, 1500, 2070, 1400, 0x48, Active, Not Active, Active, Not Active"])
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
+    assert bench.parse_clocks([]) is None and bench.parse_clocks(["garbage"]) is None
