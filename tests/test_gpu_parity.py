@@ -103,6 +103,28 @@ def test_zero_load_gives_zero_solution(prec):
     assert info1["converged"] and info1["iters"] > 0 and np.linalg.norm(u1) > 0
 
 
+@pytest.mark.parametrize("prec,tol_u", [(B.FP64, 1e-8), (B.MIXED, 1e-6)])
+def test_iteration_limit_returns_the_iterate(prec, tol_u):
+    """PCG stopped by its iteration limit: BDDC_ENOCONV, and the solution returned is the one
+    recovered from the third iterate, as the oracle's PCG stopped after three steps gives it.
+    The iterate is about as sensitive as the operators (perturbing the oracle's S and M by
+    eps moves it by ~eps), so the bounds are 100x the operators' accuracy on each path."""
+    prob = P.config_small()
+    av = ("edge", "face")
+    m, _, ref = oracle.run(prob, averages=av, tol=1e-14, maxit=3)
+    assert not ref.converged and ref.iters == 3
+    s = B.Solver(precision=prec, tol=1e-14, maxit=3)
+    s.set_mesh_problem(prob)
+    s.set_averages(edge=True, face=True)
+    s.setup()
+    u, info = s.solve(B.free_load_vector(prob), check=False)
+    assert info["status"] == "ENOCONV" and not info["converged"] and info["iters"] == 3
+    assert _rel(u, ref.u) < tol_u
+    with pytest.raises(B.BddcError) as e:
+        s.solve(B.free_load_vector(prob))
+    assert e.value.status == 5
+
+
 def _adaptive_case(prob, tau=10.0):
     m = oracle.Model(prob)
     m.schur()
