@@ -11,6 +11,7 @@
 //   bddc_solve        condensed right-hand side, PCG (Lemma 2.1
 //                     preconditioner), interior recovery.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -202,6 +203,7 @@ struct bddc_handle {
     static constexpr int kPhases = 9;
     cudaEvent_t ev[2 * kPhases] = {};
     bool ev_used[kPhases] = {};
+    bool nvtx_open = false;     // a phase's NVTX range is open on this thread
     double phase_ms[kPhases] = {};
     double phase_flop[kPhases] = {};
 };
@@ -224,11 +226,26 @@ void fail_check(bddc_handle *h, const char *where) {
     if (hs.code != 0) throw Error{BDDC_ECUDA, std::string(where) + ": device error " + std::to_string(hs.code)};
 }
 
+// Device phases, in the order of bddc_get_phase_times.  Each is also an NVTX range around the host
+// code that issues it, so a profiler can select a phase's kernels (e.g. ncu --nvtx --nvtx-include
+// "pcg/"); without a profiler attached the NVTX calls do nothing.  A range left open by an error
+// inside a phase is closed when the next phase begins.
+const char *const kPhaseNames[bddc_handle::kPhases] = {
+    "assembly", "interior_elimination", "coarse_setup", "pair_condensation", "face_eigen",
+    "analysis_host", "condensed_rhs", "pcg", "recovery"};
+
 void phase_begin(bddc_handle *h, int k) {
     BDDC_CUDA(cudaEventRecord(h->ev[2 * k], h->stream));
     h->ev_used[k] = true;
+    if (h->nvtx_open) nvtxRangePop();
+    nvtxRangePushA(kPhaseNames[k]);
+    h->nvtx_open = true;
 }
-void phase_end(bddc_handle *h, int k) { BDDC_CUDA(cudaEventRecord(h->ev[2 * k + 1], h->stream)); }
+void phase_end(bddc_handle *h, int k) {
+    if (h->nvtx_open) nvtxRangePop();
+    h->nvtx_open = false;
+    BDDC_CUDA(cudaEventRecord(h->ev[2 * k + 1], h->stream));
+}
 void phase_collect(bddc_handle *h, int k0, int k1) {
     for (int k = k0; k <= k1; ++k) {
         if (!h->ev_used[k]) continue;
