@@ -308,9 +308,9 @@ BDDC_API bddc_status bddc_get_edge_rows(const bddc_handle *h, int *n_rows, int *
  * BDDC preconditioner to ||r|| <= tol ||r_0|| from x_0 = 0, interior
  * recovery.  f and u are global free-dof vectors (length n_free) in memory
  * ``mem``.  info may be NULL.  f = 0 gives u = 0 with no iteration (iters 0,
- * relres 0, condition estimate 1).  Errors: BDDC_ESTATE, BDDC_ENOCONV (maxit
- * reached: u holds the solution recovered from the last iterate, info is filled),
- * BDDC_ETIMEOUT, BDDC_ECUDA. */
+ * relres 0, condition estimate 1).  Errors: BDDC_ESTATE, BDDC_EINVAL (a load with
+ * non-finite entries), BDDC_ENOCONV (maxit reached: u holds the solution recovered
+ * from the last iterate, info is filled), BDDC_ETIMEOUT, BDDC_ECUDA. */
 BDDC_API bddc_status bddc_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_info *info);
 
 /* Extreme eigenvalues of the Lanczos matrix built from the last solve's PCG

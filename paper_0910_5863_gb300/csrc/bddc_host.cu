@@ -3483,6 +3483,11 @@ void do_solve(bddc_handle *h, const double *f, double *u, int mem, bddc_solve_in
                               h->stream));
     BDDC_CUDA(cudaStreamSynchronize(h->stream));
     fail_check(h, "solve");
+    // A non-finite load makes the condensed right-hand side non-finite: PCG then stops at once
+    // (p^T S p is not positive), and the residual ratios would read 0.  Report it as a bad argument.
+    if (!std::isfinite(tr[1]))
+        throw Error{BDDC_EINVAL, "the load vector has non-finite entries (condensed right-hand side norm " +
+                                     std::to_string(tr[1]) + ")"};
     phase_collect(h, 6, 8);
     h->last_iters = it[0];
     h->alpha.assign(it[0], 0.0);

@@ -125,6 +125,25 @@ def test_iteration_limit_returns_the_iterate(prec, tol_u):
     assert e.value.status == 5
 
 
+@pytest.mark.parametrize("prec", [B.FP64, B.MIXED])
+def test_non_finite_load_is_a_bad_argument(prec):
+    """A NaN or an infinity in the load gives BDDC_EINVAL (not a zero residual), and the handle
+    then solves a finite load as before."""
+    prob = P.config_small()
+    s = B.Solver(precision=prec, tol=1e-8)
+    s.set_mesh_problem(prob)
+    s.setup()
+    f = B.free_load_vector(prob)
+    for bad in (np.nan, np.inf):
+        g = f.copy()
+        g[len(g) // 2] = bad
+        with pytest.raises(B.BddcError) as e:
+            s.solve(g)
+        assert e.value.status == 1
+    u, info = s.solve(f)
+    assert info["converged"] and np.all(np.isfinite(u))
+
+
 def _adaptive_case(prob, tau=10.0):
     m = oracle.Model(prob)
     m.schur()
